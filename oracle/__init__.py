@@ -1,0 +1,291 @@
+"""FP64 oracle for the segment-parallel Riccati solver.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it. The product path never imports,
+links or calls anything here, and nothing here imports the product package.
+
+Contents
+--------
+riccati(prob)            serial FP64 Riccati recursion in plain C (lqr_oracle.c):
+                         the plain definition of the unique optimum (Section II,
+                         Eq. 1-3; the serial method of Section III-A).
+dense_kkt(prob)          the global KKT system of Eq. 3 assembled densely and solved
+                         with numpy.linalg.solve (brute force, tiny sizes only).
+segment_summary(...)     the endpoint-constrained segment problem of Section II-B
+                         (Eq. 8) solved by a dense KKT solve with the two end states
+                         as parameters; returns the quadratic cost_to_go(x, x_term)
+                         of Eq. 9 at the segment start: (Vxx, Vzx, Vzz, vx, vz, v0).
+kkt_residual(prob, ...)  the residual of Eq. 3 and its normwise backward error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lqr_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liblqr_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc into oracle/_build (host code, any arch)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_riccati.restype = ctypes.c_int
+        lib.oracle_riccati.argtypes = [ctypes.c_int] * 3 + [d] * 18
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _dims(prob):
+    T, n, m = prob["B"].shape
+    return n, m, T
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def riccati(prob: dict, want_P: bool = True) -> dict:
+    """Serial FP64 Riccati recursion (C). Returns K,k,P,p,s,x,u,lam,cost."""
+    lib = _load()
+    n, m, T = _dims(prob)
+    arr = {k: np.ascontiguousarray(prob[k], dtype=np.float64) for k in
+           ("A", "B", "c", "Q", "R", "S", "q", "r", "x0")}
+    out = dict(K=np.empty((T, m, n)), k=np.empty((T, m)),
+               P=np.empty((T + 1, n, n)) if want_P else None, p=np.empty((T + 1, n)),
+               s=np.empty(T + 1), x=np.empty((T + 1, n)), u=np.empty((T, m)),
+               lam=np.empty((T + 1, n)) if want_P else None, cost=np.empty(1))
+    st = lib.oracle_riccati(n, m, T, _ptr(arr["A"]), _ptr(arr["B"]), _ptr(arr["c"]),
+                            _ptr(arr["Q"]), _ptr(arr["R"]), _ptr(arr["S"]), _ptr(arr["q"]),
+                            _ptr(arr["r"]), _ptr(arr["x0"]), _ptr(out["K"]), _ptr(out["k"]),
+                            _ptr(out["P"]), _ptr(out["p"]), _ptr(out["s"]), _ptr(out["x"]),
+                            _ptr(out["u"]), _ptr(out["lam"]), _ptr(out["cost"]))
+    if st == 1:
+        raise OracleError("R_t + B'P B not positive definite")
+    if st != 0:
+        raise OracleError("oracle_riccati failed with status %d" % st)
+    out["cost"] = float(out["cost"][0])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Dense KKT (brute force) -- Eq. 3 of the paper
+# ---------------------------------------------------------------------------
+
+def _sym(M):
+    return 0.5 * (M + np.swapaxes(M, -1, -2))
+
+
+def dense_kkt(prob: dict) -> dict:
+    """Assemble the KKT system of Eq. 3 densely and solve it.
+
+    Unknowns w = (x_0..x_T, u_0..u_{T-1}) and multipliers lambda_0..lambda_T,
+    with the Lagrangian f(w) + lambda_0'(x_0 - x0)
+    + sum_t lambda_{t+1}'(x_{t+1} - A_t x_t - B_t u_t - c_t), so that
+    stationarity in x_t reads Q x_t + S'u_t + q_t + lambda_t - A_t'lambda_{t+1} = 0
+    exactly as printed in Eq. 3.
+    """
+    n, m, T = _dims(prob)
+    A, B, c, Q, R, S, q, r, x0 = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r", "x0"))
+    Q = _sym(Q)
+    R = _sym(R)
+    nx = (T + 1) * n
+    nw = nx + T * m
+    nc = (T + 1) * n
+    H = np.zeros((nw, nw))
+    g = np.zeros(nw)
+    C = np.zeros((nc, nw))
+    d = np.zeros(nc)
+
+    def xs(t):
+        return slice(t * n, (t + 1) * n)
+
+    def us(t):
+        return slice(nx + t * m, nx + (t + 1) * m)
+
+    for t in range(T):
+        H[xs(t), xs(t)] = Q[t]
+        H[us(t), us(t)] = R[t]
+        H[us(t), xs(t)] = S[t]
+        H[xs(t), us(t)] = S[t].T
+        g[xs(t)] = q[t]
+        g[us(t)] = r[t]
+    H[xs(T), xs(T)] = Q[T]
+    g[xs(T)] = q[T]
+    C[0:n, xs(0)] = np.eye(n)
+    d[0:n] = x0
+    for t in range(T):
+        rows = slice((t + 1) * n, (t + 2) * n)
+        C[rows, xs(t + 1)] = np.eye(n)
+        C[rows, xs(t)] = -A[t]
+        C[rows, us(t)] = -B[t]
+        d[rows] = c[t]
+    Kmat = np.block([[H, C.T], [C, np.zeros((nc, nc))]])
+    rhs = np.concatenate([-g, d])
+    sol = np.linalg.solve(Kmat, rhs)
+    w = sol[:nw]
+    lam = sol[nw:]
+    x = w[:nx].reshape(T + 1, n)
+    u = w[nx:].reshape(T, m)
+    cost = 0.5 * w @ H @ w + g @ w
+    return dict(x=x, u=u, lam=lam.reshape(T + 1, n), cost=float(cost), kkt=Kmat, rhs=rhs)
+
+
+def segment_summary(prob: dict, t0: int, t1: int) -> dict:
+    """Endpoint-constrained problem on stages t0..t1-1 (Eq. 8: x_{t0} = x_s,
+    x_{t1} = z, no terminal cost), solved by a dense KKT solve with (x_s, z)
+    as right-hand-side parameters.
+
+    Its optimal value is the quadratic of Eq. 9,
+        J(x_s, z) = 1/2 x_s'Vxx x_s + z'Vzx x_s + 1/2 z'Vzz z + vx'x_s + vz'z + v0,
+    read off through the envelope identity dJ/dx_s = -nu_init, dJ/dz = -nu_term
+    (nu = the multipliers of the two endpoint constraints, same sign convention
+    as Eq. 3 and Eq. 12).
+    """
+    n, m, T = _dims(prob)
+    if not (0 <= t0 < t1 <= T):
+        raise ValueError("bad segment")
+    L = t1 - t0
+    A, B, c, Q, R, S, q, r = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r"))
+    Q = _sym(Q)
+    R = _sym(R)
+    nx = (L + 1) * n
+    nw = nx + L * m
+    nc = (L + 2) * n
+    H = np.zeros((nw, nw))
+    g = np.zeros(nw)
+    C = np.zeros((nc, nw))
+    d0 = np.zeros(nc)
+
+    def xs(i):
+        return slice(i * n, (i + 1) * n)
+
+    def us(i):
+        return slice(nx + i * m, nx + (i + 1) * m)
+
+    for i in range(L):
+        t = t0 + i
+        H[xs(i), xs(i)] = Q[t]
+        H[us(i), us(i)] = R[t]
+        H[us(i), xs(i)] = S[t]
+        H[xs(i), us(i)] = S[t].T
+        g[xs(i)] = q[t]
+        g[us(i)] = r[t]
+        rows = slice((i + 1) * n, (i + 2) * n)
+        C[rows, xs(i + 1)] = np.eye(n)
+        C[rows, xs(i)] = -A[t]
+        C[rows, us(i)] = -B[t]
+        d0[rows] = c[t]
+    C[0:n, xs(0)] = np.eye(n)                      # x_{t0} = x_s
+    C[(L + 1) * n:(L + 2) * n, xs(L)] = np.eye(n)  # x_{t1} = z
+    Kmat = np.block([[H, C.T], [C, np.zeros((nc, nc))]])
+    # right-hand sides: [zero parameters | x_s = e_i | z = e_i]
+    rhs = np.zeros((nw + nc, 1 + 2 * n))
+    rhs[:nw, 0] = -g
+    rhs[nw:, 0] = d0
+    for i in range(n):
+        rhs[nw + i, 1 + i] = 1.0
+        rhs[nw + (L + 1) * n + i, 1 + n + i] = 1.0
+    sol = np.linalg.solve(Kmat, rhs)
+    nu_init = sol[nw:nw + n]                  # (n, 1+2n)
+    nu_term = sol[nw + (L + 1) * n:nw + nc]   # (n, 1+2n)
+    Vxx = -nu_init[:, 1:1 + n]
+    Vzz = -nu_term[:, 1 + n:]
+    Vzx = -nu_term[:, 1:1 + n]
+    vx = -nu_init[:, 0]
+    vz = -nu_term[:, 0]
+    w0 = sol[:nw, 0]
+    v0 = 0.5 * w0 @ H @ w0 + g @ w0
+    return dict(Vxx=Vxx, Vzx=Vzx, Vzz=Vzz, vx=vx, vz=vz, v0=float(v0),
+                Vxz_from_init=-nu_init[:, 1 + n:])
+
+
+def kkt_blocks_residual(prob: dict, x, u, lam):
+    """Residual blocks of Eq. 3 at (x, u, lambda), FP64:
+      rx_t = Q x_t + S'u_t + q_t + lam_t - A'lam_{t+1}   (t < T)
+      ru_t = S x_t + R u_t + r_t - B'lam_{t+1}
+      rxT  = Q_T x_T + q_T + lam_T
+      r0   = x_0 - x0
+      rd_t = x_{t+1} - A x_t - B u_t - c_t
+    """
+    A, B, c, Q, R, S, q, r, x0 = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r", "x0"))
+    Q = _sym(Q)
+    R = _sym(R)
+    T = B.shape[0]
+    xt, xn = x[:T], x[1:]
+    lt, ln = lam[:T], lam[1:]
+    rx = (np.einsum("tij,tj->ti", Q[:T], xt) + np.einsum("tji,tj->ti", S, u) + q[:T] + lt
+          - np.einsum("tji,tj->ti", A, ln))
+    ru = (np.einsum("tij,tj->ti", S, xt) + np.einsum("tij,tj->ti", R, u) + r
+          - np.einsum("tji,tj->ti", B, ln))
+    rxT = Q[T] @ x[T] + q[T] + lam[T]
+    r0 = x[0] - x0
+    rd = xn - np.einsum("tij,tj->ti", A, xt) - np.einsum("tij,tj->ti", B, u) - c
+    return dict(rx=rx, ru=ru, rxT=rxT, r0=r0, rd=rd)
+
+
+def kkt_residual(prob: dict, x, u, lam) -> dict:
+    """Normwise backward error of (x, u, lambda) for the KKT system of Eq. 3:
+        eta = |KKT w - b|_inf / (|KKT|_inf |w|_inf + |b|_inf),
+    with |KKT|_inf the largest absolute row sum, computed block by block, and
+    b = (-q, -r, -q_T, x0, c). Also returns rel = |KKT w - b|_inf / |b|_inf."""
+    A, B, c, Q, R, S, q, r, x0 = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r", "x0"))
+    Qs = _sym(Q)
+    Rs = _sym(R)
+    T = B.shape[0]
+    res = kkt_blocks_residual(prob, x, u, lam)
+    rnorm = max(np.abs(v).max() for v in res.values())
+    # row sums of |KKT|
+    row_x = (np.abs(Qs[:T]).sum(-1) + np.abs(S).sum(-2) + 1.0 + np.abs(A).sum(-2))
+    row_u = np.abs(S).sum(-1) + np.abs(Rs).sum(-1) + np.abs(B).sum(-2)
+    row_xT = np.abs(Qs[T]).sum(-1) + 1.0
+    row_d = 1.0 + np.abs(A).sum(-1) + np.abs(B).sum(-1)
+    knorm = max(row_x.max(), row_u.max(), row_xT.max(), 1.0, row_d.max())
+    wnorm = max(np.abs(x).max(), np.abs(u).max(), np.abs(lam).max())
+    bnorm = max(np.abs(q).max(), np.abs(r).max(), np.abs(x0).max(), np.abs(c).max())
+    return dict(eta=rnorm / (knorm * wnorm + bnorm), rel=rnorm / bnorm, rnorm=rnorm,
+                knorm=knorm, wnorm=wnorm, bnorm=bnorm)
+
+
+def stage_costs(prob: dict, x, u) -> float:
+    """Objective of Eq. 1-2 along a trajectory (x, u)."""
+    A, B, c, Q, R, S, q, r = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r"))
+    T = B.shape[0]
+    xt = x[:T]
+    J = (0.5 * np.einsum("ti,tij,tj->", xt, Q[:T], xt) + np.einsum("ti,tij,tj->", u, S, xt)
+         + 0.5 * np.einsum("ti,tij,tj->", u, R, u) + np.einsum("ti,ti->", q[:T], xt)
+         + np.einsum("ti,ti->", r, u))
+    J += 0.5 * x[T] @ Q[T] @ x[T] + q[T] @ x[T]
+    return float(J)
+
+
+def rel_err(a, ref) -> float:
+    """Normwise relative error max|a - ref| / max|ref| over the stacked tensor."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.abs(ref).max()
+    num = np.abs(a - ref).max()
+    return float(num / den) if den > 0 else float(num)

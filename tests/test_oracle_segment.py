@@ -1,0 +1,164 @@
+"""Pins of the oracle's endpoint-constrained segment summary (Section II-B, Eq. 8-9).
+
+The summary comes from a sparse-KKT solve with parametric right-hand sides. It
+is checked against two independent formulations:
+  * the serial Riccati recursion: minimising J(x_s, z) + V_{t1}(z) over z must
+    give V_{t0} (Bellman's principle on the split of Eq. 5-6);
+  * a condensed brute force: states eliminated, the endpoint constraint handled
+    by a null-space parametrisation of the controls, J evaluated at random
+    (x_s, z) points.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _quad(summ, xs, z):
+    return (0.5 * xs @ summ["Vxx"] @ xs + z @ summ["Vzx"] @ xs + 0.5 * z @ summ["Vzz"] @ z
+            + summ["vx"] @ xs + summ["vz"] @ z + summ["v0"])
+
+
+def _condensed_value(prob, t0, t1, xs, z):
+    """min over u_{t0..t1-1} of the segment cost with x_{t0}=xs, x_{t1}=z,
+    by eliminating the states and parametrising the feasible controls."""
+    A, B, c, Q, R, S, q, r = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r"))
+    T, n, m = B.shape
+    L = t1 - t0
+    # x_i = Phi_i xs + G_i u + h_i  (u stacked, length L*m)
+    Phi = np.eye(n)
+    G = np.zeros((n, L * m))
+    h = np.zeros(n)
+    Hu = np.zeros((L * m, L * m))
+    gu = np.zeros(L * m)
+    const = 0.0
+    for i in range(L):
+        t = t0 + i
+        x_aff = (Phi @ xs + h, G)  # x_i = x_aff[0] + G u
+        E = np.zeros((m, L * m))
+        E[:, i * m:(i + 1) * m] = np.eye(m)  # u_i = E u
+        xa, Gx = x_aff
+        Qs = 0.5 * (Q[t] + Q[t].T)
+        Rs = 0.5 * (R[t] + R[t].T)
+        # 1/2 x'Qx + u'Sx + 1/2 u'Ru + q'x + r'u with x = xa + Gx u, u_i = E u
+        Hu += Gx.T @ Qs @ Gx + E.T @ S[t] @ Gx + Gx.T @ S[t].T @ E + E.T @ Rs @ E
+        gu += Gx.T @ (Qs @ xa + q[t]) + E.T @ (S[t] @ xa + r[t])
+        const += 0.5 * xa @ Qs @ xa + q[t] @ xa
+        Phi = A[t] @ Phi
+        G = A[t] @ G + B[t] @ E
+        h = A[t] @ h + c[t]
+    # endpoint: Phi xs + h + G u = z
+    u_p = np.linalg.lstsq(G, z - Phi @ xs - h, rcond=None)[0]
+    assert np.abs(G @ u_p - (z - Phi @ xs - h)).max() < 1e-9
+    N = scipy.linalg.null_space(G)
+    if N.shape[1] == 0:
+        u = u_p
+    else:
+        # min over y of 1/2 (u_p + N y)'Hu(u_p + N y) + gu'(u_p + N y)
+        y = np.linalg.solve(N.T @ Hu @ N, -N.T @ (Hu @ u_p + gu))
+        u = u_p + N @ y
+    return 0.5 * u @ Hu @ u + gu @ u + const
+
+
+@pytest.mark.parametrize("n,m,L,cross", [(2, 1, 3, False), (3, 1, 5, True), (4, 2, 4, True),
+                                         (4, 2, 2, False), (5, 2, 6, True), (3, 3, 1, True),
+                                         (5, 3, 4, True)])
+def test_summary_vs_condensed_brute_force(n, m, L, cross):
+    prob = workloads.make_problem(n, m, L + 3, seed=30 + n + L, cross=cross)
+    t0, t1 = 1, 1 + L
+    summ = oracle.segment_summary(prob, t0, t1)
+    g = np.random.default_rng(0)
+    for _ in range(4):
+        xs = g.standard_normal(n)
+        z = g.standard_normal(n)
+        J_ref = _condensed_value(prob, t0, t1, xs, z)
+        assert abs(_quad(summ, xs, z) - J_ref) <= 1e-9 * max(1.0, abs(J_ref))
+    for k in ("Vxx", "Vzz"):
+        assert np.abs(summ[k] - summ[k].T).max() <= 1e-9 * np.abs(summ[k]).max()
+    # the two ways of reading the cross block agree (dJ/dx_s vs dJ/dz)
+    assert np.abs(summ["Vxz_from_init"] - summ["Vzx"].T).max() <= 1e-9 * np.abs(summ["Vzx"]).max()
+
+
+@pytest.mark.parametrize("n,m,T,t0,t1", [(4, 2, 12, 3, 8), (6, 2, 20, 0, 9), (5, 5, 8, 2, 3),
+                                         (6, 4, 14, 5, 13)])
+def test_summary_composes_with_serial_value_function(n, m, T, t0, t1):
+    """V_{t0}(x) = min_z J(x, z) + V_{t1}(z):
+       P_{t0} = Vxx - Vzx'(Vzz + P_{t1})^{-1} Vzx,
+       p_{t0} = vx  - Vzx'(Vzz + P_{t1})^{-1}(vz + p_{t1})."""
+    prob = workloads.make_problem(n, m, T, seed=40 + t0, cross=True)
+    ric = oracle.riccati(prob)
+    summ = oracle.segment_summary(prob, t0, t1)
+    D = summ["Vzz"] + ric["P"][t1]
+    P0 = summ["Vxx"] - summ["Vzx"].T @ np.linalg.solve(D, summ["Vzx"])
+    p0 = summ["vx"] - summ["Vzx"].T @ np.linalg.solve(D, summ["vz"] + ric["p"][t1])
+    assert oracle.rel_err(P0, ric["P"][t0]) < 1e-9
+    assert oracle.rel_err(p0, ric["p"][t0]) < 1e-9
+
+
+def test_link_coupling_at_global_optimum():
+    """Eq. 10-11: at the optimal link point x_link = x*_tau the multiplier of the
+    first sub-problem's end constraint and the second's start multiplier
+    cancel, i.e. dJ_1/dz + dJ_2/dx_s = 0 for consecutive segments."""
+    n, m, T = 4, 2, 15
+    prob = workloads.make_problem(n, m, T, seed=51, cross=True)
+    ric = oracle.riccati(prob)
+    x = ric["x"]
+    b = [0, 5, 10]
+    s0 = oracle.segment_summary(prob, b[0], b[1])
+    s1 = oracle.segment_summary(prob, b[1], b[2])
+    z = x[b[1]]
+    g_end = s0["Vzx"] @ x[b[0]] + s0["Vzz"] @ z + s0["vz"]
+    g_start = s1["Vxx"] @ z + s1["Vzx"].T @ x[b[2]] + s1["vx"]
+    assert np.abs(g_end + g_start).max() <= 1e-9 * np.abs(g_end).max()
+    # and -dJ/dx_s at the start of segment 1 is the global multiplier lambda_tau
+    assert oracle.rel_err(-g_start, ric["lam"][b[1]]) < 1e-9
+
+
+def test_double_integrator_split_equals_serial():
+    """Section III-A: with J = 3 sub-trajectories the undisturbed optimal
+    trajectory of the split method equals the serial Riccati trajectory.
+    The split here is carried out with oracle summaries and a dense link solve."""
+    with open(os.path.join(GOLDEN, "double_integrator.json")) as f:
+        cfg = json.load(f)
+    prob = workloads.double_integrator(T=cfg["T_chosen"], dt=cfg["dt_chosen"], alpha=cfg["alpha"],
+                                       alpha_T=cfg["alpha_T"], beta=cfg["beta"])
+    assert list(prob["x0"]) == cfg["x0"]
+    T = prob["B"].shape[0]
+    n = 2
+    J = cfg["J"]
+    bnd = [round(j * T / J) for j in range(J + 1)]
+    ric = oracle.riccati(prob)
+    summ = [oracle.segment_summary(prob, bnd[j], bnd[j + 1]) for j in range(J - 1)]
+    # last segment: serial value function at its start
+    P_last, p_last = ric["P"][bnd[J - 1]], ric["p"][bnd[J - 1]]
+    # stationarity of sum_j J_j in the link points z_1..z_{J-1}
+    N = (J - 1) * n
+    M = np.zeros((N, N))
+    rhs = np.zeros(N)
+    for j in range(1, J):
+        sl = slice((j - 1) * n, j * n)
+        prev = summ[j - 1]
+        M[sl, sl] += prev["Vzz"]
+        rhs[sl] -= prev["vz"]
+        if j == 1:
+            rhs[sl] -= prev["Vzx"] @ prob["x0"]
+        else:
+            M[sl, slice((j - 2) * n, (j - 1) * n)] += prev["Vzx"]
+        if j < J - 1:
+            cur = summ[j]
+            M[sl, sl] += cur["Vxx"]
+            M[sl, slice(j * n, (j + 1) * n)] += cur["Vzx"].T
+            rhs[sl] -= cur["vx"]
+        else:
+            M[sl, sl] += P_last
+            rhs[sl] -= p_last
+    z = np.linalg.solve(M, rhs).reshape(J - 1, n)
+    for j in range(1, J):
+        assert np.abs(z[j - 1] - ric["x"][bnd[j]]).max() < 1e-9
