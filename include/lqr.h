@@ -1,0 +1,157 @@
+/*
+ * liblqr: segment-parallel Riccati recursion for discrete-time, time-varying,
+ * finite-horizon LQR on one GB300 GPU (sm_103a).
+ *
+ * Problem (Section II, Eq. 1-2 of Laine & Tomlin, "The Parallelization of
+ * Riccati Recursion"):
+ *     minimise  sum_{t<T} 1/2 x_t'Q_t x_t + u_t'S_t x_t + 1/2 u_t'R_t u_t + q_t'x_t + r_t'u_t
+ *               + 1/2 x_T'Q_T x_T + q_T'x_T
+ *     subject to x_{t+1} = A_t x_t + B_t u_t + c_t,  x_0 = x0.
+ * The paper's names: Q_xx = Q, Q_uu = R, Q_ux = S (m x n), q_x1 = q, q_u1 = r,
+ * F_x = A, F_u = B, f_1 = c, x_init = x0. R_t must be positive definite and the
+ * problem strictly convex (Section II, assumption after Eq. 2).
+ *
+ * Method (Sections II-A to II-C): the horizon is split into K segments. Every
+ * segment but the last runs the constraint-explicit backward sweep of Section
+ * II-B with its end state x_term as a parameter; the last runs a plain Riccati
+ * sweep from the terminal cost. The segment summaries are coupled through the
+ * link equations of Eq. 10-11 (a block-tridiagonal FP64 system in the K-1 link
+ * states), whose backward elimination yields the global value function at the
+ * segment boundaries. A second, exact sweep per segment (the smoothing pass of
+ * Section III-A, started from that global value function) then gives the serial
+ * feedback policies K_t, k_t, and a forward rollout per segment from its link
+ * state gives x_t, u_t and the multipliers lambda_t of Eq. 3.
+ *
+ * Memory and layout. All problem and solution arrays are DEVICE pointers owned
+ * by the caller, row-major, stage-major and contiguous:
+ *     A[T][n][n]  B[T][n][m]  c[T][n]  Q[T+1][n][n] (slot T = Q_T)
+ *     R[T][m][m]  S[T][m][n] (NULL means S = 0)  q[T+1][n] (slot T = q_T)
+ *     r[T][m]     x0[n]
+ *     K[T][m][n]  k[T][m]  x[T+1][n]  u[T][m]  P[T+1][n][n]  p[T+1][n]  lam[T+1][n]
+ * Q and R are read symmetrised, 1/2 (M + M'). The element type is double for
+ * LQR_FP64 and LQR_MIXED_*, float for LQR_FP32.
+ *
+ * Streams and errors. Every call validates its arguments on the host first and
+ * returns LQR_ERR_INVALID_ARG without touching the GPU when they are wrong.
+ * Solves are enqueued on the caller's stream (a cudaStream_t passed as void*;
+ * NULL = the legacy default stream) and return before the GPU finishes.
+ * Conditions found on the device (a non positive-definite pivot, a segment that
+ * cannot absorb its end constraint, non-finite values) are recorded in a status
+ * word of the handle and read back by lqr_report(), which synchronises the
+ * stream. No call traps or aborts. A handle must not be used from two host
+ * threads at once; solves on one handle are stream-ordered on the stream given.
+ */
+#ifndef LQR_H
+#define LQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LQR_OK = 0,
+  LQR_ERR_INVALID_ARG = 1,        /* bad pointer, size or option (host check)              */
+  LQR_ERR_NOT_PD = 2,             /* R_t + B_t'P B_t or a link block not positive definite */
+  LQR_ERR_SEGMENT_INFEASIBLE = 3, /* a segment cannot absorb its end-point constraint      */
+  LQR_ERR_NONFINITE = 4,          /* NaN or Inf produced                                   */
+  LQR_ERR_NO_CONVERGENCE = 5,     /* iterative refinement did not reach opts.tol           */
+  LQR_ERR_TIMEOUT = 6,            /* a bounded device wait ran out                         */
+  LQR_ERR_CUDA = 7,               /* a CUDA runtime call failed                            */
+  LQR_ERR_OOM = 8,                /* workspace allocation failed                           */
+  LQR_ERR_UNSUPPORTED = 9         /* valid request this build does not implement           */
+} lqr_status;
+
+typedef enum {
+  LQR_FP64 = 0,       /* all arithmetic in FP64 (the plain method)                          */
+  LQR_FP32 = 1,       /* FP32 data and arithmetic; FP64 factor of R+B'PB and link solve     */
+  LQR_MIXED_TF32 = 2, /* FP64 data; FP32 sweeps, FP64 factor/link solve, FP64 KKT refinement */
+  LQR_MIXED_BF16 = 3  /* reserved                                                            */
+} lqr_precision;
+
+typedef struct lqr_handle lqr_handle;
+
+/* One problem: dimensions and device pointers (layout above). */
+typedef struct {
+  int n, m, T;
+  const void *A, *B, *c, *Q, *R, *S, *q, *r, *x0;
+} lqr_problem;
+
+/* Outputs: caller-allocated device arrays; any may be NULL except where noted.
+ * x and u are written when non-NULL; lam needs x and u. */
+typedef struct {
+  void *K, *k, *x, *u, *P, *p, *lam;
+} lqr_solution;
+
+typedef struct {
+  lqr_precision prec;
+  int num_segments;   /* K >= 1; 0 = choose automatically                         */
+  double tol;         /* KKT backward-error target of the refinement (MIXED)      */
+  int max_refine;     /* refinement iterations allowed (MIXED)                     */
+  int debug_checks;   /* 1 = also verify each segment's rollout meets its link state */
+} lqr_opts;
+
+/* Scalars of the last solve, read back by lqr_report(). */
+typedef struct {
+  int status;          /* lqr_status of the device side of the last solve */
+  int num_segments;    /* K used                                          */
+  int refine_iters;    /* refinement iterations run                       */
+  int bad_stage;       /* first stage index a device check flagged, or -1 */
+  double cost;         /* optimal objective J* (Eq. 1) along x, u         */
+  double kkt_residual; /* normwise backward error of Eq. 3 when computed, else -1 */
+} lqr_report_t;
+
+/* Per-segment summary written by lqr_segment_summaries (FP64, per segment j):
+ * Vxx[n][n], Vzx[n][n], Vzz[n][n], vx[n], vz[n], i.e. the quadratic
+ * cost_to_go_{b_j}(x, x_term) of Eq. 9 at the segment start, with
+ * x_term = the segment's end state. The last segment stores its plain Riccati
+ * value (P at its start in the Vxx slot, p in the vx slot, zeros elsewhere). */
+#define LQR_SUMMARY_DOUBLES(n) (3 * (size_t)(n) * (size_t)(n) + 2 * (size_t)(n))
+
+/* Create a handle on CUDA device `device`. workspace_hint (bytes) pre-sizes the
+ * device workspace; 0 = grow on first use. The handle owns the workspace. */
+lqr_status lqr_create(lqr_handle **h, int device, size_t workspace_hint);
+
+/* Free the handle and its workspace (synchronises the device first). */
+lqr_status lqr_destroy(lqr_handle *h);
+
+/* Segment boundaries b_0 = 0 < b_1 < ... < b_K = T used for K segments:
+ * b_j = floor(j*T/K). Writes K+1 ints to bounds (host memory). Fails with
+ * LQR_ERR_SEGMENT_INFEASIBLE when some segment would be shorter than
+ * ceil(n/m) stages, the least a segment needs to reach an arbitrary end state
+ * (Section II-B, the feasibility remark after Eq. 16). */
+lqr_status lqr_partition(int n, int m, int T, int K, int *bounds);
+
+/* Solve one problem (Sections II-A..II-C). Asynchronous on `stream`. */
+lqr_status lqr_solve(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts,
+                     const lqr_solution *sol, void *stream);
+
+/* The same solve with HOST problem and solution pointers: copies the inputs
+ * to the handle's device staging area, solves, copies the requested outputs
+ * back and synchronises `stream` before returning. Host buffers should be
+ * pinned for full copy bandwidth. */
+lqr_status lqr_solve_host(lqr_handle *h, const lqr_problem *prob_host, const lqr_opts *opts,
+                          const lqr_solution *sol_host, void *stream);
+
+/* Step A1 alone: the per-segment parametric backward sweeps (Section II-B,
+ * Eq. 9-16). Writes K summaries of LQR_SUMMARY_DOUBLES(n) doubles each to the
+ * device array `summaries` (FP64). */
+lqr_status lqr_segment_summaries(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts,
+                                 double *summaries, void *stream);
+
+/* Synchronise `stream` and read back the scalars of the last solve on h. */
+lqr_status lqr_report(lqr_handle *h, void *stream, lqr_report_t *out);
+
+/* Human-readable name of a status code (static string). */
+const char *lqr_status_string(lqr_status s);
+
+/* Number of kernels the last lqr_solve / lqr_segment_summaries call enqueued. */
+int lqr_last_launch_count(const lqr_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQR_H */

@@ -1,0 +1,266 @@
+// CTA-cooperative dense linear algebra on small row-major matrices held in
+// shared or global memory (generic addressing). Every routine is executed by
+// all threads of the block; routines do NOT end with a barrier unless stated,
+// so independent routines can run back to back and the caller places the
+// __syncthreads() that orders dependent phases.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace lqr {
+
+template <typename T>
+__device__ __forceinline__ T ld_val(const T* p) { return *p; }
+
+// ---------------------------------------------------------------------------
+// Matrix product with a per-element epilogue.
+//   acc(i,j) = sum_k opA(i,k) * opB(k,j),  0 <= i < M, 0 <= j < N
+//   opA(i,k) = TA ? A[k*lda + i] : A[i*lda + k]
+//   opB(k,j) = TB ? B[j*ldb + k] : B[k*ldb + j]
+// Each thread owns RM x RN output tiles; tiles are dealt round-robin over the
+// block, consecutive threads take consecutive column tiles of one row tile.
+// ---------------------------------------------------------------------------
+template <int RM, int RN, bool TA, bool TB, typename Tacc, typename XA, typename XB, typename Epi>
+__device__ __forceinline__ void cta_mm(int M, int N, int K, const XA* A, int lda,
+                                       const XB* B, int ldb, Epi epi) {
+  const int tm = (M + RM - 1) / RM, tn = (N + RN - 1) / RN;
+  const int ntiles = tm * tn;
+  for (int tile = threadIdx.x; tile < ntiles; tile += blockDim.x) {
+    const int i0 = (tile / tn) * RM, j0 = (tile % tn) * RN;
+    Tacc acc[RM][RN];
+#pragma unroll
+    for (int a = 0; a < RM; ++a)
+#pragma unroll
+      for (int b = 0; b < RN; ++b) acc[a][b] = Tacc(0);
+    int ia[RM], jb[RN];
+#pragma unroll
+    for (int a = 0; a < RM; ++a) ia[a] = min(i0 + a, M - 1);  // clamp: rows past M are discarded
+#pragma unroll
+    for (int b = 0; b < RN; ++b) jb[b] = min(j0 + b, N - 1);
+    for (int k = 0; k < K; ++k) {
+      Tacc av[RM], bv[RN];
+#pragma unroll
+      for (int a = 0; a < RM; ++a)
+        av[a] = static_cast<Tacc>(TA ? A[(size_t)k * lda + ia[a]] : A[(size_t)ia[a] * lda + k]);
+#pragma unroll
+      for (int b = 0; b < RN; ++b)
+        bv[b] = static_cast<Tacc>(TB ? B[(size_t)jb[b] * ldb + k] : B[(size_t)k * ldb + jb[b]]);
+#pragma unroll
+      for (int a = 0; a < RM; ++a)
+#pragma unroll
+        for (int b = 0; b < RN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < RM; ++a)
+#pragma unroll
+      for (int b = 0; b < RN; ++b)
+        if (i0 + a < M && j0 + b < N) epi(i0 + a, j0 + b, acc[a][b]);
+  }
+}
+
+// --- epilogues --------------------------------------------------------------
+template <typename XC>
+struct EpiStore {  // C = alpha * acc
+  XC* C; int ldc; double alpha;
+  template <typename T>
+  __device__ __forceinline__ void operator()(int i, int j, T v) const {
+    C[(size_t)i * ldc + j] = static_cast<XC>(static_cast<T>(alpha) * v);
+  }
+};
+template <typename XC>
+struct EpiStoreT {  // C' = alpha * acc  (writes C[j][i])
+  XC* C; int ldc; double alpha;
+  template <typename T>
+  __device__ __forceinline__ void operator()(int i, int j, T v) const {
+    C[(size_t)j * ldc + i] = static_cast<XC>(static_cast<T>(alpha) * v);
+  }
+};
+template <typename XC>
+struct EpiAccum {  // C += alpha * acc
+  XC* C; int ldc; double alpha;
+  template <typename T>
+  __device__ __forceinline__ void operator()(int i, int j, T v) const {
+    XC* p = C + (size_t)i * ldc + j;
+    *p = static_cast<XC>(static_cast<T>(*p) + static_cast<T>(alpha) * v);
+  }
+};
+template <typename XC, typename XD>
+struct EpiAdd {  // C = alpha * acc + D (D == nullptr means 0)
+  XC* C; int ldc; double alpha; const XD* D; int ldd;
+  template <typename T>
+  __device__ __forceinline__ void operator()(int i, int j, T v) const {
+    T d = D ? static_cast<T>(D[(size_t)i * ldd + j]) : T(0);
+    C[(size_t)i * ldc + j] = static_cast<XC>(static_cast<T>(alpha) * v + d);
+  }
+};
+template <typename XC, typename XD>
+struct EpiAddSym {  // C = alpha * acc + (D + D')/2, D square with leading dimension ldd
+  XC* C; int ldc; double alpha; const XD* D; int ldd;
+  template <typename T>
+  __device__ __forceinline__ void operator()(int i, int j, T v) const {
+    T d = T(0.5) * (static_cast<T>(D[(size_t)i * ldd + j]) + static_cast<T>(D[(size_t)j * ldd + i]));
+    C[(size_t)i * ldc + j] = static_cast<XC>(static_cast<T>(alpha) * v + d);
+  }
+};
+
+// y[i] (op)= alpha * sum_k opA(i,k) x[k] ; one thread per output row.
+template <bool TA, typename Tacc, typename XA, typename XX, typename Epi>
+__device__ __forceinline__ void cta_mv(int M, int K, const XA* A, int lda,
+                                       const XX* x, int incx, Epi epi) {
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    Tacc acc = Tacc(0);
+    for (int k = 0; k < K; ++k)
+      acc = fma(static_cast<Tacc>(TA ? A[(size_t)k * lda + i] : A[(size_t)i * lda + k]),
+                static_cast<Tacc>(x[(size_t)k * incx]), acc);
+    epi(i, 0, acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// In-place lower Cholesky (FP64) of the d x d SPD matrix G (leading dim ld).
+// Right-looking, one column per step. `flag` is a shared int set to 1 when a
+// pivot is not positive (then the factor is garbage). Ends with a barrier;
+// the caller reads *flag after it.
+// ---------------------------------------------------------------------------
+__device__ inline void cta_chol(int d, double* G, int ld, int* flag) {
+  for (int j = 0; j < d; ++j) {
+    if (threadIdx.x == 0) {
+      double s = G[(size_t)j * ld + j];
+      if (!(s > 0.0) || !isfinite(s)) {
+        *flag = 1;
+        s = 1.0;  // keep the arithmetic finite; the caller discards the result
+      }
+      G[(size_t)j * ld + j] = sqrt(s);
+    }
+    __syncthreads();
+    const double inv = 1.0 / G[(size_t)j * ld + j];
+    for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) G[(size_t)i * ld + j] *= inv;
+    __syncthreads();
+    // trailing update of the lower triangle: rows i > j, columns j < k <= i
+    const int w = d - j - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int ii = e / w, kk = e % w;
+      if (kk > ii) continue;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      G[(size_t)i * ld + k] -= G[(size_t)i * ld + j] * G[(size_t)k * ld + j];
+    }
+    __syncthreads();
+  }
+}
+
+// Solve L Y = X in place (L lower d x d, leading dim ldl; X d x nc, leading dim ldx).
+// One thread per right-hand-side column. No barrier at the end.
+template <typename XX>
+__device__ __forceinline__ void cta_trsm_lower(int d, const double* L, int ldl, int nc, XX* X, int ldx) {
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    for (int i = 0; i < d; ++i) {
+      double t = static_cast<double>(X[(size_t)i * ldx + c]);
+      for (int k = 0; k < i; ++k) t -= L[(size_t)i * ldl + k] * static_cast<double>(X[(size_t)k * ldx + c]);
+      X[(size_t)i * ldx + c] = static_cast<XX>(t / L[(size_t)i * ldl + i]);
+    }
+  }
+}
+
+// Solve L' Y = X in place (L lower). No barrier at the end.
+template <typename XX>
+__device__ __forceinline__ void cta_trsm_lower_t(int d, const double* L, int ldl, int nc, XX* X, int ldx) {
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    for (int i = d - 1; i >= 0; --i) {
+      double t = static_cast<double>(X[(size_t)i * ldx + c]);
+      for (int k = i + 1; k < d; ++k) t -= L[(size_t)k * ldl + i] * static_cast<double>(X[(size_t)k * ldx + c]);
+      X[(size_t)i * ldx + c] = static_cast<XX>(t / L[(size_t)i * ldl + i]);
+    }
+  }
+}
+
+// Solve U Y = X in place (U upper d x d, row-major, leading dim ldu). No barrier.
+__device__ __forceinline__ void cta_trsm_upper(int d, const double* U, int ldu, int nc, double* X, int ldx) {
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    for (int i = d - 1; i >= 0; --i) {
+      double t = X[(size_t)i * ldx + c];
+      for (int k = i + 1; k < d; ++k) t -= U[(size_t)i * ldu + k] * X[(size_t)k * ldx + c];
+      X[(size_t)i * ldx + c] = t / U[(size_t)i * ldu + i];
+    }
+  }
+}
+
+// Solve U' Y = X in place (U upper, so U' is lower). No barrier.
+__device__ __forceinline__ void cta_trsm_upper_t(int d, const double* U, int ldu, int nc, double* X, int ldx) {
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    for (int i = 0; i < d; ++i) {
+      double t = X[(size_t)i * ldx + c];
+      for (int k = 0; k < i; ++k) t -= U[(size_t)k * ldu + i] * X[(size_t)k * ldx + c];
+      X[(size_t)i * ldx + c] = t / U[(size_t)i * ldu + i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR, FP64, in place on X (nr x nc, leading dim ld): reflects the
+// first p columns (p <= nr, p <= nc) and applies every reflection to all
+// columns to their right. On exit X[0:p,0:p] upper holds R, X[i][j] (i > j,
+// j < p) holds the reflector tail, vhead[j] its head and beta[j] its scale,
+// so that H_j = I - beta_j v_j v_j' and Q' X_in = H_{p-1} ... H_0 X_in.
+// scal must point to 4 shared doubles. Ends with a barrier.
+// ---------------------------------------------------------------------------
+__device__ inline void cta_householder_qr(int nr, int nc, int p, double* X, int ld, double* vhead,
+                                          double* beta, double* scal) {
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x < 32) {
+      double s = 0.0;
+      for (int i = j + threadIdx.x; i < nr; i += 32) {
+        const double v = X[(size_t)i * ld + j];
+        s = fma(v, v, s);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (threadIdx.x == 0) {
+        const double x0 = X[(size_t)j * ld + j];
+        const double sigma = sqrt(s);
+        if (sigma == 0.0) {
+          scal[0] = 0.0;   // alpha
+          beta[j] = 0.0;
+          vhead[j] = 0.0;
+        } else {
+          const double alpha = x0 >= 0.0 ? -sigma : sigma;
+          vhead[j] = x0 - alpha;
+          beta[j] = 1.0 / (sigma * (sigma + fabs(x0)));
+          scal[0] = alpha;
+        }
+      }
+    }
+    __syncthreads();
+    const double bj = beta[j], v0 = vhead[j];
+    for (int c = j + 1 + threadIdx.x; c < nc; c += blockDim.x) {
+      double s = v0 * X[(size_t)j * ld + c];
+      for (int i = j + 1; i < nr; ++i) s = fma(X[(size_t)i * ld + j], X[(size_t)i * ld + c], s);
+      s *= bj;
+      X[(size_t)j * ld + c] -= s * v0;
+      for (int i = j + 1; i < nr; ++i) X[(size_t)i * ld + c] -= s * X[(size_t)i * ld + j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) X[(size_t)j * ld + j] = (bj == 0.0) ? X[(size_t)j * ld + j] : scal[0];
+    __syncthreads();
+  }
+}
+
+// Apply H_j (j = 0..p-1 in that order, i.e. Q') or in reverse order (i.e. Q)
+// to the columns of Y (nr x nc, leading dim ldy), using reflectors stored by
+// cta_householder_qr in V (leading dim ldv). Ends with a barrier.
+__device__ inline void cta_householder_apply(int nr, int p, const double* V, int ldv, const double* vhead,
+                                             const double* beta, int nc, double* Y, int ldy, bool transpose_q) {
+  for (int jj = 0; jj < p; ++jj) {
+    const int j = transpose_q ? jj : p - 1 - jj;
+    const double bj = beta[j], v0 = vhead[j];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      double s = v0 * Y[(size_t)j * ldy + c];
+      for (int i = j + 1; i < nr; ++i) s = fma(V[(size_t)i * ldv + j], Y[(size_t)i * ldy + c], s);
+      s *= bj;
+      Y[(size_t)j * ldy + c] -= s * v0;
+      for (int i = j + 1; i < nr; ++i) Y[(size_t)i * ldy + c] -= s * V[(size_t)i * ldv + j];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace lqr

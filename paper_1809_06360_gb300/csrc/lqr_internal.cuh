@@ -1,0 +1,178 @@
+// Internal types shared by the liblqr kernels and the host orchestration.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cta_linalg.cuh"
+#include "lqr.h"
+
+namespace lqr {
+
+constexpr int kBlock = 256;           // threads per CTA of the sweep / rollout kernels
+constexpr int kStaticSmemReserve = 1024;
+
+// Segment j of a K-way split of T stages covers [seg_begin(j), seg_begin(j+1)).
+__host__ __device__ inline int seg_begin(int T, int K, int j) {
+  return (int)(((long long)j * (long long)T) / (long long)K);
+}
+
+// Per-problem FP64 workspace, offsets in doubles from ProbDesc::ws.
+struct WsLayout {
+  long long summ;   // K * (3n^2 + 2n)   segment summaries (Eq. 9 at each segment start)
+  long long Pi;     // (K+1) * n^2       global value Hessian at b_j (j = 0..K-1 used)
+  long long pi;     // (K+1) * n         global value gradient at b_j
+  long long Gam;    // K * n^2           link feedback z_{j+1} = Gam_j z_j + gam_j
+  long long gam;    // K * n
+  long long z;      // (K+1) * n         link states z_j = x_{b_j}
+  long long costp;  // K                 partial objective per segment
+  long long total;
+};
+
+__host__ __device__ inline WsLayout ws_layout(int n, int K) {
+  WsLayout w;
+  const long long nn = (long long)n * n;
+  long long o = 0;
+  w.summ = o;  o += (long long)K * (3 * nn + 2 * n);
+  w.Pi = o;    o += (long long)(K + 1) * nn;
+  w.pi = o;    o += (long long)(K + 1) * n;
+  w.Gam = o;   o += (long long)K * nn;
+  w.gam = o;   o += (long long)K * n;
+  w.z = o;     o += (long long)(K + 1) * n;
+  w.costp = o; o += K;
+  w.total = (o + 31) & ~31LL;
+  return w;
+}
+
+// One problem as the kernels see it.
+struct ProbDesc {
+  const void *A, *B, *c, *Q, *R, *S, *q, *r, *x0;   // element type TS
+  void *K, *k, *x, *u, *P, *p, *lam;                 // element type TS, may be null
+  double* ws;                 // WsLayout base
+  double* scratch;            // nseg * scratch_per_unit doubles (spilled sweep buffers)
+  long long scratch_per_unit; // doubles
+  int* status;                // [0] = lqr_status, [1] = first flagged stage
+  double* report;             // [0] = cost (written by the finalize kernel)
+  int n, m, T, nseg;
+  int unit0;                  // first unit (segment) index of this problem in a launch
+  int pad;
+};
+
+// Kernel-argument view of the problems of one launch: a single problem is
+// passed by value, a batch through a device array plus a unit -> problem map.
+struct ProbTable {
+  ProbDesc single;
+  const ProbDesc* probs;      // device array (batched) or nullptr
+  const int* unit_prob;       // device array: unit -> problem index (batched)
+  int nprob;
+};
+
+__device__ __forceinline__ const ProbDesc& prob_of_unit(const ProbTable& tab, int unit) {
+  return tab.probs ? tab.probs[tab.unit_prob[unit]] : tab.single;
+}
+__device__ __forceinline__ const ProbDesc& prob_at(const ProbTable& tab, int i) {
+  return tab.probs ? tab.probs[i] : tab.single;
+}
+
+// First error wins; records the stage that raised it.
+__device__ __forceinline__ void raise_status(int* st, int code, int stage) {
+  if (atomicCAS(st, 0, code) == 0) atomicExch(st + 1, stage);
+}
+
+// ---------------------------------------------------------------------------
+// Placement plan of the segment-sweep buffers: each buffer lives in dynamic
+// shared memory while the budget lasts (in priority order), otherwise in the
+// unit's slice of global scratch. Identical on host and device.
+// ---------------------------------------------------------------------------
+enum SweepBuf {
+  SB_VXX = 0,  // TC  n x n        V_xx (then M_xx)
+  SB_AB,       // TC  n x ldAB     [A_t | B_t | c_t]
+  SB_T1,       // TC  n x ldAB     V_xx [A|B|c] (+v_x), later V_zx A
+  SB_F,        // TC  m x ldF      [M_ux | M_zu' | m_u]  (then W = L^-1 F, then policy)
+  SB_MUU,      // TC  m x m        M_uu
+  SB_L64,      // f64 m x m        Cholesky factor of M_uu (aliases SB_MUU when TC = double)
+  SB_VEC,      // TC  4n           v_x, v_z, m_z, spare
+  SB_VZX,      // TC  n x n        V_zx          (parametric sweep only)
+  SB_HH,       // f64 2m           Householder heads and scales
+  SB_G,        // f64 m x (2n+1)   constrained-stage policy [K_x | K_z | k_1]
+  SB_E,        // f64 m x (2n+1)   F + M_uu G, also M~ (m x m)
+  SB_H,        // f64 n x (2n+1)   constraint_to_go [H_x | H_z | h_1] (Eq. 9b), r rows used
+  SB_AUG,      // f64 workspace of the range/null-space split
+  SB_COUNT
+};
+
+enum SweepMode { MODE_PARAM = 0, MODE_TERMINAL = 1, MODE_POLICY = 2 };
+
+struct SweepPlan {
+  int ldAB, ldF, ldG, ldH, ldAug;
+  long long off[SB_COUNT];    // byte offset (smem or scratch)
+  unsigned smem_mask;         // bit b set = buffer b in shared memory
+  long long smem_bytes;       // dynamic shared memory used
+  long long scratch_bytes;    // global scratch per unit
+};
+
+__host__ __device__ inline long long align16(long long b) { return (b + 15) & ~15LL; }
+
+__host__ __device__ inline void make_plan(SweepPlan& P, int n, int m, int mode, int tc_size,
+                                          long long smem_budget) {
+  const bool param = (mode == MODE_PARAM);
+  P.ldAB = n + m + 1;
+  P.ldF = param ? 2 * n + 1 : n + 1;
+  P.ldG = 2 * n + 1;
+  P.ldH = 2 * n + 1;
+  // [N_u | N_x | N_z | n_1] (n rows) or [N_u' | F | M_uu] (m rows, at most n + ldF + m columns)
+  const long long aug1 = (long long)n * (m + 2 * n + 1);
+  const long long aug2 = (long long)m * (n + (2 * n + 1) + m);
+  P.ldAug = 0;  // chosen per stage
+  long long bytes[SB_COUNT];
+  const long long tc = tc_size;
+  bytes[SB_VXX] = tc * n * n;
+  bytes[SB_AB] = tc * n * P.ldAB;
+  bytes[SB_T1] = tc * n * P.ldAB;
+  bytes[SB_F] = tc * m * P.ldF;
+  bytes[SB_MUU] = tc * m * m;
+  bytes[SB_L64] = (tc_size == 8) ? 0 : 8LL * m * m;
+  bytes[SB_VEC] = tc * 4 * n;
+  bytes[SB_VZX] = param ? tc * n * n : 0;
+  bytes[SB_HH] = param ? 8LL * 2 * m : 0;
+  bytes[SB_G] = param ? 8LL * m * P.ldG : 0;
+  bytes[SB_E] = param ? 8LL * m * (P.ldG > m ? P.ldG : m) : 0;
+  bytes[SB_H] = param ? 8LL * n * P.ldH : 0;
+  bytes[SB_AUG] = param ? 8LL * (aug1 > aug2 ? aug1 : aug2) : 0;
+  long long s = 0, g = 0;
+  P.smem_mask = 0;
+  for (int b = 0; b < SB_COUNT; ++b) {
+    const long long sz = align16(bytes[b]);
+    if (sz == 0) { P.off[b] = 0; continue; }
+    if (s + sz <= smem_budget) {
+      P.off[b] = s; s += sz; P.smem_mask |= (1u << b);
+    } else {
+      P.off[b] = g; g += sz;
+    }
+  }
+  P.smem_bytes = s;
+  P.scratch_bytes = g;
+}
+
+template <typename T>
+__device__ __forceinline__ T* plan_ptr(const SweepPlan& P, int b, unsigned char* smem, unsigned char* scratch) {
+  return reinterpret_cast<T*>(((P.smem_mask >> b) & 1u) ? smem + P.off[b] : scratch + P.off[b]);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files, called by lqr_api.cu).
+// ---------------------------------------------------------------------------
+// phase 0: A1 (parametric sweeps + terminal sweep); phase 1: A4 (policy sweeps)
+template <typename TS, typename TC>
+cudaError_t launch_seg_sweep(const ProbTable& tab, int nunits, int phase, long long smem_bytes,
+                             long long smem_budget, int store_P, cudaStream_t st);
+template <typename TS, typename TC>
+long long sweep_smem_needed(int n, int m, long long smem_budget, long long* scratch_doubles);
+
+cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
+
+template <typename TS, typename TC>
+cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st);
+
+cudaError_t launch_finalize(const ProbTable& tab, int nprob, cudaStream_t st);
+
+}  // namespace lqr

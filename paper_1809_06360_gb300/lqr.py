@@ -1,0 +1,239 @@
+"""Thin ctypes binding of liblqr (include/lqr.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of
+liblqr.so. The functions carry the C names; `Solver` wraps them for torch
+tensors (device memory and the current CUDA stream come from PyTorch).
+There is no CPU fallback: without the compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+
+LQR_OK = 0
+STATUS_NAMES = {0: "LQR_OK", 1: "LQR_ERR_INVALID_ARG", 2: "LQR_ERR_NOT_PD", 3: "LQR_ERR_SEGMENT_INFEASIBLE",
+                4: "LQR_ERR_NONFINITE", 5: "LQR_ERR_NO_CONVERGENCE", 6: "LQR_ERR_TIMEOUT", 7: "LQR_ERR_CUDA",
+                8: "LQR_ERR_OOM", 9: "LQR_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+
+PROBLEM_FIELDS = ("A", "B", "c", "Q", "R", "S", "q", "r", "x0")
+SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
+
+# Exported symbols declared in include/lqr.h
+EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
+           "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count")
+
+
+class lqr_problem(ctypes.Structure):
+    _fields_ = [("n", c_int), ("m", c_int), ("T", c_int)] + [(f, c_void_p) for f in PROBLEM_FIELDS]
+
+
+class lqr_solution(ctypes.Structure):
+    _fields_ = [(f, c_void_p) for f in SOLUTION_FIELDS]
+
+
+class lqr_opts(ctypes.Structure):
+    _fields_ = [("prec", c_int), ("num_segments", c_int), ("tol", c_double), ("max_refine", c_int),
+                ("debug_checks", c_int)]
+
+
+class lqr_report_t(ctypes.Structure):
+    _fields_ = [("status", c_int), ("num_segments", c_int), ("refine_iters", c_int), ("bad_stage", c_int),
+                ("cost", c_double), ("kkt_residual", c_double)]
+
+
+class LqrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s" % (where, STATUS_NAMES.get(status, str(status))))
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load liblqr.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("liblqr.so not found at %s; run paper_1809_06360_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.lqr_create.argtypes = [P(c_void_p), c_int, c_size_t]
+    lib.lqr_destroy.argtypes = [c_void_p]
+    lib.lqr_partition.argtypes = [c_int, c_int, c_int, c_int, P(c_int)]
+    lib.lqr_solve.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p]
+    lib.lqr_solve_host.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p]
+    lib.lqr_segment_summaries.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_void_p, c_void_p]
+    lib.lqr_report.argtypes = [c_void_p, c_void_p, P(lqr_report_t)]
+    lib.lqr_status_string.argtypes = [c_int]
+    lib.lqr_status_string.restype = ctypes.c_char_p
+    lib.lqr_last_launch_count.argtypes = [c_void_p]
+    for name in ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
+                 "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count"):
+        getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != LQR_OK:
+        raise LqrError(st, where)
+
+
+# --- C-named wrappers ---------------------------------------------------------
+
+def lqr_create(device: int = 0, workspace_hint: int = 0) -> int:
+    h = c_void_p()
+    _check(load().lqr_create(ctypes.byref(h), device, workspace_hint), "lqr_create")
+    return h.value
+
+
+def lqr_destroy(h: int) -> None:
+    _check(load().lqr_destroy(h), "lqr_destroy")
+
+
+def lqr_partition(n: int, m: int, T: int, K: int) -> list[int]:
+    b = (c_int * (K + 1))()
+    _check(load().lqr_partition(n, m, T, K, b), "lqr_partition")
+    return list(b)
+
+
+def lqr_solve(h: int, prob: lqr_problem, opts: lqr_opts, sol: lqr_solution, stream: int | None) -> None:
+    _check(load().lqr_solve(h, ctypes.byref(prob), ctypes.byref(opts), ctypes.byref(sol), stream or None),
+           "lqr_solve")
+
+
+def lqr_solve_host(h: int, prob: lqr_problem, opts: lqr_opts, sol: lqr_solution, stream: int | None) -> None:
+    _check(load().lqr_solve_host(h, ctypes.byref(prob), ctypes.byref(opts), ctypes.byref(sol), stream or None),
+           "lqr_solve_host")
+
+
+def lqr_segment_summaries(h: int, prob: lqr_problem, opts: lqr_opts, summaries_ptr: int, stream: int | None):
+    _check(load().lqr_segment_summaries(h, ctypes.byref(prob), ctypes.byref(opts), summaries_ptr, stream or None),
+           "lqr_segment_summaries")
+
+
+def lqr_report(h: int, stream: int | None) -> dict:
+    rep = lqr_report_t()
+    _check(load().lqr_report(h, stream or None, ctypes.byref(rep)), "lqr_report")
+    return dict(status=rep.status, status_name=STATUS_NAMES.get(rep.status, str(rep.status)),
+                num_segments=rep.num_segments, refine_iters=rep.refine_iters, bad_stage=rep.bad_stage,
+                cost=rep.cost, kkt_residual=rep.kkt_residual)
+
+
+def lqr_status_string(status: int) -> str:
+    return load().lqr_status_string(status).decode()
+
+
+def lqr_last_launch_count(h: int) -> int:
+    return load().lqr_last_launch_count(h)
+
+
+# --- torch convenience -------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+class Solver:
+    """One liblqr handle bound to a CUDA device; problems are dicts of torch tensors."""
+
+    def __init__(self, device: int = 0, workspace_hint: int = 0):
+        self.device = device
+        self.h = lqr_create(device, workspace_hint)
+
+    def close(self):
+        if self.h:
+            lqr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _dims(prob):
+        T, n, m = prob["B"].shape
+        return int(n), int(m), int(T)
+
+    @staticmethod
+    def make_problem_struct(prob, ptr) -> lqr_problem:
+        n, m, T = Solver._dims(prob)
+        p = lqr_problem(n=n, m=m, T=T)
+        for f in PROBLEM_FIELDS:
+            v = prob.get(f)
+            setattr(p, f, ptr(v) if v is not None else None)
+        return p
+
+    def _stream(self, stream):
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        return stream.cuda_stream
+
+    def alloc_solution(self, prob, want=("K", "k", "x", "u", "lam")):
+        torch = _torch()
+        n, m, T = self._dims(prob)
+        dt = prob["A"].dtype
+        dev = prob["A"].device
+        shapes = dict(K=(T, m, n), k=(T, m), x=(T + 1, n), u=(T, m), P=(T + 1, n, n), p=(T + 1, n),
+                      lam=(T + 1, n))
+        out = {k: torch.empty(shapes[k], dtype=dt, device=dev) for k in want}
+        if "P" in out and "p" not in out:
+            out["p"] = torch.empty(shapes["p"], dtype=dt, device=dev)
+        return out
+
+    def solve(self, prob, num_segments=0, prec="fp64", out=None, want=("K", "k", "x", "u", "lam"),
+              stream=None, tol=1e-8, max_refine=0):
+        """Enqueue a solve on `stream` (torch stream; default current). Returns the output tensors."""
+        if out is None:
+            out = self.alloc_solution(prob, want)
+        ptr = lambda t: t.data_ptr()
+        p = self.make_problem_struct(prob, ptr)
+        s = lqr_solution(**{f: (out[f].data_ptr() if f in out else None) for f in SOLUTION_FIELDS})
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
+                     debug_checks=0)
+        lqr_solve(self.h, p, o, s, self._stream(stream))
+        return out
+
+    def report(self, stream=None) -> dict:
+        return lqr_report(self.h, self._stream(stream))
+
+    def segment_summaries(self, prob, num_segments, prec="fp64", stream=None):
+        torch = _torch()
+        n, m, T = self._dims(prob)
+        buf = torch.empty((num_segments, 3 * n * n + 2 * n), dtype=torch.float64, device=prob["A"].device)
+        p = self.make_problem_struct(prob, lambda t: t.data_ptr())
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0)
+        lqr_segment_summaries(self.h, p, o, buf.data_ptr(), self._stream(stream))
+        return buf
+
+    def solve_host(self, prob_np, num_segments=0, prec="fp64", out_np=None, want=("K", "k", "x", "u"),
+                   stream=None):
+        """Host-memory solve (numpy arrays, ideally pinned): copies in, solves, copies out, synchronises."""
+        import numpy as np
+        n, m, T = self._dims(prob_np)
+        if out_np is None:
+            dt = prob_np["A"].dtype
+            shapes = dict(K=(T, m, n), k=(T, m), x=(T + 1, n), u=(T, m), P=(T + 1, n, n), p=(T + 1, n),
+                          lam=(T + 1, n))
+            out_np = {k: np.empty(shapes[k], dtype=dt) for k in want}
+        p = self.make_problem_struct(prob_np, lambda a: a.ctypes.data)
+        s = lqr_solution(**{f: (out_np[f].ctypes.data if f in out_np else None) for f in SOLUTION_FIELDS})
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0)
+        lqr_solve_host(self.h, p, o, s, self._stream(stream))
+        return out_np

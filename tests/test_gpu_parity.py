@@ -1,0 +1,152 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerance (FP64 path): normwise relative error <= 1e-9 on K_t, k_t, x_t, u_t
+and lambda_t, the acceptance bound of the plain FP64 method. Summaries of the
+parametric segment sweep are compared with the oracle's dense-KKT summary."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_06360_gb300 import Solver, build
+    build.build()
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def to_dev(prob, dtype=torch.float64):
+    return {k: torch.from_numpy(v).to("cuda:0", dtype) for k, v in prob.items()}
+
+
+def check_vs_oracle(solver, prob, K, tol=TOL64, prec="fp64", want_P=False):
+    ref = oracle.riccati(prob)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    want = ("K", "k", "x", "u", "lam") + (("P",) if want_P else ())
+    out = solver.solve(to_dev(prob, dt), num_segments=K, prec=prec, want=want)
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    errs = {k: oracle.rel_err(out[k].double().cpu().numpy(), ref[k]) for k in want}
+    if want_P:
+        errs["p"] = oracle.rel_err(out["p"].double().cpu().numpy(), ref["p"])
+    errs["cost"] = abs(rep["cost"] - ref["cost"]) / max(1.0, abs(ref["cost"]))
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (K, errs)
+    return out, rep, errs
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 8, 16, 42])
+def test_config0_fp64_all_K(solver, K):
+    """n=12, m=4, T=128: every K from 1 to T/ceil(n/m) (ragged segments for K=3, 42)."""
+    check_vs_oracle(solver, workloads.config0(), K)
+
+
+@pytest.mark.parametrize("n,m,T,K,cross", [
+    (5, 2, 37, 4, True),     # n % m != 0: a mixed range/null-space stage per segment
+    (7, 3, 61, 7, True),
+    (8, 3, 24, 8, False),    # segments of exactly ceil(n/m) stages
+    (4, 4, 9, 9, True),      # n == m, one stage per segment
+    (3, 5, 20, 20, True),    # m > n
+    (1, 1, 6, 3, True),      # scalar
+    (16, 2, 200, 12, True),  # long constrained tails (8 stages)
+    (33, 7, 150, 5, True),   # odd sizes, ragged register tiles
+])
+def test_shapes_fp64(solver, n, m, T, K, cross):
+    prob = workloads.make_problem(n, m, T, seed=100 + n + m + T, cross=cross)
+    check_vs_oracle(solver, prob, K, want_P=True)
+
+
+def test_single_stage_problem(solver):
+    check_vs_oracle(solver, workloads.make_problem(3, 2, 1, seed=9, cross=True), 1)
+
+
+@pytest.mark.parametrize("n,m,T,K", [(5, 2, 30, 5), (6, 3, 24, 4), (7, 3, 27, 3), (4, 1, 20, 4)])
+def test_segment_summaries_vs_dense_kkt(solver, n, m, T, K):
+    prob = workloads.make_problem(n, m, T, seed=200 + n * m, cross=True)
+    summ = solver.segment_summaries(to_dev(prob), K).cpu().numpy()
+    from paper_1809_06360_gb300 import lqr
+    b = lqr.lqr_partition(n, m, T, K)
+    nn = n * n
+    for j in range(K - 1):
+        ref = oracle.segment_summary(prob, b[j], b[j + 1])
+        got = dict(Vxx=summ[j, :nn].reshape(n, n), Vzx=summ[j, nn:2 * nn].reshape(n, n),
+                   Vzz=summ[j, 2 * nn:3 * nn].reshape(n, n), vx=summ[j, 3 * nn:3 * nn + n],
+                   vz=summ[j, 3 * nn + n:])
+        for k in ("Vxx", "Vzx", "Vzz", "vx", "vz"):
+            assert oracle.rel_err(got[k], ref[k]) < 1e-9, (j, k)
+    # the last segment carries the serial value function at its start
+    ric = oracle.riccati(prob)
+    assert oracle.rel_err(summ[K - 1, :nn].reshape(n, n), ric["P"][b[K - 1]]) < 1e-9
+
+
+def test_K_invariance_bitwise_determinism(solver):
+    prob = workloads.make_problem(10, 3, 90, seed=77, cross=True)
+    dev = to_dev(prob)
+    xs = []
+    for K in (1, 5, 9, 22):
+        out = solver.solve(dev, num_segments=K)
+        xs.append(out["x"].cpu().numpy())
+    for x in xs[1:]:
+        assert oracle.rel_err(x, xs[0]) < 1e-10
+    a = solver.solve(dev, num_segments=9)["K"].cpu().numpy()
+    b = solver.solve(dev, num_segments=9)["K"].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_config1_fp64_full_size(solver):
+    """The bench workload (n=64, m=32, T=4096, rho(A)<=1.02) at K=64 against the
+    full oracle (a few seconds of serial FP64 on the host)."""
+    prob = workloads.config1()
+    check_vs_oracle(solver, prob, 64)
+
+
+def test_host_entry_point_matches_device(solver):
+    prob = workloads.make_problem(12, 4, 64, seed=5)
+    dev = solver.solve(to_dev(prob), num_segments=4)
+    host = solver.solve_host(prob, num_segments=4, want=("K", "k", "x", "u"))
+    for k in ("K", "k", "x", "u"):
+        assert np.array_equal(dev[k].cpu().numpy(), host[k])
+
+
+def test_not_pd_is_reported(solver):
+    prob = workloads.make_problem(6, 2, 40, seed=3)
+    prob["R"][30] = -np.eye(2) * 50.0
+    solver.solve(to_dev(prob), num_segments=4)
+    rep = solver.report()
+    assert rep["status_name"] == "LQR_ERR_NOT_PD"
+    # the handle stays usable
+    check_vs_oracle(solver, workloads.make_problem(6, 2, 40, seed=4), 4)
+
+
+def test_host_validation(solver):
+    from paper_1809_06360_gb300 import lqr
+    prob = to_dev(workloads.make_problem(12, 4, 64, seed=5))
+    with pytest.raises(lqr.LqrError) as e:
+        solver.solve(prob, num_segments=32)  # 2-stage segments < ceil(12/4)
+    assert e.value.status == 3
+    with pytest.raises(lqr.LqrError) as e:
+        solver.solve(prob, num_segments=65)
+    assert e.value.status == 1
+
+
+def test_fp32_path_error_is_bounded(solver):
+    """FP32 data and arithmetic (FP64 Cholesky and link solve): the error
+    against the FP64 oracle, per quantity, on the n=12 workload."""
+    prob = workloads.config0()
+    ref = oracle.riccati(prob)
+    out = solver.solve(to_dev(prob, torch.float32), num_segments=8, prec="fp32")
+    assert solver.report()["status"] == 0
+    for k in ("K", "k", "x", "u"):
+        err = oracle.rel_err(out[k].double().cpu().numpy(), ref[k])
+        assert err < 1e-3, (k, err)
