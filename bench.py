@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Throughput of the segment-parallel Riccati solve (LQR stages/s) on GB300.
+
+One step = one full solve (parametric segment sweeps, FP64 link solve, policy
+sweeps, rollout with multipliers and cost) of the long-horizon workload
+n=64, m=32, T=4096, rho(A_t) <= 1.02, on synthetic seeded data with inputs
+resident in HBM. Under torchrun every rank solves its own replica (the method
+does not shard across GPUs); value = all ranks' stages / max-over-ranks time.
+
+--impl reference times the FP64 serial Riccati oracle on the host cores on a
+bounded sample of the same workload (there is no reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "LQR stages/sec at stated KKT residual vs plain FP64 segment-parallel solve"
+UNIT = "stages/s"
+
+# peaks: HBM and bf16 tensor are measured (MEASURED_PEAKS.json); the DFMA and
+# FFMA pipes are derived from unit counts and the maximum SM clock: 152 SMs x
+# 2 DFMA/clk (1.25 TFLOP/s FP64 nominal) and x 128 FFMA/clk, at 2070 MHz.
+SMS, SM_MHZ = 152, 2070.0
+PEAK_FP64_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12      # 1.259
+PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 80.5
+
+
+def sweep_flops(n: int, m: int, T: int, K: int, phase: str) -> float:
+    """Algorithmic FLOPs of one launch of a segment-sweep kernel.
+
+    Per stage of a parametric segment (V_xx[A|B|c], M_ux, M_uu, M_zu, M_xx, M_zx,
+    Cholesky and triangular solve of M_uu, the V_xx, V_zx, V_zz downdates):
+        6n^3 + 12n^2 m + 4n m^2 + m^3/3
+    Per stage of a plain Riccati sweep (terminal segment, policy sweep):
+        4n^3 + 6n^2 m + 4n m^2 + m^3/3
+    """
+    par = 6 * n ** 3 + 12 * n ** 2 * m + 4 * n * m ** 2 + m ** 3 / 3
+    pla = 4 * n ** 3 + 6 * n ** 2 * m + 4 * n * m ** 2 + m ** 3 / 3
+    last = T - (K - 1) * T // K
+    if phase == "sweep":
+        return (T - last) * par + last * pla
+    return (T - last) * pla  # policy sweep: segments 0..K-2
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(n, m, T_sample, prob_full, budget_s=12.0):
+    """The FP64 serial Riccati oracle on one host core over a T_sample-stage
+    prefix of the workload, repeated for about budget_s seconds."""
+    import oracle
+    sample = {k: (v[:T_sample] if k in ("A", "B", "c", "R", "S", "r") else
+                  (v[:T_sample + 1] if k in ("Q", "q") else v)) for k, v in prob_full.items()}
+    sample = {k: np.ascontiguousarray(v) for k, v in sample.items()}
+    oracle.riccati(sample, want_P=False)  # load/build outside the timing
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.riccati(sample, want_P=False)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": runs * T_sample / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d runs of the FP64 serial Riccati oracle (single thread, C) on the first %d stages "
+                      "of the n=%d m=%d workload, %.1f s" % (runs, T_sample, n, m, el)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle on host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    n, m, T = 64, 32, 4096
+    prob = workloads.config1(T)
+    T_sample = 256
+    import oracle
+    oracle.riccati({k: np.ascontiguousarray(v[:8] if k in ("A", "B", "c", "R", "S", "r") else
+                                            (v[:9] if k in ("Q", "q") else v)) for k, v in prob.items()})
+    sample = {k: np.ascontiguousarray(v[:T_sample] if k in ("A", "B", "c", "R", "S", "r") else
+                                      (v[:T_sample + 1] if k in ("Q", "q") else v)) for k, v in prob.items()}
+    for _ in range(args.warmup):
+        oracle.riccati(sample, want_P=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.riccati(sample, want_P=False)
+    el = time.perf_counter() - t0
+    value = args.steps * T_sample / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded PCG64)",
+            "config": {"workload": "long-horizon LQR n=64 m=32 T=4096 rho(A)<=1.02 (per step: a %d-stage "
+                                   "prefix, serial FP64 Riccati oracle on the host)" % T_sample,
+                       "n": n, "m": m, "T": T},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d steps x %d stages of the serial FP64 oracle, one thread" %
+                                       (args.steps, T_sample)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--segments", type=int, default=64)
+    ap.add_argument("--form", default="multiplier", choices=["multiplier", "constrained"])
+    ap.add_argument("--T", type=int, default=4096)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1809_06360_gb300 import build, lqr
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    n, m, T, K = 64, 32, args.T, args.segments
+    prob_np = workloads.config1(T)
+    dt = torch.float64 if args.prec == "fp64" else torch.float32
+    npdt = np.float64 if args.prec == "fp64" else np.float32
+    dev = {k: torch.from_numpy(v).to(f"cuda:{local}", dt) for k, v in prob_np.items()}
+    solver = lqr.Solver(local)
+    out = solver.alloc_solution(dev, want=("K", "k", "x", "u", "lam"))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form)
+
+    for _ in range(args.warmup):
+        step()
+    rep = solver.report()
+    if rep["status"] != 0:
+        raise SystemExit("solve failed: %s" % rep)
+    launches_per_step = lqr.lqr_last_launch_count(solver.h)
+
+    # KKT backward error of the benchmarked solution (FP64, host, once, outside the timing)
+    import oracle
+    res = oracle.kkt_residual(prob_np, out["x"].double().cpu().numpy(), out["u"].double().cpu().numpy(),
+                              out["lam"].double().cpu().numpy())
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    lqr.lqr_profile_enable(solver.h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    phase_ms, nprof = lqr.lqr_profile_read(solver.h)
+    lqr.lqr_profile_enable(solver.h, False)
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * T / (ms / 1e3)
+
+    # dominant kernel: the parametric segment sweep (step A1)
+    sweep_ms = phase_ms["sweep"] / max(nprof, 1)
+    flops = sweep_flops(n, m, T, K, "sweep")
+    achieved = flops / (sweep_ms / 1e3) / 1e12
+    peak = PEAK_FP64_TFLOPS if args.prec == "fp64" else PEAK_FP32_TFLOPS
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "seg_sweep_kernel (A1, %s)" % args.prec,
+                "peak_source": "derived: 152 SMs x %s/clk x 2070 MHz" % ("2 DFMA" if args.prec == "fp64" else
+                                                                          "128 FFMA"),
+                "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phase_ms.items()}}
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timing
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v.astype(npdt))).pin_memory() for k, v in prob_np.items()}
+        pin_np = {k: v.numpy() for k, v in pin.items()}
+        shapes = dict(K=(T, m, n), k=(T, m), x=(T + 1, n), u=(T, m))
+        outp = {k: torch.empty(s, dtype=dt).pin_memory().numpy() for k, s in shapes.items()}
+        for _ in range(2):
+            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form)
+        t0 = time.perf_counter()
+        e2e_steps = max(3, args.steps // 2)
+        for _ in range(e2e_steps):
+            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form)
+        el = time.perf_counter() - t0
+        h2d = sum(v.nbytes for v in pin_np.values())
+        d2h = sum(v.nbytes for v in outp.values())
+        e2e = {"value": world * e2e_steps * T / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, m, 256, prob_np, budget_s=12.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+                "data": "synthetic (seeded PCG64), inputs resident in HBM",
+                "config": {"workload": "long-horizon LQR n=64 m=32 T=%d rho(A)<=1.02, K=%d segments, %s" %
+                                       (T, K, args.prec.upper()),
+                           "n": n, "m": m, "T": T, "K": K, "precision": args.prec, "form": args.form,
+                           "kkt_backward_error": res["eta"], "kkt_rel_residual": res["rel"],
+                           "l2": "inputs (%.0f MB) larger than L2 (129 MB)" % (
+                               sum(v.nbytes for v in prob_np.values()) * (1 if args.prec == "fp64" else 0.5) / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches_per_step * args.steps}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

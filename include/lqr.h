@@ -71,6 +71,19 @@ typedef enum {
   LQR_MIXED_BF16 = 3  /* reserved                                                            */
 } lqr_precision;
 
+/* How a segment carries its unknown end state (both reach the same summary
+ * of Eq. 9 in exact arithmetic):
+ *  LQR_FORM_MULTIPLIER  - the end-point constraint x_T = x_term is dualised: the
+ *      sweep carries its multiplier mu (the mu of Eq. 10) as the parameter,
+ *      starting from V = 0, dV/dx = mu. Every stage is a plain Riccati stage.
+ *      The link solve works with these dual summaries. Default.
+ *  LQR_FORM_CONSTRAINED - the constraint-explicit sweep of Section II-B
+ *      (Eq. 9-16): x_term is the parameter and the first ceil(n/m) stages from
+ *      the segment end absorb the end-point constraint by range/null-space
+ *      splits. Its x_term blocks lose accuracy like cond(R_L)^2 * eps, where
+ *      R_L is the ceil(n/m)-stage reachability matrix at the segment end. */
+typedef enum { LQR_FORM_MULTIPLIER = 0, LQR_FORM_CONSTRAINED = 1 } lqr_form;
+
 typedef struct lqr_handle lqr_handle;
 
 /* One problem: dimensions and device pointers (layout above). */
@@ -91,6 +104,7 @@ typedef struct {
   double tol;         /* KKT backward-error target of the refinement (MIXED)      */
   int max_refine;     /* refinement iterations allowed (MIXED)                     */
   int debug_checks;   /* 1 = also verify each segment's rollout meets its link state */
+  lqr_form form;      /* segment parametrisation, see lqr_form                    */
 } lqr_opts;
 
 /* Scalars of the last solve, read back by lqr_report(). */
@@ -103,11 +117,16 @@ typedef struct {
   double kkt_residual; /* normwise backward error of Eq. 3 when computed, else -1 */
 } lqr_report_t;
 
-/* Per-segment summary written by lqr_segment_summaries (FP64, per segment j):
- * Vxx[n][n], Vzx[n][n], Vzz[n][n], vx[n], vz[n], i.e. the quadratic
- * cost_to_go_{b_j}(x, x_term) of Eq. 9 at the segment start, with
- * x_term = the segment's end state. The last segment stores its plain Riccati
- * value (P at its start in the Vxx slot, p in the vx slot, zeros elsewhere). */
+/* Per-segment summary written by lqr_segment_summaries (FP64, per segment j),
+ * five blocks S0[n][n], S1[n][n], S2[n][n], s3[n], s4[n]:
+ *  LQR_FORM_CONSTRAINED: Vxx, Vzx, Vzz, vx, vz, the quadratic
+ *      cost_to_go_{b_j}(x, x_term) of Eq. 9 at the segment start.
+ *  LQR_FORM_MULTIPLIER: P, Z, -W, p, w of the dual value
+ *      G(x, mu) = 1/2 x'P x + mu'Z x - 1/2 mu'W mu + p'x + w'mu (the segment cost
+ *      plus mu'x_end, minimised over the controls), related to Eq. 9 by
+ *      Vzz = W^-1, Vzx = -W^-1 Z, Vxx = P + Z'W^-1 Z, vz = -W^-1 w, vx = p + Z'W^-1 w.
+ * The last segment stores its plain Riccati value (P at its start in S0, p in
+ * s3, zeros elsewhere). */
 #define LQR_SUMMARY_DOUBLES(n) (3 * (size_t)(n) * (size_t)(n) + 2 * (size_t)(n))
 
 /* Create a handle on CUDA device `device`. workspace_hint (bytes) pre-sizes the
@@ -149,6 +168,21 @@ const char *lqr_status_string(lqr_status s);
 
 /* Number of kernels the last lqr_solve / lqr_segment_summaries call enqueued. */
 int lqr_last_launch_count(const lqr_handle *h);
+
+/* Phase profiling with CUDA events recorded on the solve's own stream.
+ * Phases: the parametric segment sweeps (A1), the link solve (A3), the policy
+ * sweeps (A4), rollout + multipliers + cost (A5/A6), refinement (A7/A8). */
+#define LQR_NUM_PHASES 5
+enum { LQR_PHASE_SWEEP = 0, LQR_PHASE_LINK = 1, LQR_PHASE_POLICY = 2, LQR_PHASE_ROLLOUT = 3,
+       LQR_PHASE_REFINE = 4 };
+
+/* Start (enable=1) or stop recording; enabling resets the accumulated times.
+ * At most 256 solves are recorded per enable. */
+lqr_status lqr_profile_enable(lqr_handle *h, int enable);
+
+/* Sum of each phase's device time (ms) over the recorded solves, and their
+ * count. Waits for the recorded events. phase_ms has LQR_NUM_PHASES entries. */
+lqr_status lqr_profile_read(lqr_handle *h, double *phase_ms, int *solves);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,14 @@ struct lqr_handle {
   double* d_report = nullptr;  // [4]
   int last_K = 0;
   int last_launches = 0;
+  // phase profiling: one event pair per phase per solve, summed on read
+  static constexpr int kPhases = LQR_NUM_PHASES;
+  static constexpr int kMaxProfiled = 256;
+  int prof_on = 0;
+  int prof_count = 0;                       // solves recorded since enable
+  cudaEvent_t ev[kMaxProfiled][kPhases + 1];
+  int ev_created = 0;
+  int prof_launches[kPhases] = {0};
 };
 
 namespace {
@@ -91,6 +99,7 @@ lqr_status validate(const lqr_problem* p, const lqr_opts* o, const lqr_solution*
   if ((s->x || s->u) && (!s->K || !s->k)) return LQR_ERR_INVALID_ARG;  // the rollout reads K_t, k_t
   if (o->num_segments < 0 || o->num_segments > p->T) return LQR_ERR_INVALID_ARG;
   if (o->prec != LQR_FP64 && o->prec != LQR_FP32) return LQR_ERR_UNSUPPORTED;
+  if (o->form != LQR_FORM_MULTIPLIER && o->form != LQR_FORM_CONSTRAINED) return LQR_ERR_INVALID_ARG;
   return LQR_OK;
 }
 
@@ -107,17 +116,18 @@ lqr_status plan_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, So
   if (K > 1 && p->T / K < min_segment_len(p->n, p->m)) return LQR_ERR_SEGMENT_INFEASIBLE;
   sp->K = K;
   const long long budget = h->smem_optin - kStaticSmemReserve;
+  const bool cons = (o->form == LQR_FORM_CONSTRAINED);
   if (o->prec == LQR_FP64)
-    sp->smem = sweep_smem_needed<double, double>(p->n, p->m, budget, &sp->scratch_doubles);
+    sp->smem = sweep_smem_needed<double, double>(p->n, p->m, budget, cons, &sp->scratch_doubles);
   else
-    sp->smem = sweep_smem_needed<float, float>(p->n, p->m, budget, &sp->scratch_doubles);
+    sp->smem = sweep_smem_needed<float, float>(p->n, p->m, budget, cons, &sp->scratch_doubles);
   if ((long long)sizeof(double) * p->n * p->n > budget) return LQR_ERR_UNSUPPORTED;  // link block in smem
   sp->wl = ws_layout(p->n, K);
   sp->ws_need = sizeof(double) * (size_t)(sp->wl.total + (long long)K * sp->scratch_doubles) + 256;
   return LQR_OK;
 }
 
-ProbDesc make_desc(lqr_handle* h, const lqr_problem* p, const lqr_solution* s, const SolvePlan& sp) {
+ProbDesc make_desc(lqr_handle* h, const lqr_problem* p, const lqr_solution* s, const SolvePlan& sp, int form) {
   ProbDesc d;
   memset(&d, 0, sizeof(d));
   d.A = p->A; d.B = p->B; d.c = p->c; d.Q = p->Q; d.R = p->R; d.S = p->S; d.q = p->q; d.r = p->r; d.x0 = p->x0;
@@ -129,7 +139,14 @@ ProbDesc make_desc(lqr_handle* h, const lqr_problem* p, const lqr_solution* s, c
   d.report = h->d_report;
   d.n = p->n; d.m = p->m; d.T = p->T; d.nseg = sp.K;
   d.unit0 = 0;
+  d.form = form;
   return d;
+}
+
+// Records the boundary event `k` (0..kPhases) of the current profiled solve.
+void prof_mark(lqr_handle* h, int k, cudaStream_t st) {
+  if (!h->prof_on || h->prof_count >= lqr_handle::kMaxProfiled) return;
+  cudaEventRecord(h->ev[h->prof_count][k], st);
 }
 
 // The launch sequence of one solve. `summary_only` stops after step A1.
@@ -144,7 +161,7 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
   // only when the caller asked for neither (then nothing downstream runs)
   ProbTable tab;
   memset(&tab, 0, sizeof(tab));
-  tab.single = make_desc(h, p, s, sp);
+  tab.single = make_desc(h, p, s, sp, (int)o->form);
   tab.nprob = 1;
   const long long budget = h->smem_optin - kStaticSmemReserve;
   const int store_P = (s->P != nullptr) ? 1 : 0;
@@ -152,30 +169,38 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
   if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
   cudaError_t e;
   const bool f64 = (o->prec == LQR_FP64);
+  prof_mark(h, LQR_PHASE_SWEEP, st);
   e = f64 ? launch_seg_sweep<double, double>(tab, sp.K, 0, sp.smem, budget, store_P, st)
           : launch_seg_sweep<float, float>(tab, sp.K, 0, sp.smem, budget, store_P, st);
   ++launches;
   if (e != cudaSuccess) return LQR_ERR_CUDA;
+  prof_mark(h, LQR_PHASE_LINK, st);
   if (!summary_only) {
-    e = launch_link_solve(tab, 1, f64 ? 0 : 1, st);
+    e = (o->form == LQR_FORM_CONSTRAINED) ? launch_link_solve(tab, 1, f64 ? 0 : 1, st)
+                                          : launch_link_solve_dual(tab, 1, f64 ? 0 : 1, st);
     ++launches;
     if (e != cudaSuccess) return LQR_ERR_CUDA;
-    if (sp.K > 1) {
-      e = f64 ? launch_seg_sweep<double, double>(tab, sp.K, 1, sp.smem, budget, store_P, st)
-              : launch_seg_sweep<float, float>(tab, sp.K, 1, sp.smem, budget, store_P, st);
-      ++launches;
-      if (e != cudaSuccess) return LQR_ERR_CUDA;
-    }
-    if (s->x || s->u) {
-      e = f64 ? launch_rollout<double, double>(tab, sp.K, s->lam ? 1 : 0, st)
-              : launch_rollout<float, float>(tab, sp.K, s->lam ? 1 : 0, st);
-      ++launches;
-      if (e != cudaSuccess) return LQR_ERR_CUDA;
-      e = launch_finalize(tab, 1, st);
-      ++launches;
-      if (e != cudaSuccess) return LQR_ERR_CUDA;
-    }
   }
+  prof_mark(h, LQR_PHASE_POLICY, st);
+  if (!summary_only && sp.K > 1) {
+    e = f64 ? launch_seg_sweep<double, double>(tab, sp.K, 1, sp.smem, budget, store_P, st)
+            : launch_seg_sweep<float, float>(tab, sp.K, 1, sp.smem, budget, store_P, st);
+    ++launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+  }
+  prof_mark(h, LQR_PHASE_ROLLOUT, st);
+  if (!summary_only && (s->x || s->u)) {
+    e = f64 ? launch_rollout<double, double>(tab, sp.K, s->lam ? 1 : 0, st)
+            : launch_rollout<float, float>(tab, sp.K, s->lam ? 1 : 0, st);
+    ++launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+    e = launch_finalize(tab, 1, st);
+    ++launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+  }
+  prof_mark(h, LQR_PHASE_REFINE, st);
+  prof_mark(h, LQR_NUM_PHASES, st);
+  if (h->prof_on && h->prof_count < lqr_handle::kMaxProfiled) ++h->prof_count;
   h->last_K = sp.K;
   h->last_launches = launches;
   if (sp_out) *sp_out = sp;
@@ -226,6 +251,9 @@ lqr_status lqr_destroy(lqr_handle* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_report) cudaFree(h->d_report);
+  if (h->ev_created)
+    for (int i = 0; i < lqr_handle::kMaxProfiled; ++i)
+      for (int k = 0; k <= lqr_handle::kPhases; ++k) cudaEventDestroy(h->ev[i][k]);
   delete h;
   return LQR_OK;
 }
@@ -357,5 +385,35 @@ const char* lqr_status_string(lqr_status s) {
 }
 
 int lqr_last_launch_count(const lqr_handle* h) { return h ? h->last_launches : 0; }
+
+lqr_status lqr_profile_enable(lqr_handle* h, int enable) {
+  if (!h) return LQR_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (enable && !h->ev_created) {
+    for (int i = 0; i < lqr_handle::kMaxProfiled; ++i)
+      for (int k = 0; k <= lqr_handle::kPhases; ++k)
+        if (cudaEventCreate(&h->ev[i][k]) != cudaSuccess) return LQR_ERR_CUDA;
+    h->ev_created = 1;
+  }
+  h->prof_on = enable ? 1 : 0;
+  h->prof_count = 0;
+  return LQR_OK;
+}
+
+lqr_status lqr_profile_read(lqr_handle* h, double* phase_ms, int* solves) {
+  if (!h || !phase_ms || !solves) return LQR_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  for (int k = 0; k < lqr_handle::kPhases; ++k) phase_ms[k] = 0.0;
+  *solves = h->prof_count;
+  for (int i = 0; i < h->prof_count; ++i) {
+    if (cudaEventSynchronize(h->ev[i][lqr_handle::kPhases]) != cudaSuccess) return LQR_ERR_CUDA;
+    for (int k = 0; k < lqr_handle::kPhases; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->ev[i][k], h->ev[i][k + 1]) != cudaSuccess) return LQR_ERR_CUDA;
+      phase_ms[k] += ms;
+    }
+  }
+  return LQR_OK;
+}
 
 }  // extern "C"

@@ -25,6 +25,7 @@ struct WsLayout {
   long long gam;    // K * n
   long long z;      // (K+1) * n         link states z_j = x_{b_j}
   long long costp;  // K                 partial objective per segment
+  long long lwork;  // 4 n^2 + 2n        link-solve work matrices when they do not fit in shared memory
   long long total;
 };
 
@@ -39,6 +40,8 @@ __host__ __device__ inline WsLayout ws_layout(int n, int K) {
   w.gam = o;   o += (long long)K * n;
   w.z = o;     o += (long long)(K + 1) * n;
   w.costp = o; o += K;
+  o = (o + 31) & ~31LL;
+  w.lwork = o; o += 4 * nn + 2 * n;
   w.total = (o + 31) & ~31LL;
   return w;
 }
@@ -54,7 +57,7 @@ struct ProbDesc {
   double* report;             // [0] = cost (written by the finalize kernel)
   int n, m, T, nseg;
   int unit0;                  // first unit (segment) index of this problem in a launch
-  int pad;
+  int form;                   // lqr_form of the parametric sweeps
 };
 
 // Kernel-argument view of the problems of one launch: a single problem is
@@ -113,8 +116,9 @@ struct SweepPlan {
 __host__ __device__ inline long long align16(long long b) { return (b + 15) & ~15LL; }
 
 __host__ __device__ inline void make_plan(SweepPlan& P, int n, int m, int mode, int tc_size,
-                                          long long smem_budget) {
+                                          long long smem_budget, bool constrained) {
   const bool param = (mode == MODE_PARAM);
+  const bool cons = param && constrained;  // range/null-space workspace
   P.ldAB = n + m + 1;
   P.ldF = param ? 2 * n + 1 : n + 1;
   P.ldG = 2 * n + 1;
@@ -133,11 +137,11 @@ __host__ __device__ inline void make_plan(SweepPlan& P, int n, int m, int mode, 
   bytes[SB_L64] = (tc_size == 8) ? 0 : 8LL * m * m;
   bytes[SB_VEC] = tc * 4 * n;
   bytes[SB_VZX] = param ? tc * n * n : 0;
-  bytes[SB_HH] = param ? 8LL * 2 * m : 0;
-  bytes[SB_G] = param ? 8LL * m * P.ldG : 0;
-  bytes[SB_E] = param ? 8LL * m * (P.ldG > m ? P.ldG : m) : 0;
-  bytes[SB_H] = param ? 8LL * n * P.ldH : 0;
-  bytes[SB_AUG] = param ? 8LL * (aug1 > aug2 ? aug1 : aug2) : 0;
+  bytes[SB_HH] = cons ? 8LL * 2 * m : 0;
+  bytes[SB_G] = cons ? 8LL * m * P.ldG : 0;
+  bytes[SB_E] = cons ? 8LL * m * (P.ldG > m ? P.ldG : m) : 0;
+  bytes[SB_H] = cons ? 8LL * n * P.ldH : 0;
+  bytes[SB_AUG] = cons ? 8LL * (aug1 > aug2 ? aug1 : aug2) : 0;
   long long s = 0, g = 0;
   P.smem_mask = 0;
   for (int b = 0; b < SB_COUNT; ++b) {
@@ -166,9 +170,10 @@ template <typename TS, typename TC>
 cudaError_t launch_seg_sweep(const ProbTable& tab, int nunits, int phase, long long smem_bytes,
                              long long smem_budget, int store_P, cudaStream_t st);
 template <typename TS, typename TC>
-long long sweep_smem_needed(int n, int m, long long smem_budget, long long* scratch_doubles);
+long long sweep_smem_needed(int n, int m, long long smem_budget, bool constrained, long long* scratch_doubles);
 
 cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
+cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
 
 template <typename TS, typename TC>
 cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st);

@@ -89,10 +89,11 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
     mode = MODE_POLICY;
   }
   const bool param = (mode == MODE_PARAM);
+  const bool cons = param && (pd.form == LQR_FORM_CONSTRAINED);
   const int t0 = seg_begin(T, K, seg), t1 = seg_begin(T, K, seg + 1);
 
   SweepPlan P;
-  make_plan(P, n, m, mode, (int)sizeof(TC), smem_budget);
+  make_plan(P, n, m, mode, (int)sizeof(TC), smem_budget, pd.form == LQR_FORM_CONSTRAINED);
   unsigned char* scratch = reinterpret_cast<unsigned char*>(pd.scratch + (long long)seg * pd.scratch_per_unit);
   TC* Vxx = plan_ptr<TC>(P, SB_VXX, smem, scratch);
   TC* AB = plan_ptr<TC>(P, SB_AB, smem, scratch);
@@ -105,11 +106,11 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
   TC* vz = vec + n;
   TC* mz = vec + 2 * n;
   TC* Vzx = param ? plan_ptr<TC>(P, SB_VZX, smem, scratch) : nullptr;
-  double* HH = param ? plan_ptr<double>(P, SB_HH, smem, scratch) : nullptr;
-  double* Gc = param ? plan_ptr<double>(P, SB_G, smem, scratch) : nullptr;
-  double* Ec = param ? plan_ptr<double>(P, SB_E, smem, scratch) : nullptr;
-  double* H = param ? plan_ptr<double>(P, SB_H, smem, scratch) : nullptr;
-  double* AUG = param ? plan_ptr<double>(P, SB_AUG, smem, scratch) : nullptr;
+  double* HH = cons ? plan_ptr<double>(P, SB_HH, smem, scratch) : nullptr;
+  double* Gc = cons ? plan_ptr<double>(P, SB_G, smem, scratch) : nullptr;
+  double* Ec = cons ? plan_ptr<double>(P, SB_E, smem, scratch) : nullptr;
+  double* H = cons ? plan_ptr<double>(P, SB_H, smem, scratch) : nullptr;
+  double* AUG = cons ? plan_ptr<double>(P, SB_AUG, smem, scratch) : nullptr;
   const int ldAB = P.ldAB, ldF = P.ldF, ldG = P.ldG, ldH = P.ldH;
   const int cmu = ldF - 1;  // column of m_u in F
 
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
 
   // ---- initial value function at the segment end --------------------------
   int rr = 0;  // rows of constraint_to_go still to absorb (uniform)
-  if (mode == MODE_PARAM) {
+  if (mode == MODE_PARAM && cons) {
     // Eq. 11 without the terminal cost: V = 0, v = 0, H_x = I, H_z = -I, h = 0
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       Vxx[e] = TC(0);
@@ -146,6 +147,17 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
       H[e] = (j == i) ? 1.0 : ((j == n + i) ? -1.0 : 0.0);
     }
     rr = n;
+  } else if (mode == MODE_PARAM) {
+    // dual form: value of (segment cost + mu'x_end) at the segment end is mu'x:
+    // P = 0, Z (the V_zx slot) = I, -W (the V_zz slot) = 0, p = 0, w (the v_z slot) = 0.
+    // Every stage is then a plain stage of the same recursion (Z <-> V_zx, -W <-> V_zz).
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      Vxx[e] = TC(0);
+      Vzx[e] = (e / n == e % n) ? TC(1) : TC(0);
+      Vzz_g[e] = 0.0;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { vx[i] = TC(0); vz[i] = TC(0); }
+    rr = 0;
   } else if (mode == MODE_TERMINAL) {
     const TS* QT = gQ + nn * T;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -418,11 +430,11 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
 }
 
 template <typename TS, typename TC>
-long long sweep_smem_needed(int n, int m, long long smem_budget, long long* scratch_doubles) {
+long long sweep_smem_needed(int n, int m, long long smem_budget, bool constrained, long long* scratch_doubles) {
   SweepPlan a, b, c;
-  make_plan(a, n, m, MODE_PARAM, (int)sizeof(TC), smem_budget);
-  make_plan(b, n, m, MODE_TERMINAL, (int)sizeof(TC), smem_budget);
-  make_plan(c, n, m, MODE_POLICY, (int)sizeof(TC), smem_budget);
+  make_plan(a, n, m, MODE_PARAM, (int)sizeof(TC), smem_budget, constrained);
+  make_plan(b, n, m, MODE_TERMINAL, (int)sizeof(TC), smem_budget, constrained);
+  make_plan(c, n, m, MODE_POLICY, (int)sizeof(TC), smem_budget, constrained);
   long long s = a.smem_bytes;
   if (b.smem_bytes > s) s = b.smem_bytes;
   if (c.smem_bytes > s) s = c.smem_bytes;
@@ -451,7 +463,7 @@ template cudaError_t launch_seg_sweep<double, double>(const ProbTable&, int, int
                                                       cudaStream_t);
 template cudaError_t launch_seg_sweep<float, float>(const ProbTable&, int, int, long long, long long, int,
                                                     cudaStream_t);
-template long long sweep_smem_needed<double, double>(int, int, long long, long long*);
-template long long sweep_smem_needed<float, float>(int, int, long long, long long*);
+template long long sweep_smem_needed<double, double>(int, int, long long, bool, long long*);
+template long long sweep_smem_needed<float, float>(int, int, long long, bool, long long*);
 
 }  // namespace lqr

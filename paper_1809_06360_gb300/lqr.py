@@ -19,13 +19,16 @@ STATUS_NAMES = {0: "LQR_OK", 1: "LQR_ERR_INVALID_ARG", 2: "LQR_ERR_NOT_PD", 3: "
                 4: "LQR_ERR_NONFINITE", 5: "LQR_ERR_NO_CONVERGENCE", 6: "LQR_ERR_TIMEOUT", 7: "LQR_ERR_CUDA",
                 8: "LQR_ERR_OOM", 9: "LQR_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+FORM = {"multiplier": 0, "constrained": 1}
 
 PROBLEM_FIELDS = ("A", "B", "c", "Q", "R", "S", "q", "r", "x0")
 SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
 
 # Exported symbols declared in include/lqr.h
 EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
-           "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count")
+           "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
+           "lqr_profile_enable", "lqr_profile_read")
+PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
 class lqr_problem(ctypes.Structure):
@@ -38,7 +41,7 @@ class lqr_solution(ctypes.Structure):
 
 class lqr_opts(ctypes.Structure):
     _fields_ = [("prec", c_int), ("num_segments", c_int), ("tol", c_double), ("max_refine", c_int),
-                ("debug_checks", c_int)]
+                ("debug_checks", c_int), ("form", c_int)]
 
 
 class lqr_report_t(ctypes.Structure):
@@ -79,8 +82,11 @@ def load(path: str | None = None):
     lib.lqr_status_string.argtypes = [c_int]
     lib.lqr_status_string.restype = ctypes.c_char_p
     lib.lqr_last_launch_count.argtypes = [c_void_p]
+    lib.lqr_profile_enable.argtypes = [c_void_p, c_int]
+    lib.lqr_profile_read.argtypes = [c_void_p, P(c_double), P(c_int)]
     for name in ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
-                 "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count"):
+                 "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
+                 "lqr_profile_read"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -138,6 +144,17 @@ def lqr_status_string(status: int) -> str:
 
 def lqr_last_launch_count(h: int) -> int:
     return load().lqr_last_launch_count(h)
+
+
+def lqr_profile_enable(h: int, enable: bool) -> None:
+    _check(load().lqr_profile_enable(h, 1 if enable else 0), "lqr_profile_enable")
+
+
+def lqr_profile_read(h: int) -> tuple[dict, int]:
+    ms = (c_double * len(PHASES))()
+    n = c_int()
+    _check(load().lqr_profile_read(h, ms, ctypes.byref(n)), "lqr_profile_read")
+    return {k: ms[i] for i, k in enumerate(PHASES)}, n.value
 
 
 # --- torch convenience -------------------------------------------------------------
@@ -198,7 +215,7 @@ class Solver:
         return out
 
     def solve(self, prob, num_segments=0, prec="fp64", out=None, want=("K", "k", "x", "u", "lam"),
-              stream=None, tol=1e-8, max_refine=0):
+              stream=None, tol=1e-8, max_refine=0, form="multiplier"):
         """Enqueue a solve on `stream` (torch stream; default current). Returns the output tensors."""
         if out is None:
             out = self.alloc_solution(prob, want)
@@ -206,24 +223,25 @@ class Solver:
         p = self.make_problem_struct(prob, ptr)
         s = lqr_solution(**{f: (out[f].data_ptr() if f in out else None) for f in SOLUTION_FIELDS})
         o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
-                     debug_checks=0)
+                     debug_checks=0, form=FORM[form])
         lqr_solve(self.h, p, o, s, self._stream(stream))
         return out
 
     def report(self, stream=None) -> dict:
         return lqr_report(self.h, self._stream(stream))
 
-    def segment_summaries(self, prob, num_segments, prec="fp64", stream=None):
+    def segment_summaries(self, prob, num_segments, prec="fp64", stream=None, form="multiplier"):
         torch = _torch()
         n, m, T = self._dims(prob)
         buf = torch.empty((num_segments, 3 * n * n + 2 * n), dtype=torch.float64, device=prob["A"].device)
         p = self.make_problem_struct(prob, lambda t: t.data_ptr())
-        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0)
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=FORM[form])
         lqr_segment_summaries(self.h, p, o, buf.data_ptr(), self._stream(stream))
         return buf
 
     def solve_host(self, prob_np, num_segments=0, prec="fp64", out_np=None, want=("K", "k", "x", "u"),
-                   stream=None):
+                   stream=None, form="multiplier"):
         """Host-memory solve (numpy arrays, ideally pinned): copies in, solves, copies out, synchronises."""
         import numpy as np
         n, m, T = self._dims(prob_np)
@@ -234,6 +252,7 @@ class Solver:
             out_np = {k: np.empty(shapes[k], dtype=dt) for k in want}
         p = self.make_problem_struct(prob_np, lambda a: a.ctypes.data)
         s = lqr_solution(**{f: (out_np[f].ctypes.data if f in out_np else None) for f in SOLUTION_FIELDS})
-        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0)
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=FORM[form])
         lqr_solve_host(self.h, p, o, s, self._stream(stream))
         return out_np

@@ -30,11 +30,14 @@ def to_dev(prob, dtype=torch.float64):
     return {k: torch.from_numpy(v).to("cuda:0", dtype) for k, v in prob.items()}
 
 
-def check_vs_oracle(solver, prob, K, tol=TOL64, prec="fp64", want_P=False):
+FORMS = ["multiplier", "constrained"]
+
+
+def check_vs_oracle(solver, prob, K, tol=TOL64, prec="fp64", want_P=False, form="multiplier"):
     ref = oracle.riccati(prob)
     dt = torch.float64 if prec == "fp64" else torch.float32
     want = ("K", "k", "x", "u", "lam") + (("P",) if want_P else ())
-    out = solver.solve(to_dev(prob, dt), num_segments=K, prec=prec, want=want)
+    out = solver.solve(to_dev(prob, dt), num_segments=K, prec=prec, want=want, form=form)
     rep = solver.report()
     assert rep["status"] == 0, rep
     errs = {k: oracle.rel_err(out[k].double().cpu().numpy(), ref[k]) for k in want}
@@ -46,10 +49,11 @@ def check_vs_oracle(solver, prob, K, tol=TOL64, prec="fp64", want_P=False):
     return out, rep, errs
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("K", [1, 2, 3, 8, 16, 42])
-def test_config0_fp64_all_K(solver, K):
+def test_config0_fp64_all_K(solver, K, form):
     """n=12, m=4, T=128: every K from 1 to T/ceil(n/m) (ragged segments for K=3, 42)."""
-    check_vs_oracle(solver, workloads.config0(), K)
+    check_vs_oracle(solver, workloads.config0(), K, form=form)
 
 
 @pytest.mark.parametrize("n,m,T,K,cross", [
@@ -62,29 +66,41 @@ def test_config0_fp64_all_K(solver, K):
     (16, 2, 200, 12, True),  # long constrained tails (8 stages)
     (33, 7, 150, 5, True),   # odd sizes, ragged register tiles
 ])
-def test_shapes_fp64(solver, n, m, T, K, cross):
+@pytest.mark.parametrize("form", FORMS)
+def test_shapes_fp64(solver, n, m, T, K, cross, form):
     prob = workloads.make_problem(n, m, T, seed=100 + n + m + T, cross=cross)
-    check_vs_oracle(solver, prob, K, want_P=True)
+    check_vs_oracle(solver, prob, K, want_P=True, form=form)
 
 
 def test_single_stage_problem(solver):
     check_vs_oracle(solver, workloads.make_problem(3, 2, 1, seed=9, cross=True), 1)
 
 
+def dual_of(ref):
+    """The dual summary (P, Z, -W, p, w) equivalent to the primal Eq. 9 summary:
+    W = Vzz^-1, Z = -W Vzx, P = Vxx - Vzx'W Vzx, w = -W vz, p = vx - Vzx'W vz."""
+    W = np.linalg.inv(ref["Vzz"])
+    return dict(Vxx=ref["Vxx"] - ref["Vzx"].T @ W @ ref["Vzx"], Vzx=-W @ ref["Vzx"], Vzz=-W,
+                vx=ref["vx"] - ref["Vzx"].T @ W @ ref["vz"], vz=-W @ ref["vz"])
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("n,m,T,K", [(5, 2, 30, 5), (6, 3, 24, 4), (7, 3, 27, 3), (4, 1, 20, 4)])
-def test_segment_summaries_vs_dense_kkt(solver, n, m, T, K):
+def test_segment_summaries_vs_dense_kkt(solver, n, m, T, K, form):
     prob = workloads.make_problem(n, m, T, seed=200 + n * m, cross=True)
-    summ = solver.segment_summaries(to_dev(prob), K).cpu().numpy()
+    summ = solver.segment_summaries(to_dev(prob), K, form=form).cpu().numpy()
     from paper_1809_06360_gb300 import lqr
     b = lqr.lqr_partition(n, m, T, K)
     nn = n * n
     for j in range(K - 1):
         ref = oracle.segment_summary(prob, b[j], b[j + 1])
+        if form == "multiplier":
+            ref = dual_of(ref)
         got = dict(Vxx=summ[j, :nn].reshape(n, n), Vzx=summ[j, nn:2 * nn].reshape(n, n),
                    Vzz=summ[j, 2 * nn:3 * nn].reshape(n, n), vx=summ[j, 3 * nn:3 * nn + n],
                    vz=summ[j, 3 * nn + n:])
         for k in ("Vxx", "Vzx", "Vzz", "vx", "vz"):
-            assert oracle.rel_err(got[k], ref[k]) < 1e-9, (j, k)
+            assert oracle.rel_err(got[k], ref[k]) < 1e-8, (j, k, oracle.rel_err(got[k], ref[k]))
     # the last segment carries the serial value function at its start
     ric = oracle.riccati(prob)
     assert oracle.rel_err(summ[K - 1, :nn].reshape(n, n), ric["P"][b[K - 1]]) < 1e-9
@@ -104,11 +120,30 @@ def test_K_invariance_bitwise_determinism(solver):
     assert np.array_equal(a, b)
 
 
-def test_config1_fp64_full_size(solver):
-    """The bench workload (n=64, m=32, T=4096, rho(A)<=1.02) at K=64 against the
-    full oracle (a few seconds of serial FP64 on the host)."""
+@pytest.fixture(scope="module")
+def config1():
     prob = workloads.config1()
-    check_vs_oracle(solver, prob, 64)
+    return prob, oracle.riccati(prob)
+
+
+@pytest.mark.parametrize("K", [16, 64, 256, 1024])
+def test_config1_fp64_full_size(solver, config1, K):
+    """The bench workload (n=64, m=32, T=4096, rho(A)<=1.02) for every K of the
+    sweep, against the full serial oracle, at 1e-9 (multiplier form)."""
+    prob, _ = config1
+    check_vs_oracle(solver, prob, K)
+
+
+def test_config1_constrained_form_accuracy(solver, config1):
+    """The constraint-explicit form of Section II-B on the same workload: the
+    policies stay exact but its x_term blocks carry cond(R_L)^2 * eps error
+    (R_L = the 2-stage reachability at a segment end, cond up to ~3e4 here), so
+    the trajectory error is ~1e-8: bounded by 1e-6 and reported, not 1e-9."""
+    prob, ref = config1
+    out = solver.solve(to_dev(prob), num_segments=64, form="constrained")
+    assert solver.report()["status"] == 0
+    assert oracle.rel_err(out["K"].cpu().numpy(), ref["K"]) < 1e-12
+    assert oracle.rel_err(out["x"].cpu().numpy(), ref["x"]) < 1e-6
 
 
 def test_host_entry_point_matches_device(solver):
@@ -140,6 +175,9 @@ def test_host_validation(solver):
     assert e.value.status == 1
 
 
+FP32_BOUND = {"K": 1e-4, "k": 1e-4, "x": 1e-4, "u": 1e-4}
+
+
 def test_fp32_path_error_is_bounded(solver):
     """FP32 data and arithmetic (FP64 Cholesky and link solve): the error
     against the FP64 oracle, per quantity, on the n=12 workload."""
@@ -149,4 +187,17 @@ def test_fp32_path_error_is_bounded(solver):
     assert solver.report()["status"] == 0
     for k in ("K", "k", "x", "u"):
         err = oracle.rel_err(out[k].double().cpu().numpy(), ref[k])
-        assert err < 1e-3, (k, err)
+        assert err < FP32_BOUND[k], (k, err)
+
+
+@pytest.mark.parametrize("K", [64, 256])
+def test_fp32_config1_full_size(solver, config1, K):
+    """FP32 sweeps with FP64 factor and link solve on the bench workload; the
+    per-quantity error against the FP64 oracle is bounded (and printed)."""
+    prob, ref = config1
+    out = solver.solve(to_dev(prob, torch.float32), num_segments=K, prec="fp32")
+    assert solver.report()["status"] == 0
+    errs = {k: oracle.rel_err(out[k].double().cpu().numpy(), ref[k]) for k in ("K", "k", "x", "u", "lam")}
+    print("fp32 config1 K=%d errors:" % K, errs)
+    for k in ("K", "k", "x", "u"):
+        assert errs[k] < 1e-3, errs
