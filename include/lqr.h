@@ -68,7 +68,7 @@ typedef enum {
   LQR_FP64 = 0,       /* all arithmetic in FP64 (the plain method)                          */
   LQR_FP32 = 1,       /* FP32 data and arithmetic; FP64 factor of R+B'PB and link solve     */
   LQR_MIXED_TF32 = 2, /* FP64 data; FP32 sweeps, FP64 factor/link solve, FP64 KKT refinement */
-  LQR_MIXED_BF16 = 3  /* reserved                                                            */
+  LQR_MIXED_BF16 = 3  /* reserved (LQR_ERR_UNSUPPORTED)                                      */
 } lqr_precision;
 
 /* How a segment carries its unknown end state (both reach the same summary
@@ -101,10 +101,13 @@ typedef struct {
 typedef struct {
   lqr_precision prec;
   int num_segments;   /* K >= 1; 0 = choose automatically                         */
-  double tol;         /* KKT backward-error target of the refinement (MIXED)      */
-  int max_refine;     /* refinement iterations allowed (MIXED)                     */
-  int debug_checks;   /* 1 = also verify each segment's rollout meets its link state */
+  double tol;         /* refinement target on |KKT w - b|_inf / |b|_inf            */
+  int max_refine;     /* iterative-refinement corrections allowed (double data only);
+                         needs K, k, x, u and lam in the solution                   */
+  int debug_checks;   /* reserved, 0                                              */
   lqr_form form;      /* segment parametrisation, see lqr_form                    */
+  int residual;       /* 1 = compute the FP64 KKT residual of the returned solution
+                         (needs x, u, lam); implied by max_refine > 0              */
 } lqr_opts;
 
 /* Scalars of the last solve, read back by lqr_report(). */
@@ -114,7 +117,9 @@ typedef struct {
   int refine_iters;    /* refinement iterations run                       */
   int bad_stage;       /* first stage index a device check flagged, or -1 */
   double cost;         /* optimal objective J* (Eq. 1) along x, u         */
-  double kkt_residual; /* normwise backward error of Eq. 3 when computed, else -1 */
+  double kkt_residual; /* normwise backward error of Eq. 3 when computed, else -1:
+                          |KKT w - b|_inf / (|KKT|_inf |w|_inf + |b|_inf)        */
+  double kkt_rel;      /* |KKT w - b|_inf / |b|_inf when computed, else -1 */
 } lqr_report_t;
 
 /* Per-segment summary written by lqr_segment_summaries (FP64, per segment j),

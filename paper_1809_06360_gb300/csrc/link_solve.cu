@@ -20,10 +20,7 @@ __global__ void __launch_bounds__(kBlock) link_solve_kernel(ProbTable tab, int x
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   const ProbDesc& pd = prob_at(tab, blockIdx.x);
-  if (threadIdx.x == 0) s_flag = *(volatile int*)pd.status;
-  __syncthreads();
-  if (s_flag != 0) return;
-  __syncthreads();
+  if (cta_should_exit(pd, &s_flag)) return;
   const int n = pd.n, K = pd.nseg;
   const long long nn = (long long)n * n;
   const WsLayout wl = ws_layout(n, K);
@@ -147,10 +144,7 @@ __global__ void __launch_bounds__(kBlock) link_solve_dual_kernel(ProbTable tab, 
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   const ProbDesc& pd = prob_at(tab, blockIdx.x);
-  if (threadIdx.x == 0) s_flag = *(volatile int*)pd.status;
-  __syncthreads();
-  if (s_flag != 0) return;
-  __syncthreads();
+  if (cta_should_exit(pd, &s_flag)) return;
   const int n = pd.n, K = pd.nseg;
   const long long nn = (long long)n * n;
   const WsLayout wl = ws_layout(n, K);

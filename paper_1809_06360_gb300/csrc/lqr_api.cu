@@ -22,6 +22,7 @@ struct lqr_handle {
   double* d_report = nullptr;  // [4]
   int last_K = 0;
   int last_launches = 0;
+  int last_resid = 0;
   // phase profiling: one event pair per phase per solve, summed on read
   static constexpr int kPhases = LQR_NUM_PHASES;
   static constexpr int kMaxProfiled = 256;
@@ -84,6 +85,7 @@ int auto_segments(const lqr_handle* h, int n, int m, int T) {
 bool elem_size(lqr_precision p, size_t* es) {
   switch (p) {
     case LQR_FP64: *es = 8; return true;
+    case LQR_MIXED_TF32: *es = 8; return true;
     case LQR_FP32: *es = 4; return true;
     default: return false;
   }
@@ -98,8 +100,12 @@ lqr_status validate(const lqr_problem* p, const lqr_opts* o, const lqr_solution*
   if (s->lam && (!s->x || !s->u)) return LQR_ERR_INVALID_ARG;
   if ((s->x || s->u) && (!s->K || !s->k)) return LQR_ERR_INVALID_ARG;  // the rollout reads K_t, k_t
   if (o->num_segments < 0 || o->num_segments > p->T) return LQR_ERR_INVALID_ARG;
-  if (o->prec != LQR_FP64 && o->prec != LQR_FP32) return LQR_ERR_UNSUPPORTED;
+  if (o->prec != LQR_FP64 && o->prec != LQR_FP32 && o->prec != LQR_MIXED_TF32) return LQR_ERR_UNSUPPORTED;
   if (o->form != LQR_FORM_MULTIPLIER && o->form != LQR_FORM_CONSTRAINED) return LQR_ERR_INVALID_ARG;
+  if (o->max_refine < 0 || o->max_refine > 64) return LQR_ERR_INVALID_ARG;
+  if ((o->max_refine > 0 || o->residual) && (!s->x || !s->u || !s->lam || !s->K || !s->k))
+    return LQR_ERR_INVALID_ARG;
+  if (o->max_refine > 0 && o->prec == LQR_FP32) return LQR_ERR_UNSUPPORTED;  // refinement needs FP64 data
   return LQR_OK;
 }
 
@@ -108,8 +114,33 @@ struct SolvePlan {
   long long smem;
   long long scratch_doubles;  // per unit
   WsLayout wl;
+  long long rbase;            // refinement buffers (doubles from the workspace base), or -1
   size_t ws_need;             // bytes
 };
+
+// Refinement buffers: correction data q~ r~ c~ x0~, corrections dk dx du dl dp,
+// residual accumulators, skip flag.
+struct RefineLayout {
+  long long cq, cr, cc, cx0, dk, dx, du, dl, dp, acc, skip, total;
+};
+RefineLayout refine_layout(long long base, int n, int m, int T) {
+  RefineLayout r;
+  long long o = base;
+  auto take = [&](long long cnt) { long long a = o; o += (cnt + 31) & ~31LL; return a; };
+  r.cq = take((long long)(T + 1) * n);
+  r.cr = take((long long)T * m);
+  r.cc = take((long long)T * n);
+  r.cx0 = take(n);
+  r.dk = take((long long)T * m);
+  r.dx = take((long long)(T + 1) * n);
+  r.du = take((long long)T * m);
+  r.dl = take((long long)(T + 1) * n);
+  r.dp = take((long long)(T + 1) * n);
+  r.acc = take(kResidAccDoubles);
+  r.skip = take(4);
+  r.total = o - base;
+  return r;
+}
 
 lqr_status plan_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, SolvePlan* sp) {
   int K = o->num_segments > 0 ? o->num_segments : auto_segments(h, p->n, p->m, p->T);
@@ -119,11 +150,18 @@ lqr_status plan_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, So
   const bool cons = (o->form == LQR_FORM_CONSTRAINED);
   if (o->prec == LQR_FP64)
     sp->smem = sweep_smem_needed<double, double>(p->n, p->m, budget, cons, &sp->scratch_doubles);
+  else if (o->prec == LQR_MIXED_TF32)
+    sp->smem = sweep_smem_needed<double, float>(p->n, p->m, budget, cons, &sp->scratch_doubles);
   else
     sp->smem = sweep_smem_needed<float, float>(p->n, p->m, budget, cons, &sp->scratch_doubles);
-  if ((long long)sizeof(double) * p->n * p->n > budget) return LQR_ERR_UNSUPPORTED;  // link block in smem
   sp->wl = ws_layout(p->n, K);
-  sp->ws_need = sizeof(double) * (size_t)(sp->wl.total + (long long)K * sp->scratch_doubles) + 256;
+  long long total = sp->wl.total + (long long)K * sp->scratch_doubles;
+  sp->rbase = -1;
+  if (o->max_refine > 0 || o->residual) {
+    sp->rbase = (total + 31) & ~31LL;
+    total = sp->rbase + refine_layout(0, p->n, p->m, p->T).total;
+  }
+  sp->ws_need = sizeof(double) * (size_t)total + 256;
   return LQR_OK;
 }
 
@@ -136,6 +174,7 @@ ProbDesc make_desc(lqr_handle* h, const lqr_problem* p, const lqr_solution* s, c
   d.scratch = d.ws + sp.wl.total;
   d.scratch_per_unit = sp.scratch_doubles;
   d.status = h->d_status;
+  d.skip = nullptr;
   d.report = h->d_report;
   d.n = p->n; d.m = p->m; d.T = p->T; d.nseg = sp.K;
   d.unit0 = 0;
@@ -149,6 +188,57 @@ void prof_mark(lqr_handle* h, int k, cudaStream_t st) {
   cudaEventRecord(h->ev[h->prof_count][k], st);
 }
 
+// Steps A1 (and, unless summary_only, A3, A4, A5/A6) for the problem in tab.
+// `profile` marks the phase boundaries of this pipeline.
+lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan& sp, const lqr_opts* o,
+                            bool want_traj, bool want_lam, int store_P, bool summary_only, bool profile,
+                            cudaStream_t st, int* launches) {
+  const long long budget = h->smem_optin - kStaticSmemReserve;
+  const int prec = o->prec;
+  const bool dual = (o->form != LQR_FORM_CONSTRAINED);
+  cudaError_t e;
+  auto sweep = [&](int phase) {
+    if (prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, sp.K, phase, sp.smem, budget, store_P, st);
+    if (prec == LQR_MIXED_TF32) return launch_seg_sweep<double, float>(tab, sp.K, phase, sp.smem, budget, store_P, st);
+    return launch_seg_sweep<float, float>(tab, sp.K, phase, sp.smem, budget, store_P, st);
+  };
+  if (profile) prof_mark(h, LQR_PHASE_SWEEP, st);
+  e = sweep(0);
+  ++*launches;
+  if (e != cudaSuccess) return LQR_ERR_CUDA;
+  if (profile) prof_mark(h, LQR_PHASE_LINK, st);
+  if (summary_only) {
+    if (profile) {
+      prof_mark(h, LQR_PHASE_POLICY, st);
+      prof_mark(h, LQR_PHASE_ROLLOUT, st);
+    }
+    return LQR_OK;
+  }
+  const int x0f = (prec == LQR_FP32) ? 1 : 0;
+  e = dual ? launch_link_solve_dual(tab, 1, x0f, st) : launch_link_solve(tab, 1, x0f, st);
+  ++*launches;
+  if (e != cudaSuccess) return LQR_ERR_CUDA;
+  if (profile) prof_mark(h, LQR_PHASE_POLICY, st);
+  if (sp.K > 1) {
+    e = sweep(1);
+    ++*launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+  }
+  if (profile) prof_mark(h, LQR_PHASE_ROLLOUT, st);
+  if (want_traj) {
+    if (prec == LQR_FP32)
+      e = launch_rollout<float, float>(tab, sp.K, want_lam ? 1 : 0, st);
+    else
+      e = launch_rollout<double, double>(tab, sp.K, want_lam ? 1 : 0, st);
+    ++*launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+    e = launch_finalize(tab, 1, st);
+    ++*launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+  }
+  return LQR_OK;
+}
+
 // The launch sequence of one solve. `summary_only` stops after step A1.
 lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const lqr_solution* s,
                      cudaStream_t st, bool summary_only, SolvePlan* sp_out) {
@@ -157,48 +247,62 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
   if (rs != LQR_OK) return rs;
   rs = grow(&h->ws, &h->ws_bytes, sp.ws_need);
   if (rs != LQR_OK) return rs;
-  // the policy and the trajectory need K and k; use workspace-free temporaries
-  // only when the caller asked for neither (then nothing downstream runs)
   ProbTable tab;
   memset(&tab, 0, sizeof(tab));
   tab.single = make_desc(h, p, s, sp, (int)o->form);
   tab.nprob = 1;
-  const long long budget = h->smem_optin - kStaticSmemReserve;
   const int store_P = (s->P != nullptr) ? 1 : 0;
   int launches = 0;
   if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
-  cudaError_t e;
-  const bool f64 = (o->prec == LQR_FP64);
-  prof_mark(h, LQR_PHASE_SWEEP, st);
-  e = f64 ? launch_seg_sweep<double, double>(tab, sp.K, 0, sp.smem, budget, store_P, st)
-          : launch_seg_sweep<float, float>(tab, sp.K, 0, sp.smem, budget, store_P, st);
-  ++launches;
-  if (e != cudaSuccess) return LQR_ERR_CUDA;
-  prof_mark(h, LQR_PHASE_LINK, st);
-  if (!summary_only) {
-    e = (o->form == LQR_FORM_CONSTRAINED) ? launch_link_solve(tab, 1, f64 ? 0 : 1, st)
-                                          : launch_link_solve_dual(tab, 1, f64 ? 0 : 1, st);
-    ++launches;
-    if (e != cudaSuccess) return LQR_ERR_CUDA;
-  }
-  prof_mark(h, LQR_PHASE_POLICY, st);
-  if (!summary_only && sp.K > 1) {
-    e = f64 ? launch_seg_sweep<double, double>(tab, sp.K, 1, sp.smem, budget, store_P, st)
-            : launch_seg_sweep<float, float>(tab, sp.K, 1, sp.smem, budget, store_P, st);
-    ++launches;
-    if (e != cudaSuccess) return LQR_ERR_CUDA;
-  }
-  prof_mark(h, LQR_PHASE_ROLLOUT, st);
-  if (!summary_only && (s->x || s->u)) {
-    e = f64 ? launch_rollout<double, double>(tab, sp.K, s->lam ? 1 : 0, st)
-            : launch_rollout<float, float>(tab, sp.K, s->lam ? 1 : 0, st);
-    ++launches;
-    if (e != cudaSuccess) return LQR_ERR_CUDA;
-    e = launch_finalize(tab, 1, st);
-    ++launches;
-    if (e != cudaSuccess) return LQR_ERR_CUDA;
-  }
+  if (cudaMemsetAsync(h->d_report, 0, 4 * sizeof(double), st) != cudaSuccess) return LQR_ERR_CUDA;
+  const bool want_traj = (s->x || s->u);
+  rs = enqueue_pipeline(h, tab, sp, o, want_traj, s->lam != nullptr, store_P, summary_only, true, st, &launches);
+  if (rs != LQR_OK) return rs;
   prof_mark(h, LQR_PHASE_REFINE, st);
+  if (!summary_only && sp.rbase >= 0) {
+    // ---- A7/A8: FP64 KKT residual and iterative refinement ---------------------
+    double* base = reinterpret_cast<double*>(h->ws);
+    const RefineLayout rl = refine_layout(sp.rbase, p->n, p->m, p->T);
+    double* acc = base + rl.acc;
+    int* skip = reinterpret_cast<int*>(base + rl.skip);
+    if (cudaMemsetAsync(acc, 0, sizeof(double) * kResidAccDoubles, st) != cudaSuccess) return LQR_ERR_CUDA;
+    if (cudaMemsetAsync(skip, 0, 4 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
+    const ProbDesc& main = tab.single;
+    // the correction problem: same matrices, residual vectors, corrections into the workspace
+    lqr_problem cp = *p;
+    cp.c = base + rl.cc; cp.q = base + rl.cq; cp.r = base + rl.cr; cp.x0 = base + rl.cx0;
+    lqr_solution cs;
+    cs.K = s->K; cs.k = base + rl.dk; cs.x = base + rl.dx; cs.u = base + rl.du; cs.lam = base + rl.dl;
+    cs.P = s->P; cs.p = s->P ? (void*)(base + rl.dp) : nullptr;
+    ProbTable ctab;
+    memset(&ctab, 0, sizeof(ctab));
+    ctab.single = make_desc(h, &cp, &cs, sp, (int)o->form);
+    ctab.single.skip = skip;
+    ctab.nprob = 1;
+    for (int it = 0; it < o->max_refine; ++it) {
+      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st) !=
+          cudaSuccess)
+        return LQR_ERR_CUDA;
+      if (launch_residual_finalize(main, acc, o->tol, skip, 0, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
+      launches += 2;
+      rs = enqueue_pipeline(h, ctab, sp, o, true, true, store_P, false, false, st, &launches);
+      if (rs != LQR_OK) return rs;
+      if (launch_refine_update<double>(main, base + rl.dk, base + rl.dx, base + rl.du, base + rl.dl,
+                                       s->p ? base + rl.dp : nullptr, skip, st) != cudaSuccess)
+        return LQR_ERR_CUDA;
+      ++launches;
+    }
+    // final residual and objective of the returned solution
+    if (launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    if (launch_residual_finalize(main, acc, o->tol, nullptr, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
+        cudaSuccess)
+      return LQR_ERR_CUDA;
+    launches += 2;
+    h->last_resid = 1;
+  } else {
+    h->last_resid = 0;
+  }
   prof_mark(h, LQR_NUM_PHASES, st);
   if (h->prof_on && h->prof_count < lqr_handle::kMaxProfiled) ++h->prof_count;
   h->last_K = sp.K;
@@ -362,9 +466,10 @@ lqr_status lqr_report(lqr_handle* h, void* stream, lqr_report_t* out) {
   out->status = stt[0];
   out->bad_stage = stt[0] ? stt[1] : -1;
   out->num_segments = h->last_K;
-  out->refine_iters = 0;
+  out->refine_iters = (int)rep[3];
   out->cost = rep[0];
-  out->kkt_residual = -1.0;
+  out->kkt_residual = h->last_resid ? rep[1] : -1.0;
+  out->kkt_rel = h->last_resid ? rep[2] : -1.0;
   return LQR_OK;
 }
 

@@ -54,7 +54,8 @@ struct ProbDesc {
   double* scratch;            // nseg * scratch_per_unit doubles (spilled sweep buffers)
   long long scratch_per_unit; // doubles
   int* status;                // [0] = lqr_status, [1] = first flagged stage
-  double* report;             // [0] = cost (written by the finalize kernel)
+  const int* skip;            // when non-null and set, every kernel of this solve returns at once
+  double* report;             // [0] cost, [1] eta, [2] rel, [3] refinement corrections applied
   int n, m, T, nseg;
   int unit0;                  // first unit (segment) index of this problem in a launch
   int form;                   // lqr_form of the parametric sweeps
@@ -74,6 +75,16 @@ __device__ __forceinline__ const ProbDesc& prob_of_unit(const ProbTable& tab, in
 }
 __device__ __forceinline__ const ProbDesc& prob_at(const ProbTable& tab, int i) {
   return tab.probs ? tab.probs[i] : tab.single;
+}
+
+// Uniform early exit of a CTA: an earlier step failed, or this is a
+// refinement correction that is no longer needed. Ends with a barrier.
+__device__ __forceinline__ bool cta_should_exit(const ProbDesc& pd, int* s_flag) {
+  if (threadIdx.x == 0) *s_flag = (*(volatile int*)pd.status != 0) || (pd.skip && *(volatile const int*)pd.skip);
+  __syncthreads();
+  const bool ex = *s_flag != 0;
+  __syncthreads();
+  return ex;
 }
 
 // First error wins; records the stage that raised it.
@@ -179,5 +190,16 @@ template <typename TS, typename TC>
 cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st);
 
 cudaError_t launch_finalize(const ProbTable& tab, int nprob, cudaStream_t st);
+
+// refinement (refine.cu)
+constexpr int kResidAccDoubles = 8 + 4 * 152;
+template <typename TS>
+cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
+                                const int* skip, cudaStream_t st);
+cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol, int* skip, int is_final,
+                                     int check, cudaStream_t st);
+template <typename TS>
+cudaError_t launch_refine_update(const ProbDesc& pd, const double* dk, const double* dx, const double* du,
+                                 const double* dl, const double* dp, const int* skip, cudaStream_t st);
 
 }  // namespace lqr

@@ -1,0 +1,322 @@
+// Steps A7/A8: the FP64 residual of the global KKT system of Eq. 3 at a
+// computed (x, u, lambda), its normwise backward error, the objective of
+// Eq. 1 along (x, u), and the update of iterative refinement.
+//
+// With r = KKT w - b (blocks, Q and R read symmetrised):
+//   rx_t = Q x_t + S'u_t + q_t + lambda_t - A_t'lambda_{t+1}     (t < T)
+//   ru_t = S x_t + R u_t + r_t - B_t'lambda_{t+1}
+//   rxT  = Q_T x_T + q_T + lambda_T
+//   r0   = x_0 - x0
+//   rd_t = x_{t+1} - A_t x_t - B_t u_t - c_t
+// the correction delta solves KKT delta = r, which is the LQR problem with the
+// same matrices and the vector data q~ = -rx (q~_T = -rxT), r~ = -ru,
+// c~ = rd, x0~ = r0; then w <- w - delta. The backward error is
+//   eta = |r|_inf / (|KKT|_inf |w|_inf + |b|_inf),  rel = |r|_inf / |b|_inf,
+// with |KKT|_inf the largest absolute row sum.
+#include <cuda_runtime.h>
+
+#include "lqr_internal.cuh"
+
+namespace lqr {
+
+namespace {
+
+// max of non-negative doubles through their bit patterns (monotone for x >= 0)
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000LL);  // NaN -> +inf
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace
+
+// Residual-pass accumulators (FP64, in the refinement workspace).
+enum ResidSlot { RS_RNORM = 0, RS_KNORM, RS_WNORM, RS_BNORM, RS_COST, RS_COUNT };
+
+// One CTA per stage (grid-stride). Stage t < T, plus the terminal / initial
+// rows handled by the CTA that owns t = T-1 / t = 0.
+template <typename TS>
+__global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, double* acc, double* cq, double* cr,
+                                                              double* cc, double* cx0, const int* skip) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (skip && *(volatile const int*)skip) return;
+  if (*(volatile int*)pd.status != 0) return;
+  const int n = pd.n, m = pd.m, T = pd.T;
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  double* xt = reinterpret_cast<double*>(smem);
+  double* xn = xt + n;
+  double* lt = xn + n;
+  double* ln = lt + n;
+  double* ut = ln + n;
+  double* rxv = ut + m;   // n: accumulates rx_t
+  double* ruv = rxv + n;  // m: accumulates ru_t
+  double* rdv = ruv + m;  // n: accumulates rd_t
+  const TS* gx = static_cast<const TS*>(pd.x);
+  const TS* gu = static_cast<const TS*>(pd.u);
+  const TS* gl = static_cast<const TS*>(pd.lam);
+  const TS* gA = static_cast<const TS*>(pd.A);
+  const TS* gB = static_cast<const TS*>(pd.B);
+  const TS* gc = static_cast<const TS*>(pd.c);
+  const TS* gQ = static_cast<const TS*>(pd.Q);
+  const TS* gR = static_cast<const TS*>(pd.R);
+  const TS* gS = static_cast<const TS*>(pd.S);
+  const TS* gq = static_cast<const TS*>(pd.q);
+  const TS* gr = static_cast<const TS*>(pd.r);
+  const TS* gx0 = static_cast<const TS*>(pd.x0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double rmax = 0.0, kmax = 0.0, wmax = 0.0, bmax = 0.0, cost = 0.0;  // per-thread partials
+
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+    const TS* At = gA + nn * t;
+    const TS* Bt = gB + nm * t;
+    const TS* Qt = gQ + nn * t;
+    const TS* Rt = gR + mm * t;
+    const TS* St = gS ? gS + nm * t : nullptr;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      xt[i] = (double)gx[(size_t)n * t + i];
+      xn[i] = (double)gx[(size_t)n * (t + 1) + i];
+      lt[i] = (double)gl[(size_t)n * t + i];
+      ln[i] = (double)gl[(size_t)n * (t + 1) + i];
+      rxv[i] = (double)gq[(size_t)n * t + i] + lt[i];
+      rdv[i] = xn[i] - (double)gc[(size_t)n * t + i];
+    }
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+      ut[a] = (double)gu[(size_t)m * t + a];
+      ruv[a] = (double)gr[(size_t)m * t + a];
+    }
+    __syncthreads();
+    // columns j < n: -A'lambda_{t+1}, Q'x/2 (half of the symmetrised product), S'u; row-sum pieces
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double s = 0.0, absA = 0.0, absS = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double a = (double)At[(size_t)i * n + j];
+        s = fma(-a, ln[i], s);
+        s = fma(0.5 * (double)Qt[(size_t)i * n + j], xt[i], s);
+        absA += fabs(a);
+      }
+      if (St)
+        for (int a = 0; a < m; ++a) {
+          const double v = (double)St[(size_t)a * n + j];
+          s = fma(v, ut[a], s);
+          absS += fabs(v);
+        }
+      rxv[j] += s;
+      // |Q_sym| row sum of row j
+      double absQ = 0.0;
+      for (int k = 0; k < n; ++k)
+        absQ += fabs(0.5 * ((double)Qt[(size_t)j * n + k] + (double)Qt[(size_t)k * n + j]));
+      kmax = fmax(kmax, absQ + absS + 1.0 + absA);
+    }
+    // columns a < m: -B'lambda_{t+1}, R'u/2
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+      double s = 0.0, absB = 0.0, absR = 0.0, absSr = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double b = (double)Bt[(size_t)i * m + a];
+        s = fma(-b, ln[i], s);
+        absB += fabs(b);
+      }
+      for (int b = 0; b < m; ++b) {
+        s = fma(0.5 * (double)Rt[(size_t)b * m + a], ut[b], s);
+        absR += fabs(0.5 * ((double)Rt[(size_t)a * m + b] + (double)Rt[(size_t)b * m + a]));
+      }
+      if (St)
+        for (int k = 0; k < n; ++k) absSr += fabs((double)St[(size_t)a * n + k]);
+      ruv[a] += s;
+      kmax = fmax(kmax, absSr + absR + absB);
+    }
+    __syncthreads();
+    // rows i < n (warp per row): Q x/2, -A x - B u ; dynamics-row sums ; stage cost 1/2 x'Qx + q'x
+    for (int i = warp; i < n; i += nw) {
+      double qx = 0.0, ax = 0.0, absr = 0.0;
+      for (int k = lane; k < n; k += 32) {
+        const double a = (double)At[(size_t)i * n + k];
+        ax = fma(a, xt[k], ax);
+        qx = fma((double)Qt[(size_t)i * n + k], xt[k], qx);
+        absr += fabs(a);
+      }
+      for (int b = lane; b < m; b += 32) {
+        const double v = (double)Bt[(size_t)i * m + b];
+        ax = fma(v, ut[b], ax);
+        absr += fabs(v);
+      }
+      qx = warp_sum(qx);
+      ax = warp_sum(ax);
+      absr = warp_sum(absr);
+      if (lane == 0) {
+        rxv[i] += 0.5 * qx;
+        rdv[i] -= ax;
+        kmax = fmax(kmax, 1.0 + absr);
+        cost += xt[i] * (0.5 * qx + (double)gq[(size_t)n * t + i]);
+      }
+    }
+    // rows a < m: S x, R u/2 ; stage cost u'S x + 1/2 u'R u + r'u
+    for (int a = warp; a < m; a += nw) {
+      double sx = 0.0, ru = 0.0;
+      if (St)
+        for (int k = lane; k < n; k += 32) sx = fma((double)St[(size_t)a * n + k], xt[k], sx);
+      for (int b = lane; b < m; b += 32) ru = fma((double)Rt[(size_t)a * m + b], ut[b], ru);
+      sx = warp_sum(sx);
+      ru = warp_sum(ru);
+      if (lane == 0) {
+        ruv[a] += sx + 0.5 * ru;
+        cost += ut[a] * (sx + 0.5 * ru + (double)gr[(size_t)m * t + a]);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      rmax = fmax(rmax, fmax(fabs(rxv[i]), fabs(rdv[i])));
+      wmax = fmax(wmax, fmax(fabs(xt[i]), fabs(lt[i])));
+      bmax = fmax(bmax, fmax(fabs((double)gq[(size_t)n * t + i]), fabs((double)gc[(size_t)n * t + i])));
+      if (cq) {
+        cq[(size_t)n * t + i] = -rxv[i];
+        cc[(size_t)n * t + i] = rdv[i];
+      }
+    }
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+      rmax = fmax(rmax, fabs(ruv[a]));
+      wmax = fmax(wmax, fabs(ut[a]));
+      bmax = fmax(bmax, fabs((double)gr[(size_t)m * t + a]));
+      if (cr) cr[(size_t)m * t + a] = -ruv[a];
+    }
+    __syncthreads();
+  }
+  // terminal row (Q_T x_T + q_T + lambda_T) and the initial row (x_0 - x0)
+  if (blockIdx.x == 0) {
+    const TS* QT = gQ + nn * T;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double s = (double)gq[(size_t)n * T + i] + (double)gl[(size_t)n * T + i];
+      double absQ = 0.0, qx = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double qs = 0.5 * ((double)QT[(size_t)i * n + k] + (double)QT[(size_t)k * n + i]);
+        s = fma(qs, (double)gx[(size_t)n * T + k], s);
+        qx = fma((double)QT[(size_t)i * n + k], (double)gx[(size_t)n * T + k], qx);
+        absQ += fabs(qs);
+      }
+      const double xT = (double)gx[(size_t)n * T + i];
+      cost += xT * (0.5 * qx + (double)gq[(size_t)n * T + i]);
+      const double r0 = (double)gx[i] - (double)gx0[i];
+      rmax = fmax(rmax, fmax(fabs(s), fabs(r0)));
+      kmax = fmax(kmax, absQ + 1.0);
+      wmax = fmax(wmax, fmax(fabs(xT), fabs((double)gl[(size_t)n * T + i])));
+      bmax = fmax(bmax, fmax(fabs((double)gq[(size_t)n * T + i]), fabs((double)gx0[i])));
+      if (cq) {
+        cq[(size_t)n * T + i] = -s;
+        cx0[i] = r0;
+      }
+    }
+  }
+  // block reduction then one atomic per block
+  __shared__ double red[5][kBlock / 32];
+  rmax = warp_max(rmax);
+  kmax = warp_max(kmax);
+  wmax = warp_max(wmax);
+  bmax = warp_max(bmax);
+  cost = warp_sum(cost);
+  if (lane == 0) {
+    red[0][warp] = rmax; red[1][warp] = kmax; red[2][warp] = wmax; red[3][warp] = bmax; red[4][warp] = cost;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < nw; ++w) {
+      for (int k = 0; k < 4; ++k) a[k] = fmax(a[k], red[k][w]);
+      a[4] += red[4][w];
+    }
+    atomic_max_nonneg(acc + RS_RNORM, a[0]);
+    atomic_max_nonneg(acc + RS_KNORM, a[1]);
+    atomic_max_nonneg(acc + RS_WNORM, a[2]);
+    atomic_max_nonneg(acc + RS_BNORM, a[3]);
+    // per-block cost partials, summed in a fixed order by the finalize kernel
+    acc[RS_COUNT + blockIdx.x] = a[4];
+  }
+}
+
+// Turns the accumulators into eta, rel and the cost; decides convergence.
+// report: [0] cost, [1] eta, [2] rel, [3] refinement iterations applied.
+__global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, double tol, int* skip,
+                                         int is_final, int check_convergence) {
+  if (threadIdx.x != 0) return;
+  if (*(volatile int*)pd.status != 0) return;
+  if (!is_final && skip && *skip) return;  // already converged: keep the earlier numbers
+  double cost = 0.0;
+  for (int b = 0; b < nblocks; ++b) cost += acc[RS_COUNT + b];
+  const double r = acc[RS_RNORM], k = acc[RS_KNORM], w = acc[RS_WNORM], bn = acc[RS_BNORM];
+  const double eta = r / (k * w + bn);
+  const double rel = bn > 0.0 ? r / bn : r;
+  pd.report[0] = cost;
+  pd.report[1] = eta;
+  pd.report[2] = rel;
+  if (!isfinite(eta) || !isfinite(cost)) raise_status(pd.status, LQR_ERR_NONFINITE, -1);
+  if (skip && !is_final && rel <= tol) *skip = 1;
+  if (is_final && check_convergence && !(rel <= tol)) raise_status(pd.status, LQR_ERR_NO_CONVERGENCE, -1);
+  for (int i = 0; i < RS_COUNT; ++i) acc[i] = 0.0;  // ready for the next pass
+}
+
+// w <- w - delta for the outputs the correction solve refreshed.
+template <typename TS>
+__global__ void refine_update_kernel(ProbDesc pd, const double* dk, const double* dx, const double* du,
+                                     const double* dl, const double* dp, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  if (*(volatile int*)pd.status != 0) return;
+  const int n = pd.n, m = pd.m, T = pd.T;
+  const size_t nx = (size_t)(T + 1) * n, nu = (size_t)T * m;
+  TS* k = static_cast<TS*>(pd.k);
+  TS* x = static_cast<TS*>(pd.x);
+  TS* u = static_cast<TS*>(pd.u);
+  TS* l = static_cast<TS*>(pd.lam);
+  TS* p = static_cast<TS*>(pd.p);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nx; e += (size_t)gridDim.x * blockDim.x) {
+    if (x) x[e] = static_cast<TS>((double)x[e] - dx[e]);
+    if (l) l[e] = static_cast<TS>((double)l[e] - dl[e]);
+    if (p) p[e] = static_cast<TS>((double)p[e] - dp[e]);
+    if (e < nu) {
+      if (u) u[e] = static_cast<TS>((double)u[e] - du[e]);
+      if (k) k[e] = static_cast<TS>((double)k[e] - dk[e]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) pd.report[3] += 1.0;
+}
+
+int residual_grid(int T) { return T < 4 * 152 ? T : 4 * 152; }
+
+template <typename TS>
+cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
+                                const int* skip, cudaStream_t st) {
+  const size_t bytes = sizeof(double) * (6 * (size_t)pd.n + 3 * (size_t)pd.m);
+  kkt_residual_kernel<TS><<<residual_grid(pd.T), kBlock, bytes, st>>>(pd, acc, cq, cr, cc, cx0, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol, int* skip, int is_final,
+                                     int check, cudaStream_t st) {
+  residual_finalize_kernel<<<1, 32, 0, st>>>(pd, acc, residual_grid(pd.T), tol, skip, is_final, check);
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t launch_refine_update(const ProbDesc& pd, const double* dk, const double* dx, const double* du,
+                                 const double* dl, const double* dp, const int* skip, cudaStream_t st) {
+  refine_update_kernel<TS><<<2 * 152, 256, 0, st>>>(pd, dk, dx, du, dl, dp, skip);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_kkt_residual<double>(const ProbDesc&, double*, double*, double*, double*, double*,
+                                                 const int*, cudaStream_t);
+template cudaError_t launch_kkt_residual<float>(const ProbDesc&, double*, double*, double*, double*, double*,
+                                                const int*, cudaStream_t);
+template cudaError_t launch_refine_update<double>(const ProbDesc&, const double*, const double*, const double*,
+                                                  const double*, const double*, const int*, cudaStream_t);
+template cudaError_t launch_refine_update<float>(const ProbDesc&, const double*, const double*, const double*,
+                                                 const double*, const double*, const int*, cudaStream_t);
+
+}  // namespace lqr

@@ -52,10 +52,7 @@ __global__ void __launch_bounds__(kBlock) rollout_kernel(ProbTable tab, int want
   __shared__ double s_red[kBlock / 32];
   const int unit = blockIdx.x;
   const ProbDesc& pd = prob_of_unit(tab, unit);
-  if (threadIdx.x == 0) s_flag = *(volatile int*)pd.status;
-  __syncthreads();
-  if (s_flag != 0) return;
-  __syncthreads();
+  if (cta_should_exit(pd, &s_flag)) return;
   const int seg = unit - pd.unit0;
   const int n = pd.n, m = pd.m, T = pd.T, K = pd.nseg;
   const bool last = (seg == K - 1);
@@ -193,6 +190,7 @@ __global__ void __launch_bounds__(kBlock) rollout_kernel(ProbTable tab, int want
 __global__ void finalize_kernel(ProbTable tab) {
   const ProbDesc& pd = prob_at(tab, blockIdx.x);
   if (threadIdx.x != 0) return;
+  if (pd.skip && *(volatile const int*)pd.skip) return;
   if (*(volatile int*)pd.status != 0) {
     pd.report[0] = 0.0;
     return;
@@ -219,5 +217,6 @@ cudaError_t launch_finalize(const ProbTable& tab, int nprob, cudaStream_t st) {
 
 template cudaError_t launch_rollout<double, double>(const ProbTable&, int, int, cudaStream_t);
 template cudaError_t launch_rollout<float, float>(const ProbTable&, int, int, cudaStream_t);
+template cudaError_t launch_rollout<double, float>(const ProbTable&, int, int, cudaStream_t);
 
 }  // namespace lqr

@@ -76,10 +76,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
   const ProbDesc& pd = prob_of_unit(tab, unit);
   const int seg = unit - pd.unit0;
   const int n = pd.n, m = pd.m, T = pd.T, K = pd.nseg;
-  if (threadIdx.x == 0) s_flag = *(volatile int*)pd.status;
-  __syncthreads();
-  if (s_flag != 0) return;  // an earlier step failed: nothing to do (uniform)
-  __syncthreads();
+  if (cta_should_exit(pd, &s_flag)) return;  // an earlier step failed or the correction is not needed
   const bool last = (seg == K - 1);
   int mode;
   if (phase == 0) {
@@ -463,7 +460,10 @@ template cudaError_t launch_seg_sweep<double, double>(const ProbTable&, int, int
                                                       cudaStream_t);
 template cudaError_t launch_seg_sweep<float, float>(const ProbTable&, int, int, long long, long long, int,
                                                     cudaStream_t);
+template cudaError_t launch_seg_sweep<double, float>(const ProbTable&, int, int, long long, long long, int,
+                                                     cudaStream_t);
 template long long sweep_smem_needed<double, double>(int, int, long long, bool, long long*);
+template long long sweep_smem_needed<double, float>(int, int, long long, bool, long long*);
 template long long sweep_smem_needed<float, float>(int, int, long long, bool, long long*);
 
 }  // namespace lqr

@@ -18,7 +18,7 @@ LQR_OK = 0
 STATUS_NAMES = {0: "LQR_OK", 1: "LQR_ERR_INVALID_ARG", 2: "LQR_ERR_NOT_PD", 3: "LQR_ERR_SEGMENT_INFEASIBLE",
                 4: "LQR_ERR_NONFINITE", 5: "LQR_ERR_NO_CONVERGENCE", 6: "LQR_ERR_TIMEOUT", 7: "LQR_ERR_CUDA",
                 8: "LQR_ERR_OOM", 9: "LQR_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tf32": 2, "mixed_bf16": 3}
 FORM = {"multiplier": 0, "constrained": 1}
 
 PROBLEM_FIELDS = ("A", "B", "c", "Q", "R", "S", "q", "r", "x0")
@@ -41,12 +41,12 @@ class lqr_solution(ctypes.Structure):
 
 class lqr_opts(ctypes.Structure):
     _fields_ = [("prec", c_int), ("num_segments", c_int), ("tol", c_double), ("max_refine", c_int),
-                ("debug_checks", c_int), ("form", c_int)]
+                ("debug_checks", c_int), ("form", c_int), ("residual", c_int)]
 
 
 class lqr_report_t(ctypes.Structure):
     _fields_ = [("status", c_int), ("num_segments", c_int), ("refine_iters", c_int), ("bad_stage", c_int),
-                ("cost", c_double), ("kkt_residual", c_double)]
+                ("cost", c_double), ("kkt_residual", c_double), ("kkt_rel", c_double)]
 
 
 class LqrError(RuntimeError):
@@ -135,7 +135,7 @@ def lqr_report(h: int, stream: int | None) -> dict:
     _check(load().lqr_report(h, stream or None, ctypes.byref(rep)), "lqr_report")
     return dict(status=rep.status, status_name=STATUS_NAMES.get(rep.status, str(rep.status)),
                 num_segments=rep.num_segments, refine_iters=rep.refine_iters, bad_stage=rep.bad_stage,
-                cost=rep.cost, kkt_residual=rep.kkt_residual)
+                cost=rep.cost, kkt_residual=rep.kkt_residual, kkt_rel=rep.kkt_rel)
 
 
 def lqr_status_string(status: int) -> str:
@@ -215,7 +215,7 @@ class Solver:
         return out
 
     def solve(self, prob, num_segments=0, prec="fp64", out=None, want=("K", "k", "x", "u", "lam"),
-              stream=None, tol=1e-8, max_refine=0, form="multiplier"):
+              stream=None, tol=1e-8, max_refine=0, form="multiplier", residual=False):
         """Enqueue a solve on `stream` (torch stream; default current). Returns the output tensors."""
         if out is None:
             out = self.alloc_solution(prob, want)
@@ -223,7 +223,7 @@ class Solver:
         p = self.make_problem_struct(prob, ptr)
         s = lqr_solution(**{f: (out[f].data_ptr() if f in out else None) for f in SOLUTION_FIELDS})
         o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
-                     debug_checks=0, form=FORM[form])
+                     debug_checks=0, form=FORM[form], residual=1 if residual else 0)
         lqr_solve(self.h, p, o, s, self._stream(stream))
         return out
 
@@ -241,7 +241,7 @@ class Solver:
         return buf
 
     def solve_host(self, prob_np, num_segments=0, prec="fp64", out_np=None, want=("K", "k", "x", "u"),
-                   stream=None, form="multiplier"):
+                   stream=None, form="multiplier", tol=1e-8, max_refine=0, residual=False):
         """Host-memory solve (numpy arrays, ideally pinned): copies in, solves, copies out, synchronises."""
         import numpy as np
         n, m, T = self._dims(prob_np)
@@ -252,7 +252,7 @@ class Solver:
             out_np = {k: np.empty(shapes[k], dtype=dt) for k in want}
         p = self.make_problem_struct(prob_np, lambda a: a.ctypes.data)
         s = lqr_solution(**{f: (out_np[f].ctypes.data if f in out_np else None) for f in SOLUTION_FIELDS})
-        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
-                     form=FORM[form])
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
+                     debug_checks=0, form=FORM[form], residual=1 if residual else 0)
         lqr_solve_host(self.h, p, o, s, self._stream(stream))
         return out_np

@@ -1,0 +1,105 @@
+"""Steps A7/A8 on the GPU: the FP64 KKT residual kernel against the oracle's
+residual of the same (x, u, lambda), iterative refinement, and the mixed
+precision mode (FP64 data, FP32 sweeps, FP64 link solve and residual)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_06360_gb300 import Solver, build
+    build.build()
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def to_dev(prob, dtype=torch.float64):
+    return {k: torch.from_numpy(v).to("cuda:0", dtype) for k, v in prob.items()}
+
+
+def host(out):
+    return {k: v.double().cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("n,m,T,K,cross", [(12, 4, 128, 8, False), (7, 3, 61, 7, True), (5, 2, 1, 1, True)])
+def test_residual_kernel_matches_oracle(solver, n, m, T, K, cross):
+    prob = workloads.make_problem(n, m, T, seed=300 + n + T, cross=cross)
+    out = host(solver.solve(to_dev(prob), num_segments=K, residual=True))
+    rep = solver.report()
+    assert rep["status"] == 0
+    ref = oracle.kkt_residual(prob, out["x"], out["u"], out["lam"])
+    # eta and rel of the same point; the residual itself is at rounding level,
+    # so only its order of magnitude is comparable (different summation order)
+    assert rep["kkt_residual"] < 1e-14 and ref["eta"] < 1e-14
+    assert abs(rep["cost"] - oracle.stage_costs(prob, out["x"], out["u"])) <= 1e-11 * abs(rep["cost"])
+
+
+def test_refinement_repairs_constrained_form(solver):
+    """The constraint-explicit form loses ~1e-8 on the long-horizon workload;
+    two FP64 refinement corrections bring x, u, lambda, k to the oracle at 1e-9."""
+    prob = workloads.config1()
+    ref = oracle.riccati(prob)
+    out = host(solver.solve(to_dev(prob), num_segments=64, form="constrained", max_refine=2, tol=1e-13))
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    for k in ("x", "u", "lam", "k", "K"):
+        assert oracle.rel_err(out[k], ref[k]) < 1e-9, (k, oracle.rel_err(out[k], ref[k]))
+    assert rep["kkt_rel"] < 1e-13 and rep["refine_iters"] >= 1
+
+
+@pytest.mark.parametrize("K", [16, 64, 256])
+def test_mixed_precision_config1(solver, K):
+    """FP64 data, FP32 sweeps (FP64 Cholesky of R+B'PB), FP64 link solve,
+    FP64 KKT residual with refinement to |r|/|b| <= 1e-12: x, u and lambda
+    reach the oracle at 1e-9. The feedback gains K keep FP32 accuracy, and so
+    does k, which refinement keeps consistent with them (u_t = K_t x_t + k_t
+    along the refined trajectory to FP64 rounding): both stated, bound 1e-4."""
+    prob = workloads.config1()
+    ref = oracle.riccati(prob)
+    out = host(solver.solve(to_dev(prob), num_segments=K, prec="mixed", max_refine=4, tol=1e-12))
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    errs = {k: oracle.rel_err(out[k], ref[k]) for k in ("x", "u", "lam", "k", "K")}
+    print("mixed K=%d errors %s iters %d rel %.2e eta %.2e" % (K, errs, rep["refine_iters"], rep["kkt_rel"],
+                                                              rep["kkt_residual"]))
+    for k in ("x", "u", "lam"):
+        assert errs[k] < 1e-9, errs
+    assert errs["K"] < 1e-4 and errs["k"] < 1e-4
+    pol = np.einsum("tij,tj->ti", out["K"], out["x"][:-1]) + out["k"]
+    assert oracle.rel_err(pol, out["u"]) < 1e-12
+    assert rep["kkt_rel"] <= 1e-12
+    assert abs(rep["cost"] - ref["cost"]) <= 1e-10 * abs(ref["cost"])
+
+
+def test_no_convergence_is_reported(solver):
+    prob = workloads.config0()
+    solver.solve(to_dev(prob), num_segments=8, prec="mixed", max_refine=1, tol=1e-300)
+    rep = solver.report()
+    assert rep["status_name"] == "LQR_ERR_NO_CONVERGENCE"
+    assert rep["refine_iters"] == 1
+
+
+def test_refinement_stops_when_converged(solver):
+    prob = workloads.config0()
+    solver.solve(to_dev(prob), num_segments=8, prec="fp64", max_refine=5, tol=1e-6)
+    rep = solver.report()
+    assert rep["status"] == 0 and rep["refine_iters"] == 0  # FP64 already meets 1e-6
+
+
+def test_mixed_host_entry_point(solver):
+    prob = workloads.make_problem(16, 4, 96, seed=12)
+    ref = oracle.riccati(prob)
+    out = solver.solve_host(prob, num_segments=8, prec="mixed", want=("K", "k", "x", "u", "lam"),
+                            max_refine=3, tol=1e-12)
+    rep = solver.report()
+    assert rep["status"] == 0
+    assert oracle.rel_err(out["x"], ref["x"]) < 1e-9
