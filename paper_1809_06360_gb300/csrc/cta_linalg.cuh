@@ -58,6 +58,19 @@ __device__ __forceinline__ void cta_mm(int M, int N, int K, const XA* A, int lda
   }
 }
 
+// Picks the register tile from the output shape so that thin products still
+// occupy the block: 4x4 when there are enough tiles, else 2x2, else 1x1.
+template <bool TA, bool TB, typename Tacc, typename XA, typename XB, typename Epi>
+__device__ __forceinline__ void cta_mm_auto(int M, int N, int K, const XA* A, int lda, const XB* B, int ldb, Epi epi) {
+  const int nthr = blockDim.x;
+  if (((M + 3) / 4) * ((N + 3) / 4) >= nthr / 2)
+    cta_mm<4, 4, TA, TB, Tacc>(M, N, K, A, lda, B, ldb, epi);
+  else if (((M + 1) / 2) * ((N + 1) / 2) >= nthr / 2)
+    cta_mm<2, 2, TA, TB, Tacc>(M, N, K, A, lda, B, ldb, epi);
+  else
+    cta_mm<1, 1, TA, TB, Tacc>(M, N, K, A, lda, B, ldb, epi);
+}
+
 // --- epilogues --------------------------------------------------------------
 template <typename XC>
 struct EpiStore {  // C = alpha * acc
@@ -118,57 +131,118 @@ __device__ __forceinline__ void cta_mv(int M, int K, const XA* A, int lda,
 
 // ---------------------------------------------------------------------------
 // In-place lower Cholesky (FP64) of the d x d SPD matrix G (leading dim ld).
-// Right-looking, one column per step. `flag` is a shared int set to 1 when a
-// pivot is not positive (then the factor is garbage). Ends with a barrier;
-// the caller reads *flag after it.
+// One barrier per column: in step j every thread applies the rank-1 update of
+// column j (still unscaled: A[i][k] -= A[i][j] A[k][j] / A[j][j]) to the
+// trailing elements it owns, and scales column j-1, which nobody reads in
+// step j. Thread t owns row (t >> 2) + j + 1 + 64 r and the columns
+// k = t (mod 4) of that row. The single thread that writes the final value of
+// the next pivot also computes its reciprocal, square root and reciprocal
+// square root, so each costs one FP64 division / square root per column.
+// On exit rdiag[j] = 1 / L[j][j]. `flag` (shared) is set to 1 when a pivot is
+// not positive. `piv` (shared) holds 3d doubles of scratch. Ends with a barrier.
 // ---------------------------------------------------------------------------
-__device__ inline void cta_chol(int d, double* G, int ld, int* flag) {
+__device__ __forceinline__ void chol_pivot_prep(double v, int j, double* inv, double* sq, double* isq, int* flag) {
+  const bool ok = (v > 0.0) && isfinite(v);
+  if (!ok) *flag = 1;
+  const double s = ok ? sqrt(v) : 1.0;
+  sq[j] = s;
+  isq[j] = 1.0 / s;
+  inv[j] = ok ? isq[j] * isq[j] : 0.0;
+}
+
+__device__ inline void cta_chol_piv(int d, double* G, int ld, int* flag, double* piv, double* rdiag) {
+  const int t = threadIdx.x;
+  const int nthr = blockDim.x;
+  const int rows_per_pass = nthr >> 2;
+  const int q = t & 3;
+  double* inv = piv;
+  double* sq = piv + d;
+  double* isq = piv + 2 * d;
+  if (t == 0) chol_pivot_prep(G[0], 0, inv, sq, isq, flag);
+  __syncthreads();
   for (int j = 0; j < d; ++j) {
-    if (threadIdx.x == 0) {
-      double s = G[(size_t)j * ld + j];
-      if (!(s > 0.0) || !isfinite(s)) {
-        *flag = 1;
-        s = 1.0;  // keep the arithmetic finite; the caller discards the result
-      }
-      G[(size_t)j * ld + j] = sqrt(s);
+    const double invj = inv[j];
+    for (int i = (t >> 2) + j + 1; i < d; i += rows_per_pass) {
+      const double aij = G[(size_t)i * ld + j] * invj;
+      const int k0 = j + 1 + ((q - (j + 1)) & 3);
+      for (int k = k0; k <= i; k += 4) G[(size_t)i * ld + k] -= aij * G[(size_t)k * ld + j];
     }
-    __syncthreads();
-    const double inv = 1.0 / G[(size_t)j * ld + j];
-    for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) G[(size_t)i * ld + j] *= inv;
-    __syncthreads();
-    // trailing update of the lower triangle: rows i > j, columns j < k <= i
-    const int w = d - j - 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int ii = e / w, kk = e % w;
-      if (kk > ii) continue;
-      const int i = j + 1 + ii, k = j + 1 + kk;
-      G[(size_t)i * ld + k] -= G[(size_t)i * ld + j] * G[(size_t)k * ld + j];
+    // the owner of (j+1, j+1) in this step prepares the next pivot
+    if (j + 1 < d && t == ((j + 1) & 3)) chol_pivot_prep(G[(size_t)(j + 1) * ld + (j + 1)], j + 1, inv, sq, isq, flag);
+    if (j > 0) {
+      const double s = isq[j - 1];
+      for (int i = j + t; i < d; i += nthr) G[(size_t)i * ld + (j - 1)] *= s;
+      if (t == 0) G[(size_t)(j - 1) * ld + (j - 1)] = sq[j - 1];
     }
     __syncthreads();
   }
+  if (t == 0) G[(size_t)(d - 1) * ld + (d - 1)] = sq[d - 1];
+  if (rdiag)
+    for (int j = t; j < d; j += nthr) rdiag[j] = isq[j];
+  __syncthreads();
 }
 
-// Solve L Y = X in place (L lower d x d, leading dim ldl; X d x nc, leading dim ldx).
-// One thread per right-hand-side column. No barrier at the end.
+// Convenience wrapper with static scratch (d <= 256); rdiag may be null.
+__device__ inline void cta_chol(int d, double* G, int ld, int* flag, double* rdiag = nullptr) {
+  __shared__ double s_piv[3 * 256];
+  cta_chol_piv(d, G, ld, flag, s_piv, rdiag);
+}
+
+// Triangular solves with few right-hand sides: one warp per column, the
+// column-oriented elimination spread over the lanes.
 template <typename XX>
-__device__ __forceinline__ void cta_trsm_lower(int d, const double* L, int ldl, int nc, XX* X, int ldx) {
+__device__ __forceinline__ void cta_trsm_lower_warp(int d, const double* L, int ldl, int nc, XX* X, int ldx,
+                                                    const double* rdiag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    for (int i = 0; i < d; ++i) {
+      const double xi = static_cast<double>(X[(size_t)i * ldx + c]) * rdiag[i];
+      __syncwarp();
+      if (lane == 0) X[(size_t)i * ldx + c] = static_cast<XX>(xi);
+      for (int k = i + 1 + lane; k < d; k += 32)
+        X[(size_t)k * ldx + c] = static_cast<XX>(static_cast<double>(X[(size_t)k * ldx + c]) - L[(size_t)k * ldl + i] * xi);
+      __syncwarp();
+    }
+  }
+}
+template <typename XX>
+__device__ __forceinline__ void cta_trsm_lower_t_warp(int d, const double* L, int ldl, int nc, XX* X, int ldx,
+                                                      const double* rdiag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    for (int i = d - 1; i >= 0; --i) {
+      const double xi = static_cast<double>(X[(size_t)i * ldx + c]) * rdiag[i];
+      __syncwarp();
+      if (lane == 0) X[(size_t)i * ldx + c] = static_cast<XX>(xi);
+      for (int k = lane; k < i; k += 32)
+        X[(size_t)k * ldx + c] = static_cast<XX>(static_cast<double>(X[(size_t)k * ldx + c]) - L[(size_t)i * ldl + k] * xi);
+      __syncwarp();
+    }
+  }
+}
+
+// Solve L Y = X in place (L lower d x d, leading dim ldl; X d x nc, leading dim
+// ldx) with rdiag[i] = 1 / L[i][i]; arithmetic in Tacc. One thread per column.
+// No barrier at the end.
+template <typename Tacc, typename TL, typename XX>
+__device__ __forceinline__ void cta_trsm_lower(int d, const TL* L, int ldl, const TL* rdiag, int nc, XX* X, int ldx) {
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     for (int i = 0; i < d; ++i) {
-      double t = static_cast<double>(X[(size_t)i * ldx + c]);
-      for (int k = 0; k < i; ++k) t -= L[(size_t)i * ldl + k] * static_cast<double>(X[(size_t)k * ldx + c]);
-      X[(size_t)i * ldx + c] = static_cast<XX>(t / L[(size_t)i * ldl + i]);
+      Tacc t = static_cast<Tacc>(X[(size_t)i * ldx + c]);
+      for (int k = 0; k < i; ++k) t -= static_cast<Tacc>(L[(size_t)i * ldl + k]) * static_cast<Tacc>(X[(size_t)k * ldx + c]);
+      X[(size_t)i * ldx + c] = static_cast<XX>(t * static_cast<Tacc>(rdiag[i]));
     }
   }
 }
 
-// Solve L' Y = X in place (L lower). No barrier at the end.
-template <typename XX>
-__device__ __forceinline__ void cta_trsm_lower_t(int d, const double* L, int ldl, int nc, XX* X, int ldx) {
+// Solve L' Y = X in place (L lower), rdiag[i] = 1 / L[i][i]. No barrier.
+template <typename Tacc, typename TL, typename XX>
+__device__ __forceinline__ void cta_trsm_lower_t(int d, const TL* L, int ldl, const TL* rdiag, int nc, XX* X, int ldx) {
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     for (int i = d - 1; i >= 0; --i) {
-      double t = static_cast<double>(X[(size_t)i * ldx + c]);
-      for (int k = i + 1; k < d; ++k) t -= L[(size_t)k * ldl + i] * static_cast<double>(X[(size_t)k * ldx + c]);
-      X[(size_t)i * ldx + c] = static_cast<XX>(t / L[(size_t)i * ldl + i]);
+      Tacc t = static_cast<Tacc>(X[(size_t)i * ldx + c]);
+      for (int k = i + 1; k < d; ++k) t -= static_cast<Tacc>(L[(size_t)k * ldl + i]) * static_cast<Tacc>(X[(size_t)k * ldx + c]);
+      X[(size_t)i * ldx + c] = static_cast<XX>(t * static_cast<Tacc>(rdiag[i]));
     }
   }
 }

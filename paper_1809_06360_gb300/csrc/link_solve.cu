@@ -10,15 +10,21 @@
 //     Pi_j = V_xx^j - G_j'G_j,               pi_j = v_x^j - G_j'g_j
 // followed by the forward substitution z_0 = x0,
 //     z_{j+1} = -D_j^{-1}(V_zx^j z_j + v_z^j + pi_{j+1}) = Gam_j z_j + gam_j.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
 
 #include "lqr_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lqr {
 
 __global__ void __launch_bounds__(kBlock) link_solve_kernel(ProbTable tab, int x0_is_float) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
+  __shared__ double s_rd[256];
   const ProbDesc& pd = prob_at(tab, blockIdx.x);
   if (cta_should_exit(pd, &s_flag)) return;
   const int n = pd.n, K = pd.nseg;
@@ -61,18 +67,18 @@ __global__ void __launch_bounds__(kBlock) link_solve_kernel(ProbTable tab, int x
     for (int i = threadIdx.x; i < n; i += blockDim.x) g[i] = vz[i] + pn[i];
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
-    cta_chol(n, L, n, &s_flag);
+    cta_chol(n, L, n, &s_flag, s_rd);
     if (s_flag) {
       if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
       return;
     }
-    cta_trsm_lower<double>(n, L, n, n, G, n);
+    cta_trsm_lower<double>(n, L, n, s_rd, n, G, n);
     if (threadIdx.x == blockDim.x - 1) {
       // g <- L^{-1} g by one thread (a single right-hand side)
       for (int i = 0; i < n; ++i) {
         double t = g[i];
         for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * g[k];
-        g[i] = t / L[(size_t)i * n + i];
+        g[i] = t * s_rd[i];
       }
     }
     __syncthreads();
@@ -87,12 +93,12 @@ __global__ void __launch_bounds__(kBlock) link_solve_kernel(ProbTable tab, int x
       Pj[(size_t)k * n + i] = a;
     }
     // Gam_j = -L'^{-1} G_j, gam_j = -L'^{-1} g_j (in place)
-    cta_trsm_lower_t<double>(n, L, n, n, G, n);
+    cta_trsm_lower_t<double>(n, L, n, s_rd, n, G, n);
     if (threadIdx.x == blockDim.x - 1) {
       for (int i = n - 1; i >= 0; --i) {
         double t = g[i];
         for (int k = i + 1; k < n; ++k) t -= L[(size_t)k * n + i] * g[k];
-        g[i] = t / L[(size_t)i * n + i];
+        g[i] = t * s_rd[i];
       }
     }
     __syncthreads();
@@ -116,7 +122,7 @@ cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, 
   if (tab.probs) return cudaErrorInvalidValue;  // batched launches pass nmax through launch_link_solve_n
   const size_t bytes = sizeof(double) * (size_t)nmax * nmax;
   static size_t configured = 0;
-  if (bytes > 48 * 1024 && bytes > configured) {
+  if (bytes > configured) {
     cudaError_t e = cudaFuncSetAttribute(link_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = bytes;
@@ -143,6 +149,8 @@ cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, 
 __global__ void __launch_bounds__(kBlock) link_solve_dual_kernel(ProbTable tab, int x0_is_float, long long smem_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
+  __shared__ double s_rdc[256];
+  __shared__ double s_rdl[256];
   const ProbDesc& pd = prob_at(tab, blockIdx.x);
   if (cta_should_exit(pd, &s_flag)) return;
   const int n = pd.n, K = pd.nseg;
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) link_solve_dual_kernel(ProbTable tab, 
     cta_mv<false, double>(n, n, Wneg, n, pn, 1, EpiAdd<double, double>{gam, 1, 1.0, w, 1});
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
-    cta_chol(n, C, n, &s_flag);
+    cta_chol(n, C, n, &s_flag, s_rdc);
     if (s_flag) {
       if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
       return;
@@ -209,18 +217,18 @@ __global__ void __launch_bounds__(kBlock) link_solve_dual_kernel(ProbTable tab, 
     for (int i = threadIdx.x; i < n; i += blockDim.x) Ld[(long long)i * n + i] += 1.0;
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
-    cta_chol(n, Ld, n, &s_flag);
+    cta_chol(n, Ld, n, &s_flag, s_rdl);
     if (s_flag) {
       if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
       return;
     }
     // F = Ld^-1 E ; t = Ld^-1 (C'v)
-    cta_trsm_lower<double>(n, Ld, n, n, E, n);
+    cta_trsm_lower<double>(n, Ld, n, s_rdl, n, E, n);
     if (threadIdx.x == blockDim.x - 1) {
       for (int i = 0; i < n; ++i) {
         double a = tv[i];
         for (int k = 0; k < i; ++k) a -= Ld[(long long)i * n + k] * tv[k];
-        tv[i] = a / Ld[(long long)i * n + i];
+        tv[i] = a * s_rdl[i];
       }
     }
     __syncthreads();
@@ -239,12 +247,12 @@ __global__ void __launch_bounds__(kBlock) link_solve_dual_kernel(ProbTable tab, 
       Pj[(size_t)k * n + i] = a;
     }
     // F <- Ld^-T F ; t2 = Ld^-T t
-    cta_trsm_lower_t<double>(n, Ld, n, n, E, n);
+    cta_trsm_lower_t<double>(n, Ld, n, s_rdl, n, E, n);
     if (threadIdx.x == blockDim.x - 1) {
       for (int i = n - 1; i >= 0; --i) {
         double a = tv[i];
         for (int k = i + 1; k < n; ++k) a -= Ld[(long long)k * n + i] * t2[k];
-        t2[i] = a / Ld[(long long)i * n + i];
+        t2[i] = a * s_rdl[i];
       }
     }
     __syncthreads();
@@ -264,8 +272,275 @@ __global__ void __launch_bounds__(kBlock) link_solve_dual_kernel(ProbTable tab, 
   }
 }
 
+// Single right-hand-side triangular solves by one warp (column-oriented: after
+// y_i is known every lane updates its later entries). y is in shared memory.
+__device__ inline void warp_trsv_lower(int n, const double* L, int ld, const double* rd, double* y) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < n; ++i) {
+    const double yi = y[i] * rd[i];
+    __syncwarp();
+    if (lane == 0) y[i] = yi;
+    for (int k = i + 1 + lane; k < n; k += 32) y[k] -= L[(size_t)k * ld + i] * yi;
+    __syncwarp();
+  }
+}
+__device__ inline void warp_trsv_lower_t(int n, const double* L, int ld, const double* rd, double* y) {
+  const int lane = threadIdx.x & 31;
+  for (int i = n - 1; i >= 0; --i) {
+    const double yi = y[i] * rd[i];
+    __syncwarp();
+    if (lane == 0) y[i] = yi;
+    for (int k = lane; k < i; k += 32) y[k] -= L[(size_t)i * ld + k] * yi;
+    __syncwarp();
+  }
+}
+
+// Copy the column slabs owned by the other CTAs of the cluster into the local
+// copy of the n x n matrix M (distributed shared memory reads).
+template <int CL>
+__device__ inline void cluster_gather_cols(cg::cluster_group& cluster, double* M, int n, int rank) {
+  for (int r2 = 0; r2 < CL; ++r2) {
+    if (r2 == rank) continue;
+    const double* rem = cluster.map_shared_rank(M, r2);
+    const int d0 = r2 * n / CL, d1 = (r2 + 1) * n / CL, w = d1 - d0;
+    if (w <= 0) continue;
+    for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
+      const int i = e / w, jj = d0 + e % w;
+      M[(size_t)i * n + jj] = rem[(size_t)i * n + jj];
+    }
+  }
+}
+
+// The same dual link recursion as link_solve_dual_kernel, with each link step
+// spread over a cluster of CL CTAs: every CTA owns a slab of columns of the
+// n x n products (W C, C'Z, C'W C, Ld^-1 E, F'F, Z - W C Ld^-T F) and the
+// slabs are exchanged through distributed shared memory; the two n x n
+// Cholesky factorisations per link are computed redundantly by every CTA
+// (deterministic, so all CTAs hold bitwise-identical factors).
+template <int CL>
+__global__ void __launch_bounds__(kBlock) link_solve_dual_cluster_kernel(ProbTable tab, int x0_is_float, int stage_inputs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_flag;
+  __shared__ double s_rdc[256];
+  __shared__ double s_rdl[256];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const ProbDesc& pd = prob_at(tab, blockIdx.x / CL);
+  // the exit decision reads state written by earlier kernels only: cluster-uniform
+  if (cta_should_exit(pd, &s_flag)) return;
+  const int n = pd.n, K = pd.nseg;
+  const long long nn = (long long)n * n;
+  const WsLayout wl = ws_layout(n, K);
+  double* ws = pd.ws;
+  double* z = ws + wl.z;
+  if (rank == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      z[i] = x0_is_float ? (double)static_cast<const float*>(pd.x0)[i] : static_cast<const double*>(pd.x0)[i];
+  if (K == 1) return;
+  double* C = reinterpret_cast<double*>(smem);
+  double* Tm = C + nn;
+  double* Ld = Tm + nn;
+  double* E = Ld + nn;
+  double* v = E + nn;   // w_j - W_j pi_{j+1}
+  double* tv = v + n;   // C'v, then Ld^-1 C'v
+  double* t2 = tv + n;  // Ld^-T t
+  // per-link inputs staged in shared memory by one coalesced copy (when they fit)
+  double* Wn_s = t2 + n;      // -W_j
+  double* Z_s = Wn_s + nn;    // Z_j
+  double* vec_s = Z_s + nn;   // w_j, p_j, pi_{j+1}
+  const bool staged = stage_inputs != 0;
+  const int c0 = rank * n / CL, c1 = (rank + 1) * n / CL, ns = c1 - c0;
+  const long long sstride = 3 * nn + 2 * n;
+  if (rank == 0) {
+    const double* S = ws + wl.summ + (long long)(K - 1) * sstride;
+    double* Pi = ws + wl.Pi + (long long)(K - 1) * nn;
+    double* pi = ws + wl.pi + (long long)(K - 1) * n;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) Pi[e] = S[e];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) pi[i] = S[3 * nn + i];
+  }
+  cluster.sync();
+  for (int j = K - 2; j >= 0; --j) {
+    const double* S = ws + wl.summ + (long long)j * sstride;
+    const double* Pseg = S;
+    const double* Z = S + nn;
+    const double* Wneg = S + 2 * nn;
+    const double* ps = S + 3 * nn;
+    const double* w = S + 3 * nn + n;
+    const double* Pn = ws + wl.Pi + (long long)(j + 1) * nn;
+    const double* pn = ws + wl.pi + (long long)(j + 1) * n;
+    if (staged) {
+      for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        Wn_s[e] = Wneg[e];
+        Z_s[e] = Z[e];
+      }
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        vec_s[i] = w[i];
+        vec_s[n + i] = ps[i];
+        vec_s[2 * n + i] = pn[i];
+      }
+      Wneg = Wn_s;
+      Z = Z_s;
+      w = vec_s;
+      ps = vec_s + n;
+      pn = vec_s + 2 * n;
+      __syncthreads();
+    }
+    double* Pj = ws + wl.Pi + (long long)j * nn;
+    double* pj = ws + wl.pi + (long long)j * n;
+    double* Gam = ws + wl.Gam + (long long)j * nn;
+    double* gam = ws + wl.gam + (long long)j * n;
+    // (A) redundant: C = chol(Pi_{j+1}), v = w - W pi_{j+1}
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) C[e] = Pn[e];
+    cta_mv<false, double>(n, n, Wneg, n, pn, 1, EpiAdd<double, double>{v, 1, 1.0, w, 1});
+    if (threadIdx.x == 0) s_flag = 0;
+    __syncthreads();
+    cta_chol(n, C, n, &s_flag, s_rdc);
+    if (s_flag) {  // identical in every CTA of the cluster
+      if (rank == 0 && threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
+      return;
+    }
+    for (int e = threadIdx.x; e < nn; e += blockDim.x)
+      if (e % n > e / n) C[e] = 0.0;
+    __syncthreads();
+    // (B) slabs of Tm = W C and E = C'Z; tv = C'v (redundant)
+    cta_mm_auto<false, false, double>(n, ns, n, Wneg, n, C + c0, n, EpiStore<double>{Tm + c0, n, -1.0});
+    cta_mm_auto<true, false, double>(n, ns, n, C, n, Z + c0, n, EpiStore<double>{E + c0, n, 1.0});
+    cta_mv<true, double>(n, n, C, n, v, 1, EpiStore<double>{tv, 1, 1.0});
+    cluster.sync();
+    cluster_gather_cols<CL>(cluster, Tm, n, rank);
+    cluster_gather_cols<CL>(cluster, E, n, rank);
+    cluster.sync();
+    // (C) slab of Ld = I + C'Tm
+    cta_mm_auto<true, false, double>(n, ns, n, C, n, Tm + c0, n, EpiStore<double>{Ld + c0, n, 1.0});
+    __syncthreads();
+    for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) Ld[(size_t)i * n + i] += 1.0;
+    cluster.sync();
+    cluster_gather_cols<CL>(cluster, Ld, n, rank);
+    cluster.sync();
+    // (D) redundant: Ld = chol(I + C'W C), t = Ld^-1 C'v
+    if (threadIdx.x == 0) s_flag = 0;
+    __syncthreads();
+    cta_chol(n, Ld, n, &s_flag, s_rdl);
+    if (s_flag) {
+      if (rank == 0 && threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
+      return;
+    }
+    if (threadIdx.x < 32) warp_trsv_lower(n, Ld, n, s_rdl, tv);
+    // (E) slab of F = Ld^-1 E (in place)
+    cta_trsm_lower_warp<double>(n, Ld, n, ns, E + c0, n, s_rdl);
+    cluster.sync();
+    cluster_gather_cols<CL>(cluster, E, n, rank);
+    cluster.sync();
+    // (F) slabs of Pi_j = P_j + F'F and Gam_j = Z - Tm Ld^-T F; rank 0: pi_j, gam_j
+    cta_mm_auto<true, false, double>(n, ns, n, E, n, E + c0, n, EpiAdd<double, double>{Pj + c0, n, 1.0, Pseg + c0, n});
+    for (int e = threadIdx.x; e < n * ns; e += blockDim.x) {
+      const int i = e / ns, jj = c0 + e % ns;
+      C[(size_t)i * n + jj] = E[(size_t)i * n + jj];
+    }
+    __syncthreads();
+    cta_trsm_lower_t_warp<double>(n, Ld, n, ns, C + c0, n, s_rdl);
+    if (rank == 0 && threadIdx.x >= blockDim.x - 32) {
+      for (int i = threadIdx.x & 31; i < n; i += 32) t2[i] = tv[i];
+      __syncwarp();
+      warp_trsv_lower_t(n, Ld, n, s_rdl, t2);
+    }
+    __syncthreads();
+    cta_mm_auto<false, false, double>(n, ns, n, Tm, n, C + c0, n, EpiAdd<double, double>{Gam + c0, n, -1.0, Z + c0, n});
+    if (rank == 0) {
+      // pi_j = p_j + Z'pi_{j+1} + F't ; gam_j = v - Tm t2
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double a = ps[i];
+        for (int k = 0; k < n; ++k) a = fma(Z[(size_t)k * n + i], pn[k], fma(E[(size_t)k * n + i], tv[k], a));
+        pj[i] = a;
+        double g = v[i];
+        for (int k = 0; k < n; ++k) g = fma(-Tm[(size_t)i * n + k], t2[k], g);
+        gam[i] = g;
+      }
+    }
+    cluster.sync();  // Pi_j, pi_j visible to the cluster; slabs free for reuse
+  }
+  if (rank != 0) return;
+  for (int j = 0; j + 1 < K; ++j) {
+    const double* G = ws + wl.Gam + (long long)j * nn;
+    const double* g = ws + wl.gam + (long long)j * n;
+    cta_mv<false, double>(n, n, G, n, z + (long long)j * n, 1,
+                          EpiAdd<double, double>{z + (long long)(j + 1) * n, 1, 1.0, g, 1});
+    __syncthreads();
+  }
+}
+
+template <int CL>
+static cudaError_t launch_dual_cluster(const ProbTable& tab, int nprob, int x0_is_float, size_t bytes,
+                                       cudaStream_t st) {
+  static size_t configured = 0;
+  if (bytes > configured) {
+    cudaError_t e = cudaFuncSetAttribute(link_solve_dual_cluster_kernel<CL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    if (CL > 8) {
+      e = cudaFuncSetAttribute(link_solve_dual_cluster_kernel<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    configured = bytes;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL * nprob, 1, 1);
+  cfg.blockDim = dim3(kBlock, 1, 1);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int staged = (bytes >= sizeof(double) * (6 * (size_t)tab.single.n * tab.single.n + 6 * (size_t)tab.single.n)) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, link_solve_dual_cluster_kernel<CL>, tab, x0_is_float, staged);
+}
+
+// cluster width used for the link solve (0 = single CTA); set by launch_link_solve_dual
+static int g_link_cluster = -1;
+cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
+
+int link_cluster_width() { return g_link_cluster; }
+
 cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st) {
   if (tab.probs) return cudaErrorInvalidValue;
+  cudaError_t r = launch_link_solve_dual_impl(tab, nprob, x0_is_float, st);
+  static int reported = -2;
+  if (getenv("LQR_DEBUG") && reported != g_link_cluster) {
+    fprintf(stderr, "liblqr: link solve on %d-CTA clusters (0 = single CTA), n=%d K=%d\n", g_link_cluster,
+            tab.single.n, tab.single.nseg);
+    reported = g_link_cluster;
+  }
+  return r;
+}
+
+cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st) {
+  {
+    const int n = tab.single.n;
+    size_t cbytes = sizeof(double) * (6 * (size_t)n * n + 6 * (size_t)n);  // with staged inputs
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (cbytes > (size_t)optin - kStaticSmemReserve) cbytes = sizeof(double) * (4 * (size_t)n * n + 3 * (size_t)n);
+    if (n >= 16 && tab.single.nseg > 1 && cbytes <= (size_t)optin - kStaticSmemReserve) {
+      cudaError_t e = launch_dual_cluster<16>(tab, nprob, x0_is_float, cbytes, st);
+      if (e == cudaSuccess) {
+        g_link_cluster = 16;
+        return cudaSuccess;
+      }
+      cudaGetLastError();  // 16-CTA clusters not available: portable width
+      e = launch_dual_cluster<8>(tab, nprob, x0_is_float, cbytes, st);
+      if (e == cudaSuccess) {
+        g_link_cluster = 8;
+        return cudaSuccess;
+      }
+      cudaGetLastError();
+    }
+  }
+  g_link_cluster = 0;
   const int n = tab.single.n;
   size_t bytes = sizeof(double) * (4 * (size_t)n * n + 2 * (size_t)n);
   int optin = 0, dev = 0;
@@ -273,7 +548,7 @@ cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_fl
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (bytes > (size_t)optin - kStaticSmemReserve) bytes = 0;  // work matrices go to the global workspace
   static size_t configured = 0;
-  if (bytes > 48 * 1024 && bytes > configured) {
+  if (bytes > configured) {
     cudaError_t e = cudaFuncSetAttribute(link_solve_dual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = bytes;

@@ -94,7 +94,7 @@ bool elem_size(lqr_precision p, size_t* es) {
 lqr_status validate(const lqr_problem* p, const lqr_opts* o, const lqr_solution* s) {
   if (!p || !o || !s) return LQR_ERR_INVALID_ARG;
   if (p->n < 1 || p->m < 1 || p->T < 1) return LQR_ERR_INVALID_ARG;
-  if (p->n > 512 || p->m > 512) return LQR_ERR_INVALID_ARG;
+  if (p->n > 256 || p->m > 256) return LQR_ERR_INVALID_ARG;
   if (!p->A || !p->B || !p->c || !p->Q || !p->R || !p->q || !p->r || !p->x0) return LQR_ERR_INVALID_ARG;
   if ((s->P == nullptr) != (s->p == nullptr)) return LQR_ERR_INVALID_ARG;
   if (s->lam && (!s->x || !s->u)) return LQR_ERR_INVALID_ARG;

@@ -9,7 +9,7 @@
 namespace lqr {
 
 constexpr int kBlock = 256;           // threads per CTA of the sweep / rollout kernels
-constexpr int kStaticSmemReserve = 1024;
+constexpr int kStaticSmemReserve = 12 * 1024;  // static shared memory of the kernels (pivot scratch, flags)
 
 // Segment j of a K-way split of T stages covers [seg_begin(j), seg_begin(j+1)).
 __host__ __device__ inline int seg_begin(int T, int K, int j) {

@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   __shared__ double s_scal[4];
+  __shared__ double s_rd[256];   // 1 / L[i][i] of the current FP64 factor
+  __shared__ TC s_rdc[256];      // the same in the compute type
 
   const int unit = blockIdx.x;
   const ProbDesc& pd = prob_of_unit(tab, unit);
@@ -225,14 +227,25 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
       }
       if (threadIdx.x == 0) s_flag = 0;
       __syncthreads();
-      cta_chol(m, L64, m, &s_flag);
+      cta_chol(m, L64, m, &s_flag, s_rd);
       if (s_flag) {
         if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
         failed = true;
         break;
       }
+      // the factor is computed in FP64 and applied in the compute type
+      const TC* Lc = reinterpret_cast<const TC*>(L64);
+      if (sizeof(TC) != 8) {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) Muu[e] = static_cast<TC>(L64[e]);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) s_rdc[i] = static_cast<TC>(s_rd[i]);
+        Lc = Muu;
+        __syncthreads();
+      } else {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) s_rdc[i] = static_cast<TC>(s_rd[i]);
+        __syncthreads();
+      }
       // W = L^{-1} [M_ux | M_zu' | m_u]
-      cta_trsm_lower<TC>(m, L64, m, ldF, F, ldF);
+      cta_trsm_lower<TC>(m, Lc, m, s_rdc, ldF, F, ldF);
       __syncthreads();
       // V_xx = M_xx - W_x'W_x ;  v_x = m_x - W_x'w
       cta_mm<RMg, RNg, true, false, TC>(n, n, m, F, ldF, F, ldF, EpiAccum<TC>{Vxx, n, -1.0});
@@ -246,7 +259,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
       __syncthreads();
       if (!param) {
         // policy [K_t | k_t] = -L'^{-1} W
-        cta_trsm_lower_t<TC>(m, L64, m, ldF, F, ldF);
+        cta_trsm_lower_t<TC>(m, Lc, m, s_rdc, ldF, F, ldF);
         __syncthreads();
         if (gK)
           for (int e = threadIdx.x; e < m * n; e += blockDim.x)
@@ -359,7 +372,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
                                                EpiAccum<double>{AUG + (size_t)rr * ld2 + rr, ld2, 1.0});
         if (threadIdx.x == 0) s_flag = 0;
         __syncthreads();
-        cta_chol(m - rr, Ec + (size_t)rr * m + rr, m, &s_flag);
+        cta_chol(m - rr, Ec + (size_t)rr * m + rr, m, &s_flag, s_rd);
         if (s_flag) {
           if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
           failed = true;
@@ -371,9 +384,9 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
           Gc[(size_t)(rr + a) * ldG + j] = -AUG[(size_t)(rr + a) * ld2 + rr + j];
         }
         __syncthreads();
-        cta_trsm_lower<double>(m - rr, Ec + (size_t)rr * m + rr, m, ldG, Gc + (size_t)rr * ldG, ldG);
+        cta_trsm_lower<double>(m - rr, Ec + (size_t)rr * m + rr, m, s_rd, ldG, Gc + (size_t)rr * ldG, ldG);
         __syncthreads();
-        cta_trsm_lower_t<double>(m - rr, Ec + (size_t)rr * m + rr, m, ldG, Gc + (size_t)rr * ldG, ldG);
+        cta_trsm_lower_t<double>(m - rr, Ec + (size_t)rr * m + rr, m, s_rd, ldG, Gc + (size_t)rr * ldG, ldG);
         __syncthreads();
         // G = Q_f [Y; W]
         cta_householder_apply(m, rr, AUG, ld2, vhead, beta, ldG, Gc, ldG, false);
@@ -446,7 +459,7 @@ template <typename TS, typename TC>
 cudaError_t launch_seg_sweep(const ProbTable& tab, int nunits, int phase, long long smem_bytes,
                              long long smem_budget, int store_P, cudaStream_t st) {
   static int configured_bytes = -1;  // per template instance
-  if (smem_bytes > 48 * 1024 && configured_bytes < (int)smem_bytes) {
+  if (configured_bytes < (int)smem_bytes) {  // dynamic + static may pass 48 KB even below 48 KB dynamic
     cudaError_t e = cudaFuncSetAttribute(seg_sweep_kernel<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes);
     if (e != cudaSuccess) return e;
