@@ -159,6 +159,23 @@ lqr_status lqr_solve(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opt
 lqr_status lqr_solve_host(lqr_handle *h, const lqr_problem *prob_host, const lqr_opts *opts,
                           const lqr_solution *sol_host, void *stream);
 
+/* Many independent problems of uneven n, m, T in one solve (a batch): one
+ * launch per step over all (problem, segment) units, with the segment count
+ * of each problem chosen from the batch shape (one segment per problem when
+ * the batch has at least one problem per SM) unless opts->num_segments > 0
+ * fixes it. probs and sols are HOST arrays of nprob entries whose pointers are
+ * device arrays (layout above); all problems share opts (precision, form
+ * LQR_FORM_MULTIPLIER; no refinement). segments (host, nprob ints, or NULL)
+ * receives the segment count used per problem. Asynchronous on `stream`;
+ * the host arrays may be reused as soon as the call returns. */
+lqr_status lqr_solve_batched(lqr_handle *h, int nprob, const lqr_problem *probs, const lqr_opts *opts,
+                             const lqr_solution *sols, int *segments, void *stream);
+
+/* Synchronise `stream` and read back per-problem status (lqr_status) and
+ * objective J* of the last lqr_solve_batched call (host arrays of nprob
+ * entries; cost may be NULL). */
+lqr_status lqr_report_batched(lqr_handle *h, void *stream, int nprob, int *status, double *cost);
+
 /* Step A1 alone: the per-segment parametric backward sweeps (Section II-B,
  * Eq. 9-16). Writes K summaries of LQR_SUMMARY_DOUBLES(n) doubles each to the
  * device array `summaries` (FP64). */

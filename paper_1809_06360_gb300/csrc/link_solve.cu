@@ -121,11 +121,9 @@ cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, 
   int nmax = tab.probs ? 0 : tab.single.n;
   if (tab.probs) return cudaErrorInvalidValue;  // batched launches pass nmax through launch_link_solve_n
   const size_t bytes = sizeof(double) * (size_t)nmax * nmax;
-  static size_t configured = 0;
-  if (bytes > configured) {
-    cudaError_t e = cudaFuncSetAttribute(link_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  {
+    cudaError_t e = raise_dyn_smem((const void*)link_solve_kernel, bytes);
     if (e != cudaSuccess) return e;
-    configured = bytes;
   }
   link_solve_kernel<<<nprob, kBlock, bytes, st>>>(tab, x0_is_float);
   return cudaGetLastError();
@@ -472,16 +470,13 @@ __global__ void __launch_bounds__(kBlock) link_solve_dual_cluster_kernel(ProbTab
 template <int CL>
 static cudaError_t launch_dual_cluster(const ProbTable& tab, int nprob, int x0_is_float, size_t bytes,
                                        cudaStream_t st) {
-  static size_t configured = 0;
-  if (bytes > configured) {
-    cudaError_t e = cudaFuncSetAttribute(link_solve_dual_cluster_kernel<CL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  {
+    cudaError_t e = raise_dyn_smem((const void*)link_solve_dual_cluster_kernel<CL>, bytes);
     if (e != cudaSuccess) return e;
     if (CL > 8) {
       e = cudaFuncSetAttribute(link_solve_dual_cluster_kernel<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
-    configured = bytes;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL * nprob, 1, 1);
@@ -517,6 +512,21 @@ cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_fl
   return r;
 }
 
+cudaError_t launch_link_solve_dual_batched(const ProbTable& tab, int nprob, int nmax, int x0_is_float,
+                                          cudaStream_t st) {
+  size_t bytes = sizeof(double) * (4 * (size_t)nmax * nmax + 2 * (size_t)nmax);
+  int optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (bytes > (size_t)optin - kStaticSmemReserve) bytes = 0;
+  {
+    cudaError_t e = raise_dyn_smem((const void*)link_solve_dual_kernel, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  link_solve_dual_kernel<<<nprob, kBlock, bytes, st>>>(tab, x0_is_float, (long long)bytes);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st) {
   {
     const int n = tab.single.n;
@@ -547,11 +557,9 @@ cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (bytes > (size_t)optin - kStaticSmemReserve) bytes = 0;  // work matrices go to the global workspace
-  static size_t configured = 0;
-  if (bytes > configured) {
-    cudaError_t e = cudaFuncSetAttribute(link_solve_dual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  {
+    cudaError_t e = raise_dyn_smem((const void*)link_solve_dual_kernel, bytes);
     if (e != cudaSuccess) return e;
-    configured = bytes;
   }
   link_solve_dual_kernel<<<nprob, kBlock, bytes, st>>>(tab, x0_is_float, (long long)bytes);
   return cudaGetLastError();

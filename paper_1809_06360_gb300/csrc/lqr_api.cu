@@ -10,6 +10,26 @@
 
 using namespace lqr;
 
+namespace lqr {
+cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
+  struct Entry { const void* f; int dev; size_t bytes; };
+  static Entry table[64];
+  static int count = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < count; ++i)
+    if (table[i].f == func && table[i].dev == dev) {
+      if (bytes <= table[i].bytes) return cudaSuccess;
+      cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e == cudaSuccess) table[i].bytes = bytes;
+      return e;
+    }
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && count < 64) table[count++] = Entry{func, dev, bytes};
+  return e;
+}
+}  // namespace lqr
+
 struct lqr_handle {
   int device = 0;
   int num_sms = 0;
@@ -23,6 +43,14 @@ struct lqr_handle {
   int last_K = 0;
   int last_launches = 0;
   int last_resid = 0;
+  // batched solves: device descriptor table, per-problem status/report, pinned staging
+  unsigned char* bdev = nullptr;
+  size_t bdev_bytes = 0;
+  unsigned char* bhost = nullptr;  // pinned
+  size_t bhost_bytes = 0;
+  cudaEvent_t bhost_ev = nullptr;  // last copy out of bhost
+  int last_batch = 0;
+  size_t bstatus_off = 0, breport_off = 0;
   // phase profiling: one event pair per phase per solve, summed on read
   static constexpr int kPhases = LQR_NUM_PHASES;
   static constexpr int kMaxProfiled = 256;
@@ -311,9 +339,213 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
   return LQR_OK;
 }
 
+// Segment count per problem of a batch. With at least one problem per SM the
+// batch alone fills the GPU and every problem runs as one plain Riccati sweep
+// (K = 1: no parametric sweep, no link solve). Otherwise the stages are spread
+// so that the batch forms about two units per SM, with segments of at least
+// max(16, ceil(n/m)) stages.
+int batch_segments(const lqr_handle* h, int nprob, const lqr_problem* probs, int i, long long total_T, int fixedK) {
+  const lqr_problem& p = probs[i];
+  const int lmin = min_segment_len(p.n, p.m);
+  const int kmax = (lmin > 0) ? p.T / lmin : p.T;
+  int K;
+  if (fixedK > 0) {
+    K = fixedK;
+  } else if (nprob >= h->num_sms) {
+    K = 1;
+  } else {
+    const double share = (double)p.T / (double)total_T;
+    K = (int)(2.0 * h->num_sms * share + 0.5);
+    const int by_len = p.T / (lmin > 16 ? lmin : 16);
+    if (K > by_len) K = by_len;
+  }
+  if (K > kmax) K = kmax;
+  if (K < 1) K = 1;
+  return K;
+}
+
+lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const lqr_opts* o,
+                       const lqr_solution* sols, int* segments_out, cudaStream_t st) {
+  long long total_T = 0;
+  int nmax = 0, mmax = 0;
+  for (int i = 0; i < nprob; ++i) {
+    total_T += probs[i].T;
+    if (probs[i].n > nmax) nmax = probs[i].n;
+    if (probs[i].m > mmax) mmax = probs[i].m;
+  }
+  const long long budget = h->smem_optin - kStaticSmemReserve;
+  const bool cons = (o->form == LQR_FORM_CONSTRAINED);
+  // pass 1: sizes
+  long long ws_total = 0, smem_max = 0;
+  int nunits = 0;
+  bool any_split = false;
+  struct Item { int K; long long off; long long scratch; };
+  Item* items = (Item*)malloc(sizeof(Item) * (size_t)nprob);
+  if (!items) return LQR_ERR_OOM;
+  for (int i = 0; i < nprob; ++i) {
+    const lqr_problem& p = probs[i];
+    const int K = batch_segments(h, nprob, probs, i, total_T, o->num_segments);
+    if (K > 1 && p.T / K < min_segment_len(p.n, p.m)) { free(items); return LQR_ERR_SEGMENT_INFEASIBLE; }
+    long long scratch = 0, smem = 0;
+    if (o->prec == LQR_FP64) smem = sweep_smem_needed<double, double>(p.n, p.m, budget, cons, &scratch);
+    else if (o->prec == LQR_MIXED_TF32) smem = sweep_smem_needed<double, float>(p.n, p.m, budget, cons, &scratch);
+    else smem = sweep_smem_needed<float, float>(p.n, p.m, budget, cons, &scratch);
+    if (smem > smem_max) smem_max = smem;
+    const WsLayout wl = ws_layout(p.n, K);
+    items[i].K = K;
+    items[i].off = ws_total;
+    items[i].scratch = scratch;
+    ws_total += ((wl.total + (long long)K * scratch) + 31) & ~31LL;
+    nunits += K;
+    if (K > 1) any_split = true;
+    if (segments_out) segments_out[i] = K;
+  }
+  lqr_status rs = grow(&h->ws, &h->ws_bytes, sizeof(double) * (size_t)ws_total + 256);
+  if (rs != LQR_OK) { free(items); return rs; }
+  // device table: descriptors | unit map | status (2 ints each) | report (4 doubles each)
+  const size_t desc_bytes = sizeof(ProbDesc) * (size_t)nprob;
+  const size_t unit_bytes = sizeof(int) * (size_t)nunits;
+  const size_t stat_off = (desc_bytes + unit_bytes + 255) & ~(size_t)255;
+  const size_t rep_off = (stat_off + sizeof(int) * 2 * (size_t)nprob + 255) & ~(size_t)255;
+  const size_t table_bytes = rep_off + sizeof(double) * 4 * (size_t)nprob;
+  rs = grow(&h->bdev, &h->bdev_bytes, table_bytes);
+  if (rs != LQR_OK) { free(items); return rs; }
+  if (h->bhost_bytes < desc_bytes + unit_bytes) {
+    if (h->bhost) { if (h->bhost_ev) cudaEventSynchronize(h->bhost_ev); cudaFreeHost(h->bhost); h->bhost = nullptr; }
+    const size_t sz = desc_bytes + unit_bytes + (1 << 16);
+    if (cudaMallocHost(&h->bhost, sz) != cudaSuccess) { cudaGetLastError(); h->bhost_bytes = 0; free(items); return LQR_ERR_OOM; }
+    h->bhost_bytes = sz;
+  }
+  if (!h->bhost_ev && cudaEventCreateWithFlags(&h->bhost_ev, cudaEventDisableTiming) != cudaSuccess) {
+    free(items);
+    return LQR_ERR_CUDA;
+  }
+  cudaEventSynchronize(h->bhost_ev);  // the previous batch's table has left the staging buffer
+  ProbDesc* hd = reinterpret_cast<ProbDesc*>(h->bhost);
+  int* hu = reinterpret_cast<int*>(h->bhost + desc_bytes);
+  double* wsb = reinterpret_cast<double*>(h->ws);
+  int* dstat = reinterpret_cast<int*>(h->bdev + stat_off);
+  double* drep = reinterpret_cast<double*>(h->bdev + rep_off);
+  int u = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const lqr_problem& p = probs[i];
+    const lqr_solution& so = sols[i];
+    ProbDesc d;
+    memset(&d, 0, sizeof(d));
+    d.A = p.A; d.B = p.B; d.c = p.c; d.Q = p.Q; d.R = p.R; d.S = p.S; d.q = p.q; d.r = p.r; d.x0 = p.x0;
+    d.K = so.K; d.k = so.k; d.x = so.x; d.u = so.u; d.P = so.P; d.p = so.p; d.lam = so.lam;
+    const WsLayout wl = ws_layout(p.n, items[i].K);
+    d.ws = wsb + items[i].off;
+    d.scratch = d.ws + wl.total;
+    d.scratch_per_unit = items[i].scratch;
+    d.status = dstat + 2 * i;
+    d.skip = nullptr;
+    d.report = drep + 4 * i;
+    d.n = p.n; d.m = p.m; d.T = p.T; d.nseg = items[i].K;
+    d.unit0 = u;
+    d.form = (int)o->form;
+    hd[i] = d;
+    for (int j = 0; j < items[i].K; ++j) hu[u++] = i;
+  }
+  free(items);
+  if (cudaMemcpyAsync(h->bdev, h->bhost, desc_bytes + unit_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return LQR_ERR_CUDA;
+  cudaEventRecord(h->bhost_ev, st);
+  if (cudaMemsetAsync(h->bdev + stat_off, 0, table_bytes - stat_off, st) != cudaSuccess) return LQR_ERR_CUDA;
+  ProbTable tab;
+  memset(&tab, 0, sizeof(tab));
+  tab.probs = reinterpret_cast<const ProbDesc*>(h->bdev);
+  tab.unit_prob = reinterpret_cast<const int*>(h->bdev + desc_bytes);
+  tab.nprob = nprob;
+  int launches = 0;
+  int store_P = 0;
+  bool want_traj = false, want_lam = false;
+  for (int i = 0; i < nprob; ++i) {
+    if (sols[i].P) store_P = 1;
+    if (sols[i].x || sols[i].u) want_traj = true;
+    if (sols[i].lam) want_lam = true;
+  }
+  cudaError_t e;
+  auto sweep = [&](int phase) {
+    if (o->prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, nunits, phase, smem_max, budget, store_P, st);
+    if (o->prec == LQR_MIXED_TF32)
+      return launch_seg_sweep<double, float>(tab, nunits, phase, smem_max, budget, store_P, st);
+    return launch_seg_sweep<float, float>(tab, nunits, phase, smem_max, budget, store_P, st);
+  };
+  prof_mark(h, LQR_PHASE_SWEEP, st);
+  e = sweep(0);
+  ++launches;
+  if (e != cudaSuccess) return LQR_ERR_CUDA;
+  prof_mark(h, LQR_PHASE_LINK, st);
+  const int x0f = (o->prec == LQR_FP32) ? 1 : 0;
+  e = cons ? cudaErrorNotSupported : launch_link_solve_dual_batched(tab, nprob, nmax, x0f, st);
+  if (cons) return LQR_ERR_UNSUPPORTED;
+  ++launches;
+  if (e != cudaSuccess) return LQR_ERR_CUDA;
+  prof_mark(h, LQR_PHASE_POLICY, st);
+  if (any_split) {
+    e = sweep(1);
+    ++launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+  }
+  prof_mark(h, LQR_PHASE_ROLLOUT, st);
+  if (want_traj) {
+    e = (o->prec == LQR_FP32) ? launch_rollout<float, float>(tab, nunits, want_lam ? 1 : 0, st, nmax, mmax)
+                              : launch_rollout<double, double>(tab, nunits, want_lam ? 1 : 0, st, nmax, mmax);
+    ++launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+    e = launch_finalize(tab, nprob, st);
+    ++launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+  }
+  prof_mark(h, LQR_PHASE_REFINE, st);
+  prof_mark(h, LQR_NUM_PHASES, st);
+  if (h->prof_on && h->prof_count < lqr_handle::kMaxProfiled) ++h->prof_count;
+  h->last_batch = nprob;
+  h->bstatus_off = stat_off;
+  h->breport_off = rep_off;
+  h->last_launches = launches;
+  h->last_K = nunits;
+  return LQR_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+lqr_status lqr_solve_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const lqr_opts* o,
+                             const lqr_solution* sols, int* segments, void* stream) {
+  if (!h || nprob < 1 || !probs || !o || !sols) return LQR_ERR_INVALID_ARG;
+  for (int i = 0; i < nprob; ++i) {
+    lqr_status v = validate(&probs[i], o, &sols[i]);
+    if (v != LQR_OK) return v;
+  }
+  if (o->max_refine > 0 || o->residual) return LQR_ERR_UNSUPPORTED;
+  if (o->form == LQR_FORM_CONSTRAINED) return LQR_ERR_UNSUPPORTED;
+  DeviceGuard g(h->device);
+  return run_batched(h, nprob, probs, o, sols, segments, static_cast<cudaStream_t>(stream));
+}
+
+lqr_status lqr_report_batched(lqr_handle* h, void* stream, int nprob, int* status, double* cost) {
+  if (!h || nprob < 1 || nprob > h->last_batch || !status) return LQR_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return LQR_ERR_CUDA;
+  int* tmp = (int*)malloc(sizeof(int) * 2 * (size_t)nprob);
+  double* rep = (double*)malloc(sizeof(double) * 4 * (size_t)nprob);
+  if (!tmp || !rep) { free(tmp); free(rep); return LQR_ERR_OOM; }
+  lqr_status r = LQR_OK;
+  if (cudaMemcpy(tmp, h->bdev + h->bstatus_off, sizeof(int) * 2 * (size_t)nprob, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(rep, h->bdev + h->breport_off, sizeof(double) * 4 * (size_t)nprob, cudaMemcpyDeviceToHost) != cudaSuccess)
+    r = LQR_ERR_CUDA;
+  else
+    for (int i = 0; i < nprob; ++i) {
+      status[i] = tmp[2 * i];
+      if (cost) cost[i] = rep[4 * i];
+    }
+  free(tmp);
+  free(rep);
+  return r;
+}
 
 lqr_status lqr_create(lqr_handle** out, int device, size_t workspace_hint) {
   if (!out) return LQR_ERR_INVALID_ARG;
@@ -355,6 +587,9 @@ lqr_status lqr_destroy(lqr_handle* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_report) cudaFree(h->d_report);
+  if (h->bdev) cudaFree(h->bdev);
+  if (h->bhost) cudaFreeHost(h->bhost);
+  if (h->bhost_ev) cudaEventDestroy(h->bhost_ev);
   if (h->ev_created)
     for (int i = 0; i < lqr_handle::kMaxProfiled; ++i)
       for (int k = 0; k <= lqr_handle::kPhases; ++k) cudaEventDestroy(h->ev[i][k]);

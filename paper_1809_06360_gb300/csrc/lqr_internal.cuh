@@ -173,6 +173,10 @@ __device__ __forceinline__ T* plan_ptr(const SweepPlan& P, int b, unsigned char*
   return reinterpret_cast<T*>(((P.smem_mask >> b) & 1u) ? smem + P.off[b] : scratch + P.off[b]);
 }
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit; one registry
+// for all launchers of the same kernel (lqr_api.cu).
+cudaError_t raise_dyn_smem(const void* func, size_t bytes);
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files, called by lqr_api.cu).
 // ---------------------------------------------------------------------------
@@ -187,7 +191,8 @@ cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, 
 cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
 
 template <typename TS, typename TC>
-cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st);
+cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st, int nmax = 0, int mmax = 0);
+cudaError_t launch_link_solve_dual_batched(const ProbTable& tab, int nprob, int nmax, int x0_is_float, cudaStream_t st);
 
 cudaError_t launch_finalize(const ProbTable& tab, int nprob, cudaStream_t st);
 

@@ -203,8 +203,8 @@ __global__ void finalize_kernel(ProbTable tab) {
 }
 
 template <typename TS, typename TC>
-cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st) {
-  const int nmax = tab.single.n, mmax = tab.single.m;
+cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st, int nmax_, int mmax_) {
+  const int nmax = nmax_ > 0 ? nmax_ : tab.single.n, mmax = mmax_ > 0 ? mmax_ : tab.single.m;
   const size_t bytes = sizeof(double) * (size_t)(3 * nmax + 2 * mmax);
   rollout_kernel<TS><<<nunits, kBlock, bytes, st>>>(tab, want_lam);
   return cudaGetLastError();
@@ -215,8 +215,8 @@ cudaError_t launch_finalize(const ProbTable& tab, int nprob, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_rollout<double, double>(const ProbTable&, int, int, cudaStream_t);
-template cudaError_t launch_rollout<float, float>(const ProbTable&, int, int, cudaStream_t);
-template cudaError_t launch_rollout<double, float>(const ProbTable&, int, int, cudaStream_t);
+template cudaError_t launch_rollout<double, double>(const ProbTable&, int, int, cudaStream_t, int, int);
+template cudaError_t launch_rollout<float, float>(const ProbTable&, int, int, cudaStream_t, int, int);
+template cudaError_t launch_rollout<double, float>(const ProbTable&, int, int, cudaStream_t, int, int);
 
 }  // namespace lqr

@@ -458,13 +458,8 @@ long long sweep_smem_needed(int n, int m, long long smem_budget, bool constraine
 template <typename TS, typename TC>
 cudaError_t launch_seg_sweep(const ProbTable& tab, int nunits, int phase, long long smem_bytes,
                              long long smem_budget, int store_P, cudaStream_t st) {
-  static int configured_bytes = -1;  // per template instance
-  if (configured_bytes < (int)smem_bytes) {  // dynamic + static may pass 48 KB even below 48 KB dynamic
-    cudaError_t e = cudaFuncSetAttribute(seg_sweep_kernel<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    configured_bytes = (int)smem_bytes;
-  }
+  cudaError_t e = raise_dyn_smem((const void*)seg_sweep_kernel<TS, TC>, (size_t)smem_bytes);
+  if (e != cudaSuccess) return e;
   seg_sweep_kernel<TS, TC><<<nunits, kBlock, (size_t)smem_bytes, st>>>(tab, phase, smem_budget, store_P);
   return cudaGetLastError();
 }

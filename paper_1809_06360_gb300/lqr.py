@@ -27,7 +27,7 @@ SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
 # Exported symbols declared in include/lqr.h
 EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
-           "lqr_profile_enable", "lqr_profile_read")
+           "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -84,9 +84,12 @@ def load(path: str | None = None):
     lib.lqr_last_launch_count.argtypes = [c_void_p]
     lib.lqr_profile_enable.argtypes = [c_void_p, c_int]
     lib.lqr_profile_read.argtypes = [c_void_p, P(c_double), P(c_int)]
+    lib.lqr_solve_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution), P(c_int),
+                                      c_void_p]
+    lib.lqr_report_batched.argtypes = [c_void_p, c_void_p, c_int, P(c_int), P(c_double)]
     for name in ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
-                 "lqr_profile_read"):
+                 "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -144,6 +147,23 @@ def lqr_status_string(status: int) -> str:
 
 def lqr_last_launch_count(h: int) -> int:
     return load().lqr_last_launch_count(h)
+
+
+def lqr_solve_batched(h: int, probs, opts: lqr_opts, sols, stream: int | None) -> list[int]:
+    n = len(probs)
+    parr = (lqr_problem * n)(*probs)
+    sarr = (lqr_solution * n)(*sols)
+    seg = (c_int * n)()
+    _check(load().lqr_solve_batched(h, n, parr, ctypes.byref(opts), sarr, seg, stream or None),
+           "lqr_solve_batched")
+    return list(seg)
+
+
+def lqr_report_batched(h: int, stream: int | None, nprob: int):
+    st = (c_int * nprob)()
+    cost = (c_double * nprob)()
+    _check(load().lqr_report_batched(h, stream or None, nprob, st, cost), "lqr_report_batched")
+    return list(st), list(cost)
 
 
 def lqr_profile_enable(h: int, enable: bool) -> None:
@@ -229,6 +249,23 @@ class Solver:
 
     def report(self, stream=None) -> dict:
         return lqr_report(self.h, self._stream(stream))
+
+    def solve_batched(self, probs, prec="fp32", num_segments=0, outs=None, want=("K", "k", "x", "u", "lam"),
+                      stream=None):
+        """Solve a list of problems (dicts of device tensors, uneven n, m, T) in one batched call.
+        Returns (outputs per problem, segment count per problem)."""
+        if outs is None:
+            outs = [self.alloc_solution(p, want) for p in probs]
+        ptr = lambda t: t.data_ptr()
+        ps = [self.make_problem_struct(p, ptr) for p in probs]
+        ss = [lqr_solution(**{f: (o[f].data_ptr() if f in o else None) for f in SOLUTION_FIELDS}) for o in outs]
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=0, residual=0)
+        seg = lqr_solve_batched(self.h, ps, o, ss, self._stream(stream))
+        return outs, seg
+
+    def report_batched(self, nprob, stream=None):
+        return lqr_report_batched(self.h, self._stream(stream), nprob)
 
     def segment_summaries(self, prob, num_segments, prec="fp64", stream=None, form="multiplier"):
         torch = _torch()
