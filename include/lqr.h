@@ -176,6 +176,28 @@ lqr_status lqr_solve_batched(lqr_handle *h, int nprob, const lqr_problem *probs,
  * entries; cost may be NULL). */
 lqr_status lqr_report_batched(lqr_handle *h, void *stream, int nprob, int *status, double *cost);
 
+/* Gradients of a scalar loss L(x, u) of the optimal trajectory with respect to
+ * every problem datum (implicit function theorem on the KKT system of Eq. 3;
+ * the KKT matrix is symmetric, so its transpose solve is one more
+ * segment-parallel Riccati solve with the same matrices and the linear costs
+ * -dL/dx, -dL/du, c = 0, x0 = 0, recomputing the segment value functions).
+ * prob: the forward problem; sol: its solution (x, u, lam required, from
+ * lqr_solve with the same opts); grad_x [T+1][n] = dL/dx, grad_u [T][m] = dL/du
+ * (device; NULL = 0). grads: device output arrays laid out like the problem
+ * (A..x0, n/m/T equal to prob's; any pointer NULL = not wanted), receiving
+ * dL/dA ... dL/dx0; dL/dQ and dL/dR are symmetric (Q and R enter symmetrised).
+ * Asynchronous on `stream`; the handle's status covers the adjoint solve. */
+lqr_status lqr_backward(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts,
+                        const lqr_solution *sol, const void *grad_x, const void *grad_u,
+                        const lqr_problem *grads, void *stream);
+
+/* lqr_backward for a batch (host arrays of nprob entries; grad_x / grad_u are
+ * host arrays of device pointers, or NULL). The adjoint solves run as one
+ * batched solve; per-problem status through lqr_report_batched. */
+lqr_status lqr_backward_batched(lqr_handle *h, int nprob, const lqr_problem *probs, const lqr_opts *opts,
+                                const lqr_solution *sols, const void *const *grad_x,
+                                const void *const *grad_u, const lqr_problem *grads, void *stream);
+
 /* Step A1 alone: the per-segment parametric backward sweeps (Section II-B,
  * Eq. 9-16). Writes K summaries of LQR_SUMMARY_DOUBLES(n) doubles each to the
  * device array `summaries` (FP64). */

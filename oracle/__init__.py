@@ -289,3 +289,63 @@ def rel_err(a, ref) -> float:
     den = np.abs(ref).max()
     num = np.abs(a - ref).max()
     return float(num / den) if den > 0 else float(num)
+
+
+# ---------------------------------------------------------------------------
+# Gradients of a loss of the optimal trajectory (brute force references)
+# ---------------------------------------------------------------------------
+
+def kkt_implicit_gradient(prob: dict, gx, gu) -> dict:
+    """dL/dtheta for every datum theta, where L has gradients gx = dL/dx
+    ((T+1) x n) and gu = dL/du (T x m) at the optimum, by differentiating the
+    KKT system of Eq. 3 entry by entry: the assembly is linear in the data, so
+    d(KKT)/dtheta_e and d(rhs)/dtheta_e are the assembly of the unit change of
+    theta_e (exactly), and dw/dtheta_e = -KKT^{-1} (dKKT w - drhs).
+    Tiny problems only (one assembly per entry)."""
+    import scipy.linalg
+    base = dense_kkt(prob)
+    Kmat, rhs = base["kkt"], base["rhs"]
+    lu = scipy.linalg.lu_factor(Kmat)
+    w = scipy.linalg.lu_solve(lu, rhs)
+    n, m, T = _dims(prob)
+    nw = (T + 1) * n + T * m
+    g = np.zeros(Kmat.shape[0])
+    g[:(T + 1) * n] = np.asarray(gx).ravel()
+    g[(T + 1) * n:nw] = np.asarray(gu).ravel()
+    out = {}
+    for key in ("A", "B", "c", "Q", "R", "S", "q", "r", "x0"):
+        arr = prob[key]
+        grad = np.zeros_like(arr)
+        flat = grad.reshape(-1)
+        for e in range(arr.size):
+            pert = {k: v.copy() for k, v in prob.items()}
+            pert[key].reshape(-1)[e] += 1.0
+            pk = dense_kkt(pert)
+            dK = pk["kkt"] - Kmat
+            db = pk["rhs"] - rhs
+            dw = -scipy.linalg.lu_solve(lu, dK @ w - db)
+            flat[e] = g @ dw
+        out[key] = grad
+    return out
+
+
+def fd_gradient(prob: dict, loss, keys=None, h: float = 1e-6, entries: int | None = None, seed: int = 0) -> dict:
+    """Central finite differences (step h) of loss(riccati(prob)) with the
+    serial C oracle; loss maps the oracle's output dict to a float. With
+    `entries`, only that many randomly chosen entries per array are perturbed
+    (the others are NaN)."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for key in keys or ("A", "B", "c", "Q", "R", "S", "q", "r", "x0"):
+        arr = prob[key]
+        grad = np.full(arr.shape, np.nan)
+        idx = np.arange(arr.size) if entries is None else rng.choice(arr.size, size=min(entries, arr.size),
+                                                                       replace=False)
+        for e in idx:
+            p1 = {k: v.copy() for k, v in prob.items()}
+            p2 = {k: v.copy() for k, v in prob.items()}
+            p1[key].reshape(-1)[e] += h
+            p2[key].reshape(-1)[e] -= h
+            grad.reshape(-1)[e] = (loss(riccati(p1)) - loss(riccati(p2))) / (2 * h)
+        out[key] = grad
+    return out

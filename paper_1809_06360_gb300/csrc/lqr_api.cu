@@ -49,6 +49,8 @@ struct lqr_handle {
   unsigned char* bhost = nullptr;  // pinned
   size_t bhost_bytes = 0;
   cudaEvent_t bhost_ev = nullptr;  // last copy out of bhost
+  unsigned char* adj = nullptr;    // adjoint problems' vectors and solutions
+  size_t adj_bytes = 0;
   int last_batch = 0;
   size_t bstatus_off = 0, breport_off = 0;
   // phase profiling: one event pair per phase per solve, summed on read
@@ -320,9 +322,11 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
         return LQR_ERR_CUDA;
       ++launches;
     }
-    // final residual and objective of the returned solution
-    if (launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st) != cudaSuccess)
-      return LQR_ERR_CUDA;
+    // final residual and objective of the returned solution (in the data's element type)
+    const cudaError_t er = (o->prec == LQR_FP32)
+        ? launch_kkt_residual<float>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st)
+        : launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    if (er != cudaSuccess) return LQR_ERR_CUDA;
     if (launch_residual_finalize(main, acc, o->tol, nullptr, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
         cudaSuccess)
       return LQR_ERR_CUDA;
@@ -509,9 +513,119 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
   return LQR_OK;
 }
 
+// Per-problem adjoint buffers (element size es): q~ r~ c~ x0~ | K~ k~ xi_x xi_u xi_l.
+struct AdjLayout { size_t q, r, c, x0, K, k, x, u, l, total; };
+AdjLayout adj_layout(size_t base, int n, int m, int T, size_t es) {
+  AdjLayout a;
+  size_t o = base;
+  auto take = [&](size_t elems) { size_t r = o; o += (elems * es + 255) & ~(size_t)255; return r; };
+  a.q = take((size_t)(T + 1) * n); a.r = take((size_t)T * m); a.c = take((size_t)T * n); a.x0 = take(n);
+  a.K = take((size_t)T * m * n); a.k = take((size_t)T * m); a.x = take((size_t)(T + 1) * n);
+  a.u = take((size_t)T * m); a.l = take((size_t)(T + 1) * n);
+  a.total = o - base;
+  return a;
+}
+
+lqr_status validate_backward(const lqr_problem* p, const lqr_opts* o, const lqr_solution* s, const lqr_problem* g) {
+  if (!g) return LQR_ERR_INVALID_ARG;
+  if (!s || !s->x || !s->u || !s->lam) return LQR_ERR_INVALID_ARG;
+  lqr_solution none;
+  memset(&none, 0, sizeof(none));
+  lqr_status v = validate(p, o, &none);
+  if (v != LQR_OK) return v;
+  if (g->n != p->n || g->m != p->m || g->T != p->T) return LQR_ERR_INVALID_ARG;
+  return LQR_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+lqr_status lqr_backward(lqr_handle* h, const lqr_problem* prob, const lqr_opts* opts, const lqr_solution* sol,
+                        const void* grad_x, const void* grad_u, const lqr_problem* grads, void* stream) {
+  if (!h) return LQR_ERR_INVALID_ARG;
+  lqr_status v = validate_backward(prob, opts, sol, grads);
+  if (v != LQR_OK) return v;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  size_t es = 0;
+  elem_size(opts->prec, &es);
+  const int n = prob->n, m = prob->m, T = prob->T;
+  const AdjLayout al = adj_layout(0, n, m, T, es);
+  lqr_status r = grow(&h->adj, &h->adj_bytes, al.total);
+  if (r != LQR_OK) return r;
+  unsigned char* b = h->adj;
+  cudaError_t e = (es == 8) ? launch_adjoint_rhs<double>(n, m, T, grad_x, grad_u, b + al.q, b + al.r, b + al.c, b + al.x0, st)
+                            : launch_adjoint_rhs<float>(n, m, T, grad_x, grad_u, b + al.q, b + al.r, b + al.c, b + al.x0, st);
+  if (e != cudaSuccess) return LQR_ERR_CUDA;
+  lqr_problem ap = *prob;
+  ap.q = b + al.q; ap.r = b + al.r; ap.c = b + al.c; ap.x0 = b + al.x0;
+  lqr_solution as;
+  memset(&as, 0, sizeof(as));
+  as.K = b + al.K; as.k = b + al.k; as.x = b + al.x; as.u = b + al.u; as.lam = b + al.l;
+  r = run_solve(h, &ap, opts, &as, st, false, nullptr);
+  if (r != LQR_OK) return r;
+  e = (es == 8) ? launch_adjoint_grad<double>(n, m, T, sol->x, sol->u, sol->lam, b + al.x, b + al.u, b + al.l, grads, st)
+                : launch_adjoint_grad<float>(n, m, T, sol->x, sol->u, sol->lam, b + al.x, b + al.u, b + al.l, grads, st);
+  if (e != cudaSuccess) return LQR_ERR_CUDA;
+  h->last_launches += 2;
+  return LQR_OK;
+}
+
+lqr_status lqr_backward_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const lqr_opts* opts,
+                                const lqr_solution* sols, const void* const* grad_x, const void* const* grad_u,
+                                const lqr_problem* grads, void* stream) {
+  if (!h || nprob < 1 || !probs || !opts || !sols || !grads) return LQR_ERR_INVALID_ARG;
+  if (opts->max_refine > 0 || opts->residual || opts->form == LQR_FORM_CONSTRAINED) return LQR_ERR_UNSUPPORTED;
+  for (int i = 0; i < nprob; ++i) {
+    lqr_status v = validate_backward(&probs[i], opts, &sols[i], &grads[i]);
+    if (v != LQR_OK) return v;
+  }
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  size_t es = 0;
+  elem_size(opts->prec, &es);
+  size_t total = 0;
+  for (int i = 0; i < nprob; ++i) total += adj_layout(0, probs[i].n, probs[i].m, probs[i].T, es).total;
+  lqr_status r = grow(&h->adj, &h->adj_bytes, total);
+  if (r != LQR_OK) return r;
+  lqr_problem* ap = (lqr_problem*)malloc(sizeof(lqr_problem) * (size_t)nprob);
+  lqr_solution* as = (lqr_solution*)malloc(sizeof(lqr_solution) * (size_t)nprob);
+  if (!ap || !as) { free(ap); free(as); return LQR_ERR_OOM; }
+  size_t off = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const lqr_problem& p = probs[i];
+    const AdjLayout al = adj_layout(off, p.n, p.m, p.T, es);
+    off += al.total;
+    unsigned char* b = h->adj;
+    cudaError_t e = (es == 8)
+        ? launch_adjoint_rhs<double>(p.n, p.m, p.T, grad_x ? grad_x[i] : nullptr, grad_u ? grad_u[i] : nullptr,
+                                     b + al.q, b + al.r, b + al.c, b + al.x0, st)
+        : launch_adjoint_rhs<float>(p.n, p.m, p.T, grad_x ? grad_x[i] : nullptr, grad_u ? grad_u[i] : nullptr,
+                                    b + al.q, b + al.r, b + al.c, b + al.x0, st);
+    if (e != cudaSuccess) { free(ap); free(as); return LQR_ERR_CUDA; }
+    ap[i] = p;
+    ap[i].q = b + al.q; ap[i].r = b + al.r; ap[i].c = b + al.c; ap[i].x0 = b + al.x0;
+    memset(&as[i], 0, sizeof(lqr_solution));
+    as[i].K = b + al.K; as[i].k = b + al.k; as[i].x = b + al.x; as[i].u = b + al.u; as[i].lam = b + al.l;
+  }
+  r = run_batched(h, nprob, ap, opts, as, nullptr, st);
+  if (r == LQR_OK) {
+    for (int i = 0; i < nprob; ++i) {
+      const lqr_problem& p = probs[i];
+      cudaError_t e = (es == 8)
+          ? launch_adjoint_grad<double>(p.n, p.m, p.T, sols[i].x, sols[i].u, sols[i].lam, as[i].x, as[i].u, as[i].lam,
+                                        &grads[i], st)
+          : launch_adjoint_grad<float>(p.n, p.m, p.T, sols[i].x, sols[i].u, sols[i].lam, as[i].x, as[i].u, as[i].lam,
+                                       &grads[i], st);
+      if (e != cudaSuccess) { r = LQR_ERR_CUDA; break; }
+    }
+  }
+  free(ap);
+  free(as);
+  return r;
+}
+
 
 lqr_status lqr_solve_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const lqr_opts* o,
                              const lqr_solution* sols, int* segments, void* stream) {
@@ -588,6 +702,7 @@ lqr_status lqr_destroy(lqr_handle* h) {
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_report) cudaFree(h->d_report);
   if (h->bdev) cudaFree(h->bdev);
+  if (h->adj) cudaFree(h->adj);
   if (h->bhost) cudaFreeHost(h->bhost);
   if (h->bhost_ev) cudaEventDestroy(h->bhost_ev);
   if (h->ev_created)

@@ -196,6 +196,14 @@ cudaError_t launch_link_solve_dual_batched(const ProbTable& tab, int nprob, int 
 
 cudaError_t launch_finalize(const ProbTable& tab, int nprob, cudaStream_t st);
 
+// adjoint (adjoint.cu)
+template <typename TS>
+cudaError_t launch_adjoint_rhs(int n, int m, int T, const void* gx, const void* gu, void* q, void* r, void* c,
+                               void* x0, cudaStream_t st);
+template <typename TS>
+cudaError_t launch_adjoint_grad(int n, int m, int T, const void* x, const void* u, const void* lam, const void* xix,
+                                const void* xiu, const void* xil, const lqr_problem* g, cudaStream_t st);
+
 // refinement (refine.cu)
 constexpr int kResidAccDoubles = 8 + 4 * 152;
 template <typename TS>

@@ -27,7 +27,8 @@ SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
 # Exported symbols declared in include/lqr.h
 EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
-           "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched")
+           "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
+           "lqr_backward", "lqr_backward_batched")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -87,9 +88,14 @@ def load(path: str | None = None):
     lib.lqr_solve_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution), P(c_int),
                                       c_void_p]
     lib.lqr_report_batched.argtypes = [c_void_p, c_void_p, c_int, P(c_int), P(c_double)]
+    lib.lqr_backward.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p, c_void_p,
+                                 P(lqr_problem), c_void_p]
+    lib.lqr_backward_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution),
+                                         P(c_void_p), P(c_void_p), P(lqr_problem), c_void_p]
     for name in ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
-                 "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched"):
+                 "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
+                 "lqr_backward_batched"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -164,6 +170,23 @@ def lqr_report_batched(h: int, stream: int | None, nprob: int):
     cost = (c_double * nprob)()
     _check(load().lqr_report_batched(h, stream or None, nprob, st, cost), "lqr_report_batched")
     return list(st), list(cost)
+
+
+def lqr_backward(h: int, prob: lqr_problem, opts: lqr_opts, sol: lqr_solution, gx: int | None, gu: int | None,
+                 grads: lqr_problem, stream: int | None) -> None:
+    _check(load().lqr_backward(h, ctypes.byref(prob), ctypes.byref(opts), ctypes.byref(sol), gx, gu,
+                               ctypes.byref(grads), stream or None), "lqr_backward")
+
+
+def lqr_backward_batched(h: int, probs, opts: lqr_opts, sols, gxs, gus, grads, stream: int | None) -> None:
+    n = len(probs)
+    parr = (lqr_problem * n)(*probs)
+    sarr = (lqr_solution * n)(*sols)
+    garr = (lqr_problem * n)(*grads)
+    gx = (c_void_p * n)(*gxs)
+    gu = (c_void_p * n)(*gus)
+    _check(load().lqr_backward_batched(h, n, parr, ctypes.byref(opts), sarr, gx, gu, garr, stream or None),
+           "lqr_backward_batched")
 
 
 def lqr_profile_enable(h: int, enable: bool) -> None:
@@ -266,6 +289,40 @@ class Solver:
 
     def report_batched(self, nprob, stream=None):
         return lqr_report_batched(self.h, self._stream(stream), nprob)
+
+    @staticmethod
+    def _alloc_grads(prob):
+        torch = _torch()
+        return {k: torch.empty_like(prob[k]) if prob.get(k) is not None else
+                torch.zeros((prob["B"].shape[0], prob["B"].shape[2], prob["B"].shape[1]), dtype=prob["A"].dtype,
+                            device=prob["A"].device) for k in PROBLEM_FIELDS}
+
+    def backward(self, prob, sol, grad_x=None, grad_u=None, num_segments=0, prec="fp64", stream=None,
+                 form="multiplier"):
+        """dL/d(problem data) for upstream gradients dL/dx, dL/du (device tensors or None)."""
+        grads = self._alloc_grads(prob)
+        ptr = lambda t: t.data_ptr()
+        p = self.make_problem_struct(prob, ptr)
+        g = self.make_problem_struct(grads, ptr)
+        so = lqr_solution(**{f: (sol[f].data_ptr() if f in sol else None) for f in SOLUTION_FIELDS})
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=FORM[form], residual=0)
+        lqr_backward(self.h, p, o, so, grad_x.data_ptr() if grad_x is not None else None,
+                     grad_u.data_ptr() if grad_u is not None else None, g, self._stream(stream))
+        return grads
+
+    def backward_batched(self, probs, sols, grads_x, grads_u, prec="fp32", num_segments=0, stream=None):
+        ptr = lambda t: t.data_ptr()
+        grads = [self._alloc_grads(p) for p in probs]
+        ps = [self.make_problem_struct(p, ptr) for p in probs]
+        gs = [self.make_problem_struct(g, ptr) for g in grads]
+        ss = [lqr_solution(**{f: (s[f].data_ptr() if f in s else None) for f in SOLUTION_FIELDS}) for s in sols]
+        o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=0, residual=0)
+        gx = [t.data_ptr() if t is not None else None for t in grads_x]
+        gu = [t.data_ptr() if t is not None else None for t in grads_u]
+        lqr_backward_batched(self.h, ps, o, ss, gx, gu, gs, self._stream(stream))
+        return grads
 
     def segment_summaries(self, prob, num_segments, prec="fp64", stream=None, form="multiplier"):
         torch = _torch()
