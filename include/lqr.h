@@ -61,7 +61,8 @@ typedef enum {
   LQR_ERR_TIMEOUT = 6,            /* a bounded device wait ran out                         */
   LQR_ERR_CUDA = 7,               /* a CUDA runtime call failed                            */
   LQR_ERR_OOM = 8,                /* workspace allocation failed                           */
-  LQR_ERR_UNSUPPORTED = 9         /* valid request this build does not implement           */
+  LQR_ERR_UNSUPPORTED = 9,        /* valid request this build does not implement           */
+  LQR_ERR_CAPACITY = 10           /* larger than a fixed-capacity entry point accepts      */
 } lqr_status;
 
 typedef enum {
@@ -197,6 +198,30 @@ lqr_status lqr_backward(lqr_handle *h, const lqr_problem *prob, const lqr_opts *
 lqr_status lqr_backward_batched(lqr_handle *h, int nprob, const lqr_problem *probs, const lqr_opts *opts,
                                 const lqr_solution *sols, const void *const *grad_x,
                                 const void *const *grad_u, const lqr_problem *grads, void *stream);
+
+/* KKT residual of a given solution with NO device allocation. The paper has
+ * no counterpart: this serves callers that may not allocate device memory
+ * once running, such as hard real-time control loops (a model-predictive
+ * controller whose cycle budget forbids cudaMalloc after start-up) and code
+ * executing inside another framework's stream capture, and that hold no
+ * liblqr handle (a handle owns a growable workspace).
+ * Computes, for the solution sol (x, u, lam required) of prob, the same
+ * quantities lqr_solve reports with opts.residual = 1: out[0] = normwise
+ * backward error eta, out[1] = |KKT w - b|_inf / |b|_inf, out[2] = objective
+ * J along (x, u). out is a caller-allocated DEVICE buffer of 3 doubles; prec
+ * gives the element type of the data (float for LQR_FP32, else double).
+ * Scratch memory is a fixed file-scope device array of
+ * LQR_NOALLOC_MAX_STAGES + 9 doubles (about 512 KB) that every GPU loading the
+ * library holds until exit; problems with T > LQR_NOALLOC_MAX_STAGES are
+ * rejected with LQR_ERR_CAPACITY. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. The call only enqueues a
+ * memset of the array's reduction slots and one kernel on `stream`. All calls
+ * share the array, so calls whose executions overlap on the GPU (different
+ * streams, or different host threads) race: serialise them. */
+#define LQR_NOALLOC_MAX_STAGES 65536
+lqr_status lqr_kkt_residual_noalloc(const lqr_problem *prob, const lqr_solution *sol, lqr_precision prec,
+                                    double *out, void *stream);
 
 /* Step A1 alone: the per-segment parametric backward sweeps (Section II-B,
  * Eq. 9-16). Writes K summaries of LQR_SUMMARY_DOUBLES(n) doubles each to the

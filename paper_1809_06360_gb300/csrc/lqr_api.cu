@@ -835,6 +835,7 @@ const char* lqr_status_string(lqr_status s) {
     case LQR_ERR_CUDA: return "CUDA runtime error";
     case LQR_ERR_OOM: return "out of device memory";
     case LQR_ERR_UNSUPPORTED: return "unsupported request";
+    case LQR_ERR_CAPACITY: return "problem exceeds the fixed capacity of this entry point";
   }
   return "unknown status";
 }

@@ -17,7 +17,8 @@ c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_vo
 LQR_OK = 0
 STATUS_NAMES = {0: "LQR_OK", 1: "LQR_ERR_INVALID_ARG", 2: "LQR_ERR_NOT_PD", 3: "LQR_ERR_SEGMENT_INFEASIBLE",
                 4: "LQR_ERR_NONFINITE", 5: "LQR_ERR_NO_CONVERGENCE", 6: "LQR_ERR_TIMEOUT", 7: "LQR_ERR_CUDA",
-                8: "LQR_ERR_OOM", 9: "LQR_ERR_UNSUPPORTED"}
+                8: "LQR_ERR_OOM", 9: "LQR_ERR_UNSUPPORTED", 10: "LQR_ERR_CAPACITY"}
+NOALLOC_MAX_STAGES = 65536
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tf32": 2, "mixed_bf16": 3}
 FORM = {"multiplier": 0, "constrained": 1}
 
@@ -28,7 +29,7 @@ SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
 EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
-           "lqr_backward", "lqr_backward_batched")
+           "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -88,6 +89,7 @@ def load(path: str | None = None):
     lib.lqr_solve_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution), P(c_int),
                                       c_void_p]
     lib.lqr_report_batched.argtypes = [c_void_p, c_void_p, c_int, P(c_int), P(c_double)]
+    lib.lqr_kkt_residual_noalloc.argtypes = [P(lqr_problem), P(lqr_solution), c_int, c_void_p, c_void_p]
     lib.lqr_backward.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p, c_void_p,
                                  P(lqr_problem), c_void_p]
     lib.lqr_backward_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution),
@@ -95,7 +97,7 @@ def load(path: str | None = None):
     for name in ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
-                 "lqr_backward_batched"):
+                 "lqr_backward_batched", "lqr_kkt_residual_noalloc"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -170,6 +172,13 @@ def lqr_report_batched(h: int, stream: int | None, nprob: int):
     cost = (c_double * nprob)()
     _check(load().lqr_report_batched(h, stream or None, nprob, st, cost), "lqr_report_batched")
     return list(st), list(cost)
+
+
+def lqr_kkt_residual_noalloc(prob: lqr_problem, sol: lqr_solution, prec: int, out_ptr: int,
+                             stream: int | None) -> None:
+    """KKT residual (eta, rel, objective) into a caller-owned device buffer of 3 doubles; no allocation."""
+    _check(load().lqr_kkt_residual_noalloc(ctypes.byref(prob), ctypes.byref(sol), prec, out_ptr, stream or None),
+           "lqr_kkt_residual_noalloc")
 
 
 def lqr_backward(h: int, prob: lqr_problem, opts: lqr_opts, sol: lqr_solution, gx: int | None, gu: int | None,
