@@ -39,6 +39,20 @@ PEAK_FP64_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12      # 1.259
 PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 80.5
 
 
+def link_flops(n: int, K: int) -> float:
+    """Algorithmic FP64 flops of one launch of the link solve (dual form): per
+    link two n x n factorisations (n^3/3 each), W C, C'Z, C'(W C), L^-1 E, F'F,
+    L^-T F (n^3 each, triangular or symmetric halves) and (W C) G (2n^3)."""
+    return (K - 1) * (2 * n ** 3 / 3 + 6 * n ** 3 + 2 * n ** 3)
+
+
+def rollout_bytes(n: int, m: int, T: int, es: int) -> float:
+    """Algorithmic bytes of one rollout launch: per stage it reads K, k, A, B, c,
+    Q, R, S, q, r (twice A, Q, S for the multipliers) and writes x, u, lambda."""
+    per = (m * n + m + 2 * n * n + n * m + n + 2 * n * n + m * m + 2 * m * n + n + m) + (n + m + n)
+    return T * per * es
+
+
 def sweep_flops(n: int, m: int, T: int, K: int, phase: str) -> float:
     """Algorithmic FLOPs of one launch of a segment-sweep kernel.
 
@@ -179,12 +193,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--segments", type=int, default=64)
     ap.add_argument("--form", default="multiplier", choices=["multiplier", "constrained"])
     ap.add_argument("--T", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--fp64-segments", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -208,8 +224,8 @@ def main():
 
     n, m, T, K = 64, 32, args.T, args.segments
     prob_np = workloads.config1(T)
-    dt = torch.float64 if args.prec == "fp64" else torch.float32
-    npdt = np.float64 if args.prec == "fp64" else np.float32
+    dt = torch.float32 if args.prec == "fp32" else torch.float64
+    npdt = np.float32 if args.prec == "fp32" else np.float64
     dev = {k: torch.from_numpy(v).to(f"cuda:{local}", dt) for k, v in prob_np.items()}
     solver = lqr.Solver(local)
     out = solver.alloc_solution(dev, want=("K", "k", "x", "u", "lam"))
@@ -225,10 +241,11 @@ def main():
         raise SystemExit("solve failed: %s" % rep)
     launches_per_step = lqr.lqr_last_launch_count(solver.h)
 
-    # KKT backward error of the benchmarked solution (FP64, host, once, outside the timing)
-    import oracle
-    res = oracle.kkt_residual(prob_np, out["x"].double().cpu().numpy(), out["u"].double().cpu().numpy(),
-                              out["lam"].double().cpu().numpy())
+    # KKT residual of the benchmarked solution, by the library's own FP64 residual
+    # pass (step A7), once, outside the timing
+    solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form, residual=True)
+    rep_res = solver.report()
+    res = {"eta": rep_res["kkt_residual"], "rel": rep_res["kkt_rel"]}
 
     clocks = ClockSampler(local)
     if world > 1:
@@ -256,17 +273,63 @@ def main():
         ms = float(t.item())
     value = world * args.steps * T / (ms / 1e3)
 
-    # dominant kernel: the parametric segment sweep (step A1)
-    sweep_ms = phase_ms["sweep"] / max(nprof, 1)
-    flops = sweep_flops(n, m, T, K, "sweep")
-    achieved = flops / (sweep_ms / 1e3) / 1e12
-    peak = PEAK_FP64_TFLOPS if args.prec == "fp64" else PEAK_FP32_TFLOPS
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
-                "kernel": "seg_sweep_kernel (A1, %s)" % args.prec,
-                "peak_source": "derived: 152 SMs x %s/clk x 2070 MHz" % ("2 DFMA" if args.prec == "fp64" else
-                                                                          "128 FFMA"),
-                "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phase_ms.items()}}
+    # per-phase achieved rates; the roofline entry is the phase that takes the most time
+    nsolve = max(nprof, 1)
+    ph = {k: v / nsolve for k, v in phase_ms.items()}
+    fp64_pipe = args.prec == "fp64"
+    alu_peak = PEAK_FP64_TFLOPS if fp64_pipe else PEAK_FP32_TFLOPS
+    es = 4 if args.prec == "fp32" else 8
+    hbm = measured_peaks().get("hbm_gbs", 6780.4)
+    phases = {
+        "sweep": {"kernel": "seg_sweep_kernel phase 0 (A1)", "bound": "alu", "unit": "TFLOP/s",
+                  "work": sweep_flops(n, m, T, K, "sweep"), "peak": alu_peak},
+        "policy": {"kernel": "seg_sweep_kernel phase 1 (A4)", "bound": "alu", "unit": "TFLOP/s",
+                   "work": sweep_flops(n, m, T, K, "policy"), "peak": alu_peak},
+        "link": {"kernel": "link_solve_dual_cluster_kernel<16> (A3, FP64)", "bound": "alu", "unit": "TFLOP/s",
+                 "work": link_flops(n, K), "peak": PEAK_FP64_TFLOPS},
+        "rollout": {"kernel": "rollout_kernel + finalize (A5/A6)", "bound": "hbm", "unit": "GB/s",
+                    "work": rollout_bytes(n, m, T, es), "peak": hbm},
+    }
+    for k, d in phases.items():
+        t = ph.get(k, 0.0)
+        scale = 1e12 if d["unit"] == "TFLOP/s" else 1e9
+        d["ms"] = t
+        d["achieved"] = (d["work"] / (t / 1e3) / scale) if t > 0 else 0.0
+        d["frac"] = d["achieved"] / d["peak"]
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    dd = phases[dom]
+    roofline = {"bound": dd["bound"], "achieved": dd["achieved"], "peak": dd["peak"], "unit": dd["unit"],
+                "frac": dd["frac"], "traffic": None, "kernel": dd["kernel"],
+                "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2070 MHz" if dd["peak"] == PEAK_FP64_TFLOPS else
+                                "derived: 152 SMs x 128 FFMA/clk x 2070 MHz" if dd["peak"] == PEAK_FP32_TFLOPS else
+                                "measured (MEASURED_PEAKS.json hbm_gbs)"),
+                "phases": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in d.items()}
+                           for k, d in phases.items()},
+                "phase_ms_per_step": ph}
+
+    # the plain FP64 segment-parallel solve of the same workload on the same GPU
+    fp64_ref = None
+    if not args.no_fp64_ref and args.prec != "fp64":
+        dev64 = {k: torch.from_numpy(v).to(f"cuda:{local}", torch.float64) for k, v in prob_np.items()}
+        out64 = solver.alloc_solution(dev64, want=("K", "k", "x", "u", "lam"))
+        for _ in range(2):
+            solver.solve(dev64, num_segments=args.fp64_segments, prec="fp64", out=out64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        nref = 3
+        f0.record(stream)
+        for _ in range(nref):
+            solver.solve(dev64, num_segments=args.fp64_segments, prec="fp64", out=out64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / nref
+        solver.solve(dev64, num_segments=args.fp64_segments, prec="fp64", out=out64, residual=True)
+        rep64 = solver.report()
+        res64 = {"eta": rep64["kkt_residual"]}
+        fp64_ref = {"stages_per_s": T / (ms64 / 1e3), "ms_per_solve": ms64, "K": args.fp64_segments,
+                    "kkt_backward_error": res64["eta"], "steps": nref}
+        del dev64, out64
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -294,10 +357,12 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32",
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64"}[args.prec],
                 "data": "synthetic (seeded PCG64), inputs resident in HBM",
                 "config": {"workload": "long-horizon LQR n=64 m=32 T=%d rho(A)<=1.02, K=%d segments, %s" %
                                        (T, K, args.prec.upper()),
+                           "plain_fp64": fp64_ref,
+                           "speedup_vs_plain_fp64": (value / world / fp64_ref["stages_per_s"]) if fp64_ref else None,
                            "n": n, "m": m, "T": T, "K": K, "precision": args.prec, "form": args.form,
                            "kkt_backward_error": res["eta"], "kkt_rel_residual": res["rel"],
                            "l2": "inputs (%.0f MB) larger than L2 (129 MB)" % (
