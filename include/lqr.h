@@ -67,7 +67,7 @@ typedef enum {
 
 typedef enum {
   LQR_FP64 = 0,       /* all arithmetic in FP64 (the plain method)                          */
-  LQR_FP32 = 1,       /* FP32 data and arithmetic; FP64 factor of R+B'PB and link solve     */
+  LQR_FP32 = 1,       /* FP32 data and arithmetic (FP32 factor of R+B'PB); FP64 link solve */
   LQR_MIXED_TF32 = 2, /* FP64 data; FP32 sweeps, FP64 factor/link solve, FP64 KKT refinement */
   LQR_MIXED_BF16 = 3  /* reserved (LQR_ERR_UNSUPPORTED)                                      */
 } lqr_precision;

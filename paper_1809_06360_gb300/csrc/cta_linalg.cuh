@@ -129,54 +129,99 @@ __device__ __forceinline__ void cta_mv(int M, int K, const XA* A, int lda,
   }
 }
 
+// FP64 reciprocal for the serial pivot chain. On GB300 every FP64 warp
+// instruction holds the sub-partition's FP64 pipe for 64 cycles and a library
+// FP64 division costs ~430 cycles, so the pivot reciprocal is taken from the
+// FP32 hardware reciprocal and refined by two Newton-Raphson steps
+// y <- y + y (1 - d y), each of which doubles the number of correct bits
+// (24 -> 48 -> full FP64). Outside the FP32 exponent range the division is used.
+__device__ __forceinline__ double rcp_newton(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  double y = (double)__frcp_rn((float)d);
+  double e = fma(-d, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+
 // ---------------------------------------------------------------------------
-// In-place lower Cholesky (FP64) of the d x d SPD matrix G (leading dim ld).
+// In-place lower Cholesky (FP64) of the d x d SPD matrix G (leading dim ld),
+// computed as LDL' so that the serial pivot chain needs one reciprocal per
+// column and no square root; the square roots that turn L D L' into the
+// Cholesky factor are taken afterwards for all columns at once.
 // One barrier per column: in step j every thread applies the rank-1 update of
-// column j (still unscaled: A[i][k] -= A[i][j] A[k][j] / A[j][j]) to the
-// trailing elements it owns, and scales column j-1, which nobody reads in
-// step j. Thread t owns row (t >> 2) + j + 1 + 64 r and the columns
-// k = t (mod 4) of that row. The single thread that writes the final value of
-// the next pivot also computes its reciprocal, square root and reciprocal
-// square root, so each costs one FP64 division / square root per column.
-// On exit rdiag[j] = 1 / L[j][j]. `flag` (shared) is set to 1 when a pivot is
-// not positive. `piv` (shared) holds 3d doubles of scratch. Ends with a barrier.
+// column j (still unscaled: A[i][k] -= A[i][j] A[k][j] / D_j) to the trailing
+// elements it owns, and scales column j-1 by 1/D_{j-1} (unit lower L), which
+// nobody reads in step j. Thread t owns row (t >> 2) + j + 1 + 64 r and the
+// columns k = t (mod 4) of that row. The thread that writes the final value of
+// the next pivot D_{j+1} also computes its reciprocal.
+// On exit rdiag[j] = 1 / L[j][j] (if rdiag is non-null). `flag` (shared) is
+// set to 1 when a pivot is not positive. `piv` (shared) holds d doubles of
+// scratch. Ends with a barrier.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void chol_pivot_prep(double v, int j, double* inv, double* sq, double* isq, int* flag) {
+__device__ __forceinline__ void ldl_pivot_prep(double v, int j, double* inv, int* flag) {
   const bool ok = (v > 0.0) && isfinite(v);
   if (!ok) *flag = 1;
-  const double s = ok ? sqrt(v) : 1.0;
-  sq[j] = s;
-  isq[j] = 1.0 / s;
-  inv[j] = ok ? isq[j] * isq[j] : 0.0;
+  inv[j] = ok ? rcp_newton(v) : 0.0;
 }
 
 __device__ inline void cta_chol_piv(int d, double* G, int ld, int* flag, double* piv, double* rdiag) {
   const int t = threadIdx.x;
   const int nthr = blockDim.x;
-  const int rows_per_pass = nthr >> 2;
-  const int q = t & 3;
-  double* inv = piv;
-  double* sq = piv + d;
-  double* isq = piv + 2 * d;
-  if (t == 0) chol_pivot_prep(G[0], 0, inv, sq, isq, flag);
+  double* inv = piv;           // 1 / D_j                     (d)
+  double* lc0 = piv + d;       // L[:, j] for even j          (d)
+  double* lc1 = piv + 2 * d;   // L[:, j] for odd j           (d)
+  double* gc = piv + 3 * d;    // unscaled column j, contiguous (bank-conflict-free reads)
+  if (t == 0) ldl_pivot_prep(G[0], 0, inv, flag);
   __syncthreads();
   for (int j = 0; j < d; ++j) {
+    double* lc = (j & 1) ? lc1 : lc0;
+    const double* lp = (j & 1) ? lc0 : lc1;
+    // (a) column j copied to contiguous scratch, its scaled form l_ij = a_ij / D_j,
+    // and column j-1 written back as unit L
     const double invj = inv[j];
-    for (int i = (t >> 2) + j + 1; i < d; i += rows_per_pass) {
-      const double aij = G[(size_t)i * ld + j] * invj;
-      const int k0 = j + 1 + ((q - (j + 1)) & 3);
-      for (int k = k0; k <= i; k += 4) G[(size_t)i * ld + k] -= aij * G[(size_t)k * ld + j];
+    for (int i = j + 1 + t; i < d; i += nthr) {
+      const double g = G[(size_t)i * ld + j];
+      gc[i] = g;
+      lc[i] = g * invj;
     }
-    // the owner of (j+1, j+1) in this step prepares the next pivot
-    if (j + 1 < d && t == ((j + 1) & 3)) chol_pivot_prep(G[(size_t)(j + 1) * ld + (j + 1)], j + 1, inv, sq, isq, flag);
-    if (j > 0) {
-      const double s = isq[j - 1];
-      for (int i = j + t; i < d; i += nthr) G[(size_t)i * ld + (j - 1)] *= s;
-      if (t == 0) G[(size_t)(j - 1) * ld + (j - 1)] = sq[j - 1];
+    if (j > 0)
+      for (int i = j + t; i < d; i += nthr) G[(size_t)i * ld + (j - 1)] = lp[i];
+    __syncthreads();
+    // (b) trailing update of the lower triangle, elements dealt flat over the
+    // block so that every FP64 warp instruction carries full lanes; element 0
+    // is the next pivot, whose owner (thread 0) prepares its reciprocal first
+    const int w = d - j - 1;
+    const int ne = w * (w + 1) / 2;
+    for (int e = t; e < ne; e += nthr) {
+      int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      while (ii * (ii + 1) / 2 > e) --ii;
+      const int kk = e - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      const double v = G[(size_t)i * ld + k] - lc[i] * gc[k];
+      G[(size_t)i * ld + k] = v;
+      if (e == 0) ldl_pivot_prep(v, j + 1, inv, flag);
     }
     __syncthreads();
   }
-  if (t == 0) G[(size_t)(d - 1) * ld + (d - 1)] = sq[d - 1];
+  // L D L' -> Cholesky: column j times sqrt(D_j); one square root per column,
+  // all columns at once (off the pivot chain)
+  double* sq = lc0;  // the scaled-column scratch is free now
+  double* isq = lc1;
+  for (int j = t; j < d; j += nthr) {
+    const double Dj = G[(size_t)j * ld + j];
+    const double r = (Dj > 0.0) ? rsqrt(Dj) : 1.0;
+    isq[j] = r;
+    sq[j] = (Dj > 0.0) ? Dj * r : 1.0;
+  }
+  __syncthreads();
+  for (int e = t; e < d * d; e += nthr) {
+    const int i = e / d, j = e % d;
+    if (j > i) continue;
+    G[(size_t)i * ld + j] = (i == j) ? sq[j] : G[(size_t)i * ld + j] * sq[j];
+  }
   if (rdiag)
     for (int j = t; j < d; j += nthr) rdiag[j] = isq[j];
   __syncthreads();
@@ -184,38 +229,111 @@ __device__ inline void cta_chol_piv(int d, double* G, int ld, int* flag, double*
 
 // Convenience wrapper with static scratch (d <= 256); rdiag may be null.
 __device__ inline void cta_chol(int d, double* G, int ld, int* flag, double* rdiag = nullptr) {
-  __shared__ double s_piv[3 * 256];
+  __shared__ double s_piv[4 * 256];
   cta_chol_piv(d, G, ld, flag, s_piv, rdiag);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 Cholesky of the d x d SPD matrix G in place (lower), same column
+// scheme as the FP64 one but with the FP32 hardware reciprocal square root on
+// the pivot chain: one pivot per barrier, full-lane trailing updates.
+// rdiag[j] = 1 / L[j][j]. `piv` (shared) holds d floats. Ends with a barrier.
+// ---------------------------------------------------------------------------
+__device__ inline void cta_chol_f32(int d, float* G, int ld, int* flag, float* piv, float* rdiag) {
+  // piv: 2d floats: [0, d) reciprocal square roots of the pivots, [d, 2d) the
+  // current scaled column (contiguous, bank-conflict-free reads)
+  const int t = threadIdx.x;
+  const int nthr = blockDim.x;
+  float* lc = piv + d;
+  if (t == 0) {
+    const float v = G[0];
+    const bool ok = (v > 0.0f) && isfinite(v);
+    if (!ok) *flag = 1;
+    const float r = ok ? rsqrtf(v) : 1.0f;
+    piv[0] = r;
+    G[0] = ok ? v * r : 1.0f;
+  }
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    const float r = piv[j];
+    for (int i = j + 1 + t; i < d; i += nthr) {
+      const float l = G[(size_t)i * ld + j] * r;
+      G[(size_t)i * ld + j] = l;
+      lc[i] = l;
+    }
+    __syncthreads();
+    const int w = d - j - 1;
+    const int ne = w * (w + 1) / 2;
+    for (int e = t; e < ne; e += nthr) {
+      int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      while (ii * (ii + 1) / 2 > e) --ii;
+      const int kk = e - ii * (ii + 1) / 2;
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      const float v = G[(size_t)i * ld + k] - lc[i] * lc[k];
+      G[(size_t)i * ld + k] = v;
+      if (e == 0) {  // the next pivot, by its only writer
+        const bool ok = (v > 0.0f) && isfinite(v);
+        if (!ok) *flag = 1;
+        const float rr = ok ? rsqrtf(v) : 1.0f;
+        piv[j + 1] = rr;
+        G[(size_t)(j + 1) * ld + (j + 1)] = ok ? v * rr : 1.0f;
+      }
+    }
+    __syncthreads();
+  }
+  if (rdiag)
+    for (int j = t; j < d; j += nthr) rdiag[j] = piv[j];
+  __syncthreads();
+}
+
+// Inverse of the lower-triangular d x d factor L (leading dim ldl, with
+// rdiag[i] = 1 / L[i][i]) into X (lower, leading dim ldx; the strict upper
+// part is set to zero). Column c of L^{-1} is the forward substitution of
+// e_c; one thread per column. Ends with a barrier.
+template <typename T>
+__device__ inline void cta_trinv_lower(int d, const T* L, int ldl, const T* rdiag, T* X, int ldx) {
+  for (int e = threadIdx.x; e < d * d; e += blockDim.x) X[(size_t)(e / d) * ldx + (e % d)] = T(0);
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    X[(size_t)c * ldx + c] = rdiag[c];
+    for (int i = c + 1; i < d; ++i) {
+      T s = T(0);
+      for (int k = c; k < i; ++k) s = fma(L[(size_t)i * ldl + k], X[(size_t)k * ldx + c], s);
+      X[(size_t)i * ldx + c] = -s * rdiag[i];
+    }
+  }
+  __syncthreads();
 }
 
 // Triangular solves with few right-hand sides: one warp per column, the
 // column-oriented elimination spread over the lanes.
-template <typename XX>
-__device__ __forceinline__ void cta_trsm_lower_warp(int d, const double* L, int ldl, int nc, XX* X, int ldx,
-                                                    const double* rdiag) {
+template <typename XX, typename TL>
+__device__ __forceinline__ void cta_trsm_lower_warp(int d, const TL* L, int ldl, int nc, XX* X, int ldx,
+                                                    const TL* rdiag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = warp; c < nc; c += nw) {
     for (int i = 0; i < d; ++i) {
-      const double xi = static_cast<double>(X[(size_t)i * ldx + c]) * rdiag[i];
+      const TL xi = static_cast<TL>(X[(size_t)i * ldx + c]) * rdiag[i];
       __syncwarp();
       if (lane == 0) X[(size_t)i * ldx + c] = static_cast<XX>(xi);
       for (int k = i + 1 + lane; k < d; k += 32)
-        X[(size_t)k * ldx + c] = static_cast<XX>(static_cast<double>(X[(size_t)k * ldx + c]) - L[(size_t)k * ldl + i] * xi);
+        X[(size_t)k * ldx + c] = static_cast<XX>(static_cast<TL>(X[(size_t)k * ldx + c]) - L[(size_t)k * ldl + i] * xi);
       __syncwarp();
     }
   }
 }
-template <typename XX>
-__device__ __forceinline__ void cta_trsm_lower_t_warp(int d, const double* L, int ldl, int nc, XX* X, int ldx,
-                                                      const double* rdiag) {
+template <typename XX, typename TL>
+__device__ __forceinline__ void cta_trsm_lower_t_warp(int d, const TL* L, int ldl, int nc, XX* X, int ldx,
+                                                      const TL* rdiag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = warp; c < nc; c += nw) {
     for (int i = d - 1; i >= 0; --i) {
-      const double xi = static_cast<double>(X[(size_t)i * ldx + c]) * rdiag[i];
+      const TL xi = static_cast<TL>(X[(size_t)i * ldx + c]) * rdiag[i];
       __syncwarp();
       if (lane == 0) X[(size_t)i * ldx + c] = static_cast<XX>(xi);
       for (int k = lane; k < i; k += 32)
-        X[(size_t)k * ldx + c] = static_cast<XX>(static_cast<double>(X[(size_t)k * ldx + c]) - L[(size_t)i * ldl + k] * xi);
+        X[(size_t)k * ldx + c] = static_cast<XX>(static_cast<TL>(X[(size_t)k * ldx + c]) - L[(size_t)i * ldl + k] * xi);
       __syncwarp();
     }
   }

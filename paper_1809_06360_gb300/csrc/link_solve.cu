@@ -12,6 +12,8 @@
 //     z_{j+1} = -D_j^{-1}(V_zx^j z_j + v_z^j + pi_{j+1}) = Gam_j z_j + gam_j.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <type_traits>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -294,60 +296,71 @@ __device__ inline void warp_trsv_lower_t(int n, const double* L, int ld, const d
 }
 
 // Copy the column slabs owned by the other CTAs of the cluster into the local
-// copy of the n x n matrix M (distributed shared memory reads).
-template <int CL>
-__device__ inline void cluster_gather_cols(cg::cluster_group& cluster, double* M, int n, int rank) {
+// copy of the n x ld matrix M (distributed shared memory reads; 16-byte loads
+// when every slab boundary is 16-byte aligned).
+template <int CL, typename T>
+__device__ inline void cluster_gather_cols(cg::cluster_group& cluster, T* M, int n, int ncols, int ld, int rank) {
+  using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+  const bool vec = ((ld & 1) == 0) && (ncols % (2 * CL) == 0);
   for (int r2 = 0; r2 < CL; ++r2) {
     if (r2 == rank) continue;
-    const double* rem = cluster.map_shared_rank(M, r2);
-    const int d0 = r2 * n / CL, d1 = (r2 + 1) * n / CL, w = d1 - d0;
+    const T* rem = cluster.map_shared_rank(M, r2);
+    const int d0 = r2 * ncols / CL, d1 = (r2 + 1) * ncols / CL, w = d1 - d0;
     if (w <= 0) continue;
-    for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
-      const int i = e / w, jj = d0 + e % w;
-      M[(size_t)i * n + jj] = rem[(size_t)i * n + jj];
+    if (vec) {
+      const int w2 = w >> 1;
+      for (int e = threadIdx.x; e < n * w2; e += blockDim.x) {
+        const int i = e / w2, jj = d0 + 2 * (e % w2);
+        *reinterpret_cast<T2*>(M + (size_t)i * ld + jj) = *reinterpret_cast<const T2*>(rem + (size_t)i * ld + jj);
+      }
+    } else {
+      for (int e = threadIdx.x; e < n * w; e += blockDim.x) {
+        const int i = e / w, jj = d0 + e % w;
+        M[(size_t)i * ld + jj] = rem[(size_t)i * ld + jj];
+      }
     }
   }
 }
 
-// The same dual link recursion as link_solve_dual_kernel, with each link step
-// spread over a cluster of CL CTAs: every CTA owns a slab of columns of the
-// n x n products (W C, C'Z, C'W C, Ld^-1 E, F'F, Z - W C Ld^-T F) and the
-// slabs are exchanged through distributed shared memory; the two n x n
-// Cholesky factorisations per link are computed redundantly by every CTA
-// (deterministic, so all CTAs hold bitwise-identical factors).
-template <int CL>
+// The serial part of the dual link recursion, each link step spread over a
+// cluster of CL CTAs (column slabs exchanged through distributed shared
+// memory; the two n x n factorisations are computed redundantly in every CTA,
+// deterministic, so all CTAs hold identical factors). The vector recursion
+// rides along as column n of [Z_j | v_j]:
+//     C = chol(Pi_{j+1}),  v = w_j - W_j pi_{j+1},  Tm = W_j C,
+//     E = C'[Z_j | v],  Ld = chol(I + C'Tm),  F = Ld^-1 E,
+//     [Pi_j | pi_j] = [P_j | p_j + Z_j'pi_{j+1}] + F'F      (columns 0..n-1 | n)
+// Tm, Ld, 1/diag(Ld), F and v are stored per link for the parallel post-pass
+// that forms Gam_j and gam_j off the serial chain.
+template <int CL, typename T>
 __global__ void __launch_bounds__(kBlock) link_solve_dual_cluster_kernel(ProbTable tab, int x0_is_float, int stage_inputs) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
-  __shared__ double s_rdc[256];
-  __shared__ double s_rdl[256];
+  __shared__ T s_rdc[256];
+  __shared__ T s_rdl[256];
+  __shared__ float s_pivf[sizeof(T) == 4 ? 512 : 1];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const ProbDesc& pd = prob_at(tab, blockIdx.x / CL);
   // the exit decision reads state written by earlier kernels only: cluster-uniform
   if (cta_should_exit(pd, &s_flag)) return;
   const int n = pd.n, K = pd.nseg;
+  const int n1 = n + 1;
   const long long nn = (long long)n * n;
   const WsLayout wl = ws_layout(n, K);
   double* ws = pd.ws;
-  double* z = ws + wl.z;
-  if (rank == 0)
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      z[i] = x0_is_float ? (double)static_cast<const float*>(pd.x0)[i] : static_cast<const double*>(pd.x0)[i];
   if (K == 1) return;
-  double* C = reinterpret_cast<double*>(smem);
-  double* Tm = C + nn;
-  double* Ld = Tm + nn;
-  double* E = Ld + nn;
-  double* v = E + nn;   // w_j - W_j pi_{j+1}
-  double* tv = v + n;   // C'v, then Ld^-1 C'v
-  double* t2 = tv + n;  // Ld^-T t
-  // per-link inputs staged in shared memory by one coalesced copy (when they fit)
-  double* Wn_s = t2 + n;      // -W_j
-  double* Z_s = Wn_s + nn;    // Z_j
-  double* vec_s = Z_s + nn;   // w_j, p_j, pi_{j+1}
+  T* C = reinterpret_cast<T*>(smem);  // n x n
+  T* Tm = C + nn;                      // n x n
+  T* Ld = Tm + nn;                     // n x n
+  T* E = Ld + nn;                      // n x (n+1): C'[Z | v], then F
+  T* v = E + (long long)n * n1;        // n
+  T* Wn_s = v + n;                     // staged -W_j (n x n)
+  T* Z_s = Wn_s + nn;                  // staged [Z_j | v] (n x (n+1)), column n = v
+  T* vec_s = Z_s + (long long)n * n1;  // staged w_j, p_j, pi_{j+1}
   const bool staged = stage_inputs != 0;
-  const int c0 = rank * n / CL, c1 = (rank + 1) * n / CL, ns = c1 - c0;
+  const int c0 = rank * n / CL, c1 = (rank + 1) * n / CL, ns = c1 - c0;         // slab of n columns
+  const int e0 = rank * n1 / CL, e1 = (rank + 1) * n1 / CL, ens = e1 - e0;      // slab of n+1 columns
   const long long sstride = 3 * nn + 2 * n;
   if (rank == 0) {
     const double* S = ws + wl.summ + (long long)(K - 1) * sstride;
@@ -360,121 +373,169 @@ __global__ void __launch_bounds__(kBlock) link_solve_dual_cluster_kernel(ProbTab
   for (int j = K - 2; j >= 0; --j) {
     const double* S = ws + wl.summ + (long long)j * sstride;
     const double* Pseg = S;
-    const double* Z = S + nn;
+    const double* Zg = S + nn;
     const double* Wneg = S + 2 * nn;
     const double* ps = S + 3 * nn;
     const double* w = S + 3 * nn + n;
     const double* Pn = ws + wl.Pi + (long long)(j + 1) * nn;
     const double* pn = ws + wl.pi + (long long)(j + 1) * n;
-    if (staged) {
-      for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        Wn_s[e] = Wneg[e];
-        Z_s[e] = Z[e];
-      }
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        vec_s[i] = w[i];
-        vec_s[n + i] = ps[i];
-        vec_s[2 * n + i] = pn[i];
-      }
-      Wneg = Wn_s;
-      Z = Z_s;
-      w = vec_s;
-      ps = vec_s + n;
-      pn = vec_s + 2 * n;
-      __syncthreads();
-    }
     double* Pj = ws + wl.Pi + (long long)j * nn;
     double* pj = ws + wl.pi + (long long)j * n;
-    double* Gam = ws + wl.Gam + (long long)j * nn;
-    double* gam = ws + wl.gam + (long long)j * n;
-    // (A) redundant: C = chol(Pi_{j+1}), v = w - W pi_{j+1}
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) C[e] = Pn[e];
-    cta_mv<false, double>(n, n, Wneg, n, pn, 1, EpiAdd<double, double>{v, 1, 1.0, w, 1});
+    // (A) redundant: C = chol(Pi_{j+1}); inputs staged
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) C[e] = static_cast<T>(Pn[e]);
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      Wn_s[e] = static_cast<T>(Wneg[e]);
+      Z_s[(size_t)(e / n) * n1 + (e % n)] = static_cast<T>(Zg[e]);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      vec_s[i] = static_cast<T>(w[i]);
+      vec_s[n + i] = static_cast<T>(ps[i]);
+      vec_s[2 * n + i] = static_cast<T>(pn[i]);
+    }
+    (void)staged;
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
-    cta_chol(n, C, n, &s_flag, s_rdc);
+    // v = w - W pi_{j+1} into column n of Z_s (and v)
+    cta_mv<false, T>(n, n, Wn_s, n, vec_s + 2 * n, 1, EpiAdd<T, T>{v, 1, 1.0, vec_s, 1});
+    if constexpr (sizeof(T) == 8)
+      cta_chol(n, reinterpret_cast<double*>(C), n, &s_flag, reinterpret_cast<double*>(s_rdc));
+    else
+      cta_chol_f32(n, reinterpret_cast<float*>(C), n, &s_flag, s_pivf, reinterpret_cast<float*>(s_rdc));
     if (s_flag) {  // identical in every CTA of the cluster
       if (rank == 0 && threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
       return;
     }
     for (int e = threadIdx.x; e < nn; e += blockDim.x)
-      if (e % n > e / n) C[e] = 0.0;
+      if (e % n > e / n) C[e] = T(0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Z_s[(size_t)i * n1 + n] = v[i];
     __syncthreads();
-    // (B) slabs of Tm = W C and E = C'Z; tv = C'v (redundant)
-    cta_mm_auto<false, false, double>(n, ns, n, Wneg, n, C + c0, n, EpiStore<double>{Tm + c0, n, -1.0});
-    cta_mm_auto<true, false, double>(n, ns, n, C, n, Z + c0, n, EpiStore<double>{E + c0, n, 1.0});
-    cta_mv<true, double>(n, n, C, n, v, 1, EpiStore<double>{tv, 1, 1.0});
+    // (B) slabs of Tm = W C and E = C'[Z | v]
+    cta_mm_auto<false, false, T>(n, ns, n, Wn_s, n, C + c0, n, EpiStore<T>{Tm + c0, n, -1.0});
+    cta_mm_auto<true, false, T>(n, ens, n, C, n, Z_s + e0, n1, EpiStore<T>{E + e0, n1, 1.0});
     cluster.sync();
-    cluster_gather_cols<CL>(cluster, Tm, n, rank);
-    cluster_gather_cols<CL>(cluster, E, n, rank);
+    cluster_gather_cols<CL, T>(cluster, Tm, n, n, n, rank);
     cluster.sync();
     // (C) slab of Ld = I + C'Tm
-    cta_mm_auto<true, false, double>(n, ns, n, C, n, Tm + c0, n, EpiStore<double>{Ld + c0, n, 1.0});
+    cta_mm_auto<true, false, T>(n, ns, n, C, n, Tm + c0, n, EpiStore<T>{Ld + c0, n, 1.0});
     __syncthreads();
-    for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) Ld[(size_t)i * n + i] += 1.0;
+    for (int i = c0 + threadIdx.x; i < c1; i += blockDim.x) Ld[(size_t)i * n + i] += T(1);
     cluster.sync();
-    cluster_gather_cols<CL>(cluster, Ld, n, rank);
+    cluster_gather_cols<CL, T>(cluster, Ld, n, n, n, rank);
     cluster.sync();
-    // (D) redundant: Ld = chol(I + C'W C), t = Ld^-1 C'v
+    // (D) redundant: Ld = chol(I + C'W C)
     if (threadIdx.x == 0) s_flag = 0;
     __syncthreads();
-    cta_chol(n, Ld, n, &s_flag, s_rdl);
+    if constexpr (sizeof(T) == 8)
+      cta_chol(n, reinterpret_cast<double*>(Ld), n, &s_flag, reinterpret_cast<double*>(s_rdl));
+    else
+      cta_chol_f32(n, reinterpret_cast<float*>(Ld), n, &s_flag, s_pivf, reinterpret_cast<float*>(s_rdl));
     if (s_flag) {
       if (rank == 0 && threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
       return;
     }
-    if (threadIdx.x < 32) warp_trsv_lower(n, Ld, n, s_rdl, tv);
-    // (E) slab of F = Ld^-1 E (in place)
-    cta_trsm_lower_warp<double>(n, Ld, n, ns, E + c0, n, s_rdl);
+    // (E) slab of F = Ld^-1 E (in place), then the full F
+    cta_trsm_lower_warp<T>(n, Ld, n, ens, E + e0, n1, s_rdl);
     cluster.sync();
-    cluster_gather_cols<CL>(cluster, E, n, rank);
+    cluster_gather_cols<CL, T>(cluster, E, n, n1, n1, rank);
     cluster.sync();
-    // (F) slabs of Pi_j = P_j + F'F and Gam_j = Z - Tm Ld^-T F; rank 0: pi_j, gam_j
-    cta_mm_auto<true, false, double>(n, ns, n, E, n, E + c0, n, EpiAdd<double, double>{Pj + c0, n, 1.0, Pseg + c0, n});
-    for (int e = threadIdx.x; e < n * ns; e += blockDim.x) {
-      const int i = e / ns, jj = c0 + e % ns;
-      C[(size_t)i * n + jj] = E[(size_t)i * n + jj];
-    }
-    __syncthreads();
-    cta_trsm_lower_t_warp<double>(n, Ld, n, ns, C + c0, n, s_rdl);
-    if (rank == 0 && threadIdx.x >= blockDim.x - 32) {
-      for (int i = threadIdx.x & 31; i < n; i += 32) t2[i] = tv[i];
-      __syncwarp();
-      warp_trsv_lower_t(n, Ld, n, s_rdl, t2);
-    }
-    __syncthreads();
-    cta_mm_auto<false, false, double>(n, ns, n, Tm, n, C + c0, n, EpiAdd<double, double>{Gam + c0, n, -1.0, Z + c0, n});
-    if (rank == 0) {
-      // pi_j = p_j + Z'pi_{j+1} + F't ; gam_j = v - Tm t2
+    // (F) slab of [Pi_j | pi_j] = [P_j | p_j + Z'pi_{j+1}] + F'F; stores for the post-pass
+    cta_mm_auto<true, false, T>(n, ns, n, E, n1, E + c0, n1, EpiAdd<double, double>{Pj + c0, n, 1.0, Pseg + c0, n});
+    if (rank == CL - 1) {
+      // column n: pi_j = p_j + Z'pi_{j+1} + F't  (t = column n of F)
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double a = ps[i];
-        for (int k = 0; k < n; ++k) a = fma(Z[(size_t)k * n + i], pn[k], fma(E[(size_t)k * n + i], tv[k], a));
-        pj[i] = a;
-        double g = v[i];
-        for (int k = 0; k < n; ++k) g = fma(-Tm[(size_t)i * n + k], t2[k], g);
-        gam[i] = g;
+        T a = vec_s[n + i];
+        for (int k = 0; k < n; ++k)
+          a = fma(Z_s[(size_t)k * n1 + i], vec_s[2 * n + k], fma(E[(size_t)k * n1 + i], E[(size_t)k * n1 + n], a));
+        pj[i] = static_cast<double>(a);
       }
+    }
+    {
+      double* gTm = ws + wl.lkTm + (long long)j * nn;
+      double* gLd = ws + wl.lkLd + (long long)j * nn;
+      double* gRd = ws + wl.lkRd + (long long)j * n;
+      double* gF = ws + wl.lkF + (long long)j * n * n1;
+      double* gV = ws + wl.lkV + (long long)j * n;
+      for (int e = threadIdx.x; e < n * ns; e += blockDim.x) {
+        const int i = e / ns, jj = c0 + e % ns;
+        gTm[(size_t)i * n + jj] = static_cast<double>(Tm[(size_t)i * n + jj]);
+        gLd[(size_t)i * n + jj] = static_cast<double>(Ld[(size_t)i * n + jj]);
+      }
+      for (int e = threadIdx.x; e < n * ens; e += blockDim.x) {
+        const int i = e / ens, jj = e0 + e % ens;
+        gF[(size_t)i * n1 + jj] = static_cast<double>(E[(size_t)i * n1 + jj]);
+      }
+      if (rank == 0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          gRd[i] = static_cast<double>(s_rdl[i]);
+          gV[i] = static_cast<double>(v[i]);
+        }
     }
     cluster.sync();  // Pi_j, pi_j visible to the cluster; slabs free for reuse
   }
-  if (rank != 0) return;
+}
+
+// Off the serial chain, one CTA per link: G2 = Ld^-T F (columns 0..n), then
+//     Gam_j = Z_j - Tm G2[:, 0:n],   gam_j = v_j - Tm G2[:, n]      (Woodbury)
+// so that z_{j+1} = Gam_j z_j + gam_j.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) link_post_kernel(ProbTable tab) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_flag;
+  const ProbDesc& pd = tab.single;
+  if (cta_should_exit(pd, &s_flag)) return;
+  const int n = pd.n, K = pd.nseg, n1 = n + 1;
+  const int j = blockIdx.x;
+  if (j >= K - 1) return;
+  const long long nn = (long long)n * n;
+  const WsLayout wl = ws_layout(n, K);
+  double* ws = pd.ws;
+  T* G2 = reinterpret_cast<T*>(smem);    // n x (n+1)
+  T* Ld = G2 + (long long)n * n1;        // n x n
+  T* Tm = Ld + nn;                       // n x n
+  T* rd = Tm + nn;                       // n
+  for (int e = threadIdx.x; e < n * n1; e += blockDim.x) G2[e] = static_cast<T>(ws[wl.lkF + (long long)j * n * n1 + e]);
+  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+    Ld[e] = static_cast<T>(ws[wl.lkLd + (long long)j * nn + e]);
+    Tm[e] = static_cast<T>(ws[wl.lkTm + (long long)j * nn + e]);
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rd[i] = static_cast<T>(ws[wl.lkRd + (long long)j * n + i]);
+  __syncthreads();
+  cta_trsm_lower_t_warp<T>(n, Ld, n, n1, G2, n1, rd);
+  __syncthreads();
+  const double* Z = ws + wl.summ + (long long)j * (3 * nn + 2 * n) + nn;
+  cta_mm_auto<false, false, T>(n, n, n, Tm, n, G2, n1,
+                               EpiAdd<double, double>{ws + wl.Gam + (long long)j * nn, n, -1.0, Z, n});
+  cta_mv<false, T>(n, n, Tm, n, G2 + n, n1,
+                   EpiAdd<double, double>{ws + wl.gam + (long long)j * n, 1, -1.0, ws + wl.lkV + (long long)j * n, 1});
+}
+
+// The link states: z_0 = x0, z_{j+1} = Gam_j z_j + gam_j (one CTA, serial, O(K n^2)).
+__global__ void __launch_bounds__(kBlock) link_forward_kernel(ProbTable tab, int x0_is_float) {
+  __shared__ int s_flag;
+  const ProbDesc& pd = tab.single;
+  if (cta_should_exit(pd, &s_flag)) return;
+  const int n = pd.n, K = pd.nseg;
+  const long long nn = (long long)n * n;
+  const WsLayout wl = ws_layout(n, K);
+  double* z = pd.ws + wl.z;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    z[i] = x0_is_float ? (double)static_cast<const float*>(pd.x0)[i] : static_cast<const double*>(pd.x0)[i];
+  __syncthreads();
   for (int j = 0; j + 1 < K; ++j) {
-    const double* G = ws + wl.Gam + (long long)j * nn;
-    const double* g = ws + wl.gam + (long long)j * n;
-    cta_mv<false, double>(n, n, G, n, z + (long long)j * n, 1,
-                          EpiAdd<double, double>{z + (long long)(j + 1) * n, 1, 1.0, g, 1});
+    cta_mv<false, double>(n, n, pd.ws + wl.Gam + (long long)j * nn, n, z + (long long)j * n, 1,
+                          EpiAdd<double, double>{z + (long long)(j + 1) * n, 1, 1.0, pd.ws + wl.gam + (long long)j * n, 1});
     __syncthreads();
   }
 }
 
-template <int CL>
+template <int CL, typename T>
 static cudaError_t launch_dual_cluster(const ProbTable& tab, int nprob, int x0_is_float, size_t bytes,
                                        cudaStream_t st) {
   {
-    cudaError_t e = raise_dyn_smem((const void*)link_solve_dual_cluster_kernel<CL>, bytes);
+    cudaError_t e = raise_dyn_smem((const void*)link_solve_dual_cluster_kernel<CL, T>, bytes);
     if (e != cudaSuccess) return e;
     if (CL > 8) {
-      e = cudaFuncSetAttribute(link_solve_dual_cluster_kernel<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = cudaFuncSetAttribute(link_solve_dual_cluster_kernel<CL, T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
   }
@@ -490,18 +551,19 @@ static cudaError_t launch_dual_cluster(const ProbTable& tab, int nprob, int x0_i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const int staged = (bytes >= sizeof(double) * (6 * (size_t)tab.single.n * tab.single.n + 6 * (size_t)tab.single.n)) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, link_solve_dual_cluster_kernel<CL>, tab, x0_is_float, staged);
+  return cudaLaunchKernelEx(&cfg, link_solve_dual_cluster_kernel<CL, T>, tab, x0_is_float, 1);
 }
 
 // cluster width used for the link solve (0 = single CTA); set by launch_link_solve_dual
 static int g_link_cluster = -1;
 cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
+static int g_link_fp32 = 0;  // set per call by launch_link_solve_dual
 
 int link_cluster_width() { return g_link_cluster; }
 
-cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st) {
+cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st, int link_fp32) {
   if (tab.probs) return cudaErrorInvalidValue;
+  g_link_fp32 = link_fp32;
   cudaError_t r = launch_link_solve_dual_impl(tab, nprob, x0_is_float, st);
   static int reported = -2;
   if (getenv("LQR_DEBUG") && reported != g_link_cluster) {
@@ -530,22 +592,35 @@ cudaError_t launch_link_solve_dual_batched(const ProbTable& tab, int nprob, int 
 cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st) {
   {
     const int n = tab.single.n;
-    size_t cbytes = sizeof(double) * (6 * (size_t)n * n + 6 * (size_t)n);  // with staged inputs
+    const size_t nn = (size_t)n * n, n1 = (size_t)n + 1;
+    const size_t es = g_link_fp32 ? sizeof(float) : sizeof(double);
+    // C, Tm, Ld, E (n x (n+1)), v | staged -W, [Z | v], w, p, pi
+    const size_t cbytes = es * (3 * nn + n * n1 + n + nn + n * n1 + 3 * (size_t)n);
     int optin = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (cbytes > (size_t)optin - kStaticSmemReserve) cbytes = sizeof(double) * (4 * (size_t)n * n + 3 * (size_t)n);
     if (n >= 16 && tab.single.nseg > 1 && cbytes <= (size_t)optin - kStaticSmemReserve) {
-      cudaError_t e = launch_dual_cluster<16>(tab, nprob, x0_is_float, cbytes, st);
-      if (e == cudaSuccess) {
-        g_link_cluster = 16;
-        return cudaSuccess;
+      int width = 16;
+      cudaError_t e = g_link_fp32 ? launch_dual_cluster<16, float>(tab, nprob, x0_is_float, cbytes, st)
+                                  : launch_dual_cluster<16, double>(tab, nprob, x0_is_float, cbytes, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();  // 16-CTA clusters not available: portable width
+        width = 8;
+        e = g_link_fp32 ? launch_dual_cluster<8, float>(tab, nprob, x0_is_float, cbytes, st)
+                        : launch_dual_cluster<8, double>(tab, nprob, x0_is_float, cbytes, st);
       }
-      cudaGetLastError();  // 16-CTA clusters not available: portable width
-      e = launch_dual_cluster<8>(tab, nprob, x0_is_float, cbytes, st);
       if (e == cudaSuccess) {
-        g_link_cluster = 8;
-        return cudaSuccess;
+        g_link_cluster = width;
+        const size_t pbytes = es * (n * n1 + 2 * nn + n);
+        const void* post = g_link_fp32 ? (const void*)link_post_kernel<float> : (const void*)link_post_kernel<double>;
+        e = raise_dyn_smem(post, pbytes);
+        if (e != cudaSuccess) return e;
+        if (g_link_fp32)
+          link_post_kernel<float><<<tab.single.nseg - 1, kBlock, pbytes, st>>>(tab);
+        else
+          link_post_kernel<double><<<tab.single.nseg - 1, kBlock, pbytes, st>>>(tab);
+        link_forward_kernel<<<1, kBlock, 0, st>>>(tab, x0_is_float);
+        return cudaGetLastError();
       }
       cudaGetLastError();
     }

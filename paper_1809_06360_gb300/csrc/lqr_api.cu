@@ -245,7 +245,8 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
     return LQR_OK;
   }
   const int x0f = (prec == LQR_FP32) ? 1 : 0;
-  e = dual ? launch_link_solve_dual(tab, 1, x0f, st) : launch_link_solve(tab, 1, x0f, st);
+  // the boundary-coupling solve runs in FP64 except in the all-FP32 mode
+  e = dual ? launch_link_solve_dual(tab, 1, x0f, st, prec == LQR_FP32 ? 1 : 0) : launch_link_solve(tab, 1, x0f, st);
   ++*launches;
   if (e != cudaSuccess) return LQR_ERR_CUDA;
   if (profile) prof_mark(h, LQR_PHASE_POLICY, st);

@@ -26,6 +26,12 @@ struct WsLayout {
   long long z;      // (K+1) * n         link states z_j = x_{b_j}
   long long costp;  // K                 partial objective per segment
   long long lwork;  // 4 n^2 + 2n        link-solve work matrices when they do not fit in shared memory
+  // per-link factors stored by the cluster link chain for the parallel post-pass
+  long long lkTm;   // K * n^2           W_j C_{j+1}
+  long long lkLd;   // K * n^2           Cholesky factor of I + C'W_j C
+  long long lkRd;   // K * n             1 / diag(Ld)
+  long long lkF;    // K * n (n+1)       Ld^-1 C'[Z_j | v_j]
+  long long lkV;    // K * n             v_j = w_j - W_j pi_{j+1}
   long long total;
 };
 
@@ -42,6 +48,12 @@ __host__ __device__ inline WsLayout ws_layout(int n, int K) {
   w.costp = o; o += K;
   o = (o + 31) & ~31LL;
   w.lwork = o; o += 4 * nn + 2 * n;
+  o = (o + 31) & ~31LL;
+  w.lkTm = o;  o += (long long)K * nn;
+  w.lkLd = o;  o += (long long)K * nn;
+  w.lkRd = o;  o += (long long)K * n;
+  w.lkF = o;   o += (long long)K * n * (n + 1);
+  w.lkV = o;   o += (long long)K * n;
   w.total = (o + 31) & ~31LL;
   return w;
 }
@@ -105,7 +117,9 @@ enum SweepBuf {
   SB_MUU,      // TC  m x m        M_uu
   SB_L64,      // f64 m x m        Cholesky factor of M_uu (aliases SB_MUU when TC = double)
   SB_VEC,      // TC  4n           v_x, v_z, m_z, spare
+  SB_W,        // TC  m x ldF      W = L^-1 F when TC is float (TC = double solves in place)
   SB_VZX,      // TC  n x n        V_zx          (parametric sweep only)
+  SB_VZZ,      // TC  n x n        V_zz          (parametric sweep only)
   SB_HH,       // f64 2m           Householder heads and scales
   SB_G,        // f64 m x (2n+1)   constrained-stage policy [K_x | K_z | k_1]
   SB_E,        // f64 m x (2n+1)   F + M_uu G, also M~ (m x m)
@@ -147,7 +161,9 @@ __host__ __device__ inline void make_plan(SweepPlan& P, int n, int m, int mode, 
   bytes[SB_MUU] = tc * m * m;
   bytes[SB_L64] = (tc_size == 8) ? 0 : 8LL * m * m;
   bytes[SB_VEC] = tc * 4 * n;
+  bytes[SB_W] = (tc_size == 8) ? 0 : tc * m * P.ldF;
   bytes[SB_VZX] = param ? tc * n * n : 0;
+  bytes[SB_VZZ] = param ? tc * n * n : 0;
   bytes[SB_HH] = cons ? 8LL * 2 * m : 0;
   bytes[SB_G] = cons ? 8LL * m * P.ldG : 0;
   bytes[SB_E] = cons ? 8LL * m * (P.ldG > m ? P.ldG : m) : 0;
@@ -188,7 +204,8 @@ template <typename TS, typename TC>
 long long sweep_smem_needed(int n, int m, long long smem_budget, bool constrained, long long* scratch_doubles);
 
 cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
-cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
+cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st,
+                                   int link_fp32);
 
 template <typename TS, typename TC>
 cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st, int nmax = 0, int mmax = 0);

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
   __shared__ double s_scal[4];
   __shared__ double s_rd[256];   // 1 / L[i][i] of the current FP64 factor
   __shared__ TC s_rdc[256];      // the same in the compute type
+  __shared__ float s_pivf[512];  // pivot scratch of the FP32 factorisation
 
   const int unit = blockIdx.x;
   const ProbDesc& pd = prob_of_unit(tab, unit);
@@ -101,10 +102,12 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
   TC* Muu = plan_ptr<TC>(P, SB_MUU, smem, scratch);
   double* L64 = (sizeof(TC) == 8) ? reinterpret_cast<double*>(Muu) : plan_ptr<double>(P, SB_L64, smem, scratch);
   TC* vec = plan_ptr<TC>(P, SB_VEC, smem, scratch);
+  TC* Wbuf = (sizeof(TC) == 8) ? F : plan_ptr<TC>(P, SB_W, smem, scratch);
   TC* vx = vec;
   TC* vz = vec + n;
   TC* mz = vec + 2 * n;
   TC* Vzx = param ? plan_ptr<TC>(P, SB_VZX, smem, scratch) : nullptr;
+  TC* Vzz = param ? plan_ptr<TC>(P, SB_VZZ, smem, scratch) : nullptr;
   double* HH = cons ? plan_ptr<double>(P, SB_HH, smem, scratch) : nullptr;
   double* Gc = cons ? plan_ptr<double>(P, SB_G, smem, scratch) : nullptr;
   double* Ec = cons ? plan_ptr<double>(P, SB_E, smem, scratch) : nullptr;
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
 
   const WsLayout wl = ws_layout(n, K);
   double* summ = pd.ws + wl.summ + (long long)seg * (3LL * n * n + 2 * n);
-  double* Vzz_g = summ + 2LL * n * n;  // the summary slot accumulates V_zz directly
+  double* Vzz_g = summ + 2LL * n * n;  // the summary slot of V_zz (written at the end)
 
   const TS* gA = static_cast<const TS*>(pd.A);
   const TS* gB = static_cast<const TS*>(pd.B);
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       Vxx[e] = TC(0);
       Vzx[e] = TC(0);
-      Vzz_g[e] = 0.0;
+      Vzz[e] = TC(0);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) { vx[i] = TC(0); vz[i] = TC(0); }
     for (int e = threadIdx.x; e < n * ldH; e += blockDim.x) {
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       Vxx[e] = TC(0);
       Vzx[e] = (e / n == e % n) ? TC(1) : TC(0);
-      Vzz_g[e] = 0.0;
+      Vzz[e] = TC(0);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) { vx[i] = TC(0); vz[i] = TC(0); }
     rr = 0;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
       cta_mm<RMg, RNg, true, false, TC>(m, m, n, AB + n, ldAB, T1 + n, ldAB, EpiAddSym<TC, TS>{Muu, m, 1.0, Rt, m});
       if (param) {
         // M_zu' = (V_zx B)'  and  m_z = v_z + V_zx c
-        cta_mm<RMg, RNg, true, true, TC>(m, n, n, AB + n, ldAB, Vzx, n, EpiStore<TC>{F + n, ldF, 1.0});
+        cta_mm<RMg, RNg, false, false, TC>(n, m, n, Vzx, n, AB + n, ldAB, EpiStoreT<TC>{F + n, ldF, 1.0});
         cta_mv<false, TC>(n, n, Vzx, n, AB + n + m, ldAB, EpiAdd<TC, TC>{mz, 1, 1.0, vz, 1});
       }
       // M_xx = Q + A'V A  (into the V_xx buffer), m_x = q + A'(V c + v)  (into v_x)
@@ -221,45 +224,71 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
     }
 
     if (rr == 0) {
-      // ---- (4a) unconstrained stage: Cholesky of M_uu in FP64 ----------------
-      if (sizeof(TC) != 8) {
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) L64[e] = static_cast<double>(Muu[e]);
-      }
+      // ---- (4a) unconstrained stage: factor M_uu = L L' ------------------------
+      // FP64 path: FP64 factor, in-place triangular solve. Mixed path: FP64
+      // factor of the FP32-formed M_uu, applied in FP32 through L^{-1}. FP32
+      // path: FP32 factor (hardware rsqrt pivots), applied through L^{-1}.
+      TC* Wp = F;              // W = L^{-1} [M_ux | M_zu' | m_u]
+      const TC* Linv = nullptr;
       if (threadIdx.x == 0) s_flag = 0;
-      __syncthreads();
-      cta_chol(m, L64, m, &s_flag, s_rd);
-      if (s_flag) {
-        if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
-        failed = true;
-        break;
-      }
-      // the factor is computed in FP64 and applied in the compute type
-      const TC* Lc = reinterpret_cast<const TC*>(L64);
-      if (sizeof(TC) != 8) {
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) Muu[e] = static_cast<TC>(L64[e]);
+      if (sizeof(TC) == 8) {
+        __syncthreads();
+        cta_chol(m, L64, m, &s_flag, s_rd);
+        if (s_flag) {
+          if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
+          failed = true;
+          break;
+        }
         for (int i = threadIdx.x; i < m; i += blockDim.x) s_rdc[i] = static_cast<TC>(s_rd[i]);
-        Lc = Muu;
+        __syncthreads();
+        cta_trsm_lower<TC>(m, reinterpret_cast<const TC*>(L64), m, s_rdc, ldF, F, ldF);
         __syncthreads();
       } else {
-        for (int i = threadIdx.x; i < m; i += blockDim.x) s_rdc[i] = static_cast<TC>(s_rd[i]);
+        if (sizeof(TS) == 8) {
+          for (int e = threadIdx.x; e < m * m; e += blockDim.x) L64[e] = static_cast<double>(Muu[e]);
+          __syncthreads();
+          cta_chol(m, L64, m, &s_flag, s_rd);
+          if (s_flag) {
+            if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
+            failed = true;
+            break;
+          }
+          for (int e = threadIdx.x; e < m * m; e += blockDim.x) Muu[e] = static_cast<TC>(L64[e]);
+          for (int i = threadIdx.x; i < m; i += blockDim.x) s_rdc[i] = static_cast<TC>(s_rd[i]);
+          __syncthreads();
+        } else {
+          __syncthreads();
+          cta_chol_f32(m, reinterpret_cast<float*>(Muu), m, &s_flag, s_pivf, reinterpret_cast<float*>(s_rdc));
+          if (s_flag) {
+            if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
+            failed = true;
+            break;
+          }
+        }
+        TC* Li = reinterpret_cast<TC*>(L64);  // the FP64 factor buffer is free now
+        cta_trinv_lower<TC>(m, Muu, m, s_rdc, Li, m);
+        Wp = Wbuf;
+        cta_mm_auto<false, false, TC>(m, ldF, m, Li, m, F, ldF, EpiStore<TC>{Wp, ldF, 1.0});
         __syncthreads();
+        Linv = Li;
       }
-      // W = L^{-1} [M_ux | M_zu' | m_u]
-      cta_trsm_lower<TC>(m, Lc, m, s_rdc, ldF, F, ldF);
-      __syncthreads();
       // V_xx = M_xx - W_x'W_x ;  v_x = m_x - W_x'w
-      cta_mm<RMg, RNg, true, false, TC>(n, n, m, F, ldF, F, ldF, EpiAccum<TC>{Vxx, n, -1.0});
-      cta_mm<RMg, 1, true, false, TC>(n, 1, m, F, ldF, F + cmu, ldF, EpiAccum<TC>{vx, 1, -1.0});
+      cta_mm<RMg, RNg, true, false, TC>(n, n, m, Wp, ldF, Wp, ldF, EpiAccum<TC>{Vxx, n, -1.0});
+      cta_mm<RMg, 1, true, false, TC>(n, 1, m, Wp, ldF, Wp + cmu, ldF, EpiAccum<TC>{vx, 1, -1.0});
       if (param) {
         // V_zx = M_zx - W_z'W_x ; V_zz -= W_z'W_z ; v_z = m_z - W_z'w
-        cta_mm<RMg, RNg, true, false, TC>(n, n, m, F + n, ldF, F, ldF, EpiAccum<TC>{T1, ldAB, -1.0});
-        cta_mm<RMg, RNg, true, false, TC>(n, n, m, F + n, ldF, F + n, ldF, EpiAccum<double>{Vzz_g, n, -1.0});
-        cta_mm<RMg, 1, true, false, TC>(n, 1, m, F + n, ldF, F + cmu, ldF, EpiAdd<TC, TC>{vz, 1, -1.0, mz, 1});
+        cta_mm<RMg, RNg, true, false, TC>(n, n, m, Wp + n, ldF, Wp, ldF, EpiAccum<TC>{T1, ldAB, -1.0});
+        cta_mm<RMg, RNg, true, false, TC>(n, n, m, Wp + n, ldF, Wp + n, ldF, EpiAccum<TC>{Vzz, n, -1.0});
+        cta_mm<RMg, 1, true, false, TC>(n, 1, m, Wp + n, ldF, Wp + cmu, ldF, EpiAdd<TC, TC>{vz, 1, -1.0, mz, 1});
       }
       __syncthreads();
       if (!param) {
         // policy [K_t | k_t] = -L'^{-1} W
-        cta_trsm_lower_t<TC>(m, Lc, m, s_rdc, ldF, F, ldF);
+        if (Linv) {
+          cta_mm_auto<true, false, TC>(m, ldF, m, Linv, m, Wp, ldF, EpiStore<TC>{F, ldF, 1.0});
+        } else {
+          cta_trsm_lower_t<TC>(m, reinterpret_cast<const TC*>(L64), m, s_rdc, ldF, F, ldF);
+        }
         __syncthreads();
         if (gK)
           for (int e = threadIdx.x; e < m * n; e += blockDim.x)
@@ -401,13 +430,13 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
       cta_mm<RMg, 1, true, false, double>(n, 1, m, F, ldF, Gc + 2 * n, ldG, EpiAccum<TC>{vx, 1, 1.0});
       // V_zx = M_zx + F_z'G_x + G_z'E_x (T1 holds M_zx) ; V_zz += F_z'G_z + G_z'E_z ; v_z = m_z + F_z'g + G_z'e
       cta_mm<RMg, RNg, true, false, double>(n, n, m, F + n, ldF, Gc, ldG, EpiAccum<TC>{T1, ldAB, 1.0});
-      cta_mm<RMg, RNg, true, false, double>(n, n, m, F + n, ldF, Gc + n, ldG, EpiAccum<double>{Vzz_g, n, 1.0});
+      cta_mm<RMg, RNg, true, false, double>(n, n, m, F + n, ldF, Gc + n, ldG, EpiAccum<TC>{Vzz, n, 1.0});
       cta_mm<RMg, 1, true, false, double>(n, 1, m, F + n, ldF, Gc + 2 * n, ldG, EpiAdd<TC, TC>{vz, 1, 1.0, mz, 1});
       __syncthreads();
       cta_mm<RMg, RNg, true, false, double>(n, n, m, Gc, ldG, Ec, ldG, EpiAccum<TC>{Vxx, n, 1.0});
       cta_mm<RMg, 1, true, false, double>(n, 1, m, Gc, ldG, Ec + 2 * n, ldG, EpiAccum<TC>{vx, 1, 1.0});
       cta_mm<RMg, RNg, true, false, double>(n, n, m, Gc + n, ldG, Ec, ldG, EpiAccum<TC>{T1, ldAB, 1.0});
-      cta_mm<RMg, RNg, true, false, double>(n, n, m, Gc + n, ldG, Ec + n, ldG, EpiAccum<double>{Vzz_g, n, 1.0});
+      cta_mm<RMg, RNg, true, false, double>(n, n, m, Gc + n, ldG, Ec + n, ldG, EpiAccum<TC>{Vzz, n, 1.0});
       cta_mm<RMg, 1, true, false, double>(n, 1, m, Gc + n, ldG, Ec + 2 * n, ldG, EpiAccum<TC>{vz, 1, 1.0});
       __syncthreads();
       cta_copy<TC>(n, n, T1, ldAB, Vzx, n);
@@ -431,8 +460,10 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
   if (param) {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) summ[nn + e] = static_cast<double>(Vzx[e]);
     for (int i = threadIdx.x; i < n; i += blockDim.x) summ[3 * nn + n + i] = static_cast<double>(vz[i]);
-    __syncthreads();
-    cta_symmetrize<double>(n, Vzz_g, n);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      Vzz_g[e] = 0.5 * (static_cast<double>(Vzz[(size_t)i * n + j]) + static_cast<double>(Vzz[(size_t)j * n + i]));
+    }
   } else {
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) { summ[nn + e] = 0.0; summ[2 * nn + e] = 0.0; }
     for (int i = threadIdx.x; i < n; i += blockDim.x) summ[3 * nn + n + i] = 0.0;
