@@ -67,7 +67,7 @@ typedef enum {
 
 typedef enum {
   LQR_FP64 = 0,       /* all arithmetic in FP64 (the plain method)                          */
-  LQR_FP32 = 1,       /* FP32 data and arithmetic (FP32 factor of R+B'PB); FP64 link solve */
+  LQR_FP32 = 1,       /* FP32 data and arithmetic, sweeps and link solve alike               */
   LQR_MIXED_TF32 = 2, /* FP64 data; FP32 sweeps, FP64 factor/link solve, FP64 KKT refinement */
   LQR_MIXED_BF16 = 3  /* reserved (LQR_ERR_UNSUPPORTED)                                      */
 } lqr_precision;
@@ -84,6 +84,20 @@ typedef enum {
  *      splits. Its x_term blocks lose accuracy like cond(R_L)^2 * eps, where
  *      R_L is the ceil(n/m)-stage reachability matrix at the segment end. */
 typedef enum { LQR_FORM_MULTIPLIER = 0, LQR_FORM_CONSTRAINED = 1 } lqr_form;
+
+/* How the link system of Section II-A (neighbouring segments' multipliers
+ * related through the unknown link points, Eq. 10-11) is solved. Both give the
+ * same Pi_j, pi_j and link points in exact arithmetic.
+ *  LQR_LINK_CHAIN - block elimination from the last link to the first
+ *      (K-1 dependent steps), each step spread over a cluster of CTAs.
+ *  LQR_LINK_SCAN  - the segment summaries composed pairwise as an associative
+ *      suffix scan (ceil(log2 K) levels of independent compositions, one CTA
+ *      each), then the link feedback of every segment in one parallel pass;
+ *      LQR_FP32 with LQR_FORM_MULTIPLIER only (else LQR_ERR_UNSUPPORTED), and
+ *      n up to the shared-memory limit (about 80; larger n: LQR_ERR_UNSUPPORTED).
+ *      The paper does not use a scan: it solves the link system directly.
+ *  LQR_LINK_AUTO  - the scan where it applies, else the chain. */
+typedef enum { LQR_LINK_AUTO = 0, LQR_LINK_CHAIN = 1, LQR_LINK_SCAN = 2 } lqr_link;
 
 typedef struct lqr_handle lqr_handle;
 
@@ -109,6 +123,7 @@ typedef struct {
   lqr_form form;      /* segment parametrisation, see lqr_form                    */
   int residual;       /* 1 = compute the FP64 KKT residual of the returned solution
                          (needs x, u, lam); implied by max_refine > 0              */
+  lqr_link link;      /* link-system solver, see lqr_link (0 = automatic)         */
 } lqr_opts;
 
 /* Scalars of the last solve, read back by lqr_report(). */

@@ -455,4 +455,311 @@ __device__ inline void cta_householder_apply(int nr, int p, const double* V, int
   }
 }
 
+// --- asynchronous global -> shared copies (cp.async, sm_80+) ----------------
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// cnt elements of T from global src to shared dst by all threads of the block
+// (not committed): 16-byte copies when both ends are 16-byte aligned and the
+// size is a multiple of 16 bytes, else one copy per element.
+template <typename T>
+__device__ __forceinline__ void cta_copy_async(T* dst, const T* src, long long cnt) {
+  const bool v16 = (((reinterpret_cast<unsigned long long>(dst) | reinterpret_cast<unsigned long long>(src)) & 15) == 0) &&
+                   ((cnt * (long long)sizeof(T)) % 16 == 0);
+  if (v16) {
+    constexpr int per = 16 / sizeof(T);
+    const long long n16 = cnt / per;
+    for (long long e = threadIdx.x; e < n16; e += blockDim.x) cp_async16(dst + e * per, src + e * per);
+  } else {
+    for (long long e = threadIdx.x; e < cnt; e += blockDim.x) {
+      if (sizeof(T) == 8) cp_async8(dst + e, src + e);
+      else cp_async4(dst + e, src + e);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Register-blocked symmetric eliminations, one barrier per pivot.
+// The d x d matrix is cut into 4 x 4 blocks (nb = ceil(d/4) per side) that
+// live in registers, R blocks per thread at most. In step j every thread
+// reads the current column j from a shared buffer (published by the owners of
+// column j at the end of step j-1, double-buffered so that nobody waits for a
+// second barrier), updates its blocks, and the owners of column j+1 publish
+// it. Rows and columns past d are zero padding and are never stored.
+// `colbuf` (shared) holds 2 * 4nb values. Both routines end with a barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float recip_pivot(float p) { return __frcp_rn(p); }
+__device__ __forceinline__ double recip_pivot(double p) { return rcp_newton(p); }
+__device__ __forceinline__ float rsqrt_pos(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_pos(double v) { return rsqrt(v); }
+
+// Lower Cholesky factor of the SPD matrix G in place (strict upper part set to
+// zero), computed as L D L' with unscaled columns so that the pivot chain
+// needs one reciprocal per step; the square roots are taken at the end.
+// Blocks of the lower triangle only, nb(nb+1)/2 <= R * blockDim.x.
+// rdiag[k] = 1 / L[k][k] if non-null; *flag = 1 on a pivot that is not
+// positive and finite.
+template <typename T, int R>
+__device__ inline void cta_chol_reg(int d, T* G, int ld, int* flag, T* colbuf, T* rdiag) {
+  const int t = threadIdx.x, nthr = blockDim.x;
+  const int nb = (d + 3) >> 2, nb4 = 4 * nb, nlb = nb * (nb + 1) / 2;
+  T v[R][4][4];
+  int bi[R], bk[R];
+  bool own[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int blk = t + r * nthr;
+    own[r] = blk < nlb;
+    int ii = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+    while ((ii + 1) * (ii + 2) / 2 <= blk) ++ii;
+    while (ii * (ii + 1) / 2 > blk) --ii;
+    bi[r] = own[r] ? ii : 0;
+    bk[r] = own[r] ? blk - ii * (ii + 1) / 2 : 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = 4 * bi[r] + a, k = 4 * bk[r] + b;
+        v[r][a][b] = (own[r] && i < d && k <= i) ? G[(size_t)i * ld + k] : T(0);
+      }
+  }
+  for (int i = t; i < nb4; i += nthr) colbuf[i] = i < d ? G[(size_t)i * ld] : T(0);
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    const T* col = colbuf + (j & 1) * nb4;
+    T* nxt = colbuf + ((j + 1) & 1) * nb4;
+    const T p = col[j];
+    if (t == 0 && !(p > T(0) && isfinite(p))) *flag = 1;
+    const T rp = recip_pivot(p);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!own[r] || 4 * bk[r] + 3 <= j) continue;
+      T ci[4], ckr[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ci[a] = col[4 * bi[r] + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) ckr[b] = col[4 * bk[r] + b] * rp;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (4 * bk[r] + b > j) v[r][a][b] = fma(-ci[a], ckr[b], v[r][a][b]);
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * bk[r] + b == j + 1) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            if (4 * bi[r] + a >= j + 1) nxt[4 * bi[r] + a] = v[r][a][b];
+        }
+    }
+    __syncthreads();
+  }
+  // D_k on the diagonal; L = (unscaled column) / sqrt(D_k)
+  T* dg = colbuf;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (own[r] && bi[r] == bk[r])
+#pragma unroll
+      for (int a = 0; a < 4; ++a) dg[4 * bi[r] + a] = v[r][a][a];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (!own[r]) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int k = 4 * bk[r] + b;
+      if (k >= d) continue;
+      const T Dk = dg[k];
+      const T rs = Dk > T(0) ? rsqrt_pos(Dk) : T(1);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = 4 * bi[r] + a;
+        if (i < d && i >= k) G[(size_t)i * ld + k] = (i == k) ? (Dk > T(0) ? Dk * rs : T(1)) : v[r][a][b] * rs;
+      }
+    }
+  }
+  for (int e = t; e < d * d; e += nthr) {
+    const int i = e / d, k = e - i * d;
+    if (k > i) G[(size_t)i * ld + k] = T(0);
+  }
+  if (rdiag)
+    for (int k = t; k < d; k += nthr) rdiag[k] = dg[k] > T(0) ? rsqrt_pos(dg[k]) : T(1);
+  __syncthreads();
+}
+
+// Inverse of the SPD matrix G in place by symmetric Gauss-Jordan elimination
+// (the sweep operator on every pivot, which leaves -G^{-1}); blocks of the full
+// square, nb^2 <= R * blockDim.x. *flag = 1 on a pivot that is not positive.
+// sym: the input is taken as (G + G')/2.
+template <typename T, int R>
+__device__ inline void cta_spd_inverse_reg(int d, T* G, int ld, int* flag, T* colbuf, bool sym = false) {
+  const int t = threadIdx.x, nthr = blockDim.x;
+  const int nb = (d + 3) >> 2, nb4 = 4 * nb;
+  T v[R][4][4];
+  int bi[R], bk[R];
+  bool own[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int blk = t + r * nthr;
+    own[r] = blk < nb * nb;
+    bi[r] = own[r] ? blk / nb : 0;
+    bk[r] = own[r] ? blk % nb : 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = 4 * bi[r] + a, k = 4 * bk[r] + b;
+        T g = T(0);
+        if (own[r] && i < d && k < d) {
+          g = G[(size_t)i * ld + k];
+          if (sym) g = T(0.5) * (g + G[(size_t)k * ld + i]);
+        }
+        v[r][a][b] = g;
+      }
+  }
+  for (int i = t; i < nb4; i += nthr) {
+    T g = T(0);
+    if (i < d) {
+      g = G[(size_t)i * ld];
+      if (sym) g = T(0.5) * (g + G[i]);
+    }
+    colbuf[i] = g;
+  }
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    const T* col = colbuf + (j & 1) * nb4;
+    T* nxt = colbuf + ((j + 1) & 1) * nb4;
+    const T p = col[j];
+    if (t == 0 && !(p > T(0) && isfinite(p))) *flag = 1;
+    const T rp = recip_pivot(p);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!own[r]) continue;
+      T ci[4], ckr[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ci[a] = col[4 * bi[r] + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) ckr[b] = col[4 * bk[r] + b] * rp;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const bool ri = (4 * bi[r] + a == j), ck = (4 * bk[r] + b == j);
+          const T upd = fma(-ci[a], ckr[b], v[r][a][b]);
+          v[r][a][b] = ri ? (ck ? -rp : ckr[b]) : (ck ? ci[a] * rp : upd);
+        }
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * bk[r] + b == j + 1) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a) nxt[4 * bi[r] + a] = v[r][a][b];
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (!own[r]) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = 4 * bi[r] + a, k = 4 * bk[r] + b;
+        if (i < d && k < d) G[(size_t)i * ld + k] = -v[r][a][b];
+      }
+  }
+  __syncthreads();
+}
+
+// FP32 product on 4-aligned shapes with 128-bit shared/global loads:
+//   acc(i,j) = sum_k opA(i,k) B[k][j],  0 <= i < M, 0 <= j < N (M, N multiples of 4)
+//   opA(i,k) = TA ? A[k*lda + i] : A[i*lda + k]
+// A, B 16-byte aligned, lda and ldb multiples of 4. Padding rows/columns of
+// the operands must hold zeros (or finite values whose products the epilogue
+// discards). Each thread owns 4 x 4 output tiles; epi(i, j, v) for every
+// element of the padded M x N range.
+template <bool TA, typename Epi>
+__device__ __forceinline__ void cta_mm4f(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                                         Epi epi) {
+  const int tm = M >> 2, tn = N >> 2;
+  for (int tile = threadIdx.x; tile < tm * tn; tile += blockDim.x) {
+    const int i0 = (tile / tn) << 2, j0 = (tile % tn) << 2;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+    int k = 0;
+    if (!TA) {
+      for (; k + 4 <= K; k += 4) {
+        float4 av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = *reinterpret_cast<const float4*>(A + (size_t)(i0 + a) * lda + k);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bv[q] = *reinterpret_cast<const float4*>(B + (size_t)(k + q) * ldb + j0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float ak[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[a][0] = fmaf(ak[q], bv[q].x, acc[a][0]);
+            acc[a][1] = fmaf(ak[q], bv[q].y, acc[a][1]);
+            acc[a][2] = fmaf(ak[q], bv[q].z, acc[a][2]);
+            acc[a][3] = fmaf(ak[q], bv[q].w, acc[a][3]);
+          }
+        }
+      }
+    }
+    for (; k < K; ++k) {
+      float ak[4];
+      if (TA) {
+        const float4 t4 = *reinterpret_cast<const float4*>(A + (size_t)k * lda + i0);
+        ak[0] = t4.x; ak[1] = t4.y; ak[2] = t4.z; ak[3] = t4.w;
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ak[a] = A[(size_t)(i0 + a) * lda + k];
+      }
+      const float4 bv = *reinterpret_cast<const float4*>(B + (size_t)k * ldb + j0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a][0] = fmaf(ak[a], bv.x, acc[a][0]);
+        acc[a][1] = fmaf(ak[a], bv.y, acc[a][1]);
+        acc[a][2] = fmaf(ak[a], bv.z, acc[a][2]);
+        acc[a][3] = fmaf(ak[a], bv.w, acc[a][3]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) epi(i0 + a, j0 + b, acc[a][b]);
+  }
+}
+
+// y_i = epi(i, sum_k A[i*lda + k] x[k]) for i < M: one warp per row, lanes
+// stride k (conflict-free shared reads), shuffle reduction.
+template <typename T, typename Epi>
+__device__ __forceinline__ void cta_mv_warp(int M, int K, const T* A, int lda, const T* x, Epi epi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < M; i += nw) {
+    T s = T(0);
+    for (int k = lane; k < K; k += 32) s = fma(A[(size_t)i * lda + k], x[k], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) epi(i, s);
+  }
+}
+
 }  // namespace lqr

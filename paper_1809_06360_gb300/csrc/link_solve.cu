@@ -554,21 +554,32 @@ static cudaError_t launch_dual_cluster(const ProbTable& tab, int nprob, int x0_i
   return cudaLaunchKernelEx(&cfg, link_solve_dual_cluster_kernel<CL, T>, tab, x0_is_float, 1);
 }
 
-// cluster width used for the link solve (0 = single CTA); set by launch_link_solve_dual
+// link method of the last single-problem solve: -1 none yet, 0 single CTA,
+// 8/16 cluster chain width, 1000 + levels for the FP32 scan
 static int g_link_cluster = -1;
-cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
+cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st,
+                                        int* nlaunch);
 static int g_link_fp32 = 0;  // set per call by launch_link_solve_dual
 
 int link_cluster_width() { return g_link_cluster; }
 
-cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st, int link_fp32) {
+cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st, int link_fp32,
+                                   int method, int* nlaunch) {
   if (tab.probs) return cudaErrorInvalidValue;
   g_link_fp32 = link_fp32;
-  cudaError_t r = launch_link_solve_dual_impl(tab, nprob, x0_is_float, st);
+  cudaError_t r = cudaErrorNotSupported;
+  int nl = 0;
+  if (link_fp32 && method != LQR_LINK_CHAIN) {
+    r = launch_link_scan(tab, x0_is_float, st, &nl);
+    if (r == cudaSuccess) g_link_cluster = 1000 + nl - 3;
+    if (r == cudaErrorNotSupported && method == LQR_LINK_SCAN) return r;
+  }
+  if (r == cudaErrorNotSupported) r = launch_link_solve_dual_impl(tab, nprob, x0_is_float, st, &nl);
+  if (nlaunch) *nlaunch = nl;
   static int reported = -2;
   if (getenv("LQR_DEBUG") && reported != g_link_cluster) {
-    fprintf(stderr, "liblqr: link solve on %d-CTA clusters (0 = single CTA), n=%d K=%d\n", g_link_cluster,
-            tab.single.n, tab.single.nseg);
+    fprintf(stderr, "liblqr: link solve method %d (0 single CTA, 8/16 cluster chain, 1000+levels scan), n=%d K=%d\n",
+            g_link_cluster, tab.single.n, tab.single.nseg);
     reported = g_link_cluster;
   }
   return r;
@@ -589,7 +600,9 @@ cudaError_t launch_link_solve_dual_batched(const ProbTable& tab, int nprob, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st) {
+cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st,
+                                        int* nlaunch) {
+  *nlaunch = 1;
   {
     const int n = tab.single.n;
     const size_t nn = (size_t)n * n, n1 = (size_t)n + 1;
@@ -620,6 +633,7 @@ cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_
         else
           link_post_kernel<double><<<tab.single.nseg - 1, kBlock, pbytes, st>>>(tab);
         link_forward_kernel<<<1, kBlock, 0, st>>>(tab, x0_is_float);
+        *nlaunch = 3;
         return cudaGetLastError();
       }
       cudaGetLastError();

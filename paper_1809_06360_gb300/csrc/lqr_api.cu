@@ -136,6 +136,9 @@ lqr_status validate(const lqr_problem* p, const lqr_opts* o, const lqr_solution*
   if ((o->max_refine > 0 || o->residual) && (!s->x || !s->u || !s->lam || !s->K || !s->k))
     return LQR_ERR_INVALID_ARG;
   if (o->max_refine > 0 && o->prec == LQR_FP32) return LQR_ERR_UNSUPPORTED;  // refinement needs FP64 data
+  if (o->link != LQR_LINK_AUTO && o->link != LQR_LINK_CHAIN && o->link != LQR_LINK_SCAN) return LQR_ERR_INVALID_ARG;
+  if (o->link == LQR_LINK_SCAN && (o->prec != LQR_FP32 || o->form != LQR_FORM_MULTIPLIER))
+    return LQR_ERR_UNSUPPORTED;
   return LQR_OK;
 }
 
@@ -230,6 +233,10 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
   auto sweep = [&](int phase) {
     if (prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, sp.K, phase, sp.smem, budget, store_P, st);
     if (prec == LQR_MIXED_TF32) return launch_seg_sweep<double, float>(tab, sp.K, phase, sp.smem, budget, store_P, st);
+    if (dual) {
+      const cudaError_t r = launch_seg_sweep_f32(tab, sp.K, phase, tab.single.n, tab.single.m, budget, store_P, st);
+      if (r != cudaErrorNotSupported) return r;
+    }
     return launch_seg_sweep<float, float>(tab, sp.K, phase, sp.smem, budget, store_P, st);
   };
   if (profile) prof_mark(h, LQR_PHASE_SWEEP, st);
@@ -246,8 +253,15 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
   }
   const int x0f = (prec == LQR_FP32) ? 1 : 0;
   // the boundary-coupling solve runs in FP64 except in the all-FP32 mode
-  e = dual ? launch_link_solve_dual(tab, 1, x0f, st, prec == LQR_FP32 ? 1 : 0) : launch_link_solve(tab, 1, x0f, st);
-  ++*launches;
+  if (dual) {
+    int nl = 0;
+    e = launch_link_solve_dual(tab, 1, x0f, st, prec == LQR_FP32 ? 1 : 0, o->link, &nl);
+    *launches += nl;
+    if (e == cudaErrorNotSupported) return LQR_ERR_UNSUPPORTED;
+  } else {
+    e = launch_link_solve(tab, 1, x0f, st);
+    ++*launches;
+  }
   if (e != cudaSuccess) return LQR_ERR_CUDA;
   if (profile) prof_mark(h, LQR_PHASE_POLICY, st);
   if (sp.K > 1) {
@@ -257,10 +271,11 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
   }
   if (profile) prof_mark(h, LQR_PHASE_ROLLOUT, st);
   if (want_traj) {
+    const int xu = (tab.single.x && tab.single.u) ? 1 : 0;
     if (prec == LQR_FP32)
-      e = launch_rollout<float, float>(tab, sp.K, want_lam ? 1 : 0, st);
+      e = launch_rollout<float, float>(tab, sp.K, want_lam ? 1 : 0, st, 0, 0, xu);
     else
-      e = launch_rollout<double, double>(tab, sp.K, want_lam ? 1 : 0, st);
+      e = launch_rollout<double, double>(tab, sp.K, want_lam ? 1 : 0, st, 0, 0, xu);
     ++*launches;
     if (e != cudaSuccess) return LQR_ERR_CUDA;
     e = launch_finalize(tab, 1, st);
@@ -465,16 +480,22 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
   int launches = 0;
   int store_P = 0;
   bool want_traj = false, want_lam = false;
+  int all_xu = 1;
   for (int i = 0; i < nprob; ++i) {
     if (sols[i].P) store_P = 1;
     if (sols[i].x || sols[i].u) want_traj = true;
     if (sols[i].lam) want_lam = true;
+    if (!sols[i].x || !sols[i].u) all_xu = 0;
   }
   cudaError_t e;
   auto sweep = [&](int phase) {
     if (o->prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, nunits, phase, smem_max, budget, store_P, st);
     if (o->prec == LQR_MIXED_TF32)
       return launch_seg_sweep<double, float>(tab, nunits, phase, smem_max, budget, store_P, st);
+    if (!cons) {
+      const cudaError_t r = launch_seg_sweep_f32(tab, nunits, phase, nmax, mmax, budget, store_P, st);
+      if (r != cudaErrorNotSupported) return r;
+    }
     return launch_seg_sweep<float, float>(tab, nunits, phase, smem_max, budget, store_P, st);
   };
   prof_mark(h, LQR_PHASE_SWEEP, st);
@@ -495,8 +516,8 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
   }
   prof_mark(h, LQR_PHASE_ROLLOUT, st);
   if (want_traj) {
-    e = (o->prec == LQR_FP32) ? launch_rollout<float, float>(tab, nunits, want_lam ? 1 : 0, st, nmax, mmax)
-                              : launch_rollout<double, double>(tab, nunits, want_lam ? 1 : 0, st, nmax, mmax);
+    e = (o->prec == LQR_FP32) ? launch_rollout<float, float>(tab, nunits, want_lam ? 1 : 0, st, nmax, mmax, all_xu)
+                              : launch_rollout<double, double>(tab, nunits, want_lam ? 1 : 0, st, nmax, mmax, all_xu);
     ++launches;
     if (e != cudaSuccess) return LQR_ERR_CUDA;
     e = launch_finalize(tab, nprob, st);

@@ -32,6 +32,7 @@ struct WsLayout {
   long long lkRd;   // K * n             1 / diag(Ld)
   long long lkF;    // K * n (n+1)       Ld^-1 C'[Z_j | v_j]
   long long lkV;    // K * n             v_j = w_j - W_j pi_{j+1}
+  long long scan;   // 3 K scan_elem_floats(n) / 2   FP32 link-scan elements (base, ping, pong)
   long long total;
 };
 
@@ -54,8 +55,17 @@ __host__ __device__ inline WsLayout ws_layout(int n, int K) {
   w.lkRd = o;  o += (long long)K * n;
   w.lkF = o;   o += (long long)K * n * (n + 1);
   w.lkV = o;   o += (long long)K * n;
+  o = (o + 31) & ~31LL;
+  w.scan = o;
+  if (K > 1) o += (3LL * K * (((3 * nn + 2 * n) + 3) & ~3LL) + 1) / 2;
   w.total = (o + 31) & ~31LL;
   return w;
+}
+
+// Floats per element of the FP32 link scan: P | Z | -W (n x n each) | p | w,
+// rounded up to a multiple of 4 (16-byte aligned elements).
+__host__ __device__ inline long long scan_elem_floats(int n) {
+  return ((3LL * n * n + 2LL * n) + 3) & ~3LL;
 }
 
 // One problem as the kernels see it.
@@ -204,11 +214,26 @@ template <typename TS, typename TC>
 long long sweep_smem_needed(int n, int m, long long smem_budget, bool constrained, long long* scratch_doubles);
 
 cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st);
+// The FP32 multiplier-form segment sweep (steps A1/A4) on padded 4 x 4 tiles;
+// cudaErrorNotSupported (nothing launched) when its plan does not fit.
+cudaError_t launch_seg_sweep_f32(const ProbTable& tab, int nunits, int phase, int nmax, int mmax,
+                                 long long smem_budget, int store_P, cudaStream_t st);
+long long fast_sweep_smem_bytes(int n, int m);
+
+// Dual link solve of one problem. link_fp32 selects FP32 arithmetic; method
+// is an lqr_link value (the scan needs link_fp32). *nlaunch = kernels launched.
 cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st,
-                                   int link_fp32);
+                                   int link_fp32, int method, int* nlaunch);
+// The FP32 suffix-scan link solve; cudaErrorNotSupported (nothing launched)
+// when the problem shape does not fit.
+cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t st, int* launches);
+size_t link_scan_smem_bytes(int n);
 
 template <typename TS, typename TC>
-cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st, int nmax = 0, int mmax = 0);
+// has_xu: every problem of the launch has x and u outputs (the streaming
+// kernel re-reads them for the multiplier pass).
+cudaError_t launch_rollout(const ProbTable& tab, int nunits, int want_lam, cudaStream_t st, int nmax = 0, int mmax = 0,
+                           int has_xu = 0);
 cudaError_t launch_link_solve_dual_batched(const ProbTable& tab, int nprob, int nmax, int x0_is_float, cudaStream_t st);
 
 cudaError_t launch_finalize(const ProbTable& tab, int nprob, cudaStream_t st);

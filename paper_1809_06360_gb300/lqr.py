@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "LQR_OK", 1: "LQR_ERR_INVALID_ARG", 2: "LQR_ERR_NOT_PD", 3: "
 NOALLOC_MAX_STAGES = 65536
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tf32": 2, "mixed_bf16": 3}
 FORM = {"multiplier": 0, "constrained": 1}
+LINK = {"auto": 0, "chain": 1, "scan": 2}
 
 PROBLEM_FIELDS = ("A", "B", "c", "Q", "R", "S", "q", "r", "x0")
 SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
@@ -43,7 +44,7 @@ class lqr_solution(ctypes.Structure):
 
 class lqr_opts(ctypes.Structure):
     _fields_ = [("prec", c_int), ("num_segments", c_int), ("tol", c_double), ("max_refine", c_int),
-                ("debug_checks", c_int), ("form", c_int), ("residual", c_int)]
+                ("debug_checks", c_int), ("form", c_int), ("residual", c_int), ("link", c_int)]
 
 
 class lqr_report_t(ctypes.Structure):
@@ -223,6 +224,10 @@ class Solver:
         self.device = device
         self.h = lqr_create(device, workspace_hint)
 
+    def last_launch_count(self) -> int:
+        """Kernels launched by the last solve on this handle."""
+        return lqr_last_launch_count(self.h)
+
     def close(self):
         if self.h:
             lqr_destroy(self.h)
@@ -267,7 +272,7 @@ class Solver:
         return out
 
     def solve(self, prob, num_segments=0, prec="fp64", out=None, want=("K", "k", "x", "u", "lam"),
-              stream=None, tol=1e-8, max_refine=0, form="multiplier", residual=False):
+              stream=None, tol=1e-8, max_refine=0, form="multiplier", residual=False, link="auto"):
         """Enqueue a solve on `stream` (torch stream; default current). Returns the output tensors."""
         if out is None:
             out = self.alloc_solution(prob, want)
@@ -275,7 +280,7 @@ class Solver:
         p = self.make_problem_struct(prob, ptr)
         s = lqr_solution(**{f: (out[f].data_ptr() if f in out else None) for f in SOLUTION_FIELDS})
         o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
-                     debug_checks=0, form=FORM[form], residual=1 if residual else 0)
+                     debug_checks=0, form=FORM[form], residual=1 if residual else 0, link=LINK[link])
         lqr_solve(self.h, p, o, s, self._stream(stream))
         return out
 
@@ -344,7 +349,7 @@ class Solver:
         return buf
 
     def solve_host(self, prob_np, num_segments=0, prec="fp64", out_np=None, want=("K", "k", "x", "u"),
-                   stream=None, form="multiplier", tol=1e-8, max_refine=0, residual=False):
+                   stream=None, form="multiplier", tol=1e-8, max_refine=0, residual=False, link="auto"):
         """Host-memory solve (numpy arrays, ideally pinned): copies in, solves, copies out, synchronises."""
         import numpy as np
         n, m, T = self._dims(prob_np)
@@ -356,6 +361,6 @@ class Solver:
         p = self.make_problem_struct(prob_np, lambda a: a.ctypes.data)
         s = lqr_solution(**{f: (out_np[f].ctypes.data if f in out_np else None) for f in SOLUTION_FIELDS})
         o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
-                     debug_checks=0, form=FORM[form], residual=1 if residual else 0)
+                     debug_checks=0, form=FORM[form], residual=1 if residual else 0, link=LINK[link])
         lqr_solve_host(self.h, p, o, s, self._stream(stream))
         return out_np

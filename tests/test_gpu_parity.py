@@ -179,8 +179,8 @@ FP32_BOUND = {"K": 1e-4, "k": 1e-4, "x": 1e-4, "u": 1e-4}
 
 
 def test_fp32_path_error_is_bounded(solver):
-    """FP32 data and arithmetic (FP64 Cholesky and link solve): the error
-    against the FP64 oracle, per quantity, on the n=12 workload."""
+    """FP32 data and arithmetic (sweeps and link solve): the error against
+    the FP64 oracle, per quantity, on the n=12 workload."""
     prob = workloads.config0()
     ref = oracle.riccati(prob)
     out = solver.solve(to_dev(prob, torch.float32), num_segments=8, prec="fp32")
@@ -192,8 +192,8 @@ def test_fp32_path_error_is_bounded(solver):
 
 @pytest.mark.parametrize("K", [64, 256])
 def test_fp32_config1_full_size(solver, config1, K):
-    """FP32 sweeps with FP64 factor and link solve on the bench workload; the
-    per-quantity error against the FP64 oracle is bounded (and printed)."""
+    """The all-FP32 path on the bench workload; the per-quantity error
+    against the FP64 oracle is bounded (and printed)."""
     prob, ref = config1
     out = solver.solve(to_dev(prob, torch.float32), num_segments=K, prec="fp32")
     assert solver.report()["status"] == 0
