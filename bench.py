@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Throughput of the segment-parallel Riccati solve (LQR stages/s) on GB300.
 
-One step = one full solve (parametric segment sweeps, FP64 link solve, policy
+One step = one full solve (parametric segment sweeps, link solve, policy
 sweeps, rollout with multipliers and cost) of the long-horizon workload
 n=64, m=32, T=4096, rho(A_t) <= 1.02, on synthetic seeded data with inputs
 resident in HBM. Under torchrun every rank solves its own replica (the method
@@ -40,10 +40,26 @@ PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 80.5
 
 
 def link_flops(n: int, K: int) -> float:
-    """Algorithmic FP64 flops of one launch of the link solve (dual form): per
+    """Algorithmic FP64 flops of the block-elimination link solve (dual form): per
     link two n x n factorisations (n^3/3 each), W C, C'Z, C'(W C), L^-1 E, F'F,
     L^-T F (n^3 each, triangular or symmetric halves) and (W C) G (2n^3)."""
     return (K - 1) * (2 * n ** 3 / 3 + 6 * n ** 3 + 2 * n ** 3)
+
+
+def link_scan_flops(n: int, K: int) -> float:
+    """Algorithmic FP32 flops of the scan link solve as implemented: every
+    composition has one Cholesky factor (n^3/3) and one Gauss-Jordan inverse
+    (2n^3) of n x n matrices plus 2n^3 per n x n product: 11 products for a
+    full composition, 5 when the later element already holds the global value
+    function (P, p only), 6 for the feedback pass; levels s = 1, 2, 4, .. < K
+    have max(0, K - 2s) full and min(K - s, s) final compositions."""
+    fac = n ** 3 / 3 + 2 * n ** 3
+    full, final, post = fac + 22 * n ** 3, fac + 10 * n ** 3, fac + 12 * n ** 3
+    tot, s = 0.0, 1
+    while s < K:
+        tot += max(0, K - 2 * s) * full + min(K - s, s) * final
+        s *= 2
+    return tot + (K - 1) * post
 
 
 def rollout_bytes(n: int, m: int, T: int, es: int) -> float:
@@ -54,16 +70,18 @@ def rollout_bytes(n: int, m: int, T: int, es: int) -> float:
 
 
 def sweep_flops(n: int, m: int, T: int, K: int, phase: str) -> float:
-    """Algorithmic FLOPs of one launch of a segment-sweep kernel.
+    """Algorithmic FLOPs of one launch of a segment-sweep kernel, counted for the
+    FP32 kernel's evaluation order (2 flops per multiply-add).
 
-    Per stage of a parametric segment (V_xx[A|B|c], M_ux, M_uu, M_zu, M_xx, M_zx,
-    Cholesky and triangular solve of M_uu, the V_xx, V_zx, V_zz downdates):
-        6n^3 + 12n^2 m + 4n m^2 + m^3/3
+    Per stage of a parametric segment: V[A|B|c], B'(V[A|B|c]) (M_ux, M_uu, m_u),
+    A'V A, Z B, Z A, the Gauss-Jordan inverse of M_uu (2m^3), H = M_uu^-1 [M_ux |
+    M_zu' | m_u] and the V_xx, Z, -W downdates:
+        6n^3 + 12n^2 m + 6n m^2 + 2m^3
     Per stage of a plain Riccati sweep (terminal segment, policy sweep):
-        4n^3 + 6n^2 m + 4n m^2 + m^3/3
+        4n^3 + 6n^2 m + 4n m^2 + 2m^3
     """
-    par = 6 * n ** 3 + 12 * n ** 2 * m + 4 * n * m ** 2 + m ** 3 / 3
-    pla = 4 * n ** 3 + 6 * n ** 2 * m + 4 * n * m ** 2 + m ** 3 / 3
+    par = 6 * n ** 3 + 12 * n ** 2 * m + 6 * n * m ** 2 + 2 * m ** 3
+    pla = 4 * n ** 3 + 6 * n ** 2 * m + 4 * n * m ** 2 + 2 * m ** 3
     last = T - (K - 1) * T // K
     if phase == "sweep":
         return (T - last) * par + last * pla
@@ -194,7 +212,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "mixed"])
-    ap.add_argument("--segments", type=int, default=64)
+    ap.add_argument("--segments", type=int, default=0, help="0 = the library's choice (one per SM)")
     ap.add_argument("--form", default="multiplier", choices=["multiplier", "constrained"])
     ap.add_argument("--T", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true")
@@ -240,6 +258,7 @@ def main():
     if rep["status"] != 0:
         raise SystemExit("solve failed: %s" % rep)
     launches_per_step = lqr.lqr_last_launch_count(solver.h)
+    K = rep["num_segments"]
 
     # KKT residual of the benchmarked solution, by the library's own FP64 residual
     # pass (step A7), once, outside the timing
@@ -280,14 +299,21 @@ def main():
     alu_peak = PEAK_FP64_TFLOPS if fp64_pipe else PEAK_FP32_TFLOPS
     es = 4 if args.prec == "fp32" else 8
     hbm = measured_peaks().get("hbm_gbs", 6780.4)
+    fast = args.prec == "fp32" and args.form == "multiplier"
+    sweep_k = "seg_sweep_f32_kernel" if fast else "seg_sweep_kernel"
+    if fast:
+        link = {"kernel": "link_scan_kernel levels + feedback pass + link states (A3, FP32 scan)", "bound": "alu",
+                "unit": "TFLOP/s", "work": link_scan_flops(n, K), "peak": PEAK_FP32_TFLOPS}
+    else:
+        link = {"kernel": "link_solve_dual_cluster_kernel (A3, FP64 block elimination)", "bound": "alu",
+                "unit": "TFLOP/s", "work": link_flops(n, K), "peak": PEAK_FP64_TFLOPS}
     phases = {
-        "sweep": {"kernel": "seg_sweep_kernel phase 0 (A1)", "bound": "alu", "unit": "TFLOP/s",
+        "sweep": {"kernel": sweep_k + " phase 0 (A1)", "bound": "alu", "unit": "TFLOP/s",
                   "work": sweep_flops(n, m, T, K, "sweep"), "peak": alu_peak},
-        "policy": {"kernel": "seg_sweep_kernel phase 1 (A4)", "bound": "alu", "unit": "TFLOP/s",
+        "policy": {"kernel": sweep_k + " phase 1 (A4)", "bound": "alu", "unit": "TFLOP/s",
                    "work": sweep_flops(n, m, T, K, "policy"), "peak": alu_peak},
-        "link": {"kernel": "link_solve_dual_cluster_kernel<16> (A3, FP64)", "bound": "alu", "unit": "TFLOP/s",
-                 "work": link_flops(n, K), "peak": PEAK_FP64_TFLOPS},
-        "rollout": {"kernel": "rollout_kernel + finalize (A5/A6)", "bound": "hbm", "unit": "GB/s",
+        "link": link,
+        "rollout": {"kernel": "rollout_stream_kernel + finalize (A5/A6)", "bound": "hbm", "unit": "GB/s",
                     "work": rollout_bytes(n, m, T, es), "peak": hbm},
     }
     for k, d in phases.items():

@@ -684,6 +684,561 @@ __device__ inline void cta_spd_inverse_reg(int d, T* G, int ld, int* flag, T* co
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric eliminations with one BR x BC register block per thread (the
+// block grid ceil(d/BR) x ceil(d/BC) must not exceed blockDim.x), one barrier
+// per pivot. The owner of the next pivot publishes its reciprocal together
+// with the pivot column, so a step costs each thread BR + BC shared loads and
+// BR*BC fused multiply-adds. colbuf: 2 * dp values, rpv: 2 values (shared),
+// dp = max(BR ceil(d/BR), BC ceil(d/BC)). Both end with a barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float recip_fast(float p) {
+  // hardware approximation refined by one Newton-Raphson step r += r (1 - p r)
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+  return fmaf(r, fmaf(-p, r, 1.0f), r);
+}
+__device__ __forceinline__ double recip_fast(double p) { return rcp_newton(p); }
+
+// Inverse of the SPD matrix G in place (Gauss-Jordan sweep on every pivot);
+// sym: the input is taken as (G + G')/2. *flag = 1 on a pivot that is not
+// positive and finite.
+template <typename T, int BR, int BC>
+__device__ inline void cta_spd_inverse_blk(int d, T* G, int ld, int* flag, T* colbuf, T* rpv, bool sym) {
+  const int t = threadIdx.x;
+  const int nbr = (d + BR - 1) / BR, nbc = (d + BC - 1) / BC;
+  const int dp = (nbr * BR > nbc * BC) ? nbr * BR : nbc * BC;
+  const bool own = t < nbr * nbc;
+  const int i0 = own ? (t / nbc) * BR : 0, k0 = own ? (t % nbc) * BC : 0;
+  T v[BR][BC];
+#pragma unroll
+  for (int a = 0; a < BR; ++a)
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+      const int i = i0 + a, k = k0 + b;
+      T g = T(0);
+      if (own && i < d && k < d) {
+        g = G[(size_t)i * ld + k];
+        if (sym) g = T(0.5) * (g + G[(size_t)k * ld + i]);
+      }
+      v[a][b] = g;
+    }
+  for (int i = t; i < dp; i += blockDim.x) {
+    T g = T(0);
+    if (i < d) {
+      g = G[(size_t)i * ld];
+      if (sym) g = T(0.5) * (g + G[i]);
+    }
+    colbuf[i] = g;
+    if (i == 0) {
+      if (!(g > T(0) && isfinite(g))) *flag = 1;
+      rpv[0] = recip_fast(g);
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    const T* col = colbuf + (j & 1) * dp;
+    T* nxt = colbuf + ((j + 1) & 1) * dp;
+    if (own) {
+      const T rp = rpv[j & 1];
+      T ci[BR], ckr[BC];
+#pragma unroll
+      for (int a = 0; a < BR; ++a) ci[a] = col[i0 + a];
+#pragma unroll
+      for (int b = 0; b < BC; ++b) ckr[b] = col[k0 + b] * rp;
+#pragma unroll
+      for (int a = 0; a < BR; ++a)
+#pragma unroll
+        for (int b = 0; b < BC; ++b) v[a][b] = fma(-ci[a], ckr[b], v[a][b]);
+      const bool hr = (j >= i0 && j < i0 + BR), hc = (j >= k0 && j < k0 + BC);
+      if (hr || hc) {
+#pragma unroll
+        for (int a = 0; a < BR; ++a)
+#pragma unroll
+          for (int b = 0; b < BC; ++b) {
+            const bool ri = (i0 + a == j), cj = (k0 + b == j);
+            if (ri && cj) v[a][b] = -rp;
+            else if (ri) v[a][b] = ckr[b];
+            else if (cj) v[a][b] = ci[a] * rp;
+          }
+      }
+      if (j + 1 >= k0 && j + 1 < k0 + BC) {
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+          if (k0 + b == j + 1) {
+#pragma unroll
+            for (int a = 0; a < BR; ++a) {
+              nxt[i0 + a] = v[a][b];
+              if (i0 + a == j + 1 && j + 1 < d) {
+                const T pn = v[a][b];
+                if (!(pn > T(0) && isfinite(pn))) *flag = 1;
+                rpv[(j + 1) & 1] = recip_fast(pn);
+              }
+            }
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (own)
+#pragma unroll
+    for (int a = 0; a < BR; ++a)
+#pragma unroll
+      for (int b = 0; b < BC; ++b) {
+        const int i = i0 + a, k = k0 + b;
+        if (i < d && k < d) G[(size_t)i * ld + k] = -v[a][b];
+      }
+  __syncthreads();
+}
+
+// Lower Cholesky factor of the SPD matrix G in place (strict upper part set to
+// zero) as L D L' with unscaled columns; rdiag[k] = 1 / L[k][k] if non-null.
+template <typename T, int BR, int BC>
+__device__ inline void cta_chol_blk(int d, T* G, int ld, int* flag, T* colbuf, T* rpv, T* rdiag) {
+  const int t = threadIdx.x;
+  const int nbr = (d + BR - 1) / BR, nbc = (d + BC - 1) / BC;
+  const int dp = (nbr * BR > nbc * BC) ? nbr * BR : nbc * BC;
+  bool own = t < nbr * nbc;
+  const int i0 = own ? (t / nbc) * BR : 0, k0 = own ? (t % nbc) * BC : 0;
+  own = own && (i0 + BR - 1 >= k0);  // the block meets the lower triangle
+  T v[BR][BC];
+#pragma unroll
+  for (int a = 0; a < BR; ++a)
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+      const int i = i0 + a, k = k0 + b;
+      v[a][b] = (own && i < d && k <= i) ? G[(size_t)i * ld + k] : T(0);
+    }
+  for (int i = t; i < dp; i += blockDim.x) {
+    const T g = i < d ? G[(size_t)i * ld] : T(0);
+    colbuf[i] = g;
+    if (i == 0) {
+      if (!(g > T(0) && isfinite(g))) *flag = 1;
+      rpv[0] = recip_fast(g);
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < d; ++j) {
+    const T* col = colbuf + (j & 1) * dp;
+    T* nxt = colbuf + ((j + 1) & 1) * dp;
+    if (own && k0 + BC - 1 > j) {
+      const T rp = rpv[j & 1];
+      T ci[BR], ckr[BC];
+#pragma unroll
+      for (int a = 0; a < BR; ++a) ci[a] = col[i0 + a];
+#pragma unroll
+      for (int b = 0; b < BC; ++b) ckr[b] = col[k0 + b] * rp;
+#pragma unroll
+      for (int a = 0; a < BR; ++a)
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+          if (k0 + b > j) v[a][b] = fma(-ci[a], ckr[b], v[a][b]);
+      if (j + 1 >= k0 && j + 1 < k0 + BC) {
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+          if (k0 + b == j + 1) {
+#pragma unroll
+            for (int a = 0; a < BR; ++a)
+              if (i0 + a >= j + 1) {
+                nxt[i0 + a] = v[a][b];
+                if (i0 + a == j + 1 && j + 1 < d) {
+                  const T pn = v[a][b];
+                  if (!(pn > T(0) && isfinite(pn))) *flag = 1;
+                  rpv[(j + 1) & 1] = recip_fast(pn);
+                }
+              }
+          }
+      }
+    }
+    __syncthreads();
+  }
+  T* dg = colbuf;  // D_k
+  if (own)
+#pragma unroll
+    for (int a = 0; a < BR; ++a)
+#pragma unroll
+      for (int b = 0; b < BC; ++b)
+        if (i0 + a == k0 + b && i0 + a < d) dg[i0 + a] = v[a][b];
+  __syncthreads();
+  if (own)
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+      const int k = k0 + b;
+      if (k >= d) continue;
+      const T Dk = dg[k];
+      const T rs = Dk > T(0) ? rsqrt_pos(Dk) : T(1);
+#pragma unroll
+      for (int a = 0; a < BR; ++a) {
+        const int i = i0 + a;
+        if (i < d && i >= k) G[(size_t)i * ld + k] = (i == k) ? (Dk > T(0) ? Dk * rs : T(1)) : v[a][b] * rs;
+      }
+    }
+  for (int e = t; e < d * d; e += blockDim.x) {
+    const int i = e / d, k = e - i * d;
+    if (k > i) G[(size_t)i * ld + k] = T(0);
+  }
+  if (rdiag)
+    for (int k = t; k < d; k += blockDim.x) rdiag[k] = dg[k] > T(0) ? rsqrt_pos(dg[k]) : T(1);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// 4 x 4 block eliminations: d/4 pivot steps instead of d, each a rank-4
+// update. Thread t owns the BR x BC register block (BC a multiple of 4, BR in
+// {1, 2, 4}); the block grid must not exceed blockDim.x. Rows and columns
+// past d are padding (zero; padded pivots are taken as 1).
+// Per step: (a) the threads i < d4 invert the 4 x 4 pivot block in registers
+// (redundantly) and form w_i = P^-1 c_i from the published pivot columns;
+// (b) every owner applies the update and the owners of the next pivot
+// columns publish them. Two barriers per step.
+// Shared scratch: p4_scratch_floats(d) floats, 16-byte aligned.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int p4_scratch_floats(int d) {
+  const int d4 = (d + 3) & ~3;
+  return 16 * d4 + 16;
+}
+
+// Register-block shape for d on 512 threads: 0 = (1,4), 1 = (2,4), 2 = (4,4),
+// 3 = (4,8) (block grid (d4/BR) x (d4/BC) <= 512 and both dividing d4), -1 = none.
+__host__ __device__ inline int p4_shape(int d) {
+  const int d4 = (d + 3) & ~3;
+  if (d4 <= 32) return 0;
+  if (d4 <= 64) return 1;
+  if (d4 <= 88) return 2;
+  if (d4 <= 128 && d4 % 8 == 0) return 3;
+  return -1;
+}
+
+// In-register inverse of the 4 x 4 SPD matrix m (row-major) by the sweep
+// operator: m <- m^-1. bad |= a pivot that is not positive and finite.
+template <typename T>
+__device__ __forceinline__ void inv4_spd(T m[16], bool& bad) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T p = m[j * 4 + j];
+    bad |= !(p > T(0) && isfinite(p));
+    const T r = recip_fast(p);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (i != j && k != j) m[i * 4 + k] = fma(-m[i * 4 + j] * r, m[j * 4 + k], m[i * 4 + k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k != j) m[j * 4 + k] *= r;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i != j) m[i * 4 + j] *= r;
+    m[j * 4 + j] = -r;
+  }
+#pragma unroll
+  for (int e = 0; e < 16; ++e) m[e] = -m[e];
+}
+
+// In-register lower Cholesky factor L of the 4 x 4 SPD matrix m (row-major,
+// lower triangle read) and Li = L^-1 (lower). bad |= a pivot that is not
+// positive and finite.
+template <typename T>
+__device__ __forceinline__ void chol4(const T m[16], T L[16], T Li[16], bool& bad) {
+  T rs[4];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) L[e] = T(0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    T dj = m[j * 4 + j];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < j) dj = fma(-L[j * 4 + k], L[j * 4 + k], dj);
+    bad |= !(dj > T(0) && isfinite(dj));
+    rs[j] = dj > T(0) ? rsqrt_pos(dj) : T(1);
+    L[j * 4 + j] = dj > T(0) ? dj * rs[j] : T(1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i > j) {
+        T a = m[i * 4 + j];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < j) a = fma(-L[i * 4 + k], L[j * 4 + k], a);
+        L[i * 4 + j] = a * rs[j];
+      }
+  }
+  // Li by forward substitution, 1/L_ii = rs[i]
+#pragma unroll
+  for (int e = 0; e < 16; ++e) Li[e] = T(0);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i < c) continue;
+      T a = (i == c) ? T(1) : T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k >= c && k < i) a = fma(-L[i * 4 + k], Li[k * 4 + c], a);
+      Li[i * 4 + c] = a * rs[i];
+    }
+}
+
+__device__ __forceinline__ float comp4(const float4& v, int r) {
+  return r == 0 ? v.x : (r == 1 ? v.y : (r == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+// Inverse of the SPD matrix G in place; sym: the input is taken as (G + G')/2.
+// Step J with the 4 x 4 pivot block P = L L': w_i = L^-1 c_i, u_i = L^-T w_i
+// (= P^-1 c_i); a_ik -= w_i'w_k off the pivot rows and columns (symmetric),
+// u_k / u_i on them, -P^-1 on the pivot block. *flag = 1 on a pivot block that
+// is not positive definite.
+template <int BR, int BC>
+__device__ inline void cta_spd_inverse_p4(int d, float* G, int ld, int* flag, float* scr, bool sym) {
+  static_assert(BC % 4 == 0 && (BR == 1 || BR == 2 || BR == 4), "block shape");
+  const int t = threadIdx.x;
+  const int d4 = (d + 3) & ~3;
+  const int nbr = d4 / BR, nbc = d4 / BC;
+  // row-fast mapping: the lanes of a warp share k0 and take consecutive row blocks
+  // (broadcast loads of w_k, conflict-free loads of w_i and of the matrix)
+  const bool own = t < nbr * nbc;
+  const int i0 = own ? (t % nbr) * BR : 0, k0 = own ? (t / nbr) * BC : 0;
+  float4* Cb = reinterpret_cast<float4*>(scr);  // 2 x d4: pivot columns, row i = (a_i,p0 .. a_i,p0+3)
+  float4* Wb = Cb + 2 * d4;                     // d4: w_i
+  float4* Ub = Wb + d4;                         // d4: u_i
+  float4* Pn = reinterpret_cast<float4*>(scr + 16 * d4);  // 4 rows of -P^-1
+  float v[BR][BC];
+#pragma unroll
+  for (int a = 0; a < BR; ++a)
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+      const int i = i0 + a, k = k0 + b;
+      float g = 0.0f;
+      if (own && i < d && k < d) {  // read transposed: symmetric in exact arithmetic
+        g = G[(size_t)k * ld + i];
+        if (sym) g = 0.5f * (g + G[(size_t)i * ld + k]);
+      }
+      v[a][b] = g;
+    }
+  if (own && k0 == 0)
+#pragma unroll
+    for (int a = 0; a < BR; ++a) Cb[i0 + a] = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+  bool bad = false;
+  __syncthreads();
+  for (int J = 0; J < d4 / 4; ++J) {
+    const int p0 = 4 * J;
+    const float4* C = Cb + (J & 1) * d4;
+    float4* Cn = Cb + ((J + 1) & 1) * d4;
+    if (t < d4) {  // (a) the pivot factor (redundantly), w_t and u_t
+      float m[16], L[16], Li[16];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 c = C[p0 + r];
+        m[r * 4 + 0] = c.x; m[r * 4 + 1] = c.y; m[r * 4 + 2] = c.z; m[r * 4 + 3] = c.w;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (p0 + r >= d) {  // padded pivot: identity
+#pragma unroll
+          for (int q = 0; q < 4; ++q) { m[r * 4 + q] = 0.0f; m[q * 4 + r] = 0.0f; }
+          m[r * 4 + r] = 1.0f;
+        }
+      bool b2 = false;
+      chol4(m, L, Li, b2);
+      const float4 c = C[t];
+      float w[4], u[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k <= r; ++k) s = fmaf(Li[r * 4 + k], comp4(c, k), s);
+        w[r] = s;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {  // u = Li' w
+        float s = 0.0f;
+#pragma unroll
+        for (int k = r; k < 4; ++k) s = fmaf(Li[k * 4 + r], w[k], s);
+        u[r] = s;
+      }
+      Wb[t] = make_float4(w[0], w[1], w[2], w[3]);
+      Ub[t] = make_float4(u[0], u[1], u[2], u[3]);
+      if (t == 0) {
+        bad |= b2;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {  // rows of -P^-1 = -Li' Li
+          float pr[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float s = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s = fmaf(Li[k * 4 + r], Li[k * 4 + q], s);
+            pr[q] = -s;
+          }
+          Pn[r] = make_float4(pr[0], pr[1], pr[2], pr[3]);
+        }
+      }
+    }
+    __syncthreads();
+    if (own) {  // (b) the update of the owned block
+      float4 wk[BC];
+#pragma unroll
+      for (int b = 0; b < BC; ++b) wk[b] = Wb[k0 + b];
+#pragma unroll
+      for (int a = 0; a < BR; ++a) {
+        const float4 wi = Wb[i0 + a];
+#pragma unroll
+        for (int b = 0; b < BC; ++b) v[a][b] -= dot4(wi, wk[b]);
+      }
+      // the pivot columns (u_i, or -P^-1 on the pivot rows) and the pivot rows (u_k)
+      const int kJ = p0 - k0;
+      if (kJ >= 0 && kJ < BC) {
+#pragma unroll
+        for (int a = 0; a < BR; ++a) {
+          const int i = i0 + a;
+          const float4 x = (i >= p0 && i < p0 + 4) ? Pn[i - p0] : Ub[i];
+#pragma unroll
+          for (int bq = 0; bq < BC / 4; ++bq)
+            if (4 * bq == kJ) {
+              v[a][4 * bq] = x.x; v[a][4 * bq + 1] = x.y; v[a][4 * bq + 2] = x.z; v[a][4 * bq + 3] = x.w;
+            }
+        }
+      }
+      if ((i0 <= p0 && p0 < i0 + BR) || (p0 <= i0 && i0 < p0 + 4)) {
+#pragma unroll
+        for (int a = 0; a < BR; ++a) {
+          const int r = i0 + a - p0;
+          if (r < 0 || r >= 4) continue;
+#pragma unroll
+          for (int b = 0; b < BC; ++b)
+            if (k0 + b < p0 || k0 + b >= p0 + 4) v[a][b] = comp4(Ub[k0 + b], r);
+        }
+      }
+      const int kN = p0 + 4 - k0;  // publish the next pivot columns
+      if (kN >= 0 && kN < BC)
+#pragma unroll
+        for (int bq = 0; bq < BC / 4; ++bq)
+          if (4 * bq == kN)
+#pragma unroll
+            for (int a = 0; a < BR; ++a)
+              Cn[i0 + a] = make_float4(v[a][4 * bq], v[a][4 * bq + 1], v[a][4 * bq + 2], v[a][4 * bq + 3]);
+    }
+    __syncthreads();
+  }
+  if (__syncthreads_or(bad ? 1 : 0) && t == 0) *flag = 1;
+  if (own)
+#pragma unroll
+    for (int a = 0; a < BR; ++a)
+#pragma unroll
+      for (int b = 0; b < BC; ++b) {
+        const int i = i0 + a, k = k0 + b;
+        if (i < d && k < d) G[(size_t)k * ld + i] = -v[a][b];  // the inverse is symmetric
+      }
+  __syncthreads();
+}
+
+// Lower Cholesky factor of the SPD matrix G in place (strict upper part set to
+// zero) by 4 x 4 block elimination: step J factors the pivot block D_J = L_J L_J'
+// and writes the final block column, L_J on the diagonal and w_i = L_J^-1 c_i
+// below it; the trailing matrix is downdated by w_i'w_k (symmetric).
+// rdiag[k] = 1 / L[k][k] if non-null. *flag = 1 on a non-SPD pivot block.
+template <int BR, int BC>
+__device__ inline void cta_chol_p4(int d, float* G, int ld, int* flag, float* scr, float* rdiag) {
+  static_assert(BC % 4 == 0 && (BR == 1 || BR == 2 || BR == 4), "block shape");
+  const int t = threadIdx.x;
+  const int d4 = (d + 3) & ~3, nJ = d4 / 4;
+  const int nbr = d4 / BR, nbc = d4 / BC;
+  bool own = t < nbr * nbc;
+  const int i0 = own ? (t / nbc) * BR : 0, k0 = own ? (t % nbc) * BC : 0;
+  own = own && (i0 + BR - 1 >= k0);
+  float4* Cb = reinterpret_cast<float4*>(scr);  // 2 x d4
+  float4* Wb = Cb + 2 * d4;                     // d4
+  float v[BR][BC];
+#pragma unroll
+  for (int a = 0; a < BR; ++a)
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+      const int i = i0 + a, k = k0 + b;
+      float g = 0.0f;
+      if (own && i < d && k < d) g = G[(size_t)(i >= k ? i : k) * ld + (i >= k ? k : i)];  // from the lower part
+      if (i >= d && i == k) g = 1.0f;  // padded pivots
+      v[a][b] = g;
+    }
+  if (own && k0 == 0)
+#pragma unroll
+    for (int a = 0; a < BR; ++a) Cb[i0 + a] = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+  bool bad = false;
+  __syncthreads();
+  for (int J = 0; J < nJ; ++J) {
+    const int p0 = 4 * J;
+    const float4* C = Cb + (J & 1) * d4;
+    float4* Cn = Cb + ((J + 1) & 1) * d4;
+    if (t >= p0 && t < d4) {  // (a) the pivot factor (redundantly) and the final block column
+      float m[16], L[16], Li[16];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 c = C[p0 + r];
+        m[r * 4 + 0] = c.x; m[r * 4 + 1] = c.y; m[r * 4 + 2] = c.z; m[r * 4 + 3] = c.w;
+      }
+      bool b2 = false;
+      chol4(m, L, Li, b2);
+      if (t == p0) bad |= b2;
+      float o[4];
+      if (t >= p0 + 4) {
+        const float4 c = C[t];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float s = 0.0f;
+#pragma unroll
+          for (int k = 0; k <= r; ++k) s = fmaf(Li[r * 4 + k], comp4(c, k), s);
+          o[r] = s;
+        }
+        Wb[t] = make_float4(o[0], o[1], o[2], o[3]);
+      } else {
+        float rd = 1.0f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (t - p0 == r) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = L[r * 4 + q];
+            rd = Li[r * 4 + r];
+          }
+        if (rdiag && t < d) rdiag[t] = rd;
+      }
+      if (t < d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (p0 + q < d) G[(size_t)t * ld + p0 + q] = o[q];
+    }
+    __syncthreads();
+    if (own && k0 + BC > p0 + 4) {  // (b) the trailing downdate
+#pragma unroll
+      for (int bq = 0; bq < BC / 4; ++bq) {
+        const int kb = k0 + 4 * bq;
+        if (kb < p0 + 4) continue;
+        float4 wk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wk[q] = Wb[kb + q];
+#pragma unroll
+        for (int a = 0; a < BR; ++a) {
+          if (i0 + a < kb) continue;
+          const float4 wi = Wb[i0 + a];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[a][4 * bq + q] -= dot4(wi, wk[q]);
+        }
+        if (kb == p0 + 4)
+#pragma unroll
+          for (int a = 0; a < BR; ++a)
+            if (i0 + a >= kb) Cn[i0 + a] = make_float4(v[a][4 * bq], v[a][4 * bq + 1], v[a][4 * bq + 2], v[a][4 * bq + 3]);
+      }
+    }
+    __syncthreads();
+  }
+  if (__syncthreads_or(bad ? 1 : 0) && t == 0) *flag = 1;
+  for (int e = t; e < d * d; e += blockDim.x) {  // block columns right of the diagonal block
+    const int i = e / d, k = e - i * d;
+    if ((k >> 2) > (i >> 2)) G[(size_t)i * ld + k] = 0.0f;
+  }
+  __syncthreads();
+}
+
 // FP32 product on 4-aligned shapes with 128-bit shared/global loads:
 //   acc(i,j) = sum_k opA(i,k) B[k][j],  0 <= i < M, 0 <= j < N (M, N multiples of 4)
 //   opA(i,k) = TA ? A[k*lda + i] : A[i*lda + k]
@@ -691,11 +1246,15 @@ __device__ inline void cta_spd_inverse_reg(int d, T* G, int ld, int* flag, T* co
 // the operands must hold zeros (or finite values whose products the epilogue
 // discards). Each thread owns 4 x 4 output tiles; epi(i, j, v) for every
 // element of the padded M x N range.
+// rot: tile 0 goes to thread rot (mod blockDim.x), so that consecutive
+// products of one phase can be dealt where the previous one left off.
 template <bool TA, typename Epi>
 __device__ __forceinline__ void cta_mm4f(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
-                                         Epi epi) {
+                                         Epi epi, int rot = 0) {
   const int tm = M >> 2, tn = N >> 2;
-  for (int tile = threadIdx.x; tile < tm * tn; tile += blockDim.x) {
+  const int nthr = blockDim.x;
+  const int tid = (int)((threadIdx.x + nthr - (rot % nthr)) % nthr);
+  for (int tile = tid; tile < tm * tn; tile += nthr) {
     const int i0 = (tile / tn) << 2, j0 = (tile % tn) << 2;
     float acc[4][4];
 #pragma unroll

@@ -47,9 +47,16 @@ __global__ void link_scan_init_kernel(ProbTable tab) {
   }
 }
 
-__host__ __device__ inline long long scan_smem_floats(int n) {
+// shared-memory plan of one composition (floats): Cb, Wa, Zb, Tm, Y (n4 x n4),
+// Za, E, F2 (n4 x (n4 + 4)), pb, wa (n4), the block-elimination scratch, then
+// gd, t1, gbk (n4 doubles each) and 1/diag(C) (n4).
+__host__ __device__ inline long long scan_tail_offset(int n) {
   const long long n4 = (n + 3) & ~3, ld1 = n4 + 4;
-  return 5 * n4 * n4 + 3 * n4 * ld1 + 16 * n4;
+  return 5 * n4 * n4 + 3 * n4 * ld1 + 2 * n4;
+}
+__host__ __device__ inline long long scan_smem_floats(int n) {
+  const long long n4 = (n + 3) & ~3;
+  return scan_tail_offset(n) + p4_scratch_floats(n) + 6 * n4 + n4 + 4;
 }
 
 // mode 0: one level of the suffix scan with stride s. CTA j composes element
@@ -59,8 +66,10 @@ __host__ __device__ inline long long scan_smem_floats(int n) {
 //         Pi_j, pi_j); otherwise the full composite goes to buffer dst.
 // mode 1: the feedback pass. CTA j composes the original S_j (buffer 0) with
 //         the final Pi_{j+1} and keeps M^-1 [Z_j | v] = [Gam_j | gam_j].
-template <int R>
-__global__ void __launch_bounds__(kBlock, 1) link_scan_kernel(ProbTable tab, int s, int mode, int src_buf, int dst_buf) {
+constexpr int kScanBlock = 512;  // 16 warps per composition
+
+template <int SHAPE>  // p4_shape(n): register-block shape of the block eliminations
+__global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab, int s, int mode, int src_buf, int dst_buf) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   const ProbDesc& pd = tab.single;
@@ -87,9 +96,9 @@ __global__ void __launch_bounds__(kBlock, 1) link_scan_kernel(ProbTable tab, int
   float* F2 = E + (long long)n4 * ld1;         // Y E
   float* pb = F2 + (long long)n4 * ld1;        // p_b
   float* wa = pb + n4;                         // w_a
-  float* colbuf = wa + n4;                     // 2 n4: pivot columns of the register sweeps
-                                               // then 3 n4 doubles (mode 1 refinement)
-  float* rdc = colbuf + 8 * n4;                // 1 / diag(C)
+  float* colbuf = wa + n4;                     // block-elimination scratch (16-byte aligned)
+  double* dtail = reinterpret_cast<double*>(colbuf + p4_scratch_floats(n));  // 3 n4 doubles (mode 1 refinement)
+  float* rdc = reinterpret_cast<float*>(dtail + 3 * n4);  // 1 / diag(C)
 
   {
     float4* z4 = reinterpret_cast<float4*>(smem);
@@ -114,23 +123,25 @@ __global__ void __launch_bounds__(kBlock, 1) link_scan_kernel(ProbTable tab, int
   __syncthreads();
   // v = w_a - W_a p_b (column n4 of Za); C = chol(P_b)
   cta_mv_warp<float>(n, n, Wa, n4, pb, [&](int i, float v) { Za[i * ld1 + n4] = v + wa[i]; });
-  if (R == 1 || (n4 / 4) * (n4 / 4 + 1) / 2 <= kBlock)
-    cta_chol_reg<float, 1>(n, Cb, n4, &s_flag, colbuf, rdc);
-  else
-    cta_chol_reg<float, R>(n, Cb, n4, &s_flag, colbuf, rdc);
+  if (SHAPE == 0) cta_chol_p4<1, 4>(n, Cb, n4, &s_flag, colbuf, rdc);
+  else if (SHAPE == 1) cta_chol_p4<2, 4>(n, Cb, n4, &s_flag, colbuf, rdc);
+  else cta_chol_p4<4, 4>(n, Cb, n4, &s_flag, colbuf, rdc);
   if (s_flag) {
     if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
     return;
   }
   // Tm = W_a C;  E = C'[Z_a | v]
   cta_mm4f<false>(n4, n4, n4, Wa, n4, Cb, n4, [&](int i, int k, float v) { Tm[i * n4 + k] = -v; });
-  cta_mm4f<true>(n4, ld1, n4, Cb, n4, Za, ld1, [&](int i, int k, float v) { E[i * ld1 + k] = v; });
+  cta_mm4f<true>(n4, ld1, n4, Cb, n4, Za, ld1, [&](int i, int k, float v) { E[i * ld1 + k] = v; },
+                 (n4 / 4) * (n4 / 4));
   __syncthreads();
   // Y = (I + C'Tm)^-1
   cta_mm4f<true>(n4, n4, n4, Cb, n4, Tm, n4,
                  [&](int i, int k, float v) { Y[i * n4 + k] = (i == k && i < n) ? v + 1.0f : v; });
   __syncthreads();
-  cta_spd_inverse_reg<float, R>(n, Y, n4, &s_flag, colbuf);
+  if (SHAPE == 0) cta_spd_inverse_p4<1, 4>(n, Y, n4, &s_flag, colbuf, false);
+  else if (SHAPE == 1) cta_spd_inverse_p4<2, 4>(n, Y, n4, &s_flag, colbuf, false);
+  else cta_spd_inverse_p4<4, 4>(n, Y, n4, &s_flag, colbuf, false);
   if (s_flag) {
     if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
     return;
@@ -142,7 +153,7 @@ __global__ void __launch_bounds__(kBlock, 1) link_scan_kernel(ProbTable tab, int
     // Gam_j (FP32) replaces Z_j in element j of buffer 0, read only by this CTA
     float* G = sbase + (long long)j * es + nn;
     double* g = ws + wl.gam + (long long)j * n;
-    double* gd = reinterpret_cast<double*>(colbuf + 2 * n4);  // gam (FP64)
+    double* gd = dtail;  // gam (FP64)
     double* t1 = gd + n4;
     double* gbk = t1 + n4;
     float* rf = pb;      // residual (p_b, w_a no longer needed)
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(kBlock, 1) link_scan_kernel(ProbTable tab, int
     const double* w64 = Sj + 3 * nn + n;
     const double* Pi1 = ws + wl.Pi + (long long)(j + 1) * nn;
     const double* pi1 = ws + wl.pi + (long long)(j + 1) * n;
-    __shared__ double s_wmax[kBlock / 32];
+    __shared__ double s_wmax[kScanBlock / 32];
     __shared__ double s_rn;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double rprev = INFINITY;
@@ -233,7 +244,8 @@ __global__ void __launch_bounds__(kBlock, 1) link_scan_kernel(ProbTable tab, int
   __syncthreads();
   // [Gam | gam] = [Z_a | v] - Tm F2 (in place);  U = Y Tm' (as (Tm Y)', Y symmetric)
   cta_mm4f<false>(n4, ld1, n4, Tm, n4, F2, ld1, [&](int i, int k, float v) { Za[i * ld1 + k] -= v; });
-  cta_mm4f<false>(n4, n4, n4, Tm, n4, Y, n4, [&](int i, int k, float v) { Cb[k * n4 + i] = v; });
+  cta_mm4f<false>(n4, n4, n4, Tm, n4, Y, n4, [&](int i, int k, float v) { Cb[k * n4 + i] = v; },
+                  (n4 / 4) * (ld1 / 4));
   __syncthreads();
   // Z_ab = Z_b Gam, w_ab = w_b + Z_b gam;  -(M^-1 W_a) = -W_a + Tm U
   cta_mm4f<false>(n4, ld1, n4, Zb, n4, Za, ld1, [&](int i, int k, float v) {
@@ -242,7 +254,8 @@ __global__ void __launch_bounds__(kBlock, 1) link_scan_kernel(ProbTable tab, int
       else if (k == n4) ed[3 * nn + n + i] = eb[3 * nn + n + i] + v;
     }
   });
-  cta_mm4f<false>(n4, n4, n4, Tm, n4, Cb, n4, [&](int i, int k, float v) { Wa[i * n4 + k] += v; });
+  cta_mm4f<false>(n4, n4, n4, Tm, n4, Cb, n4, [&](int i, int k, float v) { Wa[i * n4 + k] += v; },
+                  (n4 / 4) * (ld1 / 4));
   __syncthreads();
   // -W_ab = -W_b + Z_b (-(M^-1 W_a)) Z_b': V = Z_b Hn stored transposed, then Z_b V'
   cta_mm4f<false>(n4, n4, n4, Zb, n4, Wa, n4, [&](int i, int k, float v) { E[k * n4 + i] = v; });
@@ -348,18 +361,18 @@ __global__ void __launch_bounds__(kBlock) link_scan_forward_kernel(ProbTable tab
 
 size_t link_scan_smem_bytes(int n) { return sizeof(float) * (size_t)scan_smem_floats(n); }
 
-template <int R>
+template <int SHAPE>
 static cudaError_t launch_scan_levels(const ProbTable& tab, size_t bytes, cudaStream_t st) {
   const int K = tab.single.nseg;
-  cudaError_t e = raise_dyn_smem((const void*)link_scan_kernel<R>, bytes);
+  cudaError_t e = raise_dyn_smem((const void*)link_scan_kernel<SHAPE>, bytes);
   if (e != cudaSuccess) return e;
   int src = 0, dst = 1;
   for (int s = 1; s < K; s *= 2) {
-    link_scan_kernel<R><<<K - s, kBlock, bytes, st>>>(tab, s, 0, src, dst);
+    link_scan_kernel<SHAPE><<<K - s, kScanBlock, bytes, st>>>(tab, s, 0, src, dst);
     src = dst;
     dst = (dst == 1) ? 2 : 1;
   }
-  link_scan_kernel<R><<<K - 1, kBlock, bytes, st>>>(tab, 1, 1, 0, 0);
+  link_scan_kernel<SHAPE><<<K - 1, kScanBlock, bytes, st>>>(tab, 1, 1, 0, 0);
   return cudaGetLastError();
 }
 
@@ -371,12 +384,14 @@ cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t
   int optin = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int nb = ((n + 3) & ~3) / 4;
-  if (bytes > (size_t)optin - kStaticSmemReserve || nb * nb > 2 * kBlock ||
+  const int shape = p4_shape(n);
+  if (bytes > (size_t)optin - kStaticSmemReserve || shape < 0 || shape > 2 ||
       (size_t)scan_forward_smem_bytes(n) > (size_t)optin - kStaticSmemReserve)
     return cudaErrorNotSupported;
   link_scan_init_kernel<<<K, kBlock, 0, st>>>(tab);
-  cudaError_t e = (nb * nb <= kBlock) ? launch_scan_levels<1>(tab, bytes, st) : launch_scan_levels<2>(tab, bytes, st);
+  cudaError_t e = shape == 0 ? launch_scan_levels<0>(tab, bytes, st)
+                  : shape == 1 ? launch_scan_levels<1>(tab, bytes, st)
+                               : launch_scan_levels<2>(tab, bytes, st);
   if (e != cudaSuccess) return e;
   const size_t fbytes = (size_t)scan_forward_smem_bytes(n);
   e = raise_dyn_smem((const void*)link_scan_forward_kernel, fbytes);

@@ -51,8 +51,8 @@ __host__ __device__ inline FastPlan fast_plan(int n, int m) {
   P.Muu = o; o += M * M;
   P.Mzx = o; o += N * N;
   P.mz = o;  o += N;
-  P.colbuf = o; o += 2 * M;
-  P.total = o;
+  P.colbuf = o; o += p4_scratch_floats(m);  // scratch of the block elimination
+  P.total = (o + 3) & ~3LL;
   return P;
 }
 
@@ -80,14 +80,21 @@ __device__ __forceinline__ void copy_rows(float* dst, int ldd, const float* src,
 
 __device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15) == 0; }
 
-template <int R>
-__device__ __forceinline__ void invert_muu(int m, float* Muu, int M, int* flag, float* colbuf) {
-  cta_spd_inverse_reg<float, R>(m, Muu, M, flag, colbuf, true);
+// M_uu^-1 in place, 4 x 4 pivot blocks, one register block per thread (512 threads)
+template <int SHAPE>
+__device__ __forceinline__ void invert_muu(int m, float* Muu, int M, int* flag, float* scr) {
+  if (SHAPE == 0) cta_spd_inverse_p4<1, 4>(m, Muu, M, flag, scr, true);
+  else if (SHAPE == 1) cta_spd_inverse_p4<2, 4>(m, Muu, M, flag, scr, true);
+  else if (SHAPE == 2) cta_spd_inverse_p4<4, 4>(m, Muu, M, flag, scr, true);
+  else cta_spd_inverse_p4<4, 8>(m, Muu, M, flag, scr, true);
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kBlock, 1) seg_sweep_f32_kernel(ProbTable tab, int phase, int store_P) {
+constexpr int kSweepBlock = 512;  // 16 warps: latency hiding for the small products
+
+template <int SHAPE>  // p4_shape(m) of the largest m in the launch
+__global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable tab, int phase, int store_P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   const int unit = blockIdx.x;
@@ -204,31 +211,36 @@ __global__ void __launch_bounds__(kBlock, 1) seg_sweep_f32_kernel(ProbTable tab,
     cp_async_wait<1>();  // this stage's Q, R, S, q, r (the next [A|B|c] may still be in flight)
     __syncthreads();
     // ---- the M terms ---------------------------------------------------------------
-    // B'T1 = [M_ux - S | M_uu - R | m_u - r]
+    // B'T1 = [M_ux - S | M_uu - R | m_u - r]; the products of this phase are
+    // dealt round the block one after the other (rot)
+    int rot = 0;
     cta_mm4f<true>(M, ldAB, N, ab + N, ldAB, T1, ldAB, [&](int a, int j, float v) {
       if (j < N) F[a * ldF + j] = v + Ss[a * N + j];
       else if (j < cN) Muu[a * M + (j - N)] = v + Rs[a * M + (j - N)];
       else if (j == cN) F[a * ldF + 2 * N] = v + rs[a];
-    });
-    // M_xx = Q + A'T1_A (into V), m_x = q + A'T1_c (into v_x)
-    cta_mm4f<true>(N, N, N, ab, ldAB, T1, ldAB,
-                   [&](int i, int j, float v) { V[i * N + j] = v + 0.5f * (Qs[i * N + j] + Qs[j * N + i]); });
+    }, rot);
+    rot += (M / 4) * (ldAB / 4);
+    // M_xx = Q + A'T1_A (into V; the end-of-stage symmetrisation of V_xx takes
+    // care of Q's antisymmetric part), m_x = q + A'T1_c (into v_x)
+    cta_mm4f<true>(N, N, N, ab, ldAB, T1, ldAB, [&](int i, int j, float v) { V[i * N + j] = v + Qs[i * N + j]; }, rot);
+    rot += (N / 4) * (N / 4);
     cta_mm4f<true>(N, 4, N, ab, ldAB, T1 + cN, ldAB, [&](int i, int j, float v) {
       if (j == 0) vx[i] = v + qs[i];
-    });
+    }, rot);
+    rot += N / 4;
     if (param) {
       // M_zu' = (Z B)' into F[:, N:2N], m_z = w + Z c, M_zx = Z A
-      cta_mm4f<false>(N, M, N, Z, N, ab + N, ldAB, [&](int i, int a, float v) { F[a * ldF + N + i] = v; });
+      cta_mm4f<false>(N, M, N, Z, N, ab + N, ldAB, [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
+      rot += (N / 4) * (M / 4);
       cta_mm4f<false>(N, 4, N, Z, N, ab + cN, ldAB, [&](int i, int j, float v) {
         if (j == 0) mz[i] = v + vz[i];
-      });
-      cta_mm4f<false>(N, N, N, Z, N, ab, ldAB, [&](int i, int j, float v) { Mzx[i * N + j] = v; });
+      }, rot);
+      rot += N / 4;
+      cta_mm4f<false>(N, N, N, Z, N, ab, ldAB, [&](int i, int j, float v) { Mzx[i * N + j] = v; }, rot);
     }
     __syncthreads();
     // ---- M_uu^-1 (symmetrised) ------------------------------------------------------
-    if (M <= 64) invert_muu<1>(m, Muu, M, &s_flag, colbuf);
-    else if (M <= 88) invert_muu<2>(m, Muu, M, &s_flag, colbuf);
-    else invert_muu<4>(m, Muu, M, &s_flag, colbuf);
+    invert_muu<SHAPE>(m, Muu, M, &s_flag, colbuf);
     if (s_flag) {
       if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
       cp_async_wait<0>();
@@ -239,16 +251,22 @@ __global__ void __launch_bounds__(kBlock, 1) seg_sweep_f32_kernel(ProbTable tab,
     cta_mm4f<false>(M, hcols, M, Muu, M, F, ldF, [&](int a, int j, float v) { H[a * ldF + j] = v; });
     __syncthreads();
     // ---- value update ---------------------------------------------------------------------
-    cta_mm4f<true>(N, N, M, F, ldF, H, ldF, [&](int i, int j, float v) { V[i * N + j] -= v; });
+    rot = 0;
+    cta_mm4f<true>(N, N, M, F, ldF, H, ldF, [&](int i, int j, float v) { V[i * N + j] -= v; }, rot);
+    rot += (N / 4) * (N / 4);
     cta_mm4f<true>(N, 4, M, F, ldF, H + 2 * N, ldF, [&](int i, int j, float v) {
       if (j == 0) vx[i] -= v;
-    });
+    }, rot);
+    rot += N / 4;
     if (param) {
-      cta_mm4f<true>(N, N, M, F + N, ldF, H, ldF, [&](int i, int j, float v) { Z[i * N + j] = Mzx[i * N + j] - v; });
-      cta_mm4f<true>(N, N, M, F + N, ldF, H + N, ldF, [&](int i, int j, float v) { Wn[i * N + j] -= v; });
+      cta_mm4f<true>(N, N, M, F + N, ldF, H, ldF, [&](int i, int j, float v) { Z[i * N + j] = Mzx[i * N + j] - v; },
+                     rot);
+      rot += (N / 4) * (N / 4);
+      cta_mm4f<true>(N, N, M, F + N, ldF, H + N, ldF, [&](int i, int j, float v) { Wn[i * N + j] -= v; }, rot);
+      rot += (N / 4) * (N / 4);
       cta_mm4f<true>(N, 4, M, F + N, ldF, H + 2 * N, ldF, [&](int i, int j, float v) {
         if (j == 0) vz[i] = mz[i] - v;
-      });
+      }, rot);
     } else {
       // policy K_t = -H_x, k_t = -h
       if (gK)
@@ -300,10 +318,20 @@ __global__ void __launch_bounds__(kBlock, 1) seg_sweep_f32_kernel(ProbTable tab,
 cudaError_t launch_seg_sweep_f32(const ProbTable& tab, int nunits, int phase, int nmax, int mmax,
                                  long long smem_budget, int store_P, cudaStream_t st) {
   const long long bytes = fast_sweep_smem_bytes(nmax, mmax);
-  if (bytes > smem_budget || ((mmax + 3) & ~3) > 128) return cudaErrorNotSupported;
-  cudaError_t e = raise_dyn_smem((const void*)seg_sweep_f32_kernel, (size_t)bytes);
+  if (bytes > smem_budget || p4_shape(mmax) < 0) return cudaErrorNotSupported;
+  const int shape = p4_shape(mmax);
+  const void* fn = shape == 0 ? (const void*)seg_sweep_f32_kernel<0>
+                 : shape == 1 ? (const void*)seg_sweep_f32_kernel<1>
+                 : shape == 2 ? (const void*)seg_sweep_f32_kernel<2>
+                              : (const void*)seg_sweep_f32_kernel<3>;
+  cudaError_t e = raise_dyn_smem(fn, (size_t)bytes);
   if (e != cudaSuccess) return e;
-  seg_sweep_f32_kernel<<<nunits, kBlock, (size_t)bytes, st>>>(tab, phase, store_P);
+  switch (shape) {
+    case 0: seg_sweep_f32_kernel<0><<<nunits, kSweepBlock, (size_t)bytes, st>>>(tab, phase, store_P); break;
+    case 1: seg_sweep_f32_kernel<1><<<nunits, kSweepBlock, (size_t)bytes, st>>>(tab, phase, store_P); break;
+    case 2: seg_sweep_f32_kernel<2><<<nunits, kSweepBlock, (size_t)bytes, st>>>(tab, phase, store_P); break;
+    default: seg_sweep_f32_kernel<3><<<nunits, kSweepBlock, (size_t)bytes, st>>>(tab, phase, store_P); break;
+  }
   return cudaGetLastError();
 }
 
