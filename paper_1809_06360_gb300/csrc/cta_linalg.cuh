@@ -1239,6 +1239,109 @@ __device__ inline void cta_chol_p4(int d, float* G, int ld, int* flag, float* sc
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inverse of an SPD matrix by a group of threads (gtid < nthr)
+// that synchronise through bar() (a named barrier), so that the rest of the
+// block can work on something else meanwhile. Scalar pivots, one BR x BC
+// register block per thread (row-fast mapping; (ceil(d/BR)) x (ceil(d/BC))
+// blocks <= nthr), the pivot column and its reciprocal published by their
+// owners. sym: the input is taken as (G + G')/2. colbuf: 2 dp floats, rpv: 2
+// floats (shared), dp = max(BR ceil(d/BR), BC ceil(d/BC)). *flag = 1 on a
+// pivot that is not positive and finite. Ends with bar().
+// ---------------------------------------------------------------------------
+template <int BR, int BC, typename Bar>
+__device__ inline void grp_spd_inverse(int d, float* G, int ld, int* flag, float* colbuf, float* rpv, bool sym,
+                                       int gtid, int nthr, Bar bar) {
+  const int nbr = (d + BR - 1) / BR, nbc = (d + BC - 1) / BC;
+  const int dp = (nbr * BR > nbc * BC) ? nbr * BR : nbc * BC;
+  const bool own = gtid < nbr * nbc;
+  const int i0 = own ? (gtid % nbr) * BR : 0, k0 = own ? (gtid / nbr) * BC : 0;
+  float v[BR][BC];
+#pragma unroll
+  for (int a = 0; a < BR; ++a)
+#pragma unroll
+    for (int b = 0; b < BC; ++b) {
+      const int i = i0 + a, k = k0 + b;
+      float g = 0.0f;
+      if (own && i < d && k < d) {
+        g = G[(size_t)k * ld + i];
+        if (sym) g = 0.5f * (g + G[(size_t)i * ld + k]);
+      }
+      v[a][b] = g;
+    }
+  for (int i = gtid; i < dp; i += nthr) {
+    float g = 0.0f;
+    if (i < d) {
+      g = G[i];
+      if (sym) g = 0.5f * (g + G[(size_t)i * ld]);
+    }
+    colbuf[i] = g;
+    if (i == 0) rpv[0] = recip_fast(g);
+  }
+  bool bad = false;
+  if (gtid == 0) {
+    const float g = G[0];
+    bad = !(g > 0.0f && isfinite(g));
+  }
+  bar();
+  for (int j = 0; j < d; ++j) {
+    const float* col = colbuf + (j & 1) * dp;
+    float* nxt = colbuf + ((j + 1) & 1) * dp;
+    if (own) {
+      const float rp = rpv[j & 1];
+      float ci[BR], ckr[BC];
+#pragma unroll
+      for (int a = 0; a < BR; ++a) ci[a] = col[i0 + a];
+#pragma unroll
+      for (int b = 0; b < BC; ++b) ckr[b] = col[k0 + b] * rp;
+      // rank-1 update; the pivot row becomes a_jk / p, the pivot column a_ij / p
+      // and the pivot -1/p (selects, no data-dependent branches)
+#pragma unroll
+      for (int a = 0; a < BR; ++a)
+#pragma unroll
+        for (int b = 0; b < BC; ++b) {
+          const float upd = fmaf(-ci[a], ckr[b], v[a][b]);
+          const bool ri = (i0 + a == j), cj = (k0 + b == j);
+          v[a][b] = cj ? (ri ? -rp : ci[a] * rp) : (ri ? ckr[b] : upd);
+        }
+      const int bn = j + 1 - k0;  // publish the next pivot column
+      if (bn >= 0 && bn < BC) {
+#pragma unroll
+        for (int b = 0; b < BC; ++b)
+          if (b == bn)
+#pragma unroll
+            for (int a = 0; a < BR; ++a) {
+              nxt[i0 + a] = v[a][b];
+              if (i0 + a == j + 1 && j + 1 < d) {
+                const float pn = v[a][b];
+                bad |= !(pn > 0.0f && isfinite(pn));
+                rpv[(j + 1) & 1] = recip_fast(pn);
+              }
+            }
+      }
+    }
+    bar();
+  }
+  if (bad) *flag = 1;
+  if (own)
+#pragma unroll
+    for (int a = 0; a < BR; ++a)
+#pragma unroll
+      for (int b = 0; b < BC; ++b) {
+        const int i = i0 + a, k = k0 + b;
+        if (i < d && k < d) G[(size_t)k * ld + i] = -v[a][b];
+      }
+  bar();
+}
+
+// named barrier over the first nthr threads of the block (id > 0)
+struct NamedBar {
+  int id, nthr;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
+  }
+};
+
 // FP32 product on 4-aligned shapes with 128-bit shared/global loads:
 //   acc(i,j) = sum_k opA(i,k) B[k][j],  0 <= i < M, 0 <= j < N (M, N multiples of 4)
 //   opA(i,k) = TA ? A[k*lda + i] : A[i*lda + k]
@@ -1248,12 +1351,12 @@ __device__ inline void cta_chol_p4(int d, float* G, int ld, int* flag, float* sc
 // element of the padded M x N range.
 // rot: tile 0 goes to thread rot (mod blockDim.x), so that consecutive
 // products of one phase can be dealt where the previous one left off.
+// grp_mm4f: the same over a group of nthr threads, gtid the index in the group.
 template <bool TA, typename Epi>
-__device__ __forceinline__ void cta_mm4f(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
-                                         Epi epi, int rot = 0) {
+__device__ __forceinline__ void grp_mm4f(int gtid, int nthr, int M, int N, int K, const float* A, int lda,
+                                         const float* B, int ldb, Epi epi, int rot = 0) {
   const int tm = M >> 2, tn = N >> 2;
-  const int nthr = blockDim.x;
-  const int tid = (int)((threadIdx.x + nthr - (rot % nthr)) % nthr);
+  const int tid = (gtid + nthr - (rot % nthr)) % nthr;
   for (int tile = tid; tile < tm * tn; tile += nthr) {
     const int i0 = (tile / tn) << 2, j0 = (tile % tn) << 2;
     float acc[4][4];
@@ -1305,6 +1408,12 @@ __device__ __forceinline__ void cta_mm4f(int M, int N, int K, const float* A, in
 #pragma unroll
       for (int b = 0; b < 4; ++b) epi(i0 + a, j0 + b, acc[a][b]);
   }
+}
+
+template <bool TA, typename Epi>
+__device__ __forceinline__ void cta_mm4f(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                                         Epi epi, int rot = 0) {
+  grp_mm4f<TA>((int)threadIdx.x, (int)blockDim.x, M, N, K, A, lda, B, ldb, epi, rot);
 }
 
 // y_i = epi(i, sum_k A[i*lda + k] x[k]) for i < M: one warp per row, lanes

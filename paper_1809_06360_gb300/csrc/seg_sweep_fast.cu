@@ -211,36 +211,55 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     cp_async_wait<1>();  // this stage's Q, R, S, q, r (the next [A|B|c] may still be in flight)
     __syncthreads();
     // ---- the M terms ---------------------------------------------------------------
-    // B'T1 = [M_ux - S | M_uu - R | m_u - r]; the products of this phase are
-    // dealt round the block one after the other (rot)
-    int rot = 0;
+    // B'T1 = [M_ux - S | M_uu - R | m_u - r] first: M_uu^-1 only needs these.
     cta_mm4f<true>(M, ldAB, N, ab + N, ldAB, T1, ldAB, [&](int a, int j, float v) {
       if (j < N) F[a * ldF + j] = v + Ss[a * N + j];
       else if (j < cN) Muu[a * M + (j - N)] = v + Rs[a * M + (j - N)];
       else if (j == cN) F[a * ldF + 2 * N] = v + rs[a];
-    }, rot);
-    rot += (M / 4) * (ldAB / 4);
-    // M_xx = Q + A'T1_A (into V; the end-of-stage symmetrisation of V_xx takes
-    // care of Q's antisymmetric part), m_x = q + A'T1_c (into v_x)
-    cta_mm4f<true>(N, N, N, ab, ldAB, T1, ldAB, [&](int i, int j, float v) { V[i * N + j] = v + Qs[i * N + j]; }, rot);
-    rot += (N / 4) * (N / 4);
-    cta_mm4f<true>(N, 4, N, ab, ldAB, T1 + cN, ldAB, [&](int i, int j, float v) {
-      if (j == 0) vx[i] = v + qs[i];
-    }, rot);
-    rot += N / 4;
-    if (param) {
-      // M_zu' = (Z B)' into F[:, N:2N], m_z = w + Z c, M_zx = Z A
-      cta_mm4f<false>(N, M, N, Z, N, ab + N, ldAB, [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
-      rot += (N / 4) * (M / 4);
-      cta_mm4f<false>(N, 4, N, Z, N, ab + cN, ldAB, [&](int i, int j, float v) {
-        if (j == 0) mz[i] = v + vz[i];
+    });
+    __syncthreads();
+    // Then, for m <= 64, the first GT threads invert M_uu (named barrier 1)
+    // while the others form the terms that do not depend on it; for larger m
+    // the whole block does one after the other.
+    // (m <= 32: 128 threads when the parametric terms give the others more to
+    // do, else 256; m <= 64: 256)
+    const int GT = SHAPE == 0 ? (param ? 128 : 256) : (SHAPE == 1 ? 256 : 0);
+    const bool split = GT > 0;
+    const int gtid = split ? (int)threadIdx.x - GT : (int)threadIdx.x;
+    const int gthr = split ? kSweepBlock - GT : kSweepBlock;
+    if (split && (int)threadIdx.x < GT) {
+      if (SHAPE == 0 && GT == 128)
+        grp_spd_inverse<2, 4>(m, Muu, M, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+      else if (SHAPE == 0)
+        grp_spd_inverse<1, 4>(m, Muu, M, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+      else
+        grp_spd_inverse<4, 4>(m, Muu, M, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+    } else {
+      // M_xx = Q + A'T1_A (into V; the end-of-stage symmetrisation of V_xx takes
+      // care of Q's antisymmetric part), m_x = q + A'T1_c (into v_x); the products
+      // are dealt round the group one after the other (rot)
+      int rot = 0;
+      grp_mm4f<true>(gtid, gthr, N, N, N, ab, ldAB, T1, ldAB,
+                     [&](int i, int j, float v) { V[i * N + j] = v + Qs[i * N + j]; }, rot);
+      rot += (N / 4) * (N / 4);
+      grp_mm4f<true>(gtid, gthr, N, 4, N, ab, ldAB, T1 + cN, ldAB, [&](int i, int j, float v) {
+        if (j == 0) vx[i] = v + qs[i];
       }, rot);
       rot += N / 4;
-      cta_mm4f<false>(N, N, N, Z, N, ab, ldAB, [&](int i, int j, float v) { Mzx[i * N + j] = v; }, rot);
+      if (param) {
+        // M_zu' = (Z B)' into F[:, N:2N], m_z = w + Z c, M_zx = Z A
+        grp_mm4f<false>(gtid, gthr, N, M, N, Z, N, ab + N, ldAB,
+                        [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
+        rot += (N / 4) * (M / 4);
+        grp_mm4f<false>(gtid, gthr, N, 4, N, Z, N, ab + cN, ldAB, [&](int i, int j, float v) {
+          if (j == 0) mz[i] = v + vz[i];
+        }, rot);
+        rot += N / 4;
+        grp_mm4f<false>(gtid, gthr, N, N, N, Z, N, ab, ldAB, [&](int i, int j, float v) { Mzx[i * N + j] = v; }, rot);
+      }
     }
     __syncthreads();
-    // ---- M_uu^-1 (symmetrised) ------------------------------------------------------
-    invert_muu<SHAPE>(m, Muu, M, &s_flag, colbuf);
+    if (!split) invert_muu<SHAPE>(m, Muu, M, &s_flag, colbuf);
     if (s_flag) {
       if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
       cp_async_wait<0>();
@@ -251,7 +270,7 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     cta_mm4f<false>(M, hcols, M, Muu, M, F, ldF, [&](int a, int j, float v) { H[a * ldF + j] = v; });
     __syncthreads();
     // ---- value update ---------------------------------------------------------------------
-    rot = 0;
+    int rot = 0;
     cta_mm4f<true>(N, N, M, F, ldF, H, ldF, [&](int i, int j, float v) { V[i * N + j] -= v; }, rot);
     rot += (N / 4) * (N / 4);
     cta_mm4f<true>(N, 4, M, F, ldF, H + 2 * N, ldF, [&](int i, int j, float v) {
