@@ -50,13 +50,15 @@ __global__ void link_scan_init_kernel(ProbTable tab) {
 // shared-memory plan of one composition (floats): Cb, Wa, Zb, Tm, Y (n4 x n4),
 // Za, E, F2 (n4 x (n4 + 4)), pb, wa (n4), the block-elimination scratch, then
 // gd, t1, gbk (n4 doubles each) and 1/diag(C) (n4).
-__host__ __device__ inline long long scan_tail_offset(int n) {
+// ldn: leading dimension of the n4 x n4 buffers, n4 + 4 (rows four apart fall
+// in different banks) when that fits, else n4.
+__host__ __device__ inline long long scan_tail_offset(int n, int ldn) {
   const long long n4 = (n + 3) & ~3, ld1 = n4 + 4;
-  return 5 * n4 * n4 + 3 * n4 * ld1 + 2 * n4;
+  return 5 * n4 * ldn + 3 * n4 * ld1 + 2 * n4;
 }
-__host__ __device__ inline long long scan_smem_floats(int n) {
+__host__ __device__ inline long long scan_smem_floats(int n, int ldn) {
   const long long n4 = (n + 3) & ~3;
-  return scan_tail_offset(n) + p4_scratch_floats(n) + 6 * n4 + n4 + 4;
+  return scan_tail_offset(n, ldn) + p4_scratch_floats(n) + 6 * n4 + n4 + 4;
 }
 
 // mode 0: one level of the suffix scan with stride s. CTA j composes element
@@ -69,7 +71,8 @@ __host__ __device__ inline long long scan_smem_floats(int n) {
 constexpr int kScanBlock = 512;  // 16 warps per composition
 
 template <int SHAPE>  // p4_shape(n): register-block shape of the block eliminations
-__global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab, int s, int mode, int src_buf, int dst_buf) {
+__global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab, int s, int mode, int src_buf, int dst_buf,
+                                                                 int ldn) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   const ProbDesc& pd = tab.single;
@@ -87,11 +90,11 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
   float* ed = sbase + ((long long)dst_buf * K + j) * es;
 
   float* Cb = reinterpret_cast<float*>(smem);  // C = chol(P_b), later U = Y Tm'
-  float* Wa = Cb + n4 * n4;                    // -W_a, later -(M^-1 W_a)
-  float* Zb = Wa + n4 * n4;                    // Z_b
-  float* Tm = Zb + n4 * n4;                    // W_a C
-  float* Y = Tm + n4 * n4;                     // (I + C'W_a C)^-1
-  float* Za = Y + n4 * n4;                     // [Z_a | v], later [Gam | gam]     (n4 x ld1)
+  float* Wa = Cb + n4 * ldn;                   // -W_a, later -(M^-1 W_a)
+  float* Zb = Wa + n4 * ldn;                   // Z_b
+  float* Tm = Zb + n4 * ldn;                   // W_a C
+  float* Y = Tm + n4 * ldn;                    // (I + C'W_a C)^-1
+  float* Za = Y + n4 * ldn;                    // [Z_a | v], later [Gam | gam]     (n4 x ld1)
   float* E = Za + (long long)n4 * ld1;         // C'[Z_a | v], later (Z_b Hn)'
   float* F2 = E + (long long)n4 * ld1;         // Y E
   float* pb = F2 + (long long)n4 * ld1;        // p_b
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
 
   {
     float4* z4 = reinterpret_cast<float4*>(smem);
-    const long long n4f = scan_smem_floats(n) / 4;
+    const long long n4f = scan_smem_floats(n, ldn) / 4;
     for (long long i = threadIdx.x; i < n4f; i += blockDim.x) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (threadIdx.x == 0) s_flag = 0;
   }
@@ -111,10 +114,10 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
   const double* pfin = ws + wl.pi + (long long)b * n;
   for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
     const int i = (int)(e / n), k = (int)(e - (long long)i * n);
-    Cb[i * n4 + k] = bfin ? static_cast<float>(Pfin[e]) : eb[e];
+    Cb[i * ldn + k] = bfin ? static_cast<float>(Pfin[e]) : eb[e];
     Za[i * ld1 + k] = ea[nn + e];
-    Wa[i * n4 + k] = ea[2 * nn + e];
-    if (!bfin) Zb[i * n4 + k] = eb[nn + e];
+    Wa[i * ldn + k] = ea[2 * nn + e];
+    if (!bfin) Zb[i * ldn + k] = eb[nn + e];
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     pb[i] = bfin ? static_cast<float>(pfin[i]) : eb[3 * nn + i];
@@ -122,32 +125,32 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
   }
   __syncthreads();
   // v = w_a - W_a p_b (column n4 of Za); C = chol(P_b)
-  cta_mv_warp<float>(n, n, Wa, n4, pb, [&](int i, float v) { Za[i * ld1 + n4] = v + wa[i]; });
-  if (SHAPE == 0) cta_chol_p4<1, 4>(n, Cb, n4, &s_flag, colbuf, rdc);
-  else if (SHAPE == 1) cta_chol_p4<2, 4>(n, Cb, n4, &s_flag, colbuf, rdc);
-  else cta_chol_p4<4, 4>(n, Cb, n4, &s_flag, colbuf, rdc);
+  cta_mv_warp<float>(n, n, Wa, ldn, pb, [&](int i, float v) { Za[i * ld1 + n4] = v + wa[i]; });
+  if (SHAPE == 0) cta_chol_p4<1, 4>(n, Cb, ldn, &s_flag, colbuf, rdc);
+  else if (SHAPE == 1) cta_chol_p4<2, 4>(n, Cb, ldn, &s_flag, colbuf, rdc);
+  else cta_chol_p4<4, 4>(n, Cb, ldn, &s_flag, colbuf, rdc);
   if (s_flag) {
     if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
     return;
   }
   // Tm = W_a C;  E = C'[Z_a | v]
-  cta_mm4f<false>(n4, n4, n4, Wa, n4, Cb, n4, [&](int i, int k, float v) { Tm[i * n4 + k] = -v; });
-  cta_mm4f<true>(n4, ld1, n4, Cb, n4, Za, ld1, [&](int i, int k, float v) { E[i * ld1 + k] = v; },
+  cta_mm4f<false>(n4, n4, n4, Wa, ldn, Cb, ldn, [&](int i, int k, float v) { Tm[i * ldn + k] = -v; });
+  cta_mm4f<true>(n4, ld1, n4, Cb, ldn, Za, ld1, [&](int i, int k, float v) { E[i * ld1 + k] = v; },
                  (n4 / 4) * (n4 / 4));
   __syncthreads();
   // Y = (I + C'Tm)^-1
-  cta_mm4f<true>(n4, n4, n4, Cb, n4, Tm, n4,
-                 [&](int i, int k, float v) { Y[i * n4 + k] = (i == k && i < n) ? v + 1.0f : v; });
+  cta_mm4f<true>(n4, n4, n4, Cb, ldn, Tm, ldn,
+                 [&](int i, int k, float v) { Y[i * ldn + k] = (i == k && i < n) ? v + 1.0f : v; });
   __syncthreads();
-  if (SHAPE == 0) cta_spd_inverse_p4<1, 4>(n, Y, n4, &s_flag, colbuf, false);
-  else if (SHAPE == 1) cta_spd_inverse_p4<2, 4>(n, Y, n4, &s_flag, colbuf, false);
-  else cta_spd_inverse_p4<4, 4>(n, Y, n4, &s_flag, colbuf, false);
+  if (SHAPE == 0) cta_spd_inverse_p4<1, 4>(n, Y, ldn, &s_flag, colbuf, false);
+  else if (SHAPE == 1) cta_spd_inverse_p4<2, 4>(n, Y, ldn, &s_flag, colbuf, false);
+  else cta_spd_inverse_p4<4, 4>(n, Y, ldn, &s_flag, colbuf, false);
   if (s_flag) {
     if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
     return;
   }
   // F2 = Y E
-  cta_mm4f<false>(n4, ld1, n4, Y, n4, E, ld1, [&](int i, int k, float v) { F2[i * ld1 + k] = v; });
+  cta_mm4f<false>(n4, ld1, n4, Y, ldn, E, ld1, [&](int i, int k, float v) { F2[i * ld1 + k] = v; });
   __syncthreads();
   if (mode == 1) {  // [Gam_j | gam_j] = [Z_j | v] - Tm F2
     // Gam_j (FP32) replaces Z_j in element j of buffer 0, read only by this CTA
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
     float* rf = pb;      // residual (p_b, w_a no longer needed)
     float* c1 = wa;
     float* c2 = colbuf;
-    cta_mm4f<false>(n4, ld1, n4, Tm, n4, F2, ld1, [&](int i, int k, float v) {
+    cta_mm4f<false>(n4, ld1, n4, Tm, ldn, F2, ld1, [&](int i, int k, float v) {
       if (i < n) {
         if (k < n) G[(long long)i * n + k] = Za[i * ld1 + k] - v;
         else if (k == n4) gd[i] = static_cast<double>(Za[i * ld1 + n4] - v);
@@ -210,13 +213,13 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         gbk[i] = gd[i];
         float a = 0.0f;
-        for (int k = 0; k < n; ++k) a = fmaf(Cb[k * n4 + i], rf[k], a);
+        for (int k = 0; k < n; ++k) a = fmaf(Cb[k * ldn + i], rf[k], a);
         c1[i] = a;
       }
       __syncthreads();
-      cta_mv_warp<float>(n, n, Y, n4, c1, [&](int i, float v) { c2[i] = v; });
+      cta_mv_warp<float>(n, n, Y, ldn, c1, [&](int i, float v) { c2[i] = v; });
       __syncthreads();
-      cta_trsm_lower_t_warp<float, float>(n, Cb, n4, 1, c2, 1, rdc);
+      cta_trsm_lower_t_warp<float, float>(n, Cb, ldn, 1, c2, 1, rdc);
       __syncthreads();
       for (int i = threadIdx.x; i < n; i += blockDim.x) gd[i] += static_cast<double>(c2[i]);
       __syncthreads();
@@ -243,24 +246,24 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
   if (bfin) return;
   __syncthreads();
   // [Gam | gam] = [Z_a | v] - Tm F2 (in place);  U = Y Tm' (as (Tm Y)', Y symmetric)
-  cta_mm4f<false>(n4, ld1, n4, Tm, n4, F2, ld1, [&](int i, int k, float v) { Za[i * ld1 + k] -= v; });
-  cta_mm4f<false>(n4, n4, n4, Tm, n4, Y, n4, [&](int i, int k, float v) { Cb[k * n4 + i] = v; },
+  cta_mm4f<false>(n4, ld1, n4, Tm, ldn, F2, ld1, [&](int i, int k, float v) { Za[i * ld1 + k] -= v; });
+  cta_mm4f<false>(n4, n4, n4, Tm, ldn, Y, ldn, [&](int i, int k, float v) { Cb[k * ldn + i] = v; },
                   (n4 / 4) * (ld1 / 4));
   __syncthreads();
   // Z_ab = Z_b Gam, w_ab = w_b + Z_b gam;  -(M^-1 W_a) = -W_a + Tm U
-  cta_mm4f<false>(n4, ld1, n4, Zb, n4, Za, ld1, [&](int i, int k, float v) {
+  cta_mm4f<false>(n4, ld1, n4, Zb, ldn, Za, ld1, [&](int i, int k, float v) {
     if (i < n) {
       if (k < n) ed[nn + (long long)i * n + k] = v;
       else if (k == n4) ed[3 * nn + n + i] = eb[3 * nn + n + i] + v;
     }
   });
-  cta_mm4f<false>(n4, n4, n4, Tm, n4, Cb, n4, [&](int i, int k, float v) { Wa[i * n4 + k] += v; },
+  cta_mm4f<false>(n4, n4, n4, Tm, ldn, Cb, ldn, [&](int i, int k, float v) { Wa[i * ldn + k] += v; },
                   (n4 / 4) * (ld1 / 4));
   __syncthreads();
   // -W_ab = -W_b + Z_b (-(M^-1 W_a)) Z_b': V = Z_b Hn stored transposed, then Z_b V'
-  cta_mm4f<false>(n4, n4, n4, Zb, n4, Wa, n4, [&](int i, int k, float v) { E[k * n4 + i] = v; });
+  cta_mm4f<false>(n4, n4, n4, Zb, ldn, Wa, ldn, [&](int i, int k, float v) { E[k * ldn + i] = v; });
   __syncthreads();
-  cta_mm4f<false>(n4, n4, n4, Zb, n4, E, n4, [&](int i, int k, float v) {
+  cta_mm4f<false>(n4, n4, n4, Zb, ldn, E, ldn, [&](int i, int k, float v) {
     if (i < n && k < n) ed[2 * nn + (long long)i * n + k] = eb[2 * nn + (long long)i * n + k] + v;
   });
 }
@@ -359,20 +362,20 @@ __global__ void __launch_bounds__(kBlock) link_scan_forward_kernel(ProbTable tab
   cp_async_wait<0>();
 }
 
-size_t link_scan_smem_bytes(int n) { return sizeof(float) * (size_t)scan_smem_floats(n); }
+size_t link_scan_smem_bytes(int n) { return sizeof(float) * (size_t)scan_smem_floats(n, (n + 3) & ~3); }
 
 template <int SHAPE>
-static cudaError_t launch_scan_levels(const ProbTable& tab, size_t bytes, cudaStream_t st) {
+static cudaError_t launch_scan_levels(const ProbTable& tab, size_t bytes, int ldn, cudaStream_t st) {
   const int K = tab.single.nseg;
   cudaError_t e = raise_dyn_smem((const void*)link_scan_kernel<SHAPE>, bytes);
   if (e != cudaSuccess) return e;
   int src = 0, dst = 1;
   for (int s = 1; s < K; s *= 2) {
-    link_scan_kernel<SHAPE><<<K - s, kScanBlock, bytes, st>>>(tab, s, 0, src, dst);
+    link_scan_kernel<SHAPE><<<K - s, kScanBlock, bytes, st>>>(tab, s, 0, src, dst, ldn);
     src = dst;
     dst = (dst == 1) ? 2 : 1;
   }
-  link_scan_kernel<SHAPE><<<K - 1, kScanBlock, bytes, st>>>(tab, 1, 1, 0, 0);
+  link_scan_kernel<SHAPE><<<K - 1, kScanBlock, bytes, st>>>(tab, 1, 1, 0, 0, ldn);
   return cudaGetLastError();
 }
 
@@ -380,18 +383,21 @@ static cudaError_t launch_scan_levels(const ProbTable& tab, size_t bytes, cudaSt
 cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t st, int* launches) {
   const int n = tab.single.n, K = tab.single.nseg;
   if (K < 2 || tab.probs) return cudaErrorNotSupported;
-  const size_t bytes = link_scan_smem_bytes(n);
   int optin = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int n4 = (n + 3) & ~3;
+  int ldn = n4 + 4;
+  if (sizeof(float) * (size_t)scan_smem_floats(n, ldn) > (size_t)optin - kStaticSmemReserve) ldn = n4;
+  const size_t bytes = sizeof(float) * (size_t)scan_smem_floats(n, ldn);
   const int shape = p4_shape(n);
   if (bytes > (size_t)optin - kStaticSmemReserve || shape < 0 || shape > 2 ||
       (size_t)scan_forward_smem_bytes(n) > (size_t)optin - kStaticSmemReserve)
     return cudaErrorNotSupported;
   link_scan_init_kernel<<<K, kBlock, 0, st>>>(tab);
-  cudaError_t e = shape == 0 ? launch_scan_levels<0>(tab, bytes, st)
-                  : shape == 1 ? launch_scan_levels<1>(tab, bytes, st)
-                               : launch_scan_levels<2>(tab, bytes, st);
+  cudaError_t e = shape == 0 ? launch_scan_levels<0>(tab, bytes, ldn, st)
+                  : shape == 1 ? launch_scan_levels<1>(tab, bytes, ldn, st)
+                               : launch_scan_levels<2>(tab, bytes, ldn, st);
   if (e != cudaSuccess) return e;
   const size_t fbytes = (size_t)scan_forward_smem_bytes(n);
   e = raise_dyn_smem((const void*)link_scan_forward_kernel, fbytes);

@@ -23,7 +23,7 @@
 namespace lqr {
 
 struct FastPlan {
-  int N, M, ldAB, ldF;
+  int N, M, ldAB, ldF, ldV, ldM;  // ldV, ldM: padded row strides of the n x n and m x m buffers
   long long V, Z, Wn, vx, vz, ab, Q, R, S, q, r, T1, F, Muu, Mzx, mz, colbuf, total;  // float offsets
 };
 
@@ -33,23 +33,25 @@ __host__ __device__ inline FastPlan fast_plan(int n, int m) {
   P.M = (m + 3) & ~3;
   P.ldAB = P.N + P.M + 4;
   P.ldF = 2 * P.N + 4;
-  const long long N = P.N, M = P.M;
+  P.ldV = P.N + 4;  // rows four apart in different banks
+  P.ldM = P.M + 4;
+  const long long N = P.N, M = P.M, LV = P.ldV, LM = P.ldM;
   long long o = 0;
-  P.V = o;   o += N * N;
-  P.Z = o;   o += N * N;
-  P.Wn = o;  o += N * N;
+  P.V = o;   o += N * LV;
+  P.Z = o;   o += N * LV;
+  P.Wn = o;  o += N * LV;
   P.vx = o;  o += N;
   P.vz = o;  o += N;
   P.ab = o;  o += 2 * N * P.ldAB;
-  P.Q = o;   o += N * N;
+  P.Q = o;   o += N * LV;
   P.R = o;   o += M * M;
   P.S = o;   o += M * N;
   P.q = o;   o += N;
   P.r = o;   o += M;
   P.T1 = o;  o += (N * P.ldAB > M * P.ldF) ? N * P.ldAB : M * P.ldF;  // T1, then H
   P.F = o;   o += M * P.ldF;
-  P.Muu = o; o += M * M;
-  P.Mzx = o; o += N * N;
+  P.Muu = o; o += M * LM;
+  P.Mzx = o; o += N * LV;
   P.mz = o;  o += N;
   P.colbuf = o; o += p4_scratch_floats(m);  // scratch of the block elimination
   P.total = (o + 3) & ~3LL;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
   const bool param = (mode == MODE_PARAM);
   const int t0 = seg_begin(T, K, seg), t1 = seg_begin(T, K, seg + 1);
   const FastPlan P = fast_plan(n, m);
-  const int N = P.N, M = P.M, ldAB = P.ldAB, ldF = P.ldF;
+  const int N = P.N, M = P.M, ldAB = P.ldAB, ldF = P.ldF, LV = P.ldV, LM = P.ldM;
   float* sm = reinterpret_cast<float*>(smem);
   float* V = sm + P.V;
   float* Z = sm + P.Z;
@@ -170,12 +172,12 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
   };
   issue_ab(t1 - 1);
   if (mode == MODE_PARAM) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) Z[i * N + i] = 1.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Z[i * LV + i] = 1.0f;
   } else if (mode == MODE_TERMINAL) {
     const float* QT = gQ + nn * T;
     for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
       const int i = (int)(e / n), j = (int)(e - (long long)i * n);
-      V[i * N + j] = 0.5f * (QT[(long long)i * n + j] + QT[(long long)j * n + i]);
+      V[i * LV + j] = 0.5f * (QT[(long long)i * n + j] + QT[(long long)j * n + i]);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) vx[i] = gq[(long long)n * T + i];
   } else {
@@ -183,13 +185,13 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     const double* pi = pd.ws + wl.pi + (long long)(seg + 1) * n;
     for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
       const int i = (int)(e / n), j = (int)(e - (long long)i * n);
-      V[i * N + j] = static_cast<float>(Pi[e]);
+      V[i * LV + j] = static_cast<float>(Pi[e]);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) vx[i] = static_cast<float>(pi[i]);
   }
   __syncthreads();
   if (store_P && gP && mode != MODE_PARAM && last) {  // P_T, p_T
-    for (long long e = threadIdx.x; e < nn; e += blockDim.x) gP[nn * T + e] = V[(e / n) * N + (e % n)];
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) gP[nn * T + e] = V[(e / n) * LV + (e % n)];
     for (int i = threadIdx.x; i < n; i += blockDim.x) gp[(long long)n * T + i] = vx[i];
   }
 
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     __syncthreads();  // [A|B|c]_t in its slot; the previous stage is finished
     const float* ab = sm + P.ab + (long long)((t1 - 1 - t) & 1) * N * ldAB;
     // Q, R, S, q, r of this stage, then the next stage's [A|B|c]
-    copy_rows(Qs, N, gQ + nn * t, n, n, n, v16);
+    copy_rows(Qs, LV, gQ + nn * t, n, n, n, v16);
     copy_rows(Rs, M, gR + mm * t, m, m, m, v16);
     if (gS) copy_rows(Ss, N, gS + nm * t, n, m, n, v16);
     for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(qs + i, gq + (long long)n * t + i);
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     cp_async_commit();
     issue_ab(t - 1);
     // ---- T1 = V [A|B|c] + [0|0|v_x] ----------------------------------------------
-    cta_mm4f<false>(N, ldAB, N, V, N, ab, ldAB,
+    cta_mm4f<false>(N, ldAB, N, V, LV, ab, ldAB,
                     [&](int i, int j, float v) { T1[i * ldAB + j] = (j == cN) ? v + vx[i] : v; });
     cp_async_wait<1>();  // this stage's Q, R, S, q, r (the next [A|B|c] may still be in flight)
     __syncthreads();
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     // B'T1 = [M_ux - S | M_uu - R | m_u - r] first: M_uu^-1 only needs these.
     cta_mm4f<true>(M, ldAB, N, ab + N, ldAB, T1, ldAB, [&](int a, int j, float v) {
       if (j < N) F[a * ldF + j] = v + Ss[a * N + j];
-      else if (j < cN) Muu[a * M + (j - N)] = v + Rs[a * M + (j - N)];
+      else if (j < cN) Muu[a * LM + (j - N)] = v + Rs[a * M + (j - N)];
       else if (j == cN) F[a * ldF + 2 * N] = v + rs[a];
     });
     __syncthreads();
@@ -229,18 +231,18 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     const int gthr = split ? kSweepBlock - GT : kSweepBlock;
     if (split && (int)threadIdx.x < GT) {
       if (SHAPE == 0 && GT == 128)
-        grp_spd_inverse<2, 4>(m, Muu, M, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+        grp_spd_inverse<2, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
       else if (SHAPE == 0)
-        grp_spd_inverse<1, 4>(m, Muu, M, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+        grp_spd_inverse<1, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
       else
-        grp_spd_inverse<4, 4>(m, Muu, M, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+        grp_spd_inverse<4, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
     } else {
       // M_xx = Q + A'T1_A (into V; the end-of-stage symmetrisation of V_xx takes
       // care of Q's antisymmetric part), m_x = q + A'T1_c (into v_x); the products
       // are dealt round the group one after the other (rot)
       int rot = 0;
       grp_mm4f<true>(gtid, gthr, N, N, N, ab, ldAB, T1, ldAB,
-                     [&](int i, int j, float v) { V[i * N + j] = v + Qs[i * N + j]; }, rot);
+                     [&](int i, int j, float v) { V[i * LV + j] = v + Qs[i * LV + j]; }, rot);
       rot += (N / 4) * (N / 4);
       grp_mm4f<true>(gtid, gthr, N, 4, N, ab, ldAB, T1 + cN, ldAB, [&](int i, int j, float v) {
         if (j == 0) vx[i] = v + qs[i];
@@ -248,18 +250,18 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
       rot += N / 4;
       if (param) {
         // M_zu' = (Z B)' into F[:, N:2N], m_z = w + Z c, M_zx = Z A
-        grp_mm4f<false>(gtid, gthr, N, M, N, Z, N, ab + N, ldAB,
+        grp_mm4f<false>(gtid, gthr, N, M, N, Z, LV, ab + N, ldAB,
                         [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
         rot += (N / 4) * (M / 4);
-        grp_mm4f<false>(gtid, gthr, N, 4, N, Z, N, ab + cN, ldAB, [&](int i, int j, float v) {
+        grp_mm4f<false>(gtid, gthr, N, 4, N, Z, LV, ab + cN, ldAB, [&](int i, int j, float v) {
           if (j == 0) mz[i] = v + vz[i];
         }, rot);
         rot += N / 4;
-        grp_mm4f<false>(gtid, gthr, N, N, N, Z, N, ab, ldAB, [&](int i, int j, float v) { Mzx[i * N + j] = v; }, rot);
+        grp_mm4f<false>(gtid, gthr, N, N, N, Z, LV, ab, ldAB, [&](int i, int j, float v) { Mzx[i * LV + j] = v; }, rot);
       }
     }
     __syncthreads();
-    if (!split) invert_muu<SHAPE>(m, Muu, M, &s_flag, colbuf);
+    if (!split) invert_muu<SHAPE>(m, Muu, LM, &s_flag, colbuf);
     if (s_flag) {
       if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
       cp_async_wait<0>();
@@ -267,21 +269,21 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     }
     // ---- H = M_uu^-1 [M_ux | M_zu' | m_u] ---------------------------------------------
     const int hcols = param ? ldF : ldF;  // [x | z | h] columns (the z block is zero outside the param mode)
-    cta_mm4f<false>(M, hcols, M, Muu, M, F, ldF, [&](int a, int j, float v) { H[a * ldF + j] = v; });
+    cta_mm4f<false>(M, hcols, M, Muu, LM, F, ldF, [&](int a, int j, float v) { H[a * ldF + j] = v; });
     __syncthreads();
     // ---- value update ---------------------------------------------------------------------
     int rot = 0;
-    cta_mm4f<true>(N, N, M, F, ldF, H, ldF, [&](int i, int j, float v) { V[i * N + j] -= v; }, rot);
+    cta_mm4f<true>(N, N, M, F, ldF, H, ldF, [&](int i, int j, float v) { V[i * LV + j] -= v; }, rot);
     rot += (N / 4) * (N / 4);
     cta_mm4f<true>(N, 4, M, F, ldF, H + 2 * N, ldF, [&](int i, int j, float v) {
       if (j == 0) vx[i] -= v;
     }, rot);
     rot += N / 4;
     if (param) {
-      cta_mm4f<true>(N, N, M, F + N, ldF, H, ldF, [&](int i, int j, float v) { Z[i * N + j] = Mzx[i * N + j] - v; },
+      cta_mm4f<true>(N, N, M, F + N, ldF, H, ldF, [&](int i, int j, float v) { Z[i * LV + j] = Mzx[i * LV + j] - v; },
                      rot);
       rot += (N / 4) * (N / 4);
-      cta_mm4f<true>(N, N, M, F + N, ldF, H + N, ldF, [&](int i, int j, float v) { Wn[i * N + j] -= v; }, rot);
+      cta_mm4f<true>(N, N, M, F + N, ldF, H + N, ldF, [&](int i, int j, float v) { Wn[i * LV + j] -= v; }, rot);
       rot += (N / 4) * (N / 4);
       cta_mm4f<true>(N, 4, M, F + N, ldF, H + 2 * N, ldF, [&](int i, int j, float v) {
         if (j == 0) vz[i] = mz[i] - v;
@@ -301,14 +303,14 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
       const int i = e / N, j = e - i * N;
       if (j > i) {
-        const float s = 0.5f * (V[i * N + j] + V[j * N + i]);
-        V[i * N + j] = s;
-        V[j * N + i] = s;
+        const float s = 0.5f * (V[i * LV + j] + V[j * LV + i]);
+        V[i * LV + j] = s;
+        V[j * LV + i] = s;
       }
     }
     if (store_P && gP && !param) {
       __syncthreads();
-      for (long long e = threadIdx.x; e < nn; e += blockDim.x) gP[nn * t + e] = V[(e / n) * N + (e % n)];
+      for (long long e = threadIdx.x; e < nn; e += blockDim.x) gP[nn * t + e] = V[(e / n) * LV + (e % n)];
       for (int i = threadIdx.x; i < n; i += blockDim.x) gp[(long long)n * t + i] = vx[i];
     }
   }
@@ -318,10 +320,10 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
   if (mode == MODE_POLICY) return;
   for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
     const int i = (int)(e / n), j = (int)(e - (long long)i * n);
-    summ[e] = static_cast<double>(V[i * N + j]);
+    summ[e] = static_cast<double>(V[i * LV + j]);
     if (param) {
-      summ[nn + e] = static_cast<double>(Z[i * N + j]);
-      summ[2 * nn + e] = 0.5 * (static_cast<double>(Wn[i * N + j]) + static_cast<double>(Wn[j * N + i]));
+      summ[nn + e] = static_cast<double>(Z[i * LV + j]);
+      summ[2 * nn + e] = 0.5 * (static_cast<double>(Wn[i * LV + j]) + static_cast<double>(Wn[j * LV + i]));
     } else {
       summ[nn + e] = 0.0;
       summ[2 * nn + e] = 0.0;
