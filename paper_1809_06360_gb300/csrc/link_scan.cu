@@ -364,23 +364,29 @@ __global__ void __launch_bounds__(kBlock) link_scan_forward_kernel(ProbTable tab
 
 size_t link_scan_smem_bytes(int n) { return sizeof(float) * (size_t)scan_smem_floats(n, (n + 3) & ~3); }
 
+// levels: the scan levels (true) or the feedback pass (false)
 template <int SHAPE>
-static cudaError_t launch_scan_levels(const ProbTable& tab, size_t bytes, int ldn, cudaStream_t st) {
+static cudaError_t launch_scan_levels(const ProbTable& tab, size_t bytes, int ldn, cudaStream_t st, bool levels) {
   const int K = tab.single.nseg;
   cudaError_t e = raise_dyn_smem((const void*)link_scan_kernel<SHAPE>, bytes);
   if (e != cudaSuccess) return e;
-  int src = 0, dst = 1;
-  for (int s = 1; s < K; s *= 2) {
-    link_scan_kernel<SHAPE><<<K - s, kScanBlock, bytes, st>>>(tab, s, 0, src, dst, ldn);
-    src = dst;
-    dst = (dst == 1) ? 2 : 1;
+  if (levels) {
+    int src = 0, dst = 1;
+    for (int s = 1; s < K; s *= 2) {
+      link_scan_kernel<SHAPE><<<K - s, kScanBlock, bytes, st>>>(tab, s, 0, src, dst, ldn);
+      src = dst;
+      dst = (dst == 1) ? 2 : 1;
+    }
+  } else {
+    link_scan_kernel<SHAPE><<<K - 1, kScanBlock, bytes, st>>>(tab, 1, 1, 0, 0, ldn);
   }
-  link_scan_kernel<SHAPE><<<K - 1, kScanBlock, bytes, st>>>(tab, 1, 1, 0, 0, ldn);
   return cudaGetLastError();
 }
 
 // Returns cudaErrorNotSupported (nothing launched) when the shape does not fit.
-cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t st, int* launches) {
+// part: 0 = the whole solve; 1 = the summaries' conversion and the levels (Pi_j,
+// pi_j final afterwards); 2 = the feedback pass and the link states.
+cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t st, int* launches, int part) {
   const int n = tab.single.n, K = tab.single.nseg;
   if (K < 2 || tab.probs) return cudaErrorNotSupported;
   int optin = 0, dev = 0;
@@ -394,20 +400,30 @@ cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t
   if (bytes > (size_t)optin - kStaticSmemReserve || shape < 0 || shape > 2 ||
       (size_t)scan_forward_smem_bytes(n) > (size_t)optin - kStaticSmemReserve)
     return cudaErrorNotSupported;
-  link_scan_init_kernel<<<K, kBlock, 0, st>>>(tab);
-  cudaError_t e = shape == 0 ? launch_scan_levels<0>(tab, bytes, ldn, st)
-                  : shape == 1 ? launch_scan_levels<1>(tab, bytes, ldn, st)
-                               : launch_scan_levels<2>(tab, bytes, ldn, st);
-  if (e != cudaSuccess) return e;
-  const size_t fbytes = (size_t)scan_forward_smem_bytes(n);
-  e = raise_dyn_smem((const void*)link_scan_forward_kernel, fbytes);
-  if (e != cudaSuccess) return e;
-  link_scan_forward_kernel<<<1, kBlock, fbytes, st>>>(tab, x0_is_float);
-  if (launches) {
-    int lv = 0;
-    for (int s = 1; s < K; s *= 2) ++lv;
-    *launches = 3 + lv;
+  int lv = 0;
+  for (int s = 1; s < K; s *= 2) ++lv;
+  int nl = 0;
+  cudaError_t e = cudaSuccess;
+  if (part != 2) {
+    link_scan_init_kernel<<<K, kBlock, 0, st>>>(tab);
+    e = shape == 0 ? launch_scan_levels<0>(tab, bytes, ldn, st, true)
+        : shape == 1 ? launch_scan_levels<1>(tab, bytes, ldn, st, true)
+                     : launch_scan_levels<2>(tab, bytes, ldn, st, true);
+    if (e != cudaSuccess) return e;
+    nl += 1 + lv;
   }
+  if (part != 1) {
+    e = shape == 0 ? launch_scan_levels<0>(tab, bytes, ldn, st, false)
+        : shape == 1 ? launch_scan_levels<1>(tab, bytes, ldn, st, false)
+                     : launch_scan_levels<2>(tab, bytes, ldn, st, false);
+    if (e != cudaSuccess) return e;
+    const size_t fbytes = (size_t)scan_forward_smem_bytes(n);
+    e = raise_dyn_smem((const void*)link_scan_forward_kernel, fbytes);
+    if (e != cudaSuccess) return e;
+    link_scan_forward_kernel<<<1, kBlock, fbytes, st>>>(tab, x0_is_float);
+    nl += 2;
+  }
+  if (launches) *launches = nl;
   return cudaGetLastError();
 }
 

@@ -61,6 +61,9 @@ struct lqr_handle {
   cudaEvent_t ev[kMaxProfiled][kPhases + 1];
   int ev_created = 0;
   int prof_launches[kPhases] = {0};
+  // side stream: the A4 sweep runs on it next to the link tail (fork/join by events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -230,17 +233,17 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
   const int prec = o->prec;
   const bool dual = (o->form != LQR_FORM_CONSTRAINED);
   cudaError_t e;
-  auto sweep = [&](int phase) {
-    if (prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, sp.K, phase, sp.smem, budget, store_P, st);
-    if (prec == LQR_MIXED_TF32) return launch_seg_sweep<double, float>(tab, sp.K, phase, sp.smem, budget, store_P, st);
+  auto sweep = [&](int phase, cudaStream_t sst) {
+    if (prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, sp.K, phase, sp.smem, budget, store_P, sst);
+    if (prec == LQR_MIXED_TF32) return launch_seg_sweep<double, float>(tab, sp.K, phase, sp.smem, budget, store_P, sst);
     if (dual) {
-      const cudaError_t r = launch_seg_sweep_f32(tab, sp.K, phase, tab.single.n, tab.single.m, budget, store_P, st);
+      const cudaError_t r = launch_seg_sweep_f32(tab, sp.K, phase, tab.single.n, tab.single.m, budget, store_P, sst);
       if (r != cudaErrorNotSupported) return r;
     }
-    return launch_seg_sweep<float, float>(tab, sp.K, phase, sp.smem, budget, store_P, st);
+    return launch_seg_sweep<float, float>(tab, sp.K, phase, sp.smem, budget, store_P, sst);
   };
   if (profile) prof_mark(h, LQR_PHASE_SWEEP, st);
-  e = sweep(0);
+  e = sweep(0, st);
   ++*launches;
   if (e != cudaSuccess) return LQR_ERR_CUDA;
   if (profile) prof_mark(h, LQR_PHASE_LINK, st);
@@ -252,20 +255,53 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
     return LQR_OK;
   }
   const int x0f = (prec == LQR_FP32) ? 1 : 0;
-  // the boundary-coupling solve runs in FP64 except in the all-FP32 mode
-  if (dual) {
+  // FP32 multiplier form: the scan up to the final Pi_j, then the A4 sweep on the
+  // side stream while the link feedback and link states run here
+  bool scan_split = false;
+  if (dual && prec == LQR_FP32 && o->link != LQR_LINK_CHAIN && sp.K > 1) {
+    if (!h->side) {
+      if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return LQR_ERR_CUDA;
+    }
     int nl = 0;
-    e = launch_link_solve_dual(tab, 1, x0f, st, prec == LQR_FP32 ? 1 : 0, o->link, &nl);
-    *launches += nl;
-    if (e == cudaErrorNotSupported) return LQR_ERR_UNSUPPORTED;
-  } else {
-    e = launch_link_solve(tab, 1, x0f, st);
-    ++*launches;
+    e = launch_link_scan(tab, x0f, st, &nl, 1);
+    if (e == cudaSuccess) {
+      scan_split = true;
+      *launches += nl;
+    } else if (e != cudaErrorNotSupported) {
+      return LQR_ERR_CUDA;
+    }
   }
-  if (e != cudaSuccess) return LQR_ERR_CUDA;
+  if (!scan_split) {
+    // the boundary-coupling solve runs in FP64 except in the all-FP32 mode
+    if (dual) {
+      int nl = 0;
+      e = launch_link_solve_dual(tab, 1, x0f, st, prec == LQR_FP32 ? 1 : 0, o->link, &nl);
+      *launches += nl;
+      if (e == cudaErrorNotSupported) return LQR_ERR_UNSUPPORTED;
+    } else {
+      e = launch_link_solve(tab, 1, x0f, st);
+      ++*launches;
+    }
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+  }
   if (profile) prof_mark(h, LQR_PHASE_POLICY, st);
-  if (sp.K > 1) {
-    e = sweep(1);
+  if (scan_split) {
+    if (cudaEventRecord(h->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(h->side, h->ev_fork, 0) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    e = sweep(1, h->side);
+    ++*launches;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+    if (cudaEventRecord(h->ev_join, h->side) != cudaSuccess) return LQR_ERR_CUDA;
+    int nl = 0;
+    e = launch_link_scan(tab, x0f, st, &nl, 2);
+    *launches += nl;
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess) return LQR_ERR_CUDA;
+  } else if (sp.K > 1) {
+    e = sweep(1, st);
     ++*launches;
     if (e != cudaSuccess) return LQR_ERR_CUDA;
   }
@@ -730,6 +766,9 @@ lqr_status lqr_destroy(lqr_handle* h) {
   if (h->ev_created)
     for (int i = 0; i < lqr_handle::kMaxProfiled; ++i)
       for (int k = 0; k <= lqr_handle::kPhases; ++k) cudaEventDestroy(h->ev[i][k]);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
   return LQR_OK;
 }

@@ -225,8 +225,9 @@ long long fast_sweep_smem_bytes(int n, int m);
 cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st,
                                    int link_fp32, int method, int* nlaunch);
 // The FP32 suffix-scan link solve; cudaErrorNotSupported (nothing launched)
-// when the problem shape does not fit.
-cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t st, int* launches);
+// when the problem shape does not fit. part 0: all; 1: up to the final Pi_j, pi_j;
+// 2: the link feedback and the link states.
+cudaError_t launch_link_scan(const ProbTable& tab, int x0_is_float, cudaStream_t st, int* launches, int part = 0);
 size_t link_scan_smem_bytes(int n);
 
 template <typename TS, typename TC>
