@@ -1351,63 +1351,69 @@ struct NamedBar {
 // element of the padded M x N range.
 // rot: tile 0 goes to thread rot (mod blockDim.x), so that consecutive
 // products of one phase can be dealt where the previous one left off.
+// One 4 x 4 output tile at (i0, j0) of the product below (the shared body of
+// the CTA and group forms, also usable with a caller's own tile order).
+template <bool TA, typename Epi>
+__device__ __forceinline__ void mm4f_tile(int i0, int j0, int K, const float* A, int lda, const float* B, int ldb,
+                                          Epi epi) {
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+  int k = 0;
+  if (!TA) {
+    for (; k + 4 <= K; k += 4) {
+      float4 av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = *reinterpret_cast<const float4*>(A + (size_t)(i0 + a) * lda + k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = *reinterpret_cast<const float4*>(B + (size_t)(k + q) * ldb + j0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float ak[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[a][0] = fmaf(ak[q], bv[q].x, acc[a][0]);
+          acc[a][1] = fmaf(ak[q], bv[q].y, acc[a][1]);
+          acc[a][2] = fmaf(ak[q], bv[q].z, acc[a][2]);
+          acc[a][3] = fmaf(ak[q], bv[q].w, acc[a][3]);
+        }
+      }
+    }
+  }
+  for (; k < K; ++k) {
+    float ak[4];
+    if (TA) {
+      const float4 t4 = *reinterpret_cast<const float4*>(A + (size_t)k * lda + i0);
+      ak[0] = t4.x; ak[1] = t4.y; ak[2] = t4.z; ak[3] = t4.w;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ak[a] = A[(size_t)(i0 + a) * lda + k];
+    }
+    const float4 bv = *reinterpret_cast<const float4*>(B + (size_t)k * ldb + j0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      acc[a][0] = fmaf(ak[a], bv.x, acc[a][0]);
+      acc[a][1] = fmaf(ak[a], bv.y, acc[a][1]);
+      acc[a][2] = fmaf(ak[a], bv.z, acc[a][2]);
+      acc[a][3] = fmaf(ak[a], bv.w, acc[a][3]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) epi(i0 + a, j0 + b, acc[a][b]);
+}
+
 // grp_mm4f: the same over a group of nthr threads, gtid the index in the group.
 template <bool TA, typename Epi>
 __device__ __forceinline__ void grp_mm4f(int gtid, int nthr, int M, int N, int K, const float* A, int lda,
                                          const float* B, int ldb, Epi epi, int rot = 0) {
   const int tm = M >> 2, tn = N >> 2;
   const int tid = (gtid + nthr - (rot % nthr)) % nthr;
-  for (int tile = tid; tile < tm * tn; tile += nthr) {
-    const int i0 = (tile / tn) << 2, j0 = (tile % tn) << 2;
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-    int k = 0;
-    if (!TA) {
-      for (; k + 4 <= K; k += 4) {
-        float4 av[4], bv[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = *reinterpret_cast<const float4*>(A + (size_t)(i0 + a) * lda + k);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) bv[q] = *reinterpret_cast<const float4*>(B + (size_t)(k + q) * ldb + j0);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float ak[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            acc[a][0] = fmaf(ak[q], bv[q].x, acc[a][0]);
-            acc[a][1] = fmaf(ak[q], bv[q].y, acc[a][1]);
-            acc[a][2] = fmaf(ak[q], bv[q].z, acc[a][2]);
-            acc[a][3] = fmaf(ak[q], bv[q].w, acc[a][3]);
-          }
-        }
-      }
-    }
-    for (; k < K; ++k) {
-      float ak[4];
-      if (TA) {
-        const float4 t4 = *reinterpret_cast<const float4*>(A + (size_t)k * lda + i0);
-        ak[0] = t4.x; ak[1] = t4.y; ak[2] = t4.z; ak[3] = t4.w;
-      } else {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) ak[a] = A[(size_t)(i0 + a) * lda + k];
-      }
-      const float4 bv = *reinterpret_cast<const float4*>(B + (size_t)k * ldb + j0);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        acc[a][0] = fmaf(ak[a], bv.x, acc[a][0]);
-        acc[a][1] = fmaf(ak[a], bv.y, acc[a][1]);
-        acc[a][2] = fmaf(ak[a], bv.z, acc[a][2]);
-        acc[a][3] = fmaf(ak[a], bv.w, acc[a][3]);
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) epi(i0 + a, j0 + b, acc[a][b]);
-  }
+  for (int tile = tid; tile < tm * tn; tile += nthr)
+    mm4f_tile<TA>((tile / tn) << 2, (tile % tn) << 2, K, A, lda, B, ldb, epi);
 }
 
 template <bool TA, typename Epi>

@@ -213,43 +213,37 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     cp_async_wait<1>();  // this stage's Q, R, S, q, r (the next [A|B|c] may still be in flight)
     __syncthreads();
     // ---- the M terms ---------------------------------------------------------------
-    // B'T1 = [M_ux - S | M_uu - R | m_u - r] first: M_uu^-1 only needs these.
-    cta_mm4f<true>(M, ldAB, N, ab + N, ldAB, T1, ldAB, [&](int a, int j, float v) {
-      if (j < N) F[a * ldF + j] = v + Ss[a * N + j];
-      else if (j < cN) Muu[a * LM + (j - N)] = v + Rs[a * M + (j - N)];
-      else if (j == cN) F[a * ldF + 2 * N] = v + rs[a];
-    });
-    __syncthreads();
-    // Then, for m <= 64, the first GT threads invert M_uu (named barrier 1)
-    // while the others form the terms that do not depend on it; for larger m
-    // the whole block does one after the other.
-    // (m <= 32: 128 threads when the parametric terms give the others more to
-    // do, else 256; m <= 64: 256)
-    const int GT = SHAPE == 0 ? (param ? 128 : 256) : (SHAPE == 1 ? 256 : 0);
-    const bool split = GT > 0;
-    const int gtid = split ? (int)threadIdx.x - GT : (int)threadIdx.x;
-    const int gthr = split ? kSweepBlock - GT : kSweepBlock;
-    if (split && (int)threadIdx.x < GT) {
-      if (SHAPE == 0 && GT == 128)
-        grp_spd_inverse<2, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
-      else if (SHAPE == 0)
-        grp_spd_inverse<1, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
-      else
-        grp_spd_inverse<4, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
-    } else {
-      // M_xx = Q + A'T1_A (into V; the end-of-stage symmetrisation of V_xx takes
-      // care of Q's antisymmetric part), m_x = q + A'T1_c (into v_x); the products
-      // are dealt round the group one after the other (rot)
-      int rot = 0;
-      grp_mm4f<true>(gtid, gthr, N, N, N, ab, ldAB, T1, ldAB,
-                     [&](int i, int j, float v) { V[i * LV + j] = v + Qs[i * LV + j]; }, rot);
-      rot += (N / 4) * (N / 4);
-      grp_mm4f<true>(gtid, gthr, N, 4, N, ab, ldAB, T1 + cN, ldAB, [&](int i, int j, float v) {
-        if (j == 0) vx[i] = v + qs[i];
-      }, rot);
-      rot += N / 4;
-      if (param) {
-        // M_zu' = (Z B)' into F[:, N:2N], m_z = w + Z c, M_zx = Z A
+    if (param && SHAPE <= 1) {
+      // Parametric sweep, m <= 64: B'T1 = [M_ux - S | M_uu - R | m_u - r] first; then
+      // the first GT threads invert M_uu (named barrier 1) while the others form
+      // M_xx, m_x, M_zu, m_z, M_zx, which do not depend on it (measured: the
+      // inverse stays the long pole, stretched by the products beside it, and a
+      // window with more product work hides more of it).
+      cta_mm4f<true>(M, ldAB, N, ab + N, ldAB, T1, ldAB, [&](int a, int j, float v) {
+        if (j < N) F[a * ldF + j] = v + Ss[a * N + j];
+        else if (j < cN) Muu[a * LM + (j - N)] = v + Rs[a * M + (j - N)];
+        else if (j == cN) F[a * ldF + 2 * N] = v + rs[a];
+      });
+      __syncthreads();
+      const int GT = SHAPE == 0 ? 128 : 256;
+      if ((int)threadIdx.x < GT) {
+        if (SHAPE == 0)
+          grp_spd_inverse<2, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+        else
+          grp_spd_inverse<4, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+      } else {
+        // M_xx = Q + A'T1_A (into V; the end-of-stage symmetrisation of V_xx takes
+        // care of Q's antisymmetric part), m_x = q + A'T1_c, M_zu' = (Z B)' into
+        // F[:, N:2N], m_z = w + Z c, M_zx = Z A, dealt round the group (rot)
+        const int gtid = (int)threadIdx.x - GT, gthr = kSweepBlock - GT;
+        int rot = 0;
+        grp_mm4f<true>(gtid, gthr, N, N, N, ab, ldAB, T1, ldAB,
+                       [&](int i, int j, float v) { V[i * LV + j] = v + Qs[i * LV + j]; }, rot);
+        rot += (N / 4) * (N / 4);
+        grp_mm4f<true>(gtid, gthr, N, 4, N, ab, ldAB, T1 + cN, ldAB, [&](int i, int j, float v) {
+          if (j == 0) vx[i] = v + qs[i];
+        }, rot);
+        rot += N / 4;
         grp_mm4f<false>(gtid, gthr, N, M, N, Z, LV, ab + N, ldAB,
                         [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
         rot += (N / 4) * (M / 4);
@@ -259,9 +253,56 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
         rot += N / 4;
         grp_mm4f<false>(gtid, gthr, N, N, N, Z, LV, ab, ldAB, [&](int i, int j, float v) { Mzx[i * LV + j] = v; }, rot);
       }
+      __syncthreads();
+    } else {
+      // [A|B]'T1 in one product over the block: rows of A' give M_xx - Q (into V)
+      // and m_x - q (columns [0, N) and cN), rows of B' give [M_ux - S | M_uu - R |
+      // m_u - r]; the tiles of A'T1_B (= M_ux', not needed) are not formed. With the
+      // parametric terms (m > 64) Z B, Z c, Z A join the same phase; then the whole
+      // block inverts M_uu.
+      const int tA = (N / 4) * (N / 4 + 1), tB = (M / 4) * (ldAB / 4);
+      for (int tile = threadIdx.x; tile < tA + tB; tile += kSweepBlock) {
+        int i0, j0;
+        if (tile < tA) {
+          i0 = (tile / (N / 4 + 1)) * 4;
+          const int c = tile % (N / 4 + 1);
+          j0 = (c < N / 4) ? 4 * c : cN;
+        } else {
+          i0 = N + ((tile - tA) / (ldAB / 4)) * 4;
+          j0 = ((tile - tA) % (ldAB / 4)) * 4;
+        }
+        mm4f_tile<true>(i0, j0, N, ab, ldAB, T1, ldAB, [&](int i, int j, float v) {
+          if (i < N) {
+            if (j < N) V[i * LV + j] = v + Qs[i * LV + j];
+            else if (j == cN) vx[i] = v + qs[i];
+          } else {
+            const int a = i - N;
+            if (j < N) F[a * ldF + j] = v + Ss[a * N + j];
+            else if (j < cN) Muu[a * LM + (j - N)] = v + Rs[a * M + (j - N)];
+            else if (j == cN) F[a * ldF + 2 * N] = v + rs[a];
+          }
+        });
+      }
+      if (param) {
+        int rot = (tA + tB) % kSweepBlock;
+        cta_mm4f<false>(N, M, N, Z, LV, ab + N, ldAB, [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
+        rot += (N / 4) * (M / 4);
+        cta_mm4f<false>(N, 4, N, Z, LV, ab + cN, ldAB, [&](int i, int j, float v) {
+          if (j == 0) mz[i] = v + vz[i];
+        }, rot);
+        rot += N / 4;
+        cta_mm4f<false>(N, N, N, Z, LV, ab, ldAB, [&](int i, int j, float v) { Mzx[i * LV + j] = v; }, rot);
+      }
+      __syncthreads();
+      if (SHAPE == 0)  // m <= 32: one 1 x 2 block per thread of the 512
+        grp_spd_inverse<1, 2>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, kSweepBlock,
+                              NamedBar{1, kSweepBlock});
+      else if (SHAPE == 1)
+        grp_spd_inverse<2, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, kSweepBlock,
+                              NamedBar{1, kSweepBlock});
+      __syncthreads();
     }
-    __syncthreads();
-    if (!split) invert_muu<SHAPE>(m, Muu, LM, &s_flag, colbuf);
+    if (SHAPE >= 2) invert_muu<SHAPE>(m, Muu, LM, &s_flag, colbuf);
     if (s_flag) {
       if (threadIdx.x == 0) raise_status(pd.status, LQR_ERR_NOT_PD, t);
       cp_async_wait<0>();
