@@ -215,7 +215,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "mixed", "mixed_fp32"])
+    ap.add_argument("--tol", type=float, default=1e-10, help="refinement target |r|/|b| (mixed modes)")
+    ap.add_argument("--max-refine", type=int, default=6)
     ap.add_argument("--segments", type=int, default=0, help="0 = the library's choice (one per SM)")
     ap.add_argument("--form", default="multiplier", choices=["multiplier", "constrained"])
     ap.add_argument("--T", type=int, default=4096)
@@ -253,8 +255,10 @@ def main():
     out = solver.alloc_solution(dev, want=("K", "k", "x", "u", "lam"))
     stream = torch.cuda.current_stream()
 
+    mr = args.max_refine if args.prec.startswith("mixed") else 0
+
     def step():
-        solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form)
+        solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form, max_refine=mr, tol=args.tol)
 
     for _ in range(args.warmup):
         step()
@@ -266,9 +270,10 @@ def main():
 
     # KKT residual of the benchmarked solution, by the library's own FP64 residual
     # pass (step A7), once, outside the timing
-    solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form, residual=True)
+    solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form, residual=True, max_refine=mr,
+                 tol=args.tol)
     rep_res = solver.report()
-    res = {"eta": rep_res["kkt_residual"], "rel": rep_res["kkt_rel"]}
+    res = {"eta": rep_res["kkt_residual"], "rel": rep_res["kkt_rel"], "iters": rep_res["refine_iters"]}
 
     clocks = ClockSampler(local)
     if world > 1:
@@ -384,11 +389,13 @@ def main():
         shapes = dict(K=(T, m, n), k=(T, m), x=(T + 1, n), u=(T, m))
         outp = {k: torch.empty(s, dtype=dt).pin_memory().numpy() for k, s in shapes.items()}
         for _ in range(2):
-            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form)
+            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form, max_refine=mr,
+                              tol=args.tol)
         t0 = time.perf_counter()
         e2e_steps = max(3, args.steps // 2)
         for _ in range(e2e_steps):
-            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form)
+            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form, max_refine=mr,
+                              tol=args.tol)
         el = time.perf_counter() - t0
         h2d = sum(v.nbytes for v in pin_np.values())
         d2h = sum(v.nbytes for v in outp.values())
@@ -402,7 +409,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64"}[args.prec],
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64", "mixed_fp32": "f32+f64"}[args.prec],
                 "data": "synthetic (seeded PCG64), inputs resident in HBM",
                 "config": {"workload": "long-horizon LQR n=64 m=32 T=%d rho(A)<=1.02, K=%d segments, %s" %
                                        (T, K, args.prec.upper()),
@@ -410,6 +417,7 @@ def main():
                            "speedup_vs_plain_fp64": (value / world / fp64_ref["stages_per_s"]) if fp64_ref else None,
                            "n": n, "m": m, "T": T, "K": K, "precision": args.prec, "form": args.form,
                            "kkt_backward_error": res["eta"], "kkt_rel_residual": res["rel"],
+                           "refinement_corrections": res["iters"] if mr else 0,
                            "l2": "inputs (%.0f MB) larger than L2 (129 MB)" % (
                                sum(v.nbytes for v in prob_np.values()) * (1 if args.prec == "fp64" else 0.5) / 1e6),
                            "parallelism": "replicas" if world > 1 else "single GPU"},

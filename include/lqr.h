@@ -69,7 +69,10 @@ typedef enum {
   LQR_FP64 = 0,       /* all arithmetic in FP64 (the plain method)                          */
   LQR_FP32 = 1,       /* FP32 data and arithmetic, sweeps and link solve alike               */
   LQR_MIXED_TF32 = 2, /* FP64 data; FP32 sweeps, FP64 factor/link solve, FP64 KKT refinement */
-  LQR_MIXED_BF16 = 3  /* reserved (LQR_ERR_UNSUPPORTED)                                      */
+  LQR_MIXED_BF16 = 3, /* reserved (LQR_ERR_UNSUPPORTED)                                      */
+  LQR_MIXED_FP32 = 4  /* FP64 data and solution; the solve and every refinement correction run
+                         the LQR_FP32 path on an FP32 copy of the data (LQR_FORM_MULTIPLIER
+                         only), the FP64 KKT residual drives iterative refinement to opts.tol */
 } lqr_precision;
 
 /* How a segment carries its unknown end state (both reach the same summary

@@ -64,6 +64,9 @@ struct lqr_handle {
   // side stream: the A4 sweep runs on it next to the link tail (fork/join by events)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // LQR_MIXED_FP32: FP32 copy of the data, FP32 solution and correction buffers
+  unsigned char* f32 = nullptr;
+  size_t f32_bytes = 0;
 };
 
 namespace {
@@ -120,6 +123,7 @@ bool elem_size(lqr_precision p, size_t* es) {
     case LQR_FP64: *es = 8; return true;
     case LQR_MIXED_TF32: *es = 8; return true;
     case LQR_FP32: *es = 4; return true;
+    case LQR_MIXED_FP32: *es = 8; return true;
     default: return false;
   }
 }
@@ -133,14 +137,16 @@ lqr_status validate(const lqr_problem* p, const lqr_opts* o, const lqr_solution*
   if (s->lam && (!s->x || !s->u)) return LQR_ERR_INVALID_ARG;
   if ((s->x || s->u) && (!s->K || !s->k)) return LQR_ERR_INVALID_ARG;  // the rollout reads K_t, k_t
   if (o->num_segments < 0 || o->num_segments > p->T) return LQR_ERR_INVALID_ARG;
-  if (o->prec != LQR_FP64 && o->prec != LQR_FP32 && o->prec != LQR_MIXED_TF32) return LQR_ERR_UNSUPPORTED;
+  if (o->prec != LQR_FP64 && o->prec != LQR_FP32 && o->prec != LQR_MIXED_TF32 && o->prec != LQR_MIXED_FP32)
+    return LQR_ERR_UNSUPPORTED;
+  if (o->prec == LQR_MIXED_FP32 && o->form != LQR_FORM_MULTIPLIER) return LQR_ERR_UNSUPPORTED;
   if (o->form != LQR_FORM_MULTIPLIER && o->form != LQR_FORM_CONSTRAINED) return LQR_ERR_INVALID_ARG;
   if (o->max_refine < 0 || o->max_refine > 64) return LQR_ERR_INVALID_ARG;
   if ((o->max_refine > 0 || o->residual) && (!s->x || !s->u || !s->lam || !s->K || !s->k))
     return LQR_ERR_INVALID_ARG;
   if (o->max_refine > 0 && o->prec == LQR_FP32) return LQR_ERR_UNSUPPORTED;  // refinement needs FP64 data
   if (o->link != LQR_LINK_AUTO && o->link != LQR_LINK_CHAIN && o->link != LQR_LINK_SCAN) return LQR_ERR_INVALID_ARG;
-  if (o->link == LQR_LINK_SCAN && (o->prec != LQR_FP32 || o->form != LQR_FORM_MULTIPLIER))
+  if (o->link == LQR_LINK_SCAN && ((o->prec != LQR_FP32 && o->prec != LQR_MIXED_FP32) || o->form != LQR_FORM_MULTIPLIER))
     return LQR_ERR_UNSUPPORTED;
   return LQR_OK;
 }
@@ -321,9 +327,147 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
   return LQR_OK;
 }
 
+// LQR_MIXED_FP32: the FP32 path on an FP32 copy of the data, solution kept in
+// FP64, FP64 residual and refinement corrections by the FP32 path.
+lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const lqr_solution* s,
+                             cudaStream_t st, bool summary_only, SolvePlan* sp_out) {
+  SolvePlan sp;
+  lqr_status rs = plan_solve(h, p, o, &sp);
+  if (rs != LQR_OK) return rs;
+  rs = grow(&h->ws, &h->ws_bytes, sp.ws_need);
+  if (rs != LQR_OK) return rs;
+  const int n = p->n, m = p->m, T = p->T;
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  const bool want_P = (s->P != nullptr);
+  // FP32 working arrays (each 256-byte aligned)
+  size_t off = 0;
+  auto take = [&](size_t cnt) { const size_t a = off; off += (cnt + 63) & ~(size_t)63; return a; };
+  const size_t oA = take((size_t)T * nn), oB = take((size_t)T * nm), oc = take((size_t)T * n),
+               oQ = take((size_t)(T + 1) * nn), oR = take((size_t)T * mm), oS = p->S ? take((size_t)T * nm) : 0,
+               oq = take((size_t)(T + 1) * n), orr = take((size_t)T * m), ox0 = take(n);
+  const size_t oK = take((size_t)T * nm), ok = take((size_t)T * m), ox = take((size_t)(T + 1) * n),
+               ou = take((size_t)T * m), ol = take((size_t)(T + 1) * n), oP = want_P ? take((size_t)(T + 1) * nn) : 0,
+               op = want_P ? take((size_t)(T + 1) * n) : 0;
+  const size_t ocq = take((size_t)(T + 1) * n), ocr = take((size_t)T * m), occ = take((size_t)T * n),
+               ocx0 = take(n), odk = take((size_t)T * m), odx = take((size_t)(T + 1) * n), odu = take((size_t)T * m),
+               odl = take((size_t)(T + 1) * n), odp = want_P ? take((size_t)(T + 1) * n) : 0;
+  rs = grow(&h->f32, &h->f32_bytes, sizeof(float) * off);
+  if (rs != LQR_OK) return rs;
+  float* f = reinterpret_cast<float*>(h->f32);
+  lqr_problem p32 = *p;
+  p32.A = f + oA; p32.B = f + oB; p32.c = f + oc; p32.Q = f + oQ; p32.R = f + oR; p32.S = p->S ? f + oS : nullptr;
+  p32.q = f + oq; p32.r = f + orr; p32.x0 = f + ox0;
+  lqr_solution s32;
+  memset(&s32, 0, sizeof(s32));
+  if (!summary_only) {
+    s32.K = f + oK; s32.k = f + ok; s32.x = f + ox; s32.u = f + ou; s32.lam = f + ol;
+    if (want_P) { s32.P = f + oP; s32.p = f + op; }
+  }
+  {
+    ConvTable<double, float> ct;
+    ct.count = 0;
+    ct.add(p->A, (void*)p32.A, (size_t)T * nn);
+    ct.add(p->B, (void*)p32.B, (size_t)T * nm);
+    ct.add(p->c, (void*)p32.c, (size_t)T * n);
+    ct.add(p->Q, (void*)p32.Q, (size_t)(T + 1) * nn);
+    ct.add(p->R, (void*)p32.R, (size_t)T * mm);
+    ct.add(p->S, (void*)p32.S, (size_t)T * nm);
+    ct.add(p->q, (void*)p32.q, (size_t)(T + 1) * n);
+    ct.add(p->r, (void*)p32.r, (size_t)T * m);
+    ct.add(p->x0, (void*)p32.x0, (size_t)n);
+    if (launch_convert(ct, nullptr, st) != cudaSuccess) return LQR_ERR_CUDA;
+  }
+  lqr_opts o32 = *o;
+  o32.prec = LQR_FP32;
+  ProbTable tab;
+  memset(&tab, 0, sizeof(tab));
+  tab.single = make_desc(h, &p32, &s32, sp, (int)o->form);
+  tab.nprob = 1;
+  int launches = 1;
+  if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
+  if (cudaMemsetAsync(h->d_report, 0, 4 * sizeof(double), st) != cudaSuccess) return LQR_ERR_CUDA;
+  rs = enqueue_pipeline(h, tab, sp, &o32, !summary_only, !summary_only, want_P ? 1 : 0, summary_only, true, st,
+                        &launches);
+  if (rs != LQR_OK) return rs;
+  if (!summary_only) {
+    ConvTable<float, double> ct;
+    ct.count = 0;
+    ct.add(s32.K, s->K, (size_t)T * nm);
+    ct.add(s32.k, s->k, (size_t)T * m);
+    ct.add(s32.x, s->x, (size_t)(T + 1) * n);
+    ct.add(s32.u, s->u, (size_t)T * m);
+    ct.add(s32.lam, s->lam, (size_t)(T + 1) * n);
+    if (want_P) {
+      ct.add(s32.P, s->P, (size_t)(T + 1) * nn);
+      ct.add(s32.p, s->p, (size_t)(T + 1) * n);
+    }
+    if (launch_convert(ct, nullptr, st) != cudaSuccess) return LQR_ERR_CUDA;
+    ++launches;
+  }
+  prof_mark(h, LQR_PHASE_REFINE, st);
+  if (!summary_only && sp.rbase >= 0) {
+    double* base = reinterpret_cast<double*>(h->ws);
+    const RefineLayout rl = refine_layout(sp.rbase, n, m, T);
+    double* acc = base + rl.acc;
+    int* skip = reinterpret_cast<int*>(base + rl.skip);
+    if (cudaMemsetAsync(acc, 0, sizeof(double) * kResidAccDoubles, st) != cudaSuccess) return LQR_ERR_CUDA;
+    if (cudaMemsetAsync(skip, 0, 4 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
+    const ProbDesc main = make_desc(h, p, s, sp, (int)o->form);
+    // the correction problem: the FP32 matrices, FP32 copies of the residual vectors
+    lqr_problem cp = p32;
+    cp.q = f + ocq; cp.r = f + ocr; cp.c = f + occ; cp.x0 = f + ocx0;
+    lqr_solution cs;
+    cs.K = s32.K; cs.k = f + odk; cs.x = f + odx; cs.u = f + odu; cs.lam = f + odl;
+    cs.P = want_P ? s32.P : nullptr;
+    cs.p = want_P ? (void*)(f + odp) : nullptr;
+    ProbTable ctab;
+    memset(&ctab, 0, sizeof(ctab));
+    ctab.single = make_desc(h, &cp, &cs, sp, (int)o->form);
+    ctab.single.skip = skip;
+    ctab.nprob = 1;
+    for (int it = 0; it < o->max_refine; ++it) {
+      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st) !=
+          cudaSuccess)
+        return LQR_ERR_CUDA;
+      if (launch_residual_finalize(main, acc, o->tol, skip, 0, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
+      ConvTable<double, float> ct;
+      ct.count = 0;
+      ct.add(base + rl.cq, (void*)cp.q, (size_t)(T + 1) * n);
+      ct.add(base + rl.cr, (void*)cp.r, (size_t)T * m);
+      ct.add(base + rl.cc, (void*)cp.c, (size_t)T * n);
+      ct.add(base + rl.cx0, (void*)cp.x0, (size_t)n);
+      if (launch_convert(ct, skip, st) != cudaSuccess) return LQR_ERR_CUDA;
+      launches += 3;
+      rs = enqueue_pipeline(h, ctab, sp, &o32, true, true, want_P ? 1 : 0, false, false, st, &launches);
+      if (rs != LQR_OK) return rs;
+      if (launch_refine_update_f32(main, f + odk, f + odx, f + odu, f + odl, want_P ? f + odp : nullptr, skip, st) !=
+          cudaSuccess)
+        return LQR_ERR_CUDA;
+      ++launches;
+    }
+    if (launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    if (launch_residual_finalize(main, acc, o->tol, nullptr, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
+        cudaSuccess)
+      return LQR_ERR_CUDA;
+    launches += 2;
+    h->last_resid = 1;
+  } else {
+    h->last_resid = 0;
+  }
+  prof_mark(h, LQR_NUM_PHASES, st);
+  if (h->prof_on && h->prof_count < lqr_handle::kMaxProfiled) ++h->prof_count;
+  h->last_K = sp.K;
+  h->last_launches = launches;
+  if (sp_out) *sp_out = sp;
+  return LQR_OK;
+}
+
+
 // The launch sequence of one solve. `summary_only` stops after step A1.
 lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const lqr_solution* s,
                      cudaStream_t st, bool summary_only, SolvePlan* sp_out) {
+  if (o->prec == LQR_MIXED_FP32) return run_solve_mixed32(h, p, o, s, st, summary_only, sp_out);
   SolvePlan sp;
   lqr_status rs = plan_solve(h, p, o, &sp);
   if (rs != LQR_OK) return rs;
@@ -586,6 +730,7 @@ AdjLayout adj_layout(size_t base, int n, int m, int T, size_t es) {
 
 lqr_status validate_backward(const lqr_problem* p, const lqr_opts* o, const lqr_solution* s, const lqr_problem* g) {
   if (!g) return LQR_ERR_INVALID_ARG;
+  if (o && o->prec == LQR_MIXED_FP32) return LQR_ERR_UNSUPPORTED;
   if (!s || !s->x || !s->u || !s->lam) return LQR_ERR_INVALID_ARG;
   lqr_solution none;
   memset(&none, 0, sizeof(none));
@@ -689,6 +834,7 @@ lqr_status lqr_solve_batched(lqr_handle* h, int nprob, const lqr_problem* probs,
                              const lqr_solution* sols, int* segments, void* stream) {
   if (!h || nprob < 1 || !probs || !o || !sols) return LQR_ERR_INVALID_ARG;
   for (int i = 0; i < nprob; ++i) {
+    if (o->prec == LQR_MIXED_FP32) return LQR_ERR_UNSUPPORTED;
     lqr_status v = validate(&probs[i], o, &sols[i]);
     if (v != LQR_OK) return v;
   }
@@ -766,6 +912,7 @@ lqr_status lqr_destroy(lqr_handle* h) {
   if (h->ev_created)
     for (int i = 0; i < lqr_handle::kMaxProfiled; ++i)
       for (int k = 0; k <= lqr_handle::kPhases; ++k) cudaEventDestroy(h->ev[i][k]);
+  if (h->f32) cudaFree(h->f32);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);

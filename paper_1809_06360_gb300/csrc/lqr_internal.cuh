@@ -220,6 +220,28 @@ cudaError_t launch_seg_sweep_f32(const ProbTable& tab, int nunits, int phase, in
                                  long long smem_budget, int store_P, cudaStream_t st);
 long long fast_sweep_smem_bytes(int n, int m);
 
+// Element-type conversion of up to kMaxConv arrays in one launch (skip: when
+// non-null and set, nothing is done).
+constexpr int kMaxConv = 16;
+template <typename S, typename D>
+struct ConvTable {
+  const S* src[kMaxConv];
+  D* dst[kMaxConv];
+  size_t n[kMaxConv];
+  int count;
+  void add(const void* s, void* d, size_t cnt) {
+    if (!s || !d || cnt == 0) return;
+    src[count] = static_cast<const S*>(s);
+    dst[count] = static_cast<D*>(d);
+    n[count] = cnt;
+    ++count;
+  }
+};
+template <typename S, typename D>
+cudaError_t launch_convert(const ConvTable<S, D>& tab, const int* skip, cudaStream_t st);
+cudaError_t launch_refine_update_f32(const ProbDesc& pd, const float* dk, const float* dx, const float* du,
+                                     const float* dl, const float* dp, const int* skip, cudaStream_t st);
+
 // Dual link solve of one problem. link_fp32 selects FP32 arithmetic; method
 // is an lqr_link value (the scan needs link_fp32). *nlaunch = kernels launched.
 cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st,

@@ -15,6 +15,7 @@
 // launch produces eta, rel and the objective.
 #include <cuda_runtime.h>
 
+#include "kkt_stage.cuh"
 #include "lqr_internal.cuh"
 
 namespace lqr {
@@ -48,7 +49,13 @@ __device__ __forceinline__ double na_warp_sum(double v) {
   return v;
 }
 
-template <typename TS>
+static_assert(kBlock == kKktBlock, "the stage block of kkt_stage.cuh assumes kKktBlock threads");
+
+// NC > 0: the stage block of kkt_stage.cuh (the arithmetic of the refinement
+// residual pass, so both report the same numbers); NC = 0: n or m beyond its
+// register plan, the per-stage loop below (the same arithmetic as the
+// generic residual kernel of the refinement step).
+template <int NC, typename TS>
 __global__ void __launch_bounds__(kBlock) kkt_residual_noalloc_kernel(NoallocArgs a, double* scratch, double* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[5][kBlock / 32];
@@ -79,107 +86,116 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_noalloc_kernel(NoallocArg
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double rmax = 0.0, kmax = 0.0, wmax = 0.0, bmax = 0.0;
 
+  KktMax mx;
+  KktData<TS> g;
+  g.x = gx; g.u = gu; g.lam = gl; g.A = gA; g.B = gB; g.c = gc; g.Q = gQ; g.R = gR; g.S = gS; g.q = gq; g.r = gr;
+  g.n = n; g.m = m;
+
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    const TS* At = gA + nn * t;
-    const TS* Bt = gB + nm * t;
-    const TS* Qt = gQ + nn * t;
-    const TS* Rt = gR + mm * t;
-    const TS* St = gS ? gS + nm * t : nullptr;
     double cost = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      xt[i] = (double)gx[(size_t)n * t + i];
-      xn[i] = (double)gx[(size_t)n * (t + 1) + i];
-      lt[i] = (double)gl[(size_t)n * t + i];
-      ln[i] = (double)gl[(size_t)n * (t + 1) + i];
-      rxv[i] = (double)gq[(size_t)n * t + i] + lt[i];
-      rdv[i] = xn[i] - (double)gc[(size_t)n * t + i];
-    }
-    for (int b = threadIdx.x; b < m; b += blockDim.x) {
-      ut[b] = (double)gu[(size_t)m * t + b];
-      ruv[b] = (double)gr[(size_t)m * t + b];
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      double s = 0.0, absA = 0.0, absS = 0.0, absQ = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const double v = (double)At[(size_t)i * n + j];
-        s = fma(-v, ln[i], s);
-        s = fma(0.5 * (double)Qt[(size_t)i * n + j], xt[i], s);
-        absA += fabs(v);
+    if constexpr (NC > 0) {
+      cost = kkt_stage<NC, true>(g, t, reinterpret_cast<double*>(smem), mx, nullptr, nullptr, nullptr);
+    } else {
+      const TS* At = gA + nn * t;
+      const TS* Bt = gB + nm * t;
+      const TS* Qt = gQ + nn * t;
+      const TS* Rt = gR + mm * t;
+      const TS* St = gS ? gS + nm * t : nullptr;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        xt[i] = (double)gx[(size_t)n * t + i];
+        xn[i] = (double)gx[(size_t)n * (t + 1) + i];
+        lt[i] = (double)gl[(size_t)n * t + i];
+        ln[i] = (double)gl[(size_t)n * (t + 1) + i];
+        rxv[i] = (double)gq[(size_t)n * t + i] + lt[i];
+        rdv[i] = xn[i] - (double)gc[(size_t)n * t + i];
       }
-      if (St)
-        for (int b = 0; b < m; ++b) {
-          const double v = (double)St[(size_t)b * n + j];
-          s = fma(v, ut[b], s);
-          absS += fabs(v);
+      for (int b = threadIdx.x; b < m; b += blockDim.x) {
+        ut[b] = (double)gu[(size_t)m * t + b];
+        ruv[b] = (double)gr[(size_t)m * t + b];
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double s = 0.0, absA = 0.0, absS = 0.0, absQ = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double v = (double)At[(size_t)i * n + j];
+          s = fma(-v, ln[i], s);
+          s = fma(0.5 * (double)Qt[(size_t)i * n + j], xt[i], s);
+          absA += fabs(v);
         }
-      for (int k = 0; k < n; ++k)
-        absQ += fabs(0.5 * ((double)Qt[(size_t)j * n + k] + (double)Qt[(size_t)k * n + j]));
-      rxv[j] += s;
-      kmax = fmax(kmax, absQ + absS + 1.0 + absA);
-    }
-    for (int b = threadIdx.x; b < m; b += blockDim.x) {
-      double s = 0.0, absB = 0.0, absR = 0.0, absSr = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const double v = (double)Bt[(size_t)i * m + b];
-        s = fma(-v, ln[i], s);
-        absB += fabs(v);
+        if (St)
+          for (int b = 0; b < m; ++b) {
+            const double v = (double)St[(size_t)b * n + j];
+            s = fma(v, ut[b], s);
+            absS += fabs(v);
+          }
+        for (int k = 0; k < n; ++k)
+          absQ += fabs(0.5 * ((double)Qt[(size_t)j * n + k] + (double)Qt[(size_t)k * n + j]));
+        rxv[j] += s;
+        kmax = fmax(kmax, absQ + absS + 1.0 + absA);
       }
-      for (int c2 = 0; c2 < m; ++c2) {
-        s = fma(0.5 * (double)Rt[(size_t)c2 * m + b], ut[c2], s);
-        absR += fabs(0.5 * ((double)Rt[(size_t)b * m + c2] + (double)Rt[(size_t)c2 * m + b]));
+      for (int b = threadIdx.x; b < m; b += blockDim.x) {
+        double s = 0.0, absB = 0.0, absR = 0.0, absSr = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double v = (double)Bt[(size_t)i * m + b];
+          s = fma(-v, ln[i], s);
+          absB += fabs(v);
+        }
+        for (int c2 = 0; c2 < m; ++c2) {
+          s = fma(0.5 * (double)Rt[(size_t)c2 * m + b], ut[c2], s);
+          absR += fabs(0.5 * ((double)Rt[(size_t)b * m + c2] + (double)Rt[(size_t)c2 * m + b]));
+        }
+        if (St)
+          for (int k = 0; k < n; ++k) absSr += fabs((double)St[(size_t)b * n + k]);
+        ruv[b] += s;
+        kmax = fmax(kmax, absSr + absR + absB);
       }
-      if (St)
-        for (int k = 0; k < n; ++k) absSr += fabs((double)St[(size_t)b * n + k]);
-      ruv[b] += s;
-      kmax = fmax(kmax, absSr + absR + absB);
-    }
-    __syncthreads();
-    for (int i = warp; i < n; i += nw) {
-      double qx = 0.0, ax = 0.0, absr = 0.0;
-      for (int k = lane; k < n; k += 32) {
-        const double v = (double)At[(size_t)i * n + k];
-        ax = fma(v, xt[k], ax);
-        qx = fma((double)Qt[(size_t)i * n + k], xt[k], qx);
-        absr += fabs(v);
+      __syncthreads();
+      for (int i = warp; i < n; i += nw) {
+        double qx = 0.0, ax = 0.0, absr = 0.0;
+        for (int k = lane; k < n; k += 32) {
+          const double v = (double)At[(size_t)i * n + k];
+          ax = fma(v, xt[k], ax);
+          qx = fma((double)Qt[(size_t)i * n + k], xt[k], qx);
+          absr += fabs(v);
+        }
+        for (int b = lane; b < m; b += 32) {
+          const double v = (double)Bt[(size_t)i * m + b];
+          ax = fma(v, ut[b], ax);
+          absr += fabs(v);
+        }
+        qx = na_warp_sum(qx);
+        ax = na_warp_sum(ax);
+        absr = na_warp_sum(absr);
+        if (lane == 0) {
+          rxv[i] += 0.5 * qx;
+          rdv[i] -= ax;
+          kmax = fmax(kmax, 1.0 + absr);
+          cost += xt[i] * (0.5 * qx + (double)gq[(size_t)n * t + i]);
+        }
       }
-      for (int b = lane; b < m; b += 32) {
-        const double v = (double)Bt[(size_t)i * m + b];
-        ax = fma(v, ut[b], ax);
-        absr += fabs(v);
+      for (int b = warp; b < m; b += nw) {
+        double sx = 0.0, ru = 0.0;
+        if (St)
+          for (int k = lane; k < n; k += 32) sx = fma((double)St[(size_t)b * n + k], xt[k], sx);
+        for (int c2 = lane; c2 < m; c2 += 32) ru = fma((double)Rt[(size_t)b * m + c2], ut[c2], ru);
+        sx = na_warp_sum(sx);
+        ru = na_warp_sum(ru);
+        if (lane == 0) {
+          ruv[b] += sx + 0.5 * ru;
+          cost += ut[b] * (sx + 0.5 * ru + (double)gr[(size_t)m * t + b]);
+        }
       }
-      qx = na_warp_sum(qx);
-      ax = na_warp_sum(ax);
-      absr = na_warp_sum(absr);
-      if (lane == 0) {
-        rxv[i] += 0.5 * qx;
-        rdv[i] -= ax;
-        kmax = fmax(kmax, 1.0 + absr);
-        cost += xt[i] * (0.5 * qx + (double)gq[(size_t)n * t + i]);
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        rmax = fmax(rmax, fmax(fabs(rxv[i]), fabs(rdv[i])));
+        wmax = fmax(wmax, fmax(fabs(xt[i]), fabs(lt[i])));
+        bmax = fmax(bmax, fmax(fabs((double)gq[(size_t)n * t + i]), fabs((double)gc[(size_t)n * t + i])));
       }
-    }
-    for (int b = warp; b < m; b += nw) {
-      double sx = 0.0, ru = 0.0;
-      if (St)
-        for (int k = lane; k < n; k += 32) sx = fma((double)St[(size_t)b * n + k], xt[k], sx);
-      for (int c2 = lane; c2 < m; c2 += 32) ru = fma((double)Rt[(size_t)b * m + c2], ut[c2], ru);
-      sx = na_warp_sum(sx);
-      ru = na_warp_sum(ru);
-      if (lane == 0) {
-        ruv[b] += sx + 0.5 * ru;
-        cost += ut[b] * (sx + 0.5 * ru + (double)gr[(size_t)m * t + b]);
+      for (int b = threadIdx.x; b < m; b += blockDim.x) {
+        rmax = fmax(rmax, fabs(ruv[b]));
+        wmax = fmax(wmax, fabs(ut[b]));
+        bmax = fmax(bmax, fabs((double)gr[(size_t)m * t + b]));
       }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      rmax = fmax(rmax, fmax(fabs(rxv[i]), fabs(rdv[i])));
-      wmax = fmax(wmax, fmax(fabs(xt[i]), fabs(lt[i])));
-      bmax = fmax(bmax, fmax(fabs((double)gq[(size_t)n * t + i]), fabs((double)gc[(size_t)n * t + i])));
-    }
-    for (int b = threadIdx.x; b < m; b += blockDim.x) {
-      rmax = fmax(rmax, fabs(ruv[b]));
-      wmax = fmax(wmax, fabs(ut[b]));
-      bmax = fmax(bmax, fabs((double)gr[(size_t)m * t + b]));
     }
     // this stage's objective partial, summed later in stage order
     cost = na_warp_sum(cost);
@@ -221,6 +237,10 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_noalloc_kernel(NoallocArg
       scratch[T] = s;
     }
   }
+  rmax = fmax(rmax, mx.r);
+  kmax = fmax(kmax, mx.k);
+  wmax = fmax(wmax, mx.w);
+  bmax = fmax(bmax, mx.b);
   rmax = na_warp_max(rmax);
   kmax = na_warp_max(kmax);
   wmax = na_warp_max(wmax);
@@ -305,10 +325,22 @@ extern "C" lqr_status lqr_kkt_residual_noalloc(const lqr_problem* p, const lqr_s
   a.x = s->x; a.u = s->u; a.lam = s->lam;
   a.n = p->n; a.m = p->m; a.T = p->T;
   const int grid = p->T < 4 * 152 ? p->T : 4 * 152;
-  const size_t bytes = sizeof(double) * (6 * (size_t)p->n + 3 * (size_t)p->m);
-  if (prec == LQR_FP32)
-    kkt_residual_noalloc_kernel<float><<<grid, kBlock, bytes, st>>>(a, ds.ptr, out);
-  else
-    kkt_residual_noalloc_kernel<double><<<grid, kBlock, bytes, st>>>(a, ds.ptr, out);
+  const int nc = kkt_stage_cols(p->n, p->m);
+  size_t bytes = sizeof(double) * (6 * (size_t)p->n + 3 * (size_t)p->m);
+  if (nc > 0) bytes = sizeof(double) * kkt_stage_smem_doubles(p->n, p->m);  // <= 45056 B: no opt-in needed
+#define LQR_NA_LAUNCH(NC)                                                  \
+  do {                                                                     \
+    if (prec == LQR_FP32)                                                  \
+      kkt_residual_noalloc_kernel<NC, float><<<grid, kBlock, bytes, st>>>(a, ds.ptr, out);  \
+    else                                                                   \
+      kkt_residual_noalloc_kernel<NC, double><<<grid, kBlock, bytes, st>>>(a, ds.ptr, out); \
+  } while (0)
+  switch (nc) {
+    case 1: LQR_NA_LAUNCH(1); break;
+    case 2: LQR_NA_LAUNCH(2); break;
+    case 4: LQR_NA_LAUNCH(4); break;
+    default: LQR_NA_LAUNCH(0); break;
+  }
+#undef LQR_NA_LAUNCH
   return cudaGetLastError() == cudaSuccess ? LQR_OK : LQR_ERR_CUDA;
 }

@@ -15,6 +15,7 @@
 // with |KKT|_inf the largest absolute row sum.
 #include <cuda_runtime.h>
 
+#include "kkt_stage.cuh"
 #include "lqr_internal.cuh"
 
 namespace lqr {
@@ -45,9 +46,11 @@ enum ResidSlot { RS_RNORM = 0, RS_KNORM, RS_WNORM, RS_BNORM, RS_COST, RS_COUNT }
 
 // One CTA per stage (grid-stride). Stage t < T, plus the terminal / initial
 // rows handled by the CTA that owns t = T-1 / t = 0.
+// want_knorm: also the |KKT| row sums of the backward error (the final pass);
+// the refinement passes only need |r| and |b|.
 template <typename TS>
 __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, double* acc, double* cq, double* cr,
-                                                              double* cc, double* cx0, const int* skip) {
+                                                              double* cc, double* cx0, const int* skip, int want_knorm) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (skip && *(volatile const int*)skip) return;
   if (*(volatile int*)pd.status != 0) return;
@@ -98,41 +101,44 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, doubl
     // columns j < n: -A'lambda_{t+1}, Q'x/2 (half of the symmetrised product), S'u; row-sum pieces
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       double s = 0.0, absA = 0.0, absS = 0.0;
+#pragma unroll 8
       for (int i = 0; i < n; ++i) {
         const double a = (double)At[(size_t)i * n + j];
         s = fma(-a, ln[i], s);
         s = fma(0.5 * (double)Qt[(size_t)i * n + j], xt[i], s);
-        absA += fabs(a);
+        if (want_knorm) absA += fabs(a);
       }
       if (St)
         for (int a = 0; a < m; ++a) {
           const double v = (double)St[(size_t)a * n + j];
           s = fma(v, ut[a], s);
-          absS += fabs(v);
+          if (want_knorm) absS += fabs(v);
         }
       rxv[j] += s;
-      // |Q_sym| row sum of row j
-      double absQ = 0.0;
-      for (int k = 0; k < n; ++k)
-        absQ += fabs(0.5 * ((double)Qt[(size_t)j * n + k] + (double)Qt[(size_t)k * n + j]));
-      kmax = fmax(kmax, absQ + absS + 1.0 + absA);
+      if (want_knorm) {  // |Q_sym| row sum of row j
+        double absQ = 0.0;
+        for (int k = 0; k < n; ++k)
+          absQ += fabs(0.5 * ((double)Qt[(size_t)j * n + k] + (double)Qt[(size_t)k * n + j]));
+        kmax = fmax(kmax, absQ + absS + 1.0 + absA);
+      }
     }
     // columns a < m: -B'lambda_{t+1}, R'u/2
     for (int a = threadIdx.x; a < m; a += blockDim.x) {
       double s = 0.0, absB = 0.0, absR = 0.0, absSr = 0.0;
+#pragma unroll 8
       for (int i = 0; i < n; ++i) {
         const double b = (double)Bt[(size_t)i * m + a];
         s = fma(-b, ln[i], s);
-        absB += fabs(b);
+        if (want_knorm) absB += fabs(b);
       }
       for (int b = 0; b < m; ++b) {
         s = fma(0.5 * (double)Rt[(size_t)b * m + a], ut[b], s);
-        absR += fabs(0.5 * ((double)Rt[(size_t)a * m + b] + (double)Rt[(size_t)b * m + a]));
+        if (want_knorm) absR += fabs(0.5 * ((double)Rt[(size_t)a * m + b] + (double)Rt[(size_t)b * m + a]));
       }
-      if (St)
+      if (St && want_knorm)
         for (int k = 0; k < n; ++k) absSr += fabs((double)St[(size_t)a * n + k]);
       ruv[a] += s;
-      kmax = fmax(kmax, absSr + absR + absB);
+      if (want_knorm) kmax = fmax(kmax, absSr + absR + absB);
     }
     __syncthreads();
     // rows i < n (warp per row): Q x/2, -A x - B u ; dynamics-row sums ; stage cost 1/2 x'Qx + q'x
@@ -142,12 +148,12 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, doubl
         const double a = (double)At[(size_t)i * n + k];
         ax = fma(a, xt[k], ax);
         qx = fma((double)Qt[(size_t)i * n + k], xt[k], qx);
-        absr += fabs(a);
+        if (want_knorm) absr += fabs(a);
       }
       for (int b = lane; b < m; b += 32) {
         const double v = (double)Bt[(size_t)i * m + b];
         ax = fma(v, ut[b], ax);
-        absr += fabs(v);
+        if (want_knorm) absr += fabs(v);
       }
       qx = warp_sum(qx);
       ax = warp_sum(ax);
@@ -241,6 +247,83 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, doubl
   }
 }
 
+// Streaming form of the same residual (the stage block of kkt_stage.cuh);
+// grid-stride over the stages like kkt_residual_kernel.
+template <int NC, bool KN, typename TS>
+__global__ void __launch_bounds__(kKktBlock, 2)
+    kkt_residual_stream_kernel(ProbDesc pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
+                               const int* skip, int use_stash) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (skip && *(volatile const int*)skip) return;
+  if (*(volatile int*)pd.status != 0) return;
+  const int n = pd.n, T = pd.T;
+  KktData<TS> g;
+  g.x = static_cast<const TS*>(pd.x);
+  g.u = static_cast<const TS*>(pd.u);
+  g.lam = static_cast<const TS*>(pd.lam);
+  g.A = static_cast<const TS*>(pd.A);
+  g.B = static_cast<const TS*>(pd.B);
+  g.c = static_cast<const TS*>(pd.c);
+  g.Q = static_cast<const TS*>(pd.Q);
+  g.R = static_cast<const TS*>(pd.R);
+  g.S = static_cast<const TS*>(pd.S);
+  g.q = static_cast<const TS*>(pd.q);
+  g.r = static_cast<const TS*>(pd.r);
+  g.n = pd.n;
+  g.m = pd.m;
+  const TS* gx0 = static_cast<const TS*>(pd.x0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* sm = reinterpret_cast<double*>(smem);
+  double* stash = use_stash ? sm + kkt_stage_smem_doubles(pd.n, pd.m) : nullptr;
+  KktMax mx;
+  double cost = 0.0;
+  for (int t = blockIdx.x; t < T; t += gridDim.x) cost += kkt_stage<NC, KN>(g, t, sm, mx, cq, cr, cc, stash);
+  // terminal row (Q_T x_T + q_T + lambda_T) and the initial row (x_0 - x0)
+  if (blockIdx.x == 0) {
+    const TS* QT = g.Q + (size_t)n * n * T;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double s = (double)g.q[(size_t)n * T + i] + (double)g.lam[(size_t)n * T + i];
+      double absQ = 0.0, qx = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double qs = 0.5 * ((double)QT[(size_t)i * n + k] + (double)QT[(size_t)k * n + i]);
+        s = fma(qs, (double)g.x[(size_t)n * T + k], s);
+        qx = fma((double)QT[(size_t)i * n + k], (double)g.x[(size_t)n * T + k], qx);
+        absQ += fabs(qs);
+      }
+      const double xT = (double)g.x[(size_t)n * T + i];
+      cost += xT * (0.5 * qx + (double)g.q[(size_t)n * T + i]);
+      const double r0 = (double)g.x[i] - (double)gx0[i];
+      mx.r = fmax(mx.r, fmax(fabs(s), fabs(r0)));
+      if (KN) mx.k = fmax(mx.k, absQ + 1.0);
+      mx.w = fmax(mx.w, fmax(fabs(xT), fabs((double)g.lam[(size_t)n * T + i])));
+      mx.b = fmax(mx.b, fmax(fabs((double)g.q[(size_t)n * T + i]), fabs((double)gx0[i])));
+      if (cq) {
+        cq[(size_t)n * T + i] = -s;
+        cx0[i] = r0;
+      }
+    }
+  }
+  __shared__ double red[5][kKktWarps];
+  const double rm = warp_max(mx.r), km = warp_max(mx.k), wm = warp_max(mx.w), bm = warp_max(mx.b);
+  cost = warp_sum(cost);
+  if (lane == 0) {
+    red[0][warp] = rm; red[1][warp] = km; red[2][warp] = wm; red[3][warp] = bm; red[4][warp] = cost;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int w = 0; w < kKktWarps; ++w) {
+      for (int k = 0; k < 4; ++k) a[k] = fmax(a[k], red[k][w]);
+      a[4] += red[4][w];
+    }
+    atomic_max_nonneg(acc + RS_RNORM, a[0]);
+    atomic_max_nonneg(acc + RS_KNORM, a[1]);
+    atomic_max_nonneg(acc + RS_WNORM, a[2]);
+    atomic_max_nonneg(acc + RS_BNORM, a[3]);
+    acc[RS_COUNT + blockIdx.x] = a[4];
+  }
+}
+
 // Turns the accumulators into eta, rel and the cost; decides convergence.
 // report: [0] cost, [1] eta, [2] rel, [3] refinement iterations applied.
 __global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, double tol, int* skip,
@@ -292,8 +375,34 @@ int residual_grid(int T) { return T < 4 * 152 ? T : 4 * 152; }
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
                                 const int* skip, cudaStream_t st) {
+  // the refinement passes (correction vectors requested) skip the |KKT| row sums
+  const int want_knorm = (cq == nullptr) ? 1 : 0;
+  const int nc = kkt_stage_cols(pd.n, pd.m);
+  if (nc > 0) {
+    const size_t base = sizeof(double) * kkt_stage_smem_doubles(pd.n, pd.m);  // <= 45056 B at n = m = 128
+    // the |KKT| pass stages Q_t and R_t in shared memory for their symmetric row sums
+    const size_t bytes = want_knorm ? base + sizeof(double) * kkt_stash_doubles(pd.n, pd.m) : base;
+    const int g = residual_grid(pd.T);
+#define LQR_RES_LAUNCH(NC, KN)                                                                               \
+  do {                                                                                                       \
+    if (bytes > 48 * 1024 && cudaFuncSetAttribute(kkt_residual_stream_kernel<NC, KN, TS>,                     \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                                  (int)bytes) != cudaSuccess)                                \
+      return cudaGetLastError();                                                                             \
+    kkt_residual_stream_kernel<NC, KN, TS><<<g, kKktBlock, bytes, st>>>(pd, acc, cq, cr, cc, cx0, skip, KN); \
+  } while (0)
+    if (nc == 1) {
+      if (want_knorm) LQR_RES_LAUNCH(1, true); else LQR_RES_LAUNCH(1, false);
+    } else if (nc == 2) {
+      if (want_knorm) LQR_RES_LAUNCH(2, true); else LQR_RES_LAUNCH(2, false);
+    } else {
+      if (want_knorm) LQR_RES_LAUNCH(4, true); else LQR_RES_LAUNCH(4, false);
+    }
+#undef LQR_RES_LAUNCH
+    return cudaGetLastError();
+  }
   const size_t bytes = sizeof(double) * (6 * (size_t)pd.n + 3 * (size_t)pd.m);
-  kkt_residual_kernel<TS><<<residual_grid(pd.T), kBlock, bytes, st>>>(pd, acc, cq, cr, cc, cx0, skip);
+  kkt_residual_kernel<TS><<<residual_grid(pd.T), kBlock, bytes, st>>>(pd, acc, cq, cr, cc, cx0, skip, want_knorm);
   return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "LQR_OK", 1: "LQR_ERR_INVALID_ARG", 2: "LQR_ERR_NOT_PD", 3: "
                 4: "LQR_ERR_NONFINITE", 5: "LQR_ERR_NO_CONVERGENCE", 6: "LQR_ERR_TIMEOUT", 7: "LQR_ERR_CUDA",
                 8: "LQR_ERR_OOM", 9: "LQR_ERR_UNSUPPORTED", 10: "LQR_ERR_CAPACITY"}
 NOALLOC_MAX_STAGES = 65536
-PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tf32": 2, "mixed_bf16": 3}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2, "mixed_tf32": 2, "mixed_bf16": 3, "mixed_fp32": 4}
 FORM = {"multiplier": 0, "constrained": 1}
 LINK = {"auto": 0, "chain": 1, "scan": 2}
 

@@ -103,3 +103,45 @@ def test_mixed_host_entry_point(solver):
     rep = solver.report()
     assert rep["status"] == 0
     assert oracle.rel_err(out["x"], ref["x"]) < 1e-9
+
+
+@pytest.mark.parametrize("K", [64, 152])
+def test_mixed_fp32_config1(solver, K):
+    """LQR_MIXED_FP32: FP64 data; the solve and each correction run the FP32
+    path (FP32 sweeps, FP32 M_uu inverse, FP32 link scan) on an FP32 copy of the
+    data; the FP64 KKT residual drives refinement to |r|/|b| <= 1e-10. x, u and
+    lambda reach the oracle at 1e-9; K keeps FP32 accuracy (1e-4), k stays
+    consistent with the refined trajectory."""
+    prob = workloads.config1()
+    ref = oracle.riccati(prob)
+    out = host(solver.solve(to_dev(prob), num_segments=K, prec="mixed_fp32", max_refine=6, tol=1e-10))
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    errs = {k: oracle.rel_err(out[k], ref[k]) for k in ("x", "u", "lam", "k", "K")}
+    print("mixed_fp32 K=%d errors %s iters %d rel %.2e eta %.2e" % (K, errs, rep["refine_iters"], rep["kkt_rel"],
+                                                                   rep["kkt_residual"]))
+    for k in ("x", "u", "lam"):
+        assert errs[k] < 1e-9, errs
+    assert errs["K"] < 1e-4 and errs["k"] < 1e-3
+    assert rep["kkt_rel"] <= 1e-10
+    assert rep["refine_iters"] <= 4
+    assert abs(rep["cost"] - ref["cost"]) <= 1e-10 * abs(ref["cost"])
+
+
+def test_mixed_fp32_small_and_odd_shapes(solver):
+    for (n, m, T, K) in ((12, 4, 128, 8), (30, 10, 600, 37), (5, 2, 1, 1)):
+        prob = workloads.make_problem(n, m, T, seed=900 + n, rho_max=1.02)
+        ref = oracle.riccati(prob)
+        out = host(solver.solve(to_dev(prob), num_segments=K, prec="mixed_fp32", max_refine=6, tol=1e-11))
+        rep = solver.report()
+        assert rep["status"] == 0, (n, rep)
+        for k in ("x", "u", "lam"):
+            assert oracle.rel_err(out[k], ref[k]) < 1e-9, (n, k, oracle.rel_err(out[k], ref[k]))
+
+
+def test_mixed_fp32_unsupported_forms(solver):
+    from paper_1809_06360_gb300 import lqr
+    prob = workloads.config0()
+    with pytest.raises(lqr.LqrError) as e:
+        solver.solve(to_dev(prob), num_segments=8, prec="mixed_fp32", form="constrained")
+    assert e.value.status == 9
