@@ -40,7 +40,7 @@ PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 80.5
 
 # bytes per launch (read + write) measured by ncu on the default FP32 workload;
 # an entry is removed whenever its kernel changes
-NCU_TRAFFIC: dict = {"seg_sweep_f32_kernel": (224.31e6 + 248.69e6) / 2}  # A1 and A4 launches, averaged
+NCU_TRAFFIC: dict = {}  # filled from a capture of the kernel as it now stands
 
 
 def link_flops(n: int, K: int) -> float:
@@ -306,9 +306,11 @@ def main():
     ph = {k: v / nsolve for k, v in phase_ms.items()}
     fp64_pipe = args.prec == "fp64"
     alu_peak = PEAK_FP64_TFLOPS if fp64_pipe else PEAK_FP32_TFLOPS
-    es = 4 if args.prec == "fp32" else 8
     hbm = measured_peaks().get("hbm_gbs", 6780.4)
-    fast = args.prec == "fp32" and args.form == "multiplier"
+    # the FP32 fast path (FP32 sweeps, link scan and rollout) also runs every
+    # solve of the mixed FP32 mode, on its FP32 copy of the data
+    fast = args.prec in ("fp32", "mixed_fp32") and args.form == "multiplier"
+    es = 4 if fast else 8
     sweep_k = "seg_sweep_f32_kernel" if fast else "seg_sweep_kernel"
     if fast:
         link = {"kernel": "link_scan_kernel levels + feedback pass + link states (A3, FP32 scan)", "bound": "alu",
@@ -322,7 +324,8 @@ def main():
         "policy": {"kernel": sweep_k + " phase 1 (A4)", "bound": "alu", "unit": "TFLOP/s",
                    "work": sweep_flops(n, m, T, K, "policy"), "peak": alu_peak},
         "link": link,
-        "rollout": {"kernel": "rollout_stream_kernel + finalize (A5/A6)", "bound": "hbm", "unit": "GB/s",
+        "rollout": {"kernel": ("rollout_f32_kernel" if fast else "rollout_stream_kernel") + " + finalize (A5/A6)",
+                    "bound": "hbm", "unit": "GB/s",
                     "work": rollout_bytes(n, m, T, es), "peak": hbm},
     }
     for k, d in phases.items():

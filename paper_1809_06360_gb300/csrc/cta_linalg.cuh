@@ -1334,6 +1334,60 @@ __device__ inline void grp_spd_inverse(int d, float* G, int ld, int* flag, float
   bar();
 }
 
+// Inverse of the SPD m x m matrix (G + G')/2 (m <= 32, row stride ld) in
+// place by one warp: lane j holds column j in registers (rows and columns
+// beyond m are the identity), Gauss-Jordan elimination without pivoting, the
+// pivot column broadcast by shuffles; no shared-memory round trip or barrier
+// on the pivot chain. The pivot loop stays rolled (a fully unrolled 32-pivot
+// body is ~50 KB of straight-line code that one warp streams through the
+// instruction cache, measured 10x slower): blocks of four pivots, after
+// which the register column is rotated by four rows, so that pivot kb + u
+// always sits in register u. *flag = 1 on a pivot that is not positive and
+// finite. Only the calling warp takes part.
+__device__ inline void warp_spd_inverse32(int m, float* G, int ld, int* flag) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  float b[32];  // b[i] = row (kb + i) mod 32 of this lane's column at the start of block kb
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    b[i] = (i < m && lane < m) ? 0.5f * (G[i * ld + lane] + G[lane * ld + i]) : (i == lane ? 1.0f : 0.0f);
+  bool bad = false;
+#pragma unroll 1
+  for (int kb = 0; kb < 32; kb += U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = kb + u;
+      const float d = __shfl_sync(0xffffffffu, b[u], k);
+      bad |= !(d > 0.0f && isfinite(d));
+      const float r = recip_fast(d);
+      const bool piv = (lane == k);
+      // column k becomes -a_ik / d (pivot 1/d), row k a_kj / d, the rest a_ij - a_ik a_kj / d
+      const float f = piv ? r : b[u] * r;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (i == u) continue;
+        const float ci = __shfl_sync(0xffffffffu, b[i], k);
+        b[i] = fmaf(-ci, f, piv ? 0.0f : b[i]);
+      }
+      b[u] = f;
+    }
+    float t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) t[u] = b[u];
+#pragma unroll
+    for (int i = 0; i < 32 - U; ++i) b[i] = b[i + U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) b[32 - U + u] = t[u];
+  }
+  __syncwarp();  // every lane has read G before it is overwritten
+  if (lane < m)
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < m) G[i * ld + lane] = b[i];
+  if (bad && lane == 0) *flag = 1;
+  __syncwarp();
+}
+
 // named barrier over the first nthr threads of the block (id > 0)
 struct NamedBar {
   int id, nthr;

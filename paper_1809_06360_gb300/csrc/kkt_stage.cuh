@@ -103,32 +103,38 @@ struct KktLog2<1> {
   static constexpr int value = 0;
 };
 
-// One pass over the row-major R x C matrix M:
+// One pass over the row-major R x C matrix M (NCP = ceil(C / 32) register
+// columns per lane, NCP <= NC, so that no lane of a narrow matrix works on
+// padding):
 //   rowout[i] (+)= rscale sum_k M[i,k] vc[k]     (first: assign, else add)
 //   col.v[c]  +=  sum_i M[i,k] wr[i]             (wr pre-scaled by the caller)
 //   rowabs[i] (+)= sum_k |M[i,k]|,  colabs.v[c] += sum_i |M[i,k]|   (KN only)
 //   stash[i (C + 1) + k] = M[i,k]                                   (stash given)
-// Batches of RB rows (row i0 + r nw, r < RB) are loaded, then reduced together.
-template <int NC, bool KN, typename TS>
+// Batches of kKktRB rows (row i0 + r nw, r < kKktRB) are loaded, then reduced
+// together.
+constexpr int kKktRB = 4;
+
+template <int NCP, int NC, bool KN, typename TS>
 __device__ __forceinline__ void kkt_mat_pass(const TS* __restrict__ M, int R, int C, const double* vc,
                                              const double* wr, double rscale, double* rowout, bool first,
                                              KktCols<NC>& col, double* rowabs, KktCols<NC>& colabs, int warp,
-                                             int lane, double* stash = nullptr) {
-  constexpr int RB = NC == 1 ? 16 : (NC == 2 ? 8 : 4);
+                                             int lane, double* stash) {
+  static_assert(NCP <= NC, "pass columns beyond the register plan");
+  constexpr int RB = kKktRB;
   constexpr int kShift = 5 - KktLog2<RB>::value;  // lanes per row after the reduction: 1 << kShift
-  double vcl[NC];
+  double vcl[NCP];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
+  for (int c = 0; c < NCP; ++c) {
     const int k = lane + 32 * c;
     vcl[c] = k < C ? vc[k] : 0.0;
   }
   for (int i0 = warp; i0 < R; i0 += kKktWarps * RB) {
-    double v[RB][NC];
+    double v[RB][NCP];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const int i = i0 + r * kKktWarps;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
+      for (int c = 0; c < NCP; ++c) {
         const int k = lane + 32 * c;
         v[r][c] = (i < R && k < C) ? (double)__ldg(M + (size_t)i * C + k) : 0.0;
       }
@@ -141,7 +147,7 @@ __device__ __forceinline__ void kkt_mat_pass(const TS* __restrict__ M, int R, in
       d[r] = 0.0;
       a[r] = 0.0;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
+      for (int c = 0; c < NCP; ++c) {
         if (stash && i < R && lane + 32 * c < C) stash[(size_t)i * (C + 1) + lane + 32 * c] = v[r][c];
         d[r] = fma(v[r][c], vcl[c], d[r]);
         col.v[c] = fma(v[r][c], w, col.v[c]);
@@ -160,6 +166,22 @@ __device__ __forceinline__ void kkt_mat_pass(const TS* __restrict__ M, int R, in
       if (KN) rowabs[i] = first ? ar : rowabs[i] + ar;
     }
   }
+}
+
+// kkt_mat_pass with the narrowest column plan that covers C
+template <int NC, bool KN, typename TS>
+__device__ __forceinline__ void kkt_pass(const TS* __restrict__ M, int R, int C, const double* vc, const double* wr,
+                                         double rscale, double* rowout, bool first, KktCols<NC>& col,
+                                         double* rowabs, KktCols<NC>& colabs, int warp, int lane,
+                                         double* stash = nullptr) {
+  if (NC >= 4 && C > 64)
+    kkt_mat_pass<(NC >= 4 ? 4 : 1), NC, KN>(M, R, C, vc, wr, rscale, rowout, first, col, rowabs, colabs, warp, lane,
+                                            stash);
+  else if (NC >= 2 && C > 32)
+    kkt_mat_pass<(NC >= 2 ? 2 : 1), NC, KN>(M, R, C, vc, wr, rscale, rowout, first, col, rowabs, colabs, warp, lane,
+                                            stash);
+  else
+    kkt_mat_pass<1, NC, KN>(M, R, C, vc, wr, rscale, rowout, first, col, rowabs, colabs, warp, lane, stash);
 }
 
 // Row sums of |(M + M')/2| for a square d x d matrix with leading dimension
@@ -217,11 +239,11 @@ __device__ double kkt_stage(const KktData<TS>& g, int t, double* sm, KktMax& mx,
   KktCols<NC> cxs, cus, cxa, cua;
   cxs.zero(); cus.zero(); cxa.zero(); cua.zero();
   // A_t: rows A x, columns -A'lambda_{t+1}
-  kkt_mat_pass<NC, KN>(g.A + nn * t, n, n, xt, ln, 1.0, rowd, true, cxs, kd, cxa, warp, lane);
+  kkt_pass<NC, KN>(g.A + nn * t, n, n, xt, ln, 1.0, rowd, true, cxs, kd, cxa, warp, lane);
   // B_t: rows B u, columns -B'lambda_{t+1}
-  kkt_mat_pass<NC, KN>(g.B + nm * t, n, m, ut, ln, 1.0, rowd, false, cus, kd, cua, warp, lane);
+  kkt_pass<NC, KN>(g.B + nm * t, n, m, ut, ln, 1.0, rowd, false, cus, kd, cua, warp, lane);
   // Q_t: rows Q x / 2, columns Q'x / 2
-  kkt_mat_pass<NC, false>(g.Q + nn * t, n, n, xt, xh, 0.5, rowx, true, cxs, nullptr, cxa, warp, lane,
+  kkt_pass<NC, false>(g.Q + nn * t, n, n, xt, xh, 0.5, rowx, true, cxs, nullptr, cxa, warp, lane,
                           KN ? stash : nullptr);
   if (KN) {
     if (stash) {
@@ -233,7 +255,7 @@ __device__ double kkt_stage(const KktData<TS>& g, int t, double* sm, KktMax& mx,
     }
   }
   if (g.S) {  // S_t: rows S x, columns S'u
-    kkt_mat_pass<NC, KN>(g.S + nm * t, m, n, xt, ut, 1.0, rowu, true, cxs, ku, cxa, warp, lane);
+    kkt_pass<NC, KN>(g.S + nm * t, m, n, xt, ut, 1.0, rowu, true, cxs, ku, cxa, warp, lane);
   } else if (lane == 0) {  // the same writer as the R pass below
     for (int a = warp; a < m; a += kKktWarps) {
       rowu[a] = 0.0;
@@ -241,7 +263,7 @@ __device__ double kkt_stage(const KktData<TS>& g, int t, double* sm, KktMax& mx,
     }
   }
   // R_t: rows R u / 2, columns R'u / 2
-  kkt_mat_pass<NC, false>(g.R + mm * t, m, m, ut, uh, 0.5, rowu, false, cus, nullptr, cua, warp, lane,
+  kkt_pass<NC, false>(g.R + mm * t, m, m, ut, uh, 0.5, rowu, false, cus, nullptr, cua, warp, lane,
                           KN ? stash : nullptr);
   if (KN) {
     if (stash) {

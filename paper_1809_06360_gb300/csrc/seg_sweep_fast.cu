@@ -208,29 +208,76 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     cp_async_commit();
     issue_ab(t - 1);
     // ---- T1 = V [A|B|c] + [0|0|v_x] ----------------------------------------------
-    cta_mm4f<false>(N, ldAB, N, V, LV, ab, ldAB,
-                    [&](int i, int j, float v) { T1[i * ldAB + j] = (j == cN) ? v + vx[i] : v; });
+    if (SHAPE == 0) {
+      // m <= 32: only T1_B = V B and T1_c = V c + v_x here, the inputs of M_uu and
+      // m_u; T1_A = V A is formed beside the inverse below
+      cta_mm4f<false>(N, M, N, V, LV, ab + N, ldAB, [&](int i, int j, float v) { T1[i * ldAB + N + j] = v; });
+      cta_mm4f<false>(N, 4, N, V, LV, ab + cN, ldAB, [&](int i, int j, float v) {
+        if (j == 0) T1[i * ldAB + cN] = v + vx[i];
+      }, (N / 4) * (M / 4));
+    } else {
+      cta_mm4f<false>(N, ldAB, N, V, LV, ab, ldAB,
+                      [&](int i, int j, float v) { T1[i * ldAB + j] = (j == cN) ? v + vx[i] : v; });
+    }
     cp_async_wait<1>();  // this stage's Q, R, S, q, r (the next [A|B|c] may still be in flight)
     __syncthreads();
     // ---- the M terms ---------------------------------------------------------------
-    if (param && SHAPE <= 1) {
-      // Parametric sweep, m <= 64: B'T1 = [M_ux - S | M_uu - R | m_u - r] first; then
-      // the first GT threads invert M_uu (named barrier 1) while the others form
-      // M_xx, m_x, M_zu, m_z, M_zx, which do not depend on it (measured: the
-      // inverse stays the long pole, stretched by the products beside it, and a
-      // window with more product work hides more of it).
+    if (SHAPE == 0) {
+      // M_uu = R + B'T1_B and m_u = r + B'T1_c first; then warp 0 inverts M_uu
+      // (pivot columns by shuffles, no barrier) while the other 15 warps form
+      // T1_A = V A, then M_xx, m_x, M_ux and (parametric) M_zu, m_z, M_zx, which
+      // do not depend on the inverse.
+      cta_mm4f<true>(M, M, N, ab + N, ldAB, T1 + N, ldAB,
+                     [&](int a, int b, float v) { Muu[a * LM + b] = v + Rs[a * M + b]; });
+      cta_mm4f<true>(M, 4, N, ab + N, ldAB, T1 + cN, ldAB, [&](int a, int j, float v) {
+        if (j == 0) F[a * ldF + 2 * N] = v + rs[a];
+      }, (M / 4) * (M / 4));
+      __syncthreads();
+      const int warp = (int)threadIdx.x >> 5;
+      if (warp == 0) {
+        warp_spd_inverse32(m, Muu, LM, &s_flag);
+      } else {
+        constexpr int kWorkers = kSweepBlock - 32;
+        const int gtid = (int)threadIdx.x - 32;
+        grp_mm4f<false>(gtid, kWorkers, N, N, N, V, LV, ab, ldAB, [&](int i, int j, float v) { T1[i * ldAB + j] = v; });
+        NamedBar{2, kWorkers}();  // T1_A complete before M_xx overwrites V
+        int rot = 0;
+        grp_mm4f<true>(gtid, kWorkers, N, N, N, ab, ldAB, T1, ldAB,
+                       [&](int i, int j, float v) { V[i * LV + j] = v + Qs[i * LV + j]; }, rot);
+        rot += (N / 4) * (N / 4);
+        grp_mm4f<true>(gtid, kWorkers, N, 4, N, ab, ldAB, T1 + cN, ldAB, [&](int i, int j, float v) {
+          if (j == 0) vx[i] = v + qs[i];
+        }, rot);
+        rot += N / 4;
+        grp_mm4f<true>(gtid, kWorkers, M, N, N, ab + N, ldAB, T1, ldAB,
+                       [&](int a, int j, float v) { F[a * ldF + j] = v + Ss[a * N + j]; }, rot);
+        rot += (M / 4) * (N / 4);
+        if (param) {
+          grp_mm4f<false>(gtid, kWorkers, N, M, N, Z, LV, ab + N, ldAB,
+                          [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
+          rot += (N / 4) * (M / 4);
+          grp_mm4f<false>(gtid, kWorkers, N, 4, N, Z, LV, ab + cN, ldAB, [&](int i, int j, float v) {
+            if (j == 0) mz[i] = v + vz[i];
+          }, rot);
+          rot += N / 4;
+          grp_mm4f<false>(gtid, kWorkers, N, N, N, Z, LV, ab, ldAB,
+                          [&](int i, int j, float v) { Mzx[i * LV + j] = v; }, rot);
+        }
+      }
+      __syncthreads();
+    } else if (param && SHAPE == 1) {
+      // Parametric sweep, m <= 64: B'T1 = [M_ux - S | M_uu - R | m_u - r] first;
+      // then the first 256 threads invert M_uu (named barrier 1) while the others
+      // form M_xx, m_x, M_zu, m_z, M_zx, which do not depend on it.
       cta_mm4f<true>(M, ldAB, N, ab + N, ldAB, T1, ldAB, [&](int a, int j, float v) {
         if (j < N) F[a * ldF + j] = v + Ss[a * N + j];
         else if (j < cN) Muu[a * LM + (j - N)] = v + Rs[a * M + (j - N)];
         else if (j == cN) F[a * ldF + 2 * N] = v + rs[a];
       });
       __syncthreads();
-      const int GT = SHAPE == 0 ? 128 : 256;
+      constexpr int GT = 256;
       if ((int)threadIdx.x < GT) {
-        if (SHAPE == 0)
-          grp_spd_inverse<2, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
-        else
-          grp_spd_inverse<4, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
+        grp_spd_inverse<4, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, GT, NamedBar{1, GT});
       } else {
         // M_xx = Q + A'T1_A (into V; the end-of-stage symmetrisation of V_xx takes
         // care of Q's antisymmetric part), m_x = q + A'T1_c, M_zu' = (Z B)' into
@@ -244,14 +291,16 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
           if (j == 0) vx[i] = v + qs[i];
         }, rot);
         rot += N / 4;
-        grp_mm4f<false>(gtid, gthr, N, M, N, Z, LV, ab + N, ldAB,
-                        [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
-        rot += (N / 4) * (M / 4);
-        grp_mm4f<false>(gtid, gthr, N, 4, N, Z, LV, ab + cN, ldAB, [&](int i, int j, float v) {
-          if (j == 0) mz[i] = v + vz[i];
-        }, rot);
-        rot += N / 4;
-        grp_mm4f<false>(gtid, gthr, N, N, N, Z, LV, ab, ldAB, [&](int i, int j, float v) { Mzx[i * LV + j] = v; }, rot);
+        if (param) {
+          grp_mm4f<false>(gtid, gthr, N, M, N, Z, LV, ab + N, ldAB,
+                          [&](int i, int a, float v) { F[a * ldF + N + i] = v; }, rot);
+          rot += (N / 4) * (M / 4);
+          grp_mm4f<false>(gtid, gthr, N, 4, N, Z, LV, ab + cN, ldAB, [&](int i, int j, float v) {
+            if (j == 0) mz[i] = v + vz[i];
+          }, rot);
+          rot += N / 4;
+          grp_mm4f<false>(gtid, gthr, N, N, N, Z, LV, ab, ldAB, [&](int i, int j, float v) { Mzx[i * LV + j] = v; }, rot);
+        }
       }
       __syncthreads();
     } else {
@@ -294,10 +343,7 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
         cta_mm4f<false>(N, N, N, Z, LV, ab, ldAB, [&](int i, int j, float v) { Mzx[i * LV + j] = v; }, rot);
       }
       __syncthreads();
-      if (SHAPE == 0)  // m <= 32: one 1 x 2 block per thread of the 512
-        grp_spd_inverse<1, 2>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, kSweepBlock,
-                              NamedBar{1, kSweepBlock});
-      else if (SHAPE == 1)
+      if (SHAPE == 1)
         grp_spd_inverse<2, 4>(m, Muu, LM, &s_flag, colbuf, colbuf + 2 * M, true, (int)threadIdx.x, kSweepBlock,
                               NamedBar{1, kSweepBlock});
       __syncthreads();
