@@ -1,0 +1,84 @@
+"""The FP64 KKT residual pass against the oracle at points where the residual
+is well above rounding level.
+
+At a computed solution the residual is at rounding level, so only its order
+of magnitude can be compared with the oracle (summation orders differ). Here
+the solution is perturbed first (x, u and lambda each by a seeded random vector
+of relative size 1e-3), so that |KKT w - b|, the |KKT| row sums, |w| and |b|
+are all O(1) quantities: the normwise backward error eta, the relative
+residual rel and the objective of Eq. 1 must then match the oracle to FP64
+rounding. The no-allocation entry point is used because it evaluates any given
+point; it runs the same per-stage block as the residual pass of the
+refinement step. Shapes cover every register column plan (max(n, m) <= 32, <= 64,
+<= 128), matrices narrower than the plan, n and m odd, S present and absent,
+horizons longer than the grid (several stages per CTA) and the generic loop
+beyond 128."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_06360_gb300 import Solver, build
+    build.build()
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def _perturbed(prob, seed, prec):
+    """Solve, then move x, u, lambda off the solution by 1e-3 relative."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    ref = oracle.riccati(prob)
+    for k in ("x", "u", "lam"):
+        v = ref[k]
+        out[k] = v + 1e-3 * np.abs(v).max() * rng.standard_normal(v.shape)
+    if prec == "fp32":
+        out = {k: v.astype(np.float32).astype(np.float64) for k, v in out.items()}
+    return out
+
+
+@pytest.mark.parametrize("n,m,T,cross,prec", [
+    (7, 3, 61, True, "fp64"),       # one register column, odd sizes
+    (30, 10, 700, False, "fp64"),   # T > grid: several stages per CTA; S absent
+    (64, 32, 1300, True, "fp64"),   # two columns for n, one for m
+    (64, 32, 300, True, "fp32"),    # FP32 data, FP64 arithmetic
+    (80, 16, 200, True, "fp64"),    # four columns for n, one for m
+    (100, 70, 50, True, "fp64"),    # four columns for both
+    (130, 5, 20, True, "fp64"),     # beyond the register plan: the generic loop
+])
+def test_residual_at_perturbed_point_matches_oracle(solver, n, m, T, cross, prec):
+    from paper_1809_06360_gb300 import lqr
+    prob = workloads.make_problem(n, m, T, seed=900 + n + m + T, cross=cross)
+    if not cross:
+        prob["S"] = np.zeros_like(prob["S"])
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    if prec == "fp32":
+        prob = {k: v.astype(np.float32).astype(np.float64) for k, v in prob.items()}
+    sol = _perturbed(prob, seed=n * 7 + T, prec=prec)
+    dev = {k: torch.from_numpy(v).to("cuda:0", dt) for k, v in prob.items()}
+    if not cross:
+        dev["S"] = None  # the kernels' S = 0 path
+    dsol = {k: torch.from_numpy(v).to("cuda:0", dt) for k, v in sol.items()}
+    p = lqr.Solver.make_problem_struct({k: v for k, v in dev.items() if v is not None},
+                                       lambda t: t.data_ptr())
+    s = lqr.lqr_solution(**{f: (dsol[f].data_ptr() if f in dsol else None) for f in lqr.SOLUTION_FIELDS})
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda:0")
+    lqr.lqr_kkt_residual_noalloc(p, s, lqr.PRECISION[prec], out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    eta, rel, cost = out.cpu().numpy()
+    ref = oracle.kkt_residual(prob, sol["x"], sol["u"], sol["lam"])
+    ref_cost = oracle.stage_costs(prob, sol["x"], sol["u"])
+    assert ref["rel"] > 1e-6  # well above rounding level
+    assert abs(eta - ref["eta"]) <= 1e-12 * ref["eta"], (eta, ref["eta"])
+    assert abs(rel - ref["rel"]) <= 1e-12 * ref["rel"], (rel, ref["rel"])
+    assert abs(cost - ref_cost) <= 1e-12 * max(abs(ref_cost), 1.0), (cost, ref_cost)
