@@ -134,3 +134,49 @@ def test_kkt_residual_of_exact_solution_is_tiny():
     x[10, 3] += 1e-6
     res2 = oracle.kkt_residual(prob, x, ric["u"], ric["lam"])
     assert res2["rnorm"] > 1e-7
+
+
+@pytest.mark.parametrize("cross", [False, True])
+def test_kkt_residual_matches_dense_system(cross):
+    """The block formulas of the residual, |KKT| row sums and norms against the
+    dense KKT matrix of Eq. 3 (assembled entry by entry) at a point that is not
+    the solution: r = KKT z - b, eta = |r| / (max_i sum_j |KKT_ij| |z| + |b|)."""
+    n, m, T = 5, 2, 7
+    prob = workloads.make_problem(n, m, T, seed=31, cross=cross)
+    rng = np.random.default_rng(5)
+    for k in ("Q", "R"):  # nonsymmetric input: both sides read (M + M')/2
+        d = prob[k].shape[-1]
+        prob[k] = prob[k] + 0.3 * rng.standard_normal((prob[k].shape[0], d, d))
+        prob[k] = 0.5 * (prob[k] + np.swapaxes(prob[k], -1, -2)) + 0.2 * (
+            prob[k] - np.swapaxes(prob[k], -1, -2))
+    x = rng.standard_normal((T + 1, n))
+    u = rng.standard_normal((T, m))
+    lam = rng.standard_normal((T + 1, n))
+    got = oracle.kkt_residual(prob, x, u, lam)
+    dk = oracle.dense_kkt(prob)
+    K, b = dk["kkt"], dk["rhs"]
+    z = np.concatenate([x.ravel(), u.ravel(), lam.ravel()])
+    r = K @ z - b
+    rnorm = np.abs(r).max()
+    knorm = np.abs(K).sum(axis=1).max()
+    eta = rnorm / (knorm * np.abs(z).max() + np.abs(b).max())
+    assert got["rnorm"] == pytest.approx(rnorm, rel=1e-13)
+    assert got["knorm"] == pytest.approx(knorm, rel=1e-13)
+    assert got["eta"] == pytest.approx(eta, rel=1e-13)
+    assert got["rel"] == pytest.approx(rnorm / np.abs(b).max(), rel=1e-13)
+
+
+def test_stage_costs_matches_dense_quadratic():
+    """The objective of Eq. 1-2 summed stage by stage against 1/2 w'Hw + g'w with the
+    dense Hessian of the KKT system (Q, R read symmetrised, S coupling) at a random w."""
+    n, m, T = 4, 3, 6
+    prob = workloads.make_problem(n, m, T, seed=41, cross=True)
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((T + 1, n))
+    u = rng.standard_normal((T, m))
+    dk = oracle.dense_kkt(prob)
+    nw = (T + 1) * n + T * m
+    H = dk["kkt"][:nw, :nw]
+    g = -dk["rhs"][:nw]
+    w = np.concatenate([x.ravel(), u.ravel()])
+    assert oracle.stage_costs(prob, x, u) == pytest.approx(0.5 * w @ H @ w + g @ w, rel=1e-13)
