@@ -199,14 +199,14 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     cp_async_wait<0>();
     __syncthreads();  // [A|B|c]_t in its slot; the previous stage is finished
     const float* ab = sm + P.ab + (long long)((t1 - 1 - t) & 1) * N * ldAB;
-    // Q, R, S, q, r of this stage, then the next stage's [A|B|c]
+    // Q, R, S, q, r of this stage; the next stage's [A|B|c] is issued once they are
+    // in, so that they do not queue behind it
     copy_rows(Qs, LV, gQ + nn * t, n, n, n, v16);
     copy_rows(Rs, M, gR + mm * t, m, m, m, v16);
     if (gS) copy_rows(Ss, N, gS + nm * t, n, m, n, v16);
     for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(qs + i, gq + (long long)n * t + i);
     for (int a = threadIdx.x; a < m; a += blockDim.x) cp_async4(rs + a, gr + (long long)m * t + a);
     cp_async_commit();
-    issue_ab(t - 1);
     // ---- T1 = V [A|B|c] + [0|0|v_x] ----------------------------------------------
     if (SHAPE == 0) {
       // m <= 32: only T1_B = V B and T1_c = V c + v_x here, the inputs of M_uu and
@@ -219,8 +219,9 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
       cta_mm4f<false>(N, ldAB, N, V, LV, ab, ldAB,
                       [&](int i, int j, float v) { T1[i * ldAB + j] = (j == cN) ? v + vx[i] : v; });
     }
-    cp_async_wait<1>();  // this stage's Q, R, S, q, r (the next [A|B|c] may still be in flight)
+    cp_async_wait<0>();  // this stage's Q, R, S, q, r
     __syncthreads();
+    issue_ab(t - 1);  // in flight during the rest of this stage
     // ---- the M terms ---------------------------------------------------------------
     if (SHAPE == 0) {
       // M_uu = R + B'T1_B and m_u = r + B'T1_c first; then warp 0 inverts M_uu
