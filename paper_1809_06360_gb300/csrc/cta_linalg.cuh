@@ -491,207 +491,10 @@ __device__ __forceinline__ void cta_copy_async(T* dst, const T* src, long long c
   }
 }
 
-// ---------------------------------------------------------------------------
-// Register-blocked symmetric eliminations, one barrier per pivot.
-// The d x d matrix is cut into 4 x 4 blocks (nb = ceil(d/4) per side) that
-// live in registers, R blocks per thread at most. In step j every thread
-// reads the current column j from a shared buffer (published by the owners of
-// column j at the end of step j-1, double-buffered so that nobody waits for a
-// second barrier), updates its blocks, and the owners of column j+1 publish
-// it. Rows and columns past d are zero padding and are never stored.
-// `colbuf` (shared) holds 2 * 4nb values. Both routines end with a barrier.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float recip_pivot(float p) { return __frcp_rn(p); }
-__device__ __forceinline__ double recip_pivot(double p) { return rcp_newton(p); }
 __device__ __forceinline__ float rsqrt_pos(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double rsqrt_pos(double v) { return rsqrt(v); }
 
-// Lower Cholesky factor of the SPD matrix G in place (strict upper part set to
-// zero), computed as L D L' with unscaled columns so that the pivot chain
-// needs one reciprocal per step; the square roots are taken at the end.
-// Blocks of the lower triangle only, nb(nb+1)/2 <= R * blockDim.x.
-// rdiag[k] = 1 / L[k][k] if non-null; *flag = 1 on a pivot that is not
-// positive and finite.
-template <typename T, int R>
-__device__ inline void cta_chol_reg(int d, T* G, int ld, int* flag, T* colbuf, T* rdiag) {
-  const int t = threadIdx.x, nthr = blockDim.x;
-  const int nb = (d + 3) >> 2, nb4 = 4 * nb, nlb = nb * (nb + 1) / 2;
-  T v[R][4][4];
-  int bi[R], bk[R];
-  bool own[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int blk = t + r * nthr;
-    own[r] = blk < nlb;
-    int ii = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
-    while ((ii + 1) * (ii + 2) / 2 <= blk) ++ii;
-    while (ii * (ii + 1) / 2 > blk) --ii;
-    bi[r] = own[r] ? ii : 0;
-    bk[r] = own[r] ? blk - ii * (ii + 1) / 2 : 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = 4 * bi[r] + a, k = 4 * bk[r] + b;
-        v[r][a][b] = (own[r] && i < d && k <= i) ? G[(size_t)i * ld + k] : T(0);
-      }
-  }
-  for (int i = t; i < nb4; i += nthr) colbuf[i] = i < d ? G[(size_t)i * ld] : T(0);
-  __syncthreads();
-  for (int j = 0; j < d; ++j) {
-    const T* col = colbuf + (j & 1) * nb4;
-    T* nxt = colbuf + ((j + 1) & 1) * nb4;
-    const T p = col[j];
-    if (t == 0 && !(p > T(0) && isfinite(p))) *flag = 1;
-    const T rp = recip_pivot(p);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (!own[r] || 4 * bk[r] + 3 <= j) continue;
-      T ci[4], ckr[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) ci[a] = col[4 * bi[r] + a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) ckr[b] = col[4 * bk[r] + b] * rp;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (4 * bk[r] + b > j) v[r][a][b] = fma(-ci[a], ckr[b], v[r][a][b]);
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        if (4 * bk[r] + b == j + 1) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-            if (4 * bi[r] + a >= j + 1) nxt[4 * bi[r] + a] = v[r][a][b];
-        }
-    }
-    __syncthreads();
-  }
-  // D_k on the diagonal; L = (unscaled column) / sqrt(D_k)
-  T* dg = colbuf;
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (own[r] && bi[r] == bk[r])
-#pragma unroll
-      for (int a = 0; a < 4; ++a) dg[4 * bi[r] + a] = v[r][a][a];
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    if (!own[r]) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int k = 4 * bk[r] + b;
-      if (k >= d) continue;
-      const T Dk = dg[k];
-      const T rs = Dk > T(0) ? rsqrt_pos(Dk) : T(1);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = 4 * bi[r] + a;
-        if (i < d && i >= k) G[(size_t)i * ld + k] = (i == k) ? (Dk > T(0) ? Dk * rs : T(1)) : v[r][a][b] * rs;
-      }
-    }
-  }
-  for (int e = t; e < d * d; e += nthr) {
-    const int i = e / d, k = e - i * d;
-    if (k > i) G[(size_t)i * ld + k] = T(0);
-  }
-  if (rdiag)
-    for (int k = t; k < d; k += nthr) rdiag[k] = dg[k] > T(0) ? rsqrt_pos(dg[k]) : T(1);
-  __syncthreads();
-}
-
-// Inverse of the SPD matrix G in place by symmetric Gauss-Jordan elimination
-// (the sweep operator on every pivot, which leaves -G^{-1}); blocks of the full
-// square, nb^2 <= R * blockDim.x. *flag = 1 on a pivot that is not positive.
-// sym: the input is taken as (G + G')/2.
-template <typename T, int R>
-__device__ inline void cta_spd_inverse_reg(int d, T* G, int ld, int* flag, T* colbuf, bool sym = false) {
-  const int t = threadIdx.x, nthr = blockDim.x;
-  const int nb = (d + 3) >> 2, nb4 = 4 * nb;
-  T v[R][4][4];
-  int bi[R], bk[R];
-  bool own[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int blk = t + r * nthr;
-    own[r] = blk < nb * nb;
-    bi[r] = own[r] ? blk / nb : 0;
-    bk[r] = own[r] ? blk % nb : 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = 4 * bi[r] + a, k = 4 * bk[r] + b;
-        T g = T(0);
-        if (own[r] && i < d && k < d) {
-          g = G[(size_t)i * ld + k];
-          if (sym) g = T(0.5) * (g + G[(size_t)k * ld + i]);
-        }
-        v[r][a][b] = g;
-      }
-  }
-  for (int i = t; i < nb4; i += nthr) {
-    T g = T(0);
-    if (i < d) {
-      g = G[(size_t)i * ld];
-      if (sym) g = T(0.5) * (g + G[i]);
-    }
-    colbuf[i] = g;
-  }
-  __syncthreads();
-  for (int j = 0; j < d; ++j) {
-    const T* col = colbuf + (j & 1) * nb4;
-    T* nxt = colbuf + ((j + 1) & 1) * nb4;
-    const T p = col[j];
-    if (t == 0 && !(p > T(0) && isfinite(p))) *flag = 1;
-    const T rp = recip_pivot(p);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (!own[r]) continue;
-      T ci[4], ckr[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) ci[a] = col[4 * bi[r] + a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) ckr[b] = col[4 * bk[r] + b] * rp;
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const bool ri = (4 * bi[r] + a == j), ck = (4 * bk[r] + b == j);
-          const T upd = fma(-ci[a], ckr[b], v[r][a][b]);
-          v[r][a][b] = ri ? (ck ? -rp : ckr[b]) : (ck ? ci[a] * rp : upd);
-        }
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        if (4 * bk[r] + b == j + 1) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a) nxt[4 * bi[r] + a] = v[r][a][b];
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    if (!own[r]) continue;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = 4 * bi[r] + a, k = 4 * bk[r] + b;
-        if (i < d && k < d) G[(size_t)i * ld + k] = -v[r][a][b];
-      }
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// Symmetric eliminations with one BR x BC register block per thread (the
-// block grid ceil(d/BR) x ceil(d/BC) must not exceed blockDim.x), one barrier
-// per pivot. The owner of the next pivot publishes its reciprocal together
-// with the pivot column, so a step costs each thread BR + BC shared loads and
-// BR*BC fused multiply-adds. colbuf: 2 * dp values, rpv: 2 values (shared),
-// dp = max(BR ceil(d/BR), BC ceil(d/BC)). Both end with a barrier.
-// ---------------------------------------------------------------------------
+// Reciprocal of a pivot on a dependent chain.
 __device__ __forceinline__ float recip_fast(float p) {
   // hardware approximation refined by one Newton-Raphson step r += r (1 - p r)
   float r;
@@ -699,188 +502,6 @@ __device__ __forceinline__ float recip_fast(float p) {
   return fmaf(r, fmaf(-p, r, 1.0f), r);
 }
 __device__ __forceinline__ double recip_fast(double p) { return rcp_newton(p); }
-
-// Inverse of the SPD matrix G in place (Gauss-Jordan sweep on every pivot);
-// sym: the input is taken as (G + G')/2. *flag = 1 on a pivot that is not
-// positive and finite.
-template <typename T, int BR, int BC>
-__device__ inline void cta_spd_inverse_blk(int d, T* G, int ld, int* flag, T* colbuf, T* rpv, bool sym) {
-  const int t = threadIdx.x;
-  const int nbr = (d + BR - 1) / BR, nbc = (d + BC - 1) / BC;
-  const int dp = (nbr * BR > nbc * BC) ? nbr * BR : nbc * BC;
-  const bool own = t < nbr * nbc;
-  const int i0 = own ? (t / nbc) * BR : 0, k0 = own ? (t % nbc) * BC : 0;
-  T v[BR][BC];
-#pragma unroll
-  for (int a = 0; a < BR; ++a)
-#pragma unroll
-    for (int b = 0; b < BC; ++b) {
-      const int i = i0 + a, k = k0 + b;
-      T g = T(0);
-      if (own && i < d && k < d) {
-        g = G[(size_t)i * ld + k];
-        if (sym) g = T(0.5) * (g + G[(size_t)k * ld + i]);
-      }
-      v[a][b] = g;
-    }
-  for (int i = t; i < dp; i += blockDim.x) {
-    T g = T(0);
-    if (i < d) {
-      g = G[(size_t)i * ld];
-      if (sym) g = T(0.5) * (g + G[i]);
-    }
-    colbuf[i] = g;
-    if (i == 0) {
-      if (!(g > T(0) && isfinite(g))) *flag = 1;
-      rpv[0] = recip_fast(g);
-    }
-  }
-  __syncthreads();
-  for (int j = 0; j < d; ++j) {
-    const T* col = colbuf + (j & 1) * dp;
-    T* nxt = colbuf + ((j + 1) & 1) * dp;
-    if (own) {
-      const T rp = rpv[j & 1];
-      T ci[BR], ckr[BC];
-#pragma unroll
-      for (int a = 0; a < BR; ++a) ci[a] = col[i0 + a];
-#pragma unroll
-      for (int b = 0; b < BC; ++b) ckr[b] = col[k0 + b] * rp;
-#pragma unroll
-      for (int a = 0; a < BR; ++a)
-#pragma unroll
-        for (int b = 0; b < BC; ++b) v[a][b] = fma(-ci[a], ckr[b], v[a][b]);
-      const bool hr = (j >= i0 && j < i0 + BR), hc = (j >= k0 && j < k0 + BC);
-      if (hr || hc) {
-#pragma unroll
-        for (int a = 0; a < BR; ++a)
-#pragma unroll
-          for (int b = 0; b < BC; ++b) {
-            const bool ri = (i0 + a == j), cj = (k0 + b == j);
-            if (ri && cj) v[a][b] = -rp;
-            else if (ri) v[a][b] = ckr[b];
-            else if (cj) v[a][b] = ci[a] * rp;
-          }
-      }
-      if (j + 1 >= k0 && j + 1 < k0 + BC) {
-#pragma unroll
-        for (int b = 0; b < BC; ++b)
-          if (k0 + b == j + 1) {
-#pragma unroll
-            for (int a = 0; a < BR; ++a) {
-              nxt[i0 + a] = v[a][b];
-              if (i0 + a == j + 1 && j + 1 < d) {
-                const T pn = v[a][b];
-                if (!(pn > T(0) && isfinite(pn))) *flag = 1;
-                rpv[(j + 1) & 1] = recip_fast(pn);
-              }
-            }
-          }
-      }
-    }
-    __syncthreads();
-  }
-  if (own)
-#pragma unroll
-    for (int a = 0; a < BR; ++a)
-#pragma unroll
-      for (int b = 0; b < BC; ++b) {
-        const int i = i0 + a, k = k0 + b;
-        if (i < d && k < d) G[(size_t)i * ld + k] = -v[a][b];
-      }
-  __syncthreads();
-}
-
-// Lower Cholesky factor of the SPD matrix G in place (strict upper part set to
-// zero) as L D L' with unscaled columns; rdiag[k] = 1 / L[k][k] if non-null.
-template <typename T, int BR, int BC>
-__device__ inline void cta_chol_blk(int d, T* G, int ld, int* flag, T* colbuf, T* rpv, T* rdiag) {
-  const int t = threadIdx.x;
-  const int nbr = (d + BR - 1) / BR, nbc = (d + BC - 1) / BC;
-  const int dp = (nbr * BR > nbc * BC) ? nbr * BR : nbc * BC;
-  bool own = t < nbr * nbc;
-  const int i0 = own ? (t / nbc) * BR : 0, k0 = own ? (t % nbc) * BC : 0;
-  own = own && (i0 + BR - 1 >= k0);  // the block meets the lower triangle
-  T v[BR][BC];
-#pragma unroll
-  for (int a = 0; a < BR; ++a)
-#pragma unroll
-    for (int b = 0; b < BC; ++b) {
-      const int i = i0 + a, k = k0 + b;
-      v[a][b] = (own && i < d && k <= i) ? G[(size_t)i * ld + k] : T(0);
-    }
-  for (int i = t; i < dp; i += blockDim.x) {
-    const T g = i < d ? G[(size_t)i * ld] : T(0);
-    colbuf[i] = g;
-    if (i == 0) {
-      if (!(g > T(0) && isfinite(g))) *flag = 1;
-      rpv[0] = recip_fast(g);
-    }
-  }
-  __syncthreads();
-  for (int j = 0; j < d; ++j) {
-    const T* col = colbuf + (j & 1) * dp;
-    T* nxt = colbuf + ((j + 1) & 1) * dp;
-    if (own && k0 + BC - 1 > j) {
-      const T rp = rpv[j & 1];
-      T ci[BR], ckr[BC];
-#pragma unroll
-      for (int a = 0; a < BR; ++a) ci[a] = col[i0 + a];
-#pragma unroll
-      for (int b = 0; b < BC; ++b) ckr[b] = col[k0 + b] * rp;
-#pragma unroll
-      for (int a = 0; a < BR; ++a)
-#pragma unroll
-        for (int b = 0; b < BC; ++b)
-          if (k0 + b > j) v[a][b] = fma(-ci[a], ckr[b], v[a][b]);
-      if (j + 1 >= k0 && j + 1 < k0 + BC) {
-#pragma unroll
-        for (int b = 0; b < BC; ++b)
-          if (k0 + b == j + 1) {
-#pragma unroll
-            for (int a = 0; a < BR; ++a)
-              if (i0 + a >= j + 1) {
-                nxt[i0 + a] = v[a][b];
-                if (i0 + a == j + 1 && j + 1 < d) {
-                  const T pn = v[a][b];
-                  if (!(pn > T(0) && isfinite(pn))) *flag = 1;
-                  rpv[(j + 1) & 1] = recip_fast(pn);
-                }
-              }
-          }
-      }
-    }
-    __syncthreads();
-  }
-  T* dg = colbuf;  // D_k
-  if (own)
-#pragma unroll
-    for (int a = 0; a < BR; ++a)
-#pragma unroll
-      for (int b = 0; b < BC; ++b)
-        if (i0 + a == k0 + b && i0 + a < d) dg[i0 + a] = v[a][b];
-  __syncthreads();
-  if (own)
-#pragma unroll
-    for (int b = 0; b < BC; ++b) {
-      const int k = k0 + b;
-      if (k >= d) continue;
-      const T Dk = dg[k];
-      const T rs = Dk > T(0) ? rsqrt_pos(Dk) : T(1);
-#pragma unroll
-      for (int a = 0; a < BR; ++a) {
-        const int i = i0 + a;
-        if (i < d && i >= k) G[(size_t)i * ld + k] = (i == k) ? (Dk > T(0) ? Dk * rs : T(1)) : v[a][b] * rs;
-      }
-    }
-  for (int e = t; e < d * d; e += blockDim.x) {
-    const int i = e / d, k = e - i * d;
-    if (k > i) G[(size_t)i * ld + k] = T(0);
-  }
-  if (rdiag)
-    for (int k = t; k < d; k += blockDim.x) rdiag[k] = dg[k] > T(0) ? rsqrt_pos(dg[k]) : T(1);
-  __syncthreads();
-}
 
 // ---------------------------------------------------------------------------
 // 4 x 4 block eliminations: d/4 pivot steps instead of d, each a rank-4
