@@ -12,10 +12,11 @@
 // stage, on the FP64 pipe), so every matrix element is read once and used
 // twice: for its row product and for its column product. Rows go to warps
 // (row i to warp i % nw in every pass, so each row accumulator in shared
-// memory has one writer), columns to lanes (k = lane + 32 c, c < NC), and a
-// batch of RB rows is loaded before it is used. Column products stay in
-// registers until the end of the stage and are then summed over the warps
-// through shared memory.
+// memory has one writer), columns to lanes (k = lane + 32 c, c < NCP, the
+// narrowest plan that covers the matrix's columns), and a batch of kKktRB rows
+// is loaded before it is used; the row products of a batch are reduced over the
+// lanes together (kkt_rows_reduce). Column products stay in registers until the
+// end of the stage and are then summed over the warps through shared memory.
 #pragma once
 
 #include <cuda_runtime.h>
