@@ -176,6 +176,24 @@ def cpu_baseline(n, m, T_sample, prob_full, budget_s=12.0):
                       "of the n=%d m=%d workload, %.1f s" % (runs, T_sample, n, m, el)}
 
 
+def max_over_ranks(values, world, device):
+    """Elementwise maximum of per-rank floats over the process group (the
+    slowest replica sets the job's time); the values themselves at world 1."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(stages_per_replica_step: int, steps: int, world: int, seconds: float) -> float:
+    """Stages per second over all replicas: every rank solves its own copy of the
+    workload (weak scaling, no data-path collective), timed by the slowest."""
+    return world * steps * stages_per_replica_step / seconds
+
+
 def run_reference(args, rank, world):
     """Reference arm: the oracle on host cores (rank 0 only)."""
     if rank != 0:
@@ -295,11 +313,8 @@ def main():
     ms = e0.elapsed_time(e1)
     phase_ms, nprof = lqr.lqr_profile_read(solver.h)
     lqr.lqr_profile_enable(solver.h, False)
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps * T / (ms / 1e3)
+    ms = max_over_ranks([ms], world, f"cuda:{local}")[0]
+    value = whole_job_rate(T, args.steps, world, ms / 1e3)
 
     # per-phase achieved rates; the roofline entry is the phase that takes the most time
     nsolve = max(nprof, 1)
@@ -394,15 +409,17 @@ def main():
         for _ in range(2):
             solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form, max_refine=mr,
                               tol=args.tol)
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         e2e_steps = max(3, args.steps // 2)
         for _ in range(e2e_steps):
             solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form, max_refine=mr,
                               tol=args.tol)
-        el = time.perf_counter() - t0
+        el = max_over_ranks([time.perf_counter() - t0], world, f"cuda:{local}")[0]
         h2d = sum(v.nbytes for v in pin_np.values())
         d2h = sum(v.nbytes for v in outp.values())
-        e2e = {"value": world * e2e_steps * T / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": whole_job_rate(T, e2e_steps, world, el), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
 
     cpu = None
