@@ -336,9 +336,17 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   if (rs != LQR_OK) return rs;
   rs = grow(&h->ws, &h->ws_bytes, sp.ws_need);
   if (rs != LQR_OK) return rs;
-  const int n = p->n, m = p->m, T = p->T;
+  const int n = p->n, m = p->m, T = p->T, K = sp.K;
   const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
   const bool want_P = (s->P != nullptr);
+  // Corrections reuse the factorisation (K_t, P_t, M_uu^-1 of the solve; correct.cu)
+  // when the FP32 fast sweeps run and the correction kernels' plans fit; otherwise
+  // every correction is a whole FP32 solve.
+  const long long budget = h->smem_optin - kStaticSmemReserve;
+  const bool reuse = !summary_only && sp.rbase >= 0 && o->max_refine > 0 && fast_sweep_supported(n, m, budget) &&
+                     (long long)corr_seg_smem_bytes(n, m) <= budget && (long long)corr_psi_smem_bytes(n, m) <= budget &&
+                     (long long)corr_link_smem_bytes(n) <= budget;
+  const bool keep_P = want_P || reuse;
   // FP32 working arrays (each 256-byte aligned)
   size_t off = 0;
   auto take = [&](size_t cnt) { const size_t a = off; off += (cnt + 63) & ~(size_t)63; return a; };
@@ -346,11 +354,14 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
                oQ = take((size_t)(T + 1) * nn), oR = take((size_t)T * mm), oS = p->S ? take((size_t)T * nm) : 0,
                oq = take((size_t)(T + 1) * n), orr = take((size_t)T * m), ox0 = take(n);
   const size_t oK = take((size_t)T * nm), ok = take((size_t)T * m), ox = take((size_t)(T + 1) * n),
-               ou = take((size_t)T * m), ol = take((size_t)(T + 1) * n), oP = want_P ? take((size_t)(T + 1) * nn) : 0,
-               op = want_P ? take((size_t)(T + 1) * n) : 0;
+               ou = take((size_t)T * m), ol = take((size_t)(T + 1) * n), oP = keep_P ? take((size_t)(T + 1) * nn) : 0,
+               op = keep_P ? take((size_t)(T + 1) * n) : 0;
   const size_t ocq = take((size_t)(T + 1) * n), ocr = take((size_t)T * m), occ = take((size_t)T * n),
                ocx0 = take(n), odk = take((size_t)T * m), odx = take((size_t)(T + 1) * n), odu = take((size_t)T * m),
-               odl = take((size_t)(T + 1) * n), odp = want_P ? take((size_t)(T + 1) * n) : 0;
+               odl = take((size_t)(T + 1) * n), odp = keep_P ? take((size_t)(T + 1) * n) : 0;
+  const size_t oMi = reuse ? take((size_t)T * mm) : 0, oPsi = reuse ? take((size_t)K * nn) : 0,
+               oeps = reuse ? take((size_t)K * n) : 0, odel = reuse ? take((size_t)K * n) : 0,
+               opb = reuse ? take((size_t)(K + 1) * n) : 0, oxb = reuse ? take((size_t)(K + 1) * n) : 0;
   rs = grow(&h->f32, &h->f32_bytes, sizeof(float) * off);
   if (rs != LQR_OK) return rs;
   float* f = reinterpret_cast<float*>(h->f32);
@@ -361,7 +372,7 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   memset(&s32, 0, sizeof(s32));
   if (!summary_only) {
     s32.K = f + oK; s32.k = f + ok; s32.x = f + ox; s32.u = f + ou; s32.lam = f + ol;
-    if (want_P) { s32.P = f + oP; s32.p = f + op; }
+    if (keep_P) { s32.P = f + oP; s32.p = f + op; }
   }
   {
     ConvTable<double, float> ct;
@@ -382,11 +393,12 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   ProbTable tab;
   memset(&tab, 0, sizeof(tab));
   tab.single = make_desc(h, &p32, &s32, sp, (int)o->form);
+  if (reuse) tab.single.Minv = f + oMi;
   tab.nprob = 1;
   int launches = 1;
   if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
   if (cudaMemsetAsync(h->d_report, 0, 4 * sizeof(double), st) != cudaSuccess) return LQR_ERR_CUDA;
-  rs = enqueue_pipeline(h, tab, sp, &o32, !summary_only, !summary_only, want_P ? 1 : 0, summary_only, true, st,
+  rs = enqueue_pipeline(h, tab, sp, &o32, !summary_only, !summary_only, keep_P ? 1 : 0, summary_only, true, st,
                         &launches);
   if (rs != LQR_OK) return rs;
   if (!summary_only) {
@@ -425,6 +437,18 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
     ctab.single = make_desc(h, &cp, &cs, sp, (int)o->form);
     ctab.single.skip = skip;
     ctab.nprob = 1;
+    CorrArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    if (reuse) {
+      ca.A = f + oA; ca.B = f + oB; ca.K = f + oK; ca.P = f + oP; ca.Minv = f + oMi;
+      ca.cq = f + ocq; ca.cr = f + ocr; ca.cc = f + occ; ca.cx0 = f + ocx0;
+      ca.Psi = f + oPsi; ca.eps = f + oeps; ca.delta = f + odel; ca.pb = f + opb; ca.xb = f + oxb;
+      ca.dk = f + odk; ca.dp = f + odp; ca.dx = f + odx; ca.du = f + odu; ca.dl = f + odl;
+      ca.skip = skip; ca.status = h->d_status;
+      ca.n = n; ca.m = m; ca.T = T; ca.nseg = K;
+      if (launch_corr_psi(ca, st) != cudaSuccess) return LQR_ERR_CUDA;
+      ++launches;
+    }
     for (int it = 0; it < o->max_refine; ++it) {
       if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st) !=
           cudaSuccess)
@@ -438,8 +462,12 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
       ct.add(base + rl.cx0, (void*)cp.x0, (size_t)n);
       if (launch_convert(ct, skip, st) != cudaSuccess) return LQR_ERR_CUDA;
       launches += 3;
-      rs = enqueue_pipeline(h, ctab, sp, &o32, true, true, want_P ? 1 : 0, false, false, st, &launches);
-      if (rs != LQR_OK) return rs;
+      if (reuse) {
+        if (launch_correction(ca, st, &launches) != cudaSuccess) return LQR_ERR_CUDA;
+      } else {
+        rs = enqueue_pipeline(h, ctab, sp, &o32, true, true, want_P ? 1 : 0, false, false, st, &launches);
+        if (rs != LQR_OK) return rs;
+      }
       if (launch_refine_update_f32(main, f + odk, f + odx, f + odu, f + odl, want_P ? f + odp : nullptr, skip, st) !=
           cudaSuccess)
         return LQR_ERR_CUDA;

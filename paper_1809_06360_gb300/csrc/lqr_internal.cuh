@@ -81,6 +81,7 @@ struct ProbDesc {
   int n, m, T, nseg;
   int unit0;                  // first unit (segment) index of this problem in a launch
   int form;                   // lqr_form of the parametric sweeps
+  void* Minv;                 // FP32 fast path: T x m x m M_uu^-1 of the policy stages, may be null
 };
 
 // Kernel-argument view of the problems of one launch: a single problem is
@@ -203,6 +204,18 @@ __device__ __forceinline__ T* plan_ptr(const SweepPlan& P, int b, unsigned char*
 // for all launchers of the same kernel (lqr_api.cu).
 cudaError_t raise_dyn_smem(const void* func, size_t bytes);
 
+// Refinement corrections that reuse the factorisation (correct.cu): FP32
+// arrays of one problem, K = the solve's segment count.
+struct CorrArgs {
+  const float *A, *B, *K, *P, *Minv;   // the solve's data, policies, value matrices, M_uu^-1
+  const float *cq, *cr, *cc, *cx0;     // correction data q~ ((T+1) n), r~ (T m), c~ (T n), x0~ (n)
+  float *Psi, *eps, *delta, *pb, *xb;  // K n n, K n, K n, (K+1) n, (K+1) n
+  float *dk, *dp, *dx, *du, *dl;       // the correction: k~, p, x~, u~, lambda~
+  const int* skip;                     // set: converged, every kernel returns at once
+  int* status;
+  int n, m, T, nseg;
+};
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files, called by lqr_api.cu).
 // ---------------------------------------------------------------------------
@@ -219,6 +232,14 @@ cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, 
 cudaError_t launch_seg_sweep_f32(const ProbTable& tab, int nunits, int phase, int nmax, int mmax,
                                  long long smem_budget, int store_P, cudaStream_t st);
 long long fast_sweep_smem_bytes(int n, int m);
+// the FP32 fast sweeps (and with them the kept M_uu^-1) apply to (n, m)
+bool fast_sweep_supported(int n, int m, long long smem_budget);
+// refinement corrections that reuse the factorisation (correct.cu)
+size_t corr_seg_smem_bytes(int n, int m);
+size_t corr_psi_smem_bytes(int n, int m);
+size_t corr_link_smem_bytes(int n);
+cudaError_t launch_corr_psi(const CorrArgs& a, cudaStream_t st);
+cudaError_t launch_correction(const CorrArgs& a, cudaStream_t st, int* launches);
 
 // Element-type conversion of up to kMaxConv arrays in one launch (skip: when
 // non-null and set, nothing is done).

@@ -385,6 +385,13 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
         }
       if (gk)
         for (int a = threadIdx.x; a < m; a += blockDim.x) gk[(long long)m * t + a] = -H[a * ldF + 2 * N];
+      if (pd.Minv) {  // M_uu^-1, kept for refinement corrections that reuse the factorisation
+        float* gM = static_cast<float*>(pd.Minv) + mm * t;
+        for (long long e = threadIdx.x; e < mm; e += blockDim.x) {
+          const int a = (int)(e / m), b = (int)(e - (long long)a * m);
+          gM[e] = Muu[a * LM + b];
+        }
+      }
     }
     __syncthreads();
     // symmetrise V_xx
@@ -421,6 +428,10 @@ __global__ void __launch_bounds__(kSweepBlock, 1) seg_sweep_f32_kernel(ProbTable
     summ[3 * nn + i] = static_cast<double>(vx[i]);
     summ[3 * nn + n + i] = param ? static_cast<double>(vz[i]) : 0.0;
   }
+}
+
+bool fast_sweep_supported(int n, int m, long long smem_budget) {
+  return fast_sweep_smem_bytes(n, m) <= smem_budget && p4_shape(m) >= 0;
 }
 
 // cudaErrorNotSupported (nothing launched) when the plan does not fit.

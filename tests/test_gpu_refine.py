@@ -139,6 +139,24 @@ def test_mixed_fp32_small_and_odd_shapes(solver):
             assert oracle.rel_err(out[k], ref[k]) < 1e-9, (n, k, oracle.rel_err(out[k], ref[k]))
 
 
+def test_mixed_fp32_value_function_outputs(solver):
+    """With P and p requested: the trajectory is refined to FP64 accuracy while P
+    and p keep FP32 accuracy (they are not unknowns of the KKT system: P comes
+    from the FP32 sweeps, and the corrections, which reuse K_t, P_t and M_uu^-1
+    of the solve, update p consistently with lambda = -(P x + p) at that P)."""
+    prob = workloads.make_problem(12, 4, 256, seed=77, rho_max=1.02, cross=True)
+    ref = oracle.riccati(prob)
+    out = host(solver.solve(to_dev(prob), num_segments=16, prec="mixed_fp32", max_refine=6, tol=1e-11,
+                            want=("K", "k", "x", "u", "lam", "P", "p")))
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    errs = {k: oracle.rel_err(out[k], ref[k]) for k in ("x", "u", "lam", "p", "P")}
+    print("mixed_fp32 with P", errs, rep["refine_iters"])
+    for k in ("x", "u", "lam"):
+        assert errs[k] < 1e-9, errs
+    assert errs["p"] < 1e-4 and errs["P"] < 1e-4, errs
+
+
 def test_mixed_fp32_unsupported_forms(solver):
     from paper_1809_06360_gb300 import lqr
     prob = workloads.config0()
