@@ -35,6 +35,7 @@ namespace {
 
 constexpr int kCorrBlock = 256;
 constexpr int kLinkDepth = 3;  // Psi_j ring depth of the link chains
+constexpr int kLinkSplit = 4;  // threads per output of a link step (partial sums over l)
 
 __device__ __forceinline__ bool corr_exit(const CorrArgs& a, int* s_flag) {
   if (threadIdx.x == 0) *s_flag = (*(volatile int*)a.status != 0) || (a.skip && *(volatile const int*)a.skip);
@@ -84,58 +85,53 @@ __host__ __device__ inline CorrSlot corr_slot(int n, int m) {
 
 size_t corr_seg_smem_bytes(int n, int m) { return sizeof(float) * (2 * (size_t)corr_slot(n, m).size + 4 * n + 2 * m); }
 size_t corr_psi_smem_bytes(int n, int m) {
-  return sizeof(float) * ((size_t)3 * n * (n + 1) + (size_t)n * (m + 1) + (size_t)m * (n + 1));
+  const size_t N = (n + 3) & ~3, M = (m + 3) & ~3;
+  return sizeof(float) * (3 * N * (N + 4) + N * (M + 4) + M * (N + 4));
 }
-size_t corr_link_smem_bytes(int n) { return sizeof(float) * ((size_t)kLinkDepth * n * (n + 1) + 2 * n); }
+size_t corr_link_smem_bytes(int n) {
+  return sizeof(float) * ((size_t)kLinkDepth * n * (n + 1) + (1 + kLinkSplit) * (size_t)n);
+}
 
-// Psi_j = Phi_{e-1} ... Phi_b, Phi_t = A_t + B_t K_t: one CTA per segment.
+// Psi_j = Phi_{e-1} ... Phi_b, Phi_t = A_t + B_t K_t: one CTA per segment, the
+// two products of a stage on 4 x 4 register tiles (n, m padded to multiples of
+// 4 with zeros; row strides N + 4, M + 4), A_t staged in the free Psi buffer.
 __global__ void __launch_bounds__(kCorrBlock) corr_psi_kernel(CorrArgs a) {
   extern __shared__ __align__(16) float csm[];
   __shared__ int s_flag;
   if (corr_exit(a, &s_flag)) return;
   const int n = a.n, m = a.m, j = blockIdx.x;
   const int b = seg_begin(a.T, a.nseg, j), e = seg_begin(a.T, a.nseg, j + 1);
-  const int ldn = n + 1, ldm = m + 1;
-  float* Psi = csm;
-  float* Phi = Psi + n * ldn;
-  float* Tmp = Phi + n * ldn;
-  float* Bs = Tmp + n * ldn;
-  float* Ks = Bs + n * ldm;
-  for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
-    const int i = x / n, l = x - i * n;
-    Psi[i * ldn + l] = (i == l) ? 1.0f : 0.0f;
-  }
+  const int N = (n + 3) & ~3, M = (m + 3) & ~3, LD = N + 4, LDm = M + 4;
+  float* X = csm;            // Psi so far
+  float* Y = X + N * LD;     // free: A_t, then Phi_t Psi
+  float* Phi = Y + N * LD;
+  float* Bs = Phi + N * LD;  // N x LDm
+  float* Ks = Bs + N * LDm;  // M x LD
+  const int total = 3 * N * LD + N * LDm + M * LD;
+  for (int x = threadIdx.x; x < total; x += blockDim.x) csm[x] = 0.0f;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[i * LD + i] = 1.0f;
   const long long nn = (long long)n * n, nm = (long long)n * m;
   for (int t = b; t < e; ++t) {
-    copy_pad(Bs, ldm, a.B + nm * t, n, m);
-    copy_pad(Ks, ldn, a.K + nm * t, m, n);
+    copy_pad(Y, LD, a.A + nn * t, n, n);
+    copy_pad(Bs, LDm, a.B + nm * t, n, m);
+    copy_pad(Ks, LD, a.K + nm * t, m, n);
     cp_async_commit();
     cp_async_wait<0>();
+    __syncthreads();  // stage data in; the previous stage's products are finished
+    cta_mm4f<false>(N, N, M, Bs, LDm, Ks, LD, [&](int i, int l, float v) {
+      Phi[i * LD + l] = (i < n && l < n) ? v + Y[i * LD + l] : 0.0f;
+    });
     __syncthreads();
-    // Phi = A_t + B_t K_t (A read straight from global: once per element)
-    for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
-      const int i = x / n, l = x - i * n;
-      float v = a.A[nn * t + x];
-      for (int c = 0; c < m; ++c) v = fmaf(Bs[i * ldm + c], Ks[c * ldn + l], v);
-      Phi[i * ldn + l] = v;
-    }
+    cta_mm4f<false>(N, N, N, Phi, LD, X, LD, [&](int i, int l, float v) { Y[i * LD + l] = v; });
     __syncthreads();
-    for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
-      const int i = x / n, l = x - i * n;
-      float v = 0.0f;
-      for (int c = 0; c < n; ++c) v = fmaf(Phi[i * ldn + c], Psi[c * ldn + l], v);
-      Tmp[i * ldn + l] = v;
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
-      const int i = x / n, l = x - i * n;
-      Psi[i * ldn + l] = Tmp[i * ldn + l];
-    }
-    __syncthreads();
+    float* tmp = X;
+    X = Y;
+    Y = tmp;
   }
   for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
     const int i = x / n, l = x - i * n;
-    a.Psi[nn * j + x] = Psi[i * ldn + l];
+    a.Psi[nn * j + x] = X[i * LD + l];
   }
 }
 
@@ -310,16 +306,23 @@ __global__ void __launch_bounds__(kCorrBlock) corr_fwd_kernel(CorrArgs a, int mo
 
 // The link chains, one CTA. dir 0: pb[K] = q~_T, pb[j] = Psi_j'pb[j + 1] + eps_j
 // (j = K-1 .. 0). dir 1: xb[0] = x0~, xb[j + 1] = Psi_j xb[j] + delta_j. Psi_j
-// arrive through a ring of kLinkDepth slots, kLinkDepth - 1 links ahead.
+// arrive through a ring of kLinkDepth slots, kLinkDepth - 1 links ahead; each
+// output of a step is summed by kLinkSplit threads over a quarter of l each
+// (output index fastest over the threads: conflict-free reads of Psi's rows and
+// columns at the odd row stride), the partial sums combined through shared memory.
 __global__ void __launch_bounds__(kCorrBlock) corr_link_kernel(CorrArgs a, int dir) {
   extern __shared__ __align__(16) float csm[];
   __shared__ int s_flag;
   if (corr_exit(a, &s_flag)) return;
   const int n = a.n, K = a.nseg, ldn = n + 1;
   const long long nn = (long long)n * n;
+  constexpr int kRows = kCorrBlock / kLinkSplit;  // outputs per pass of the thread block
   float* ring = csm;
   float* v = ring + kLinkDepth * n * ldn;
-  float* w = v + n;
+  float* part = v + n;  // [kLinkSplit][n]
+  const int q = (int)threadIdx.x / kRows, r0 = (int)threadIdx.x % kRows;
+  const int chunk = (n + kLinkSplit - 1) / kLinkSplit;
+  const int l0 = q * chunk < n ? q * chunk : n, l1 = (q + 1) * chunk < n ? (q + 1) * chunk : n;
   auto link_of = [&](int idx) { return dir == 0 ? K - 1 - idx : idx; };
   auto issue = [&](int idx) {
     if (idx < K) copy_pad(ring + (idx % kLinkDepth) * n * ldn, ldn, a.Psi + nn * link_of(idx), n, n);
@@ -337,20 +340,22 @@ __global__ void __launch_bounds__(kCorrBlock) corr_link_kernel(CorrArgs a, int d
     __syncthreads();  // Psi of this link in its slot; v complete
     const float* Ps = ring + (idx % kLinkDepth) * n * ldn;
     const int jl = link_of(idx);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      float acc;
-      if (dir == 0) {
-        acc = a.eps[(long long)n * jl + i];
-        for (int l = 0; l < n; ++l) acc = fmaf(Ps[l * ldn + i], v[l], acc);
-      } else {
-        acc = a.delta[(long long)n * jl + i];
-        for (int l = 0; l < n; ++l) acc = fmaf(Ps[i * ldn + l], v[l], acc);
-      }
-      w[i] = acc;
-      out[(long long)n * (dir == 0 ? jl : jl + 1) + i] = acc;
+    for (int i = r0; i < n; i += kRows) {
+      float acc = 0.0f;
+      if (dir == 0)
+        for (int l = l0; l < l1; ++l) acc = fmaf(Ps[l * ldn + i], v[l], acc);
+      else
+        for (int l = l0; l < l1; ++l) acc = fmaf(Ps[i * ldn + l], v[l], acc);
+      part[q * n + i] = acc;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float acc = dir == 0 ? a.eps[(long long)n * jl + i] : a.delta[(long long)n * jl + i];
+#pragma unroll
+      for (int g = 0; g < kLinkSplit; ++g) acc += part[g * n + i];
+      v[i] = acc;
+      out[(long long)n * (dir == 0 ? jl : jl + 1) + i] = acc;
+    }
   }
   cp_async_wait<0>();
 }
