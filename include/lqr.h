@@ -70,9 +70,12 @@ typedef enum {
   LQR_FP32 = 1,       /* FP32 data and arithmetic, sweeps and link solve alike               */
   LQR_MIXED_TF32 = 2, /* FP64 data; FP32 sweeps, FP64 factor/link solve, FP64 KKT refinement */
   LQR_MIXED_BF16 = 3, /* reserved (LQR_ERR_UNSUPPORTED)                                      */
-  LQR_MIXED_FP32 = 4  /* FP64 data and solution; the solve and every refinement correction run
-                         the LQR_FP32 path on an FP32 copy of the data (LQR_FORM_MULTIPLIER
-                         only), the FP64 KKT residual drives iterative refinement to opts.tol */
+  LQR_MIXED_FP32 = 4  /* FP64 data and solution; the solve runs the LQR_FP32 path on an FP32
+                         copy of the data (LQR_FORM_MULTIPLIER only) and the FP64 KKT residual
+                         drives iterative refinement to opts.tol. Where the FP32 fast sweeps
+                         apply, each correction reuses the solve's K_t, P_t and M_uu^-1
+                         (vector-only passes over the same segments; the handle then holds
+                         (T+1) n^2 + T m^2 + K n^2 more floats), else it is a whole FP32 solve */
 } lqr_precision;
 
 /* How a segment carries its unknown end state (both reach the same summary
