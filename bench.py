@@ -40,7 +40,7 @@ PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 80.5
 
 # bytes per launch (read + write) measured by ncu on the default FP32 workload;
 # an entry is removed whenever its kernel changes
-NCU_TRAFFIC: dict = {"seg_sweep_f32_kernel": (226.00e6 + 250.49e6) / 2}  # A1 and A4 launches, averaged
+NCU_TRAFFIC: dict = {}  # none taken for the kernels as they now stand
 
 
 def link_flops(n: int, K: int) -> float:
