@@ -9,9 +9,6 @@
 
 namespace lqr {
 
-template <typename T>
-__device__ __forceinline__ T ld_val(const T* p) { return *p; }
-
 // ---------------------------------------------------------------------------
 // Matrix product with a per-element epilogue.
 //   acc(i,j) = sum_k opA(i,k) * opB(k,j),  0 <= i < M, 0 <= j < N
@@ -528,32 +525,6 @@ __host__ __device__ inline int p4_shape(int d) {
   if (d4 <= 88) return 2;
   if (d4 <= 128 && d4 % 8 == 0) return 3;
   return -1;
-}
-
-// In-register inverse of the 4 x 4 SPD matrix m (row-major) by the sweep
-// operator: m <- m^-1. bad |= a pivot that is not positive and finite.
-template <typename T>
-__device__ __forceinline__ void inv4_spd(T m[16], bool& bad) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const T p = m[j * 4 + j];
-    bad |= !(p > T(0) && isfinite(p));
-    const T r = recip_fast(p);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (i != j && k != j) m[i * 4 + k] = fma(-m[i * 4 + j] * r, m[j * 4 + k], m[i * 4 + k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (k != j) m[j * 4 + k] *= r;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (i != j) m[i * 4 + j] *= r;
-    m[j * 4 + j] = -r;
-  }
-#pragma unroll
-  for (int e = 0; e < 16; ++e) m[e] = -m[e];
 }
 
 // In-register lower Cholesky factor L of the 4 x 4 SPD matrix m (row-major,
