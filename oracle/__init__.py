@@ -15,6 +15,10 @@ segment_summary(...)     the endpoint-constrained segment problem of Section II-
                          (Eq. 8) solved by a dense KKT solve with the two end states
                          as parameters; returns the quadratic cost_to_go(x, x_term)
                          of Eq. 9 at the segment start: (Vxx, Vzx, Vzz, vx, vz, v0).
+segment_dual_summary(...) the same segment problem with its end-point constraint
+                         dualised (end cost mu'x_term): the dual value
+                         G(x_s, mu) = 1/2 x_s'P x_s + mu'Z x_s - 1/2 mu'W mu + p'x_s + w'mu,
+                         by a dense KKT solve with (x_s, mu) as parameters.
 kkt_residual(prob, ...)  the residual of Eq. 3 and its normwise backward error.
 """
 from __future__ import annotations
@@ -221,6 +225,73 @@ def segment_summary(prob: dict, t0: int, t1: int) -> dict:
     v0 = 0.5 * w0 @ H @ w0 + g @ w0
     return dict(Vxx=Vxx, Vzx=Vzx, Vzz=Vzz, vx=vx, vz=vz, v0=float(v0),
                 Vxz_from_init=-nu_init[:, 1 + n:])
+
+
+def segment_dual_summary(prob: dict, t0: int, t1: int) -> dict:
+    """The segment problem of Eq. 8 with its end-point constraint dualised:
+    stages t0..t1-1, x_{t0} = x_s, no end constraint and, in place of it, the
+    linear end cost mu'x_{t1} (mu the end multiplier of Eq. 10). Its optimal
+    value is the quadratic
+        G(x_s, mu) = 1/2 x_s'P x_s + mu'Z x_s - 1/2 mu'W mu + p'x_s + w'mu + g0,
+    and J(x_s, z) of Eq. 9 is max_mu G(x_s, mu) - mu'z. Solved by a dense KKT
+    solve with (x_s, mu) as right-hand-side parameters; the blocks are read off
+    through dG/dx_s = -nu_init (the multiplier of x_{t0} = x_s, sign of Eq. 3)
+    and dG/dmu = x_{t1} at the optimum. Returns P, Z, W, p, w, and Zt_from_init,
+    the transpose of Z as it appears in dG/dx_s (equal to Z' in exact
+    arithmetic)."""
+    n, m, T = _dims(prob)
+    if not (0 <= t0 < t1 <= T):
+        raise ValueError("bad segment")
+    L = t1 - t0
+    A, B, c, Q, R, S, q, r = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r"))
+    Q = _sym(Q)
+    R = _sym(R)
+    nx = (L + 1) * n
+    nw = nx + L * m
+    nc = (L + 1) * n
+    H = np.zeros((nw, nw))
+    g = np.zeros(nw)
+    C = np.zeros((nc, nw))
+    d0 = np.zeros(nc)
+
+    def xs(i):
+        return slice(i * n, (i + 1) * n)
+
+    def us(i):
+        return slice(nx + i * m, nx + (i + 1) * m)
+
+    for i in range(L):
+        t = t0 + i
+        H[xs(i), xs(i)] = Q[t]
+        H[us(i), us(i)] = R[t]
+        H[us(i), xs(i)] = S[t]
+        H[xs(i), us(i)] = S[t].T
+        g[xs(i)] = q[t]
+        g[us(i)] = r[t]
+        rows = slice((i + 1) * n, (i + 2) * n)
+        C[rows, xs(i + 1)] = np.eye(n)
+        C[rows, xs(i)] = -A[t]
+        C[rows, us(i)] = -B[t]
+        d0[rows] = c[t]
+    C[0:n, xs(0)] = np.eye(n)  # x_{t0} = x_s
+    Kmat = np.block([[H, C.T], [C, np.zeros((nc, nc))]])
+    # right-hand sides: [zero parameters | x_s = e_i | mu = e_i]; mu enters the
+    # gradient of the end state, so its columns sit in the stationarity rows
+    rhs = np.zeros((nw + nc, 1 + 2 * n))
+    rhs[:nw, 0] = -g
+    rhs[nw:, 0] = d0
+    for i in range(n):
+        rhs[nw + i, 1 + i] = 1.0
+        rhs[L * n + i, 1 + n + i] = -1.0
+    sol = np.linalg.solve(Kmat, rhs)
+    nu_init = sol[nw:nw + n]   # (n, 1+2n): -dG/dx_s
+    x_end = sol[L * n:nx]      # (n, 1+2n):  dG/dmu
+    P = -nu_init[:, 1:1 + n]
+    p = -nu_init[:, 0]
+    Z = x_end[:, 1:1 + n]
+    W = -x_end[:, 1 + n:]
+    w = x_end[:, 0]
+    return dict(P=P, Z=Z, W=W, p=p, w=w, Zt_from_init=-nu_init[:, 1 + n:])
 
 
 def kkt_blocks_residual(prob: dict, x, u, lam):

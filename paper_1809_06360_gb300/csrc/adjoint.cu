@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) adjoint_grad_kernel(int n, int m, int 
 template <typename TS>
 cudaError_t launch_adjoint_rhs(int n, int m, int T, const void* gx, const void* gu, void* q, void* r, void* c,
                                void* x0, cudaStream_t st) {
-  adjoint_rhs_kernel<TS><<<2 * 152, 256, 0, st>>>(n, m, T, static_cast<const TS*>(gx), static_cast<const TS*>(gu),
+  adjoint_rhs_kernel<TS><<<2 * device_sm_count(), 256, 0, st>>>(n, m, T, static_cast<const TS*>(gx), static_cast<const TS*>(gu),
                                                   static_cast<TS*>(q), static_cast<TS*>(r), static_cast<TS*>(c),
                                                   static_cast<TS*>(x0));
   return cudaGetLastError();
@@ -106,7 +106,7 @@ cudaError_t launch_adjoint_rhs(int n, int m, int T, const void* gx, const void* 
 template <typename TS>
 cudaError_t launch_adjoint_grad(int n, int m, int T, const void* x, const void* u, const void* lam, const void* xix,
                                 const void* xiu, const void* xil, const lqr_problem* g, cudaStream_t st) {
-  const int grid = T < 4 * 152 ? T : 4 * 152;
+  const int grid = T < 4 * device_sm_count() ? T : 4 * device_sm_count();
   adjoint_grad_kernel<TS><<<grid, kBlock, 0, st>>>(
       n, m, T, static_cast<const TS*>(x), static_cast<const TS*>(u), static_cast<const TS*>(lam),
       static_cast<const TS*>(xix), static_cast<const TS*>(xiu), static_cast<const TS*>(xil),

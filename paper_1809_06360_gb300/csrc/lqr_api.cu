@@ -6,11 +6,30 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "lqr_internal.cuh"
 
 using namespace lqr;
 
 namespace lqr {
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  int v = cache[dev].load(std::memory_order_acquire);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  cache[dev].store(v, std::memory_order_release);
+  return v;
+}
+
 cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
   struct Entry { const void* f; int dev; size_t bytes; };
   static Entry table[64];

@@ -200,6 +200,9 @@ __device__ __forceinline__ T* plan_ptr(const SweepPlan& P, int b, unsigned char*
   return reinterpret_cast<T*>(((P.smem_mask >> b) & 1u) ? smem + P.off[b] : scratch + P.off[b]);
 }
 
+// Multiprocessor count of the current device (looked up once per device).
+int device_sm_count();
+
 // Raises (never lowers) a kernel's dynamic shared-memory limit; one registry
 // for all launchers of the same kernel (lqr_api.cu).
 cudaError_t raise_dyn_smem(const void* func, size_t bytes);
@@ -291,7 +294,9 @@ cudaError_t launch_adjoint_grad(int n, int m, int T, const void* x, const void* 
                                 const void* xiu, const void* xil, const lqr_problem* g, cudaStream_t st);
 
 // refinement (refine.cu)
-constexpr int kResidAccDoubles = 8 + 4 * 152;
+// per-CTA objective partials of the residual pass: at most kMaxResidBlocks CTAs
+constexpr int kMaxResidBlocks = 1024;
+constexpr int kResidAccDoubles = 8 + kMaxResidBlocks;
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
                                 const int* skip, cudaStream_t st);

@@ -24,7 +24,7 @@ __global__ void convert_kernel(ConvTable<S, D> tab, const int* skip) {
 template <typename S, typename D>
 cudaError_t launch_convert(const ConvTable<S, D>& tab, const int* skip, cudaStream_t st) {
   if (tab.count == 0) return cudaSuccess;
-  convert_kernel<S, D><<<4 * 152, 256, 0, st>>>(tab, skip);
+  convert_kernel<S, D><<<4 * device_sm_count(), 256, 0, st>>>(tab, skip);
   return cudaGetLastError();
 }
 
@@ -40,10 +40,14 @@ __global__ void refine_update_f32_kernel(ProbDesc pd, const float* dk, const flo
   double* u = static_cast<double*>(pd.u);
   double* l = static_cast<double*>(pd.lam);
   double* p = static_cast<double*>(pd.p);
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nx; e += (size_t)gridDim.x * blockDim.x) {
-    if (x) x[e] -= (double)dx[e];
-    if (l) l[e] -= (double)dl[e];
-    if (p && dp) p[e] -= (double)dp[e];
+  // x, lambda, p have (T+1) n entries and u, k have T m: either may be the longer
+  const size_t ne = nx > nu ? nx : nu;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nx) {
+      if (x) x[e] -= (double)dx[e];
+      if (l) l[e] -= (double)dl[e];
+      if (p && dp) p[e] -= (double)dp[e];
+    }
     if (e < nu) {
       if (u) u[e] -= (double)du[e];
       if (k) k[e] -= (double)dk[e];
@@ -54,7 +58,7 @@ __global__ void refine_update_f32_kernel(ProbDesc pd, const float* dk, const flo
 
 cudaError_t launch_refine_update_f32(const ProbDesc& pd, const float* dk, const float* dx, const float* du,
                                      const float* dl, const float* dp, const int* skip, cudaStream_t st) {
-  refine_update_f32_kernel<<<2 * 152, 256, 0, st>>>(pd, dk, dx, du, dl, dp, skip);
+  refine_update_f32_kernel<<<2 * device_sm_count(), 256, 0, st>>>(pd, dk, dx, du, dl, dp, skip);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@
 // launch produces eta, rel and the objective.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kkt_stage.cuh"
 #include "lqr_internal.cuh"
 
@@ -282,11 +284,10 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_noalloc_kernel(NoallocArg
   }
 }
 
-struct DeviceScratch {
-  double* ptr;
-  bool ready;
-};
-static DeviceScratch g_dev_scratch[64];
+// Device address of g_noalloc_scratch per device, published with release
+// order once looked up (the lookup is idempotent, so two host threads making
+// the first call on a device at the same time both store the same address).
+static std::atomic<double*> g_dev_scratch[64];
 
 }  // namespace
 
@@ -300,12 +301,14 @@ extern "C" lqr_status lqr_kkt_residual_noalloc(const lqr_problem* p, const lqr_s
   if (p->n < 1 || p->m < 1 || p->T < 1 || p->n > 256 || p->m > 256) return LQR_ERR_INVALID_ARG;
   if (!p->A || !p->B || !p->c || !p->Q || !p->R || !p->q || !p->r || !p->x0) return LQR_ERR_INVALID_ARG;
   if (!s->x || !s->u || !s->lam) return LQR_ERR_INVALID_ARG;
-  if (prec != LQR_FP64 && prec != LQR_FP32 && prec != LQR_MIXED_TF32) return LQR_ERR_UNSUPPORTED;
+  // the mixed modes keep data and solution in FP64
+  if (prec != LQR_FP64 && prec != LQR_FP32 && prec != LQR_MIXED_TF32 && prec != LQR_MIXED_FP32)
+    return LQR_ERR_UNSUPPORTED;
   if (p->T > LQR_NOALLOC_MAX_STAGES) return LQR_ERR_CAPACITY;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LQR_ERR_CUDA;
-  DeviceScratch& ds = g_dev_scratch[dev];
-  if (!ds.ready) {
+  double* scratch = g_dev_scratch[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     // once per device, with that device current: the device address of the
     // scratch array (its host-side name is only a stand-in)
     void* ptr = nullptr;
@@ -313,27 +316,27 @@ extern "C" lqr_status lqr_kkt_residual_noalloc(const lqr_problem* p, const lqr_s
       cudaGetLastError();
       return LQR_ERR_CUDA;
     }
-    ds.ptr = static_cast<double*>(ptr);
-    ds.ready = true;
+    scratch = static_cast<double*>(ptr);
+    g_dev_scratch[dev].store(scratch, std::memory_order_release);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the reduction slots and the completion counter start at zero on every call
-  if (cudaMemsetAsync(ds.ptr + LQR_NOALLOC_MAX_STAGES + 1, 0, sizeof(double) * kNoallocSlots, st) != cudaSuccess)
+  if (cudaMemsetAsync(scratch + LQR_NOALLOC_MAX_STAGES + 1, 0, sizeof(double) * kNoallocSlots, st) != cudaSuccess)
     return LQR_ERR_CUDA;
   NoallocArgs a;
   a.A = p->A; a.B = p->B; a.c = p->c; a.Q = p->Q; a.R = p->R; a.S = p->S; a.q = p->q; a.r = p->r; a.x0 = p->x0;
   a.x = s->x; a.u = s->u; a.lam = s->lam;
   a.n = p->n; a.m = p->m; a.T = p->T;
-  const int grid = p->T < 4 * 152 ? p->T : 4 * 152;
+  const int grid = p->T < 4 * device_sm_count() ? p->T : 4 * device_sm_count();
   const int nc = kkt_stage_cols(p->n, p->m);
   size_t bytes = sizeof(double) * (6 * (size_t)p->n + 3 * (size_t)p->m);
   if (nc > 0) bytes = sizeof(double) * kkt_stage_smem_doubles(p->n, p->m);  // <= 45056 B: no opt-in needed
 #define LQR_NA_LAUNCH(NC)                                                  \
   do {                                                                     \
     if (prec == LQR_FP32)                                                  \
-      kkt_residual_noalloc_kernel<NC, float><<<grid, kBlock, bytes, st>>>(a, ds.ptr, out);  \
+      kkt_residual_noalloc_kernel<NC, float><<<grid, kBlock, bytes, st>>>(a, scratch, out);  \
     else                                                                   \
-      kkt_residual_noalloc_kernel<NC, double><<<grid, kBlock, bytes, st>>>(a, ds.ptr, out); \
+      kkt_residual_noalloc_kernel<NC, double><<<grid, kBlock, bytes, st>>>(a, scratch, out); \
   } while (0)
   switch (nc) {
     case 1: LQR_NA_LAUNCH(1); break;

@@ -358,10 +358,14 @@ __global__ void refine_update_kernel(ProbDesc pd, const double* dk, const double
   TS* u = static_cast<TS*>(pd.u);
   TS* l = static_cast<TS*>(pd.lam);
   TS* p = static_cast<TS*>(pd.p);
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nx; e += (size_t)gridDim.x * blockDim.x) {
-    if (x) x[e] = static_cast<TS>((double)x[e] - dx[e]);
-    if (l) l[e] = static_cast<TS>((double)l[e] - dl[e]);
-    if (p) p[e] = static_cast<TS>((double)p[e] - dp[e]);
+  // x, lambda, p have (T+1) n entries and u, k have T m: either may be the longer
+  const size_t ne = nx > nu ? nx : nu;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ne; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nx) {
+      if (x) x[e] = static_cast<TS>((double)x[e] - dx[e]);
+      if (l) l[e] = static_cast<TS>((double)l[e] - dl[e]);
+      if (p) p[e] = static_cast<TS>((double)p[e] - dp[e]);
+    }
     if (e < nu) {
       if (u) u[e] = static_cast<TS>((double)u[e] - du[e]);
       if (k) k[e] = static_cast<TS>((double)k[e] - dk[e]);
@@ -370,7 +374,11 @@ __global__ void refine_update_kernel(ProbDesc pd, const double* dk, const double
   if (blockIdx.x == 0 && threadIdx.x == 0) pd.report[3] += 1.0;
 }
 
-int residual_grid(int T) { return T < 4 * 152 ? T : 4 * 152; }
+int residual_grid(int T) {
+  int g = 4 * device_sm_count();
+  if (g > kMaxResidBlocks) g = kMaxResidBlocks;
+  return T < g ? T : g;
+}
 
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
@@ -415,7 +423,7 @@ cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol
 template <typename TS>
 cudaError_t launch_refine_update(const ProbDesc& pd, const double* dk, const double* dx, const double* du,
                                  const double* dl, const double* dp, const int* skip, cudaStream_t st) {
-  refine_update_kernel<TS><<<2 * 152, 256, 0, st>>>(pd, dk, dx, du, dl, dp, skip);
+  refine_update_kernel<TS><<<2 * device_sm_count(), 256, 0, st>>>(pd, dk, dx, du, dl, dp, skip);
   return cudaGetLastError();
 }
 

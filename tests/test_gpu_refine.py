@@ -105,13 +105,77 @@ def test_mixed_host_entry_point(solver):
     assert oracle.rel_err(out["x"], ref["x"]) < 1e-9
 
 
+@pytest.mark.parametrize("prec", ["mixed", "mixed_fp32"])
+@pytest.mark.parametrize("n,m,T,K", [(3, 5, 20, 4), (8, 16, 96, 8), (2, 9, 40, 5)])
+def test_refinement_with_more_controls_than_states(solver, prec, n, m, T, K):
+    """m > n: T m entries of u and k exceed the (T + 1) n entries of x and
+    lambda, and every one of them must take the refinement update. The FP32
+    solve leaves ~1e-6 errors, so a u entry the update skipped stays visibly
+    wrong (x, u, lambda at 1e-9 against the oracle). Each correction satisfies
+    du_t = K_t dx_t + dk_t, so refinement leaves d_t = u_t - K_t x_t - k_t as the
+    unrefined solve had it (FP64 rounding in the mixed mode, FP32 rounding of the
+    FP32 rollout in mixed_fp32); a k entry the update skipped would move d_t by
+    its correction."""
+    prob = workloads.make_problem(n, m, T, seed=500 + n * m, rho_max=1.02, cross=True)
+    ref = oracle.riccati(prob)
+    dev = to_dev(prob)
+    out0 = host(solver.solve(dev, num_segments=K, prec=prec, max_refine=0))
+    out = host(solver.solve(dev, num_segments=K, prec=prec, max_refine=6, tol=1e-12))
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    errs = {k: oracle.rel_err(out[k], ref[k]) for k in ("x", "u", "lam", "k", "K")}
+    print("%s m>n (%d,%d,%d,K=%d) errors %s iters %d rel %.2e" % (prec, n, m, T, K, errs, rep["refine_iters"],
+                                                                  rep["kkt_rel"]))
+    assert rep["refine_iters"] >= 1
+    for k in ("x", "u", "lam"):
+        assert errs[k] < 1e-9, errs
+    assert errs["K"] < 1e-4 and errs["k"] < 1e-3
+    assert np.array_equal(out["K"], out0["K"])
+    d0 = out0["u"] - np.einsum("tij,tj->ti", out0["K"], out0["x"][:-1]) - out0["k"]
+    d = out["u"] - np.einsum("tij,tj->ti", out["K"], out["x"][:-1]) - out["k"]
+    assert np.abs(d - d0).max() <= 1e-10 * np.abs(out["u"]).max()
+    assert rep["kkt_rel"] <= 1e-12
+
+
+def _launches_per_correction(solver, prob, K):
+    """Kernels one refinement correction enqueues (every correction is enqueued
+    up to max_refine; a converged one returns at once on the device)."""
+    dev = to_dev(prob)
+    counts = []
+    for it in (1, 2):
+        solver.solve(dev, num_segments=K, prec="mixed_fp32", max_refine=it, tol=0.0)
+        counts.append(solver.last_launch_count())
+    return counts[1] - counts[0]
+
+
+def test_mixed_fp32_correction_paths(solver):
+    """Which correction path a shape takes. n=64, m=32: corrections reuse the
+    solve's K_t, P_t and M_uu^-1 (residual, finalize, conversion, six vector
+    passes, update: 10 kernels each). n=72, m=32: the FP32 fast sweep's plan
+    does not fit in shared memory, so each correction is a whole FP32 solve
+    (more kernels); both reach the oracle at 1e-9."""
+    reuse = workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02)
+    assert _launches_per_correction(solver, reuse, 16) == 10
+    fallback = workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02)
+    assert _launches_per_correction(solver, fallback, 16) > 10
+    for prob, K in ((reuse, 16), (fallback, 16)):
+        ref = oracle.riccati(prob)
+        out = host(solver.solve(to_dev(prob), num_segments=K, prec="mixed_fp32", max_refine=8, tol=1e-11))
+        rep = solver.report()
+        assert rep["status"] == 0, rep
+        for k in ("x", "u", "lam"):
+            assert oracle.rel_err(out[k], ref[k]) < 1e-9, (prob["B"].shape, k, oracle.rel_err(out[k], ref[k]))
+
+
 @pytest.mark.parametrize("K", [64, 152])
 def test_mixed_fp32_config1(solver, K):
-    """LQR_MIXED_FP32: FP64 data; the solve and each correction run the FP32
-    path (FP32 sweeps, FP32 M_uu inverse, FP32 link scan) on an FP32 copy of the
-    data; the FP64 KKT residual drives refinement to |r|/|b| <= 1e-10. x, u and
-    lambda reach the oracle at 1e-9; K keeps FP32 accuracy (1e-4), k stays
-    consistent with the refined trajectory."""
+    """LQR_MIXED_FP32: FP64 data; the solve runs the FP32 path (FP32 sweeps,
+    FP32 M_uu inverse, FP32 link scan) on an FP32 copy of the data, and each
+    correction reuses its K_t, P_t and M_uu^-1 (vector-only passes over the
+    same segments; test_mixed_fp32_correction_paths pins which path runs); the
+    FP64 KKT residual drives refinement to |r|/|b| <= 1e-10. x, u and lambda
+    reach the oracle at 1e-9; K keeps FP32 accuracy (1e-4), k stays consistent
+    with the refined trajectory."""
     prob = workloads.config1()
     ref = oracle.riccati(prob)
     out = host(solver.solve(to_dev(prob), num_segments=K, prec="mixed_fp32", max_refine=6, tol=1e-10))

@@ -162,3 +162,97 @@ def test_double_integrator_split_equals_serial():
     z = np.linalg.solve(M, rhs).reshape(J - 1, n)
     for j in range(1, J):
         assert np.abs(z[j - 1] - ric["x"][bnd[j]]).max() < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# The dualised segment summary (end cost mu'x_term instead of x_term = z)
+# ---------------------------------------------------------------------------
+
+def _condensed_dual_value(prob, t0, t1, xs, mu):
+    """min over u_{t0..t1-1} of the segment cost plus mu'x_{t1}, x_{t0} = xs, by
+    eliminating the states (no end constraint: one unconstrained solve in u)."""
+    A, B, c, Q, R, S, q, r = (prob[k] for k in ("A", "B", "c", "Q", "R", "S", "q", "r"))
+    T, n, m = B.shape
+    L = t1 - t0
+    xa, G = xs.copy(), np.zeros((n, L * m))
+    Hu = np.zeros((L * m, L * m))
+    gu = np.zeros(L * m)
+    const = 0.0
+    for i in range(L):
+        t = t0 + i
+        E = np.zeros((m, L * m))
+        E[:, i * m:(i + 1) * m] = np.eye(m)
+        Qs = 0.5 * (Q[t] + Q[t].T)
+        Rs = 0.5 * (R[t] + R[t].T)
+        Hu += G.T @ Qs @ G + E.T @ S[t] @ G + G.T @ S[t].T @ E + E.T @ Rs @ E
+        gu += G.T @ (Qs @ xa + q[t]) + E.T @ (S[t] @ xa + r[t])
+        const += 0.5 * xa @ Qs @ xa + q[t] @ xa
+        xa = A[t] @ xa + c[t]
+        G = A[t] @ G + B[t] @ E
+    gu = gu + G.T @ mu
+    const += mu @ xa
+    u = np.linalg.solve(Hu, -gu)
+    return 0.5 * u @ Hu @ u + gu @ u + const
+
+
+def _dual_quad(d, xs, mu):
+    return (0.5 * xs @ d["P"] @ xs + mu @ d["Z"] @ xs - 0.5 * mu @ d["W"] @ mu + d["p"] @ xs + d["w"] @ mu)
+
+
+@pytest.mark.parametrize("n,m,L,cross", [(2, 1, 3, False), (3, 1, 5, True), (4, 2, 4, True),
+                                         (4, 2, 1, False), (5, 2, 6, True), (3, 5, 2, True)])
+def test_dual_summary_vs_condensed_brute_force(n, m, L, cross):
+    """G(x_s, mu) - G(0, 0) from the dense KKT blocks equals the condensed
+    minimum at random points (the constant g0 drops out of the difference)."""
+    prob = workloads.make_problem(n, m, L + 3, seed=60 + n + L, cross=cross)
+    t0, t1 = 1, 1 + L
+    d = oracle.segment_dual_summary(prob, t0, t1)
+    z0 = np.zeros(n)
+    G0 = _condensed_dual_value(prob, t0, t1, z0, z0)
+    g = np.random.default_rng(1)
+    for _ in range(4):
+        xs = g.standard_normal(n)
+        mu = g.standard_normal(n)
+        ref = _condensed_dual_value(prob, t0, t1, xs, mu) - G0
+        assert abs(_dual_quad(d, xs, mu) - ref) <= 1e-9 * max(1.0, abs(ref))
+    for k in ("P", "W"):
+        assert np.abs(d[k] - d[k].T).max() <= 1e-9 * np.abs(d[k]).max()
+    # Z read from dG/dx_s and from dG/dmu agree; W is positive semidefinite
+    assert np.abs(d["Zt_from_init"] - d["Z"].T).max() <= 1e-9 * np.abs(d["Z"]).max()
+    assert np.linalg.eigvalsh(d["W"]).min() >= -1e-12 * np.abs(d["W"]).max()
+
+
+@pytest.mark.parametrize("n,m,T,t0,t1", [(4, 2, 12, 3, 8), (5, 2, 30, 0, 6), (6, 3, 24, 4, 8)])
+def test_dual_summary_equals_primal_by_legendre(n, m, T, t0, t1):
+    """J(x_s, z) = max_mu G(x_s, mu) - mu'z (Eq. 9 from the dual value): with
+    W invertible, Vzz = W^-1, Vzx = -W^-1 Z, Vxx = P + Z'W^-1 Z, vz = -W^-1 w,
+    vx = p + Z'W^-1 w. The two dense solves share no constraint rows."""
+    prob = workloads.make_problem(n, m, T, seed=70 + t0, cross=True)
+    d = oracle.segment_dual_summary(prob, t0, t1)
+    s = oracle.segment_summary(prob, t0, t1)
+    Wi = np.linalg.inv(d["W"])
+    assert oracle.rel_err(Wi, s["Vzz"]) < 1e-9
+    assert oracle.rel_err(-Wi @ d["Z"], s["Vzx"]) < 1e-9
+    assert oracle.rel_err(d["P"] + d["Z"].T @ Wi @ d["Z"], s["Vxx"]) < 1e-9
+    assert oracle.rel_err(-Wi @ d["w"], s["vz"]) < 1e-9
+    assert oracle.rel_err(d["p"] + d["Z"].T @ Wi @ d["w"], s["vx"]) < 1e-9
+
+
+@pytest.mark.parametrize("n,m,T,t0,t1", [(4, 2, 12, 3, 8), (6, 2, 20, 0, 9), (5, 5, 8, 2, 3),
+                                         (3, 5, 10, 1, 2)])
+def test_dual_summary_composes_with_serial_value_function(n, m, T, t0, t1):
+    """With the tail's value function V_{t1} = (P1, p1), the end multiplier is
+    mu = P1 x_{t1} + p1 and x_{t1} = Z x - W mu + w, so
+       P_{t0} = P + Z'P1 (I + W P1)^-1 Z,
+       p_{t0} = p + Z'(P1 (I + W P1)^-1 (w - W p1) + p1)
+    (the link recursion of the multiplier form), also for one-stage segments
+    and m > n, where W is singular or the primal summary does not exist."""
+    prob = workloads.make_problem(n, m, T, seed=80 + t0, cross=True)
+    ric = oracle.riccati(prob)
+    d = oracle.segment_dual_summary(prob, t0, t1)
+    P1, p1 = ric["P"][t1], ric["p"][t1]
+    M = np.eye(n) + d["W"] @ P1
+    P0 = d["P"] + d["Z"].T @ P1 @ np.linalg.solve(M, d["Z"])
+    p0 = d["p"] + d["Z"].T @ (P1 @ np.linalg.solve(M, d["w"] - d["W"] @ p1) + p1)
+    assert oracle.rel_err(P0, ric["P"][t0]) < 1e-9
+    assert oracle.rel_err(p0, ric["p"][t0]) < 1e-9

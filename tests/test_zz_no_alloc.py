@@ -34,7 +34,8 @@ def _structs(prob, sol):
     return p, s
 
 
-@pytest.mark.parametrize("prec,dtype", [("fp32", torch.float32), ("fp64", torch.float64)])
+@pytest.mark.parametrize("prec,dtype", [("fp32", torch.float32), ("fp64", torch.float64),
+                                        ("mixed_fp32", torch.float64)])
 def test_noalloc_residual_matches_solve_report(solver, prec, dtype):
     from paper_1809_06360_gb300 import lqr
     prob_np = workloads.make_problem(12, 4, 200, seed=77, cross=True)

@@ -96,12 +96,16 @@ def config2(T: int = 1024) -> dict:
 
 def config3_shapes(count: int = 4096, seed: int = 1003) -> list[tuple[int, int, int]]:
     """(n, m, T) per problem of the uneven batch: T~U{32..512}, n in {8,16,32,48},
-    m~U{2..16}, each drawn from the batch seed."""
+    m~U{2..16}, drawn problem by problem from the batch seed (so the first k
+    shapes of a batch of any size are the same)."""
     g = _rng(seed)
-    ns = g.choice(np.array([8, 16, 32, 48]), size=count)
-    ms = g.integers(2, 17, size=count)
-    Ts = g.integers(32, 513, size=count)
-    return [(int(a), int(b), int(c)) for a, b, c in zip(ns, ms, Ts)]
+    out = []
+    for _ in range(count):
+        n = int(g.choice(np.array([8, 16, 32, 48])))
+        m = int(g.integers(2, 17))
+        T = int(g.integers(32, 513))
+        out.append((n, m, T))
+    return out
 
 
 def config3(count: int = 4096) -> list[dict]:
