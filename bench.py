@@ -2,9 +2,15 @@
 """Throughput of the segment-parallel Riccati solve (LQR stages/s) on GB300.
 
 One step = one full solve (parametric segment sweeps, link solve, policy
-sweeps, rollout with multipliers and cost) of the long-horizon workload
-n=64, m=32, T=4096, rho(A_t) <= 1.02, on synthetic seeded data with inputs
-resident in HBM. Under torchrun every rank solves its own replica (the method
+sweeps, rollout with multipliers and cost, and in the refined modes the FP64
+KKT residual passes and refinement corrections) of one workload, on synthetic
+seeded data with inputs resident in HBM. The default workload is the long
+horizon n=64, m=32, T=4096, rho(A_t) <= 1.02, solved in LQR_MIXED_FP32 (FP32
+solve, FP64 residual, refinement to |r|/|b| <= 1e-10): an answer of FP64
+grade, compared with the plain FP64 segment-parallel solve of the same data
+on the same GPU at its best segment count. --config 2 runs the n=128, m=64,
+T=1024, K=64 mixed-precision workload; --config 0 the n=12, m=4, T=128, K=8
+FP64 workload. Under torchrun every rank solves its own replica (the method
 does not shard across GPUs); value = all ranks' stages / max-over-ranks time.
 
 --impl reference times the FP64 serial Riccati oracle on the host cores on a
@@ -156,24 +162,33 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(n, m, T_sample, prob_full, budget_s=12.0):
-    """The FP64 serial Riccati oracle on one host core over a T_sample-stage
-    prefix of the workload, repeated for about budget_s seconds."""
+def _prefix(prob, T_sample):
+    return {k: np.ascontiguousarray(v[:T_sample] if k in ("A", "B", "c", "R", "S", "r") else
+                                    (v[:T_sample + 1] if k in ("Q", "q") else v)) for k, v in prob.items()}
+
+
+def cpu_baseline(wl, prob_full, budget_s=12.0):
+    """The FP64 serial Riccati oracle on one host core: whole solves of the
+    workload when one takes at most a few seconds (their last result also
+    serves as the reference for the per-quantity errors of the GPU answer),
+    else runs over a prefix of the workload, repeated for about budget_s s."""
     import oracle
-    sample = {k: (v[:T_sample] if k in ("A", "B", "c", "R", "S", "r") else
-                  (v[:T_sample + 1] if k in ("Q", "q") else v)) for k, v in prob_full.items()}
-    sample = {k: np.ascontiguousarray(v) for k, v in sample.items()}
-    oracle.riccati(sample, want_P=False)  # load/build outside the timing
-    runs, t0 = 0, time.perf_counter()
+    n, m, T = wl["n"], wl["m"], wl["T"]
+    T_sample = wl["cpu_stages"]
+    sample = prob_full if T_sample >= T else _prefix(prob_full, T_sample)
+    oracle.riccati(_prefix(prob_full, 2), want_P=False)  # build/load outside the timing
+    runs, t0, ref = 0, time.perf_counter(), None
     while True:
-        oracle.riccati(sample, want_P=False)
+        ref = oracle.riccati(sample, want_P=True)
         runs += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return {"value": runs * T_sample / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d runs of the FP64 serial Riccati oracle (single thread, C) on the first %d stages "
-                      "of the n=%d m=%d workload, %.1f s" % (runs, T_sample, n, m, el)}
+    what = ("the whole %d-stage workload" % T) if T_sample >= T else ("the first %d stages of the workload" % T_sample)
+    out = {"value": runs * min(T_sample, T) / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d runs of the FP64 serial Riccati oracle (single thread, C) on %s (n=%d m=%d), %.1f s" %
+                     (runs, what, n, m, el)}
+    return out, (ref if T_sample >= T else None)
 
 
 def max_over_ranks(values, world, device):
@@ -195,17 +210,17 @@ def whole_job_rate(stages_per_replica_step: int, steps: int, world: int, seconds
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the oracle on host cores (rank 0 only)."""
+    """Reference arm: the oracle on host cores (rank 0 only), per step one
+    bounded sample of the workload."""
     if rank != 0:
         return
-    n, m, T = 64, 32, 4096
-    prob = workloads.config1(T)
-    T_sample = 256
+    wl = WORKLOADS[args.config]
+    n, m, T = wl["n"], wl["m"], wl["T"]
+    prob = wl["make"]()
+    T_sample = min(wl["ref_stages"], T)
     import oracle
-    oracle.riccati({k: np.ascontiguousarray(v[:8] if k in ("A", "B", "c", "R", "S", "r") else
-                                            (v[:9] if k in ("Q", "q") else v)) for k, v in prob.items()})
-    sample = {k: np.ascontiguousarray(v[:T_sample] if k in ("A", "B", "c", "R", "S", "r") else
-                                      (v[:T_sample + 1] if k in ("Q", "q") else v)) for k, v in prob.items()}
+    oracle.riccati(_prefix(prob, 2), want_P=False)
+    sample = prob if T_sample >= T else _prefix(prob, T_sample)
     for _ in range(args.warmup):
         oracle.riccati(sample, want_P=False)
     t0 = time.perf_counter()
@@ -213,12 +228,12 @@ def run_reference(args, rank, world):
         oracle.riccati(sample, want_P=False)
     el = time.perf_counter() - t0
     value = args.steps * T_sample / el
+    what = "the whole workload" if T_sample >= T else "a %d-stage prefix" % T_sample
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded PCG64)",
-            "config": {"workload": "long-horizon LQR n=64 m=32 T=4096 rho(A)<=1.02 (per step: a %d-stage "
-                                   "prefix, serial FP64 Riccati oracle on the host)" % T_sample,
+            "config": {"workload": "%s (per step: %s, serial FP64 Riccati oracle on the host)" % (wl["name"], what),
                        "n": n, "m": m, "T": T},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d steps x %d stages of the serial FP64 oracle, one thread" %
@@ -227,22 +242,47 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# The workloads a bench line can be quoted on (seeded synthetic data).
+WORKLOADS = {
+    1: dict(name="long-horizon LQR n=64 m=32 T=4096 rho(A)<=1.02", n=64, m=32, T=4096, K=0, prec="mixed_fp32",
+            make=lambda: workloads.config1(4096), Kgrid=(16, 64, 256, 1024), fp64_K=(64, 128, 152, 256),
+            cpu_stages=4096, ref_stages=256, unrefined="fp32"),
+    2: dict(name="mixed-precision LQR n=128 m=64 T=1024 rho(A)<=1.02", n=128, m=64, T=1024, K=64, prec="mixed",
+            make=lambda: workloads.config2(1024), Kgrid=(), fp64_K=(16, 32, 64), cpu_stages=1024, ref_stages=128,
+            unrefined="fp32"),
+    0: dict(name="single LQR n=12 m=4 T=128", n=12, m=4, T=128, K=8, prec="fp64", make=workloads.config0,
+            Kgrid=(1, 8, 16), fp64_K=(8,), cpu_stages=128, ref_stages=128, unrefined=None),
+}
+
+def _timed(stream, fn, reps):
+    """Mean device time (ms) of fn() over reps calls, CUDA events on stream."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "mixed", "mixed_fp32"])
+    ap.add_argument("--config", type=int, default=1, choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "mixed", "mixed_fp32"],
+                    help="default: the workload's (mixed_fp32 for the long horizon)")
     ap.add_argument("--tol", type=float, default=1e-10, help="refinement target |r|/|b| (mixed modes)")
-    ap.add_argument("--max-refine", type=int, default=6)
-    ap.add_argument("--segments", type=int, default=0, help="0 = the library's choice (one per SM)")
+    ap.add_argument("--max-refine", type=int, default=8)
+    ap.add_argument("--segments", type=int, default=0, help="0 = the workload's K (or the library's choice)")
     ap.add_argument("--form", default="multiplier", choices=["multiplier", "constrained"])
-    ap.add_argument("--T", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-fp64-ref", action="store_true", help="skip the plain FP64 comparison solve")
-    ap.add_argument("--fp64-segments", type=int, default=128)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparison, K grid and unrefined form")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -264,19 +304,23 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
 
-    n, m, T, K = 64, 32, args.T, args.segments
-    prob_np = workloads.config1(T)
-    dt = torch.float32 if args.prec == "fp32" else torch.float64
-    npdt = np.float32 if args.prec == "fp32" else np.float64
-    dev = {k: torch.from_numpy(v).to(f"cuda:{local}", dt) for k, v in prob_np.items()}
+    wl = WORKLOADS[args.config]
+    n, m, T = wl["n"], wl["m"], wl["T"]
+    K = args.segments or wl["K"]
+    prec = args.prec or wl["prec"]
+    prob_np = wl["make"]()
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    npdt = np.float32 if prec == "fp32" else np.float64
+    device = f"cuda:{local}"
+    dev = {k: torch.from_numpy(v).to(device, dt) for k, v in prob_np.items()}
     solver = lqr.Solver(local)
     out = solver.alloc_solution(dev, want=("K", "k", "x", "u", "lam"))
     stream = torch.cuda.current_stream()
 
-    mr = args.max_refine if args.prec.startswith("mixed") else 0
+    mr = args.max_refine if prec.startswith("mixed") else 0
 
     def step():
-        solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form, max_refine=mr, tol=args.tol)
+        solver.solve(dev, num_segments=K, prec=prec, out=out, form=args.form, max_refine=mr, tol=args.tol)
 
     for _ in range(args.warmup):
         step()
@@ -288,10 +332,10 @@ def main():
 
     # KKT residual of the benchmarked solution, by the library's own FP64 residual
     # pass (step A7), once, outside the timing
-    solver.solve(dev, num_segments=K, prec=args.prec, out=out, form=args.form, residual=True, max_refine=mr,
-                 tol=args.tol)
+    solver.solve(dev, num_segments=K, prec=prec, out=out, form=args.form, residual=True, max_refine=mr, tol=args.tol)
     rep_res = solver.report()
     res = {"eta": rep_res["kkt_residual"], "rel": rep_res["kkt_rel"], "iters": rep_res["refine_iters"]}
+    answer = {k: v.double().cpu().numpy() for k, v in out.items()}
 
     clocks = ClockSampler(local)
     if world > 1:
@@ -313,25 +357,26 @@ def main():
     ms = e0.elapsed_time(e1)
     phase_ms, nprof = lqr.lqr_profile_read(solver.h)
     lqr.lqr_profile_enable(solver.h, False)
-    ms = max_over_ranks([ms], world, f"cuda:{local}")[0]
+    ms = max_over_ranks([ms], world, device)[0]
     value = whole_job_rate(T, args.steps, world, ms / 1e3)
 
-    # per-phase achieved rates; the roofline entry is the phase that takes the most time
+    # per-phase achieved rates; the roofline entry is the kernel that takes the most time
     nsolve = max(nprof, 1)
     ph = {k: v / nsolve for k, v in phase_ms.items()}
-    fp64_pipe = args.prec == "fp64"
+    fp64_pipe = prec == "fp64"
     alu_peak = PEAK_FP64_TFLOPS if fp64_pipe else PEAK_FP32_TFLOPS
     hbm = measured_peaks().get("hbm_gbs", 6780.4)
     # the FP32 fast path (FP32 sweeps, link scan and rollout) also runs every
     # solve of the mixed FP32 mode, on its FP32 copy of the data
-    fast = args.prec in ("fp32", "mixed_fp32") and args.form == "multiplier"
-    es = 4 if fast else 8
+    fast = prec in ("fp32", "mixed_fp32") and args.form == "multiplier" and n <= 64
+    es = 4 if prec in ("fp32", "mixed_fp32") else 8
     sweep_k = "seg_sweep_f32_kernel" if fast else "seg_sweep_kernel"
-    if fast:
+    if fast and K > 1:
         link = {"kernel": "link_scan_kernel levels + feedback pass + link states (A3, FP32 scan)", "bound": "alu",
                 "unit": "TFLOP/s", "work": link_scan_flops(n, K), "peak": PEAK_FP32_TFLOPS}
     else:
-        link = {"kernel": "link_solve_dual_cluster_kernel (A3, FP64 block elimination)", "bound": "alu",
+        link = {"kernel": ("link_solve_dual_cluster_kernel" if n <= 67 else "link_solve_dual_kernel") +
+                          " (A3, FP64 block elimination)", "bound": "alu",
                 "unit": "TFLOP/s", "work": link_flops(n, K), "peak": PEAK_FP64_TFLOPS}
     phases = {
         "sweep": {"kernel": sweep_k + " phase 0 (A1)", "bound": "alu", "unit": "TFLOP/s",
@@ -365,7 +410,7 @@ def main():
     # DRAM traffic per launch of the dominant kernel from an ncu capture of this
     # workload (dram__bytes_read.sum + dram__bytes_write.sum), None when not taken
     # for the kernel as it now stands
-    traffic = NCU_TRAFFIC.get(dd["kernel"].split(" ")[0]) if args.prec == "fp32" else None
+    traffic = NCU_TRAFFIC.get((dd["kernel"].split(" ")[0], args.config, prec))
     roofline = {"bound": dd["bound"], "achieved": dd["achieved"], "peak": dd["peak"], "unit": dd["unit"],
                 "frac": dd["frac"], "traffic": traffic, "kernel": dd["kernel"],
                 "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2070 MHz" if dd["peak"] == PEAK_FP64_TFLOPS else
@@ -375,29 +420,59 @@ def main():
                            for k, d in phases.items()},
                 "phase_ms_per_step": ph}
 
-    # the plain FP64 segment-parallel solve of the same workload on the same GPU
-    fp64_ref = None
-    if not args.no_fp64_ref and args.prec != "fp64":
-        dev64 = {k: torch.from_numpy(v).to(f"cuda:{local}", torch.float64) for k, v in prob_np.items()}
+    extras = {}
+    if not args.no_extras:
+        # the plain FP64 segment-parallel solve of the same workload on the same GPU,
+        # at its best segment count
+        dev64 = dev if dt == torch.float64 else {k: torch.from_numpy(v).to(device, torch.float64)
+                                                 for k, v in prob_np.items()}
         out64 = solver.alloc_solution(dev64, want=("K", "k", "x", "u", "lam"))
-        for _ in range(2):
-            solver.solve(dev64, num_segments=args.fp64_segments, prec="fp64", out=out64)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        nref = 3
-        f0.record(stream)
-        for _ in range(nref):
-            solver.solve(dev64, num_segments=args.fp64_segments, prec="fp64", out=out64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1) / nref
-        solver.solve(dev64, num_segments=args.fp64_segments, prec="fp64", out=out64, residual=True)
+        sweep64 = {}
+        for Kf in wl["fp64_K"]:
+            f = lambda: solver.solve(dev64, num_segments=Kf, prec="fp64", out=out64)
+            f()
+            sweep64[Kf] = _timed(stream, f, 2)
+        Kbest = min(sweep64, key=sweep64.get)
+        f = lambda: solver.solve(dev64, num_segments=Kbest, prec="fp64", out=out64)
+        nref = 10
+        ms64 = _timed(stream, f, nref)
+        solver.solve(dev64, num_segments=Kbest, prec="fp64", out=out64, residual=True)
         rep64 = solver.report()
-        res64 = {"eta": rep64["kkt_residual"]}
-        fp64_ref = {"stages_per_s": T / (ms64 / 1e3), "ms_per_solve": ms64, "K": args.fp64_segments,
-                    "kkt_backward_error": res64["eta"], "steps": nref}
-        del dev64, out64
+        extras["plain_fp64"] = {"stages_per_s": T / (ms64 / 1e3), "ms_per_solve": ms64, "K": Kbest,
+                                "K_swept_ms": {str(k): round(v, 4) for k, v in sweep64.items()},
+                                "kkt_backward_error": rep64["kkt_residual"], "kkt_rel_residual": rep64["kkt_rel"],
+                                "steps": nref}
+        extras["speedup_vs_plain_fp64"] = value / world / extras["plain_fp64"]["stages_per_s"]
+        del out64
+        # the same mode over the segment-count grid of the workload
+        grid = {}
+        for Kg in wl["Kgrid"]:
+            if Kg > T // max(1, -(-n // m)):
+                continue
+            f = lambda: solver.solve(dev, num_segments=Kg, prec=prec, out=out, form=args.form, max_refine=mr,
+                                     tol=args.tol)
+            f()
+            t = _timed(stream, f, 5)
+            solver.solve(dev, num_segments=Kg, prec=prec, out=out, form=args.form, residual=True, max_refine=mr,
+                         tol=args.tol)
+            r = solver.report()
+            grid[str(Kg)] = {"stages_per_s": T / (t / 1e3), "ms_per_solve": t, "kkt_rel_residual": r["kkt_rel"],
+                             "refinement_corrections": r["refine_iters"] if mr else 0}
+        if grid:
+            extras["K_grid"] = grid
+        # the unrefined FP32 answer of the same workload (what the refined mode starts from)
+        if wl["unrefined"] and prec != wl["unrefined"]:
+            d32 = {k: v.float() for k, v in dev64.items()}
+            o32 = solver.alloc_solution(d32, want=("K", "k", "x", "u", "lam"))
+            f = lambda: solver.solve(d32, num_segments=K, prec="fp32", out=o32, form=args.form)
+            f()
+            t = _timed(stream, f, 10)
+            solver.solve(d32, num_segments=K, prec="fp32", out=o32, form=args.form, residual=True)
+            r = solver.report()
+            extras["fp32_unrefined"] = {"stages_per_s": T / (t / 1e3), "ms_per_solve": t, "K": K,
+                                        "kkt_backward_error": r["kkt_residual"], "kkt_rel_residual": r["kkt_rel"]}
+            del d32, o32
+        del dev64
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timing
     e2e = None
@@ -405,43 +480,49 @@ def main():
         pin = {k: torch.from_numpy(np.ascontiguousarray(v.astype(npdt))).pin_memory() for k, v in prob_np.items()}
         pin_np = {k: v.numpy() for k, v in pin.items()}
         shapes = dict(K=(T, m, n), k=(T, m), x=(T + 1, n), u=(T, m))
+        if mr:
+            shapes["lam"] = (T + 1, n)  # refinement corrects the multipliers too
         outp = {k: torch.empty(s, dtype=dt).pin_memory().numpy() for k, s in shapes.items()}
         for _ in range(2):
-            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form, max_refine=mr,
+            solver.solve_host(pin_np, num_segments=K, prec=prec, out_np=outp, form=args.form, max_refine=mr,
                               tol=args.tol)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         e2e_steps = max(3, args.steps // 2)
         for _ in range(e2e_steps):
-            solver.solve_host(pin_np, num_segments=K, prec=args.prec, out_np=outp, form=args.form, max_refine=mr,
+            solver.solve_host(pin_np, num_segments=K, prec=prec, out_np=outp, form=args.form, max_refine=mr,
                               tol=args.tol)
-        el = max_over_ranks([time.perf_counter() - t0], world, f"cuda:{local}")[0]
+        el = max_over_ranks([time.perf_counter() - t0], world, device)[0]
         h2d = sum(v.nbytes for v in pin_np.values())
         d2h = sum(v.nbytes for v in outp.values())
         e2e = {"value": whole_job_rate(T, e2e_steps, world, el), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
 
-    cpu = None
+    cpu, errors = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(n, m, 256, prob_np, budget_s=12.0)
+        cpu, ref = cpu_baseline(wl, prob_np, budget_s=12.0)
+        if ref is not None:
+            errors = {k: float(np.abs(answer[k] - ref[k]).max() / np.abs(ref[k]).max())
+                      for k in ("K", "k", "x", "u", "lam")}
 
     if rank == 0:
+        config = {"workload": "%s, K=%d segments, %s" % (wl["name"], K, prec.upper()),
+                  "n": n, "m": m, "T": T, "K": K, "precision": prec, "form": args.form,
+                  "kkt_backward_error": res["eta"], "kkt_rel_residual": res["rel"],
+                  "refinement_corrections": res["iters"] if mr else 0,
+                  "refine_tol": args.tol if mr else None,
+                  "errors_vs_fp64_oracle": errors,
+                  "l2": "inputs (%.0f MB) larger than L2 (129 MB)" % (
+                      sum(v.nbytes for v in prob_np.values()) * (1 if es == 8 else 0.5) / 1e6),
+                  "parallelism": "replicas" if world > 1 else "single GPU"}
+        config.update(extras)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64", "mixed_fp32": "f32+f64"}[args.prec],
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64", "mixed_fp32": "f32+f64"}[prec],
                 "data": "synthetic (seeded PCG64), inputs resident in HBM",
-                "config": {"workload": "long-horizon LQR n=64 m=32 T=%d rho(A)<=1.02, K=%d segments, %s" %
-                                       (T, K, args.prec.upper()),
-                           "plain_fp64": fp64_ref,
-                           "speedup_vs_plain_fp64": (value / world / fp64_ref["stages_per_s"]) if fp64_ref else None,
-                           "n": n, "m": m, "T": T, "K": K, "precision": args.prec, "form": args.form,
-                           "kkt_backward_error": res["eta"], "kkt_rel_residual": res["rel"],
-                           "refinement_corrections": res["iters"] if mr else 0,
-                           "l2": "inputs (%.0f MB) larger than L2 (129 MB)" % (
-                               sum(v.nbytes for v in prob_np.values()) * (1 if args.prec == "fp64" else 0.5) / 1e6),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "config": config, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * args.steps}
         print(json.dumps(line), flush=True)
     solver.close()

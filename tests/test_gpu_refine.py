@@ -227,3 +227,33 @@ def test_mixed_fp32_unsupported_forms(solver):
     with pytest.raises(lqr.LqrError) as e:
         solver.solve(to_dev(prob), num_segments=8, prec="mixed_fp32", form="constrained")
     assert e.value.status == 9
+
+
+@pytest.fixture(scope="module")
+def config2():
+    prob = workloads.config2()
+    return prob, oracle.riccati(prob)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "mixed_fp32"])
+def test_config2_refined(solver, config2, prec):
+    """The mixed-precision workload n=128, m=64, T=1024, K=64: FP64 data, FP32
+    segment sweeps (in the mixed mode with the FP64 Cholesky factor of
+    R + B'PB), FP64 KKT residual and refinement to |r|/|b| <= 1e-8. x, u and
+    lambda reach the oracle at 1e-9; K_t, k_t and P_t are not unknowns of the
+    KKT system and keep the accuracy of the FP32 sweeps, stated per quantity
+    (bound 1e-4)."""
+    prob, ref = config2
+    out = host(solver.solve(to_dev(prob), num_segments=64, prec=prec, max_refine=8, tol=1e-8,
+                            want=("K", "k", "x", "u", "lam", "P", "p")))
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    errs = {k: oracle.rel_err(out[k], ref[k]) for k in ("x", "u", "lam", "K", "k", "P", "p")}
+    print("config2 %s errors %s iters %d rel %.2e eta %.2e" % (prec, errs, rep["refine_iters"], rep["kkt_rel"],
+                                                             rep["kkt_residual"]))
+    assert rep["kkt_rel"] <= 1e-8
+    for k in ("x", "u", "lam"):
+        assert errs[k] < 1e-9, errs
+    for k in ("K", "k", "P", "p"):
+        assert errs[k] < 1e-4, errs
+    assert abs(rep["cost"] - ref["cost"]) <= 1e-10 * abs(ref["cost"])
