@@ -509,6 +509,244 @@ __global__ void __launch_bounds__(kBlock) link_post_kernel(ProbTable tab) {
                    EpiAdd<double, double>{ws + wl.gam + (long long)j * n, 1, -1.0, ws + wl.lkV + (long long)j * n, 1});
 }
 
+// ---------------------------------------------------------------------------
+// FP32 link chain in one CTA for the sizes the cluster chain cannot hold
+// (n > 67, n a multiple of 8): the serial part of the dual block elimination,
+//     C = chol(Pi_{j+1}),  Tm = W_j C,  [E | e] = C'[Z_j | v_j],  v_j = w_j - W_j pi_{j+1},
+//     Ld = chol(I + C'Tm),  [F | t] = Ld^-1 [E | e],
+//     Pi_j = P_j + F'F,  pi_j = p_j + Z_j'pi_{j+1} + F't,
+// with Tm, Ld, 1/diag(Ld), [F | t] and v_j stored per link for the parallel
+// post-pass (link_post_kernel<float>) that forms Gam_j, gam_j off the chain.
+// Three n x (n + 4) FP32 work matrices in shared memory; products on 4 x 4
+// register tiles, in place where the output overwrites an operand (every tile
+// computed into registers before any is stored).
+// ---------------------------------------------------------------------------
+constexpr int kChainF32Block = 512;
+constexpr int kChainMaxTiles = 3;  // ceil(32 * 33 / 512) tiles per thread at n = 128
+
+__host__ __device__ inline long long chain_f32_smem_floats(int n) {
+  const long long ld = n + 4;
+  return 3 * (long long)n * ld + p4_scratch_floats(n) + 4LL * n + 8;
+}
+
+// One 4 x 4 tile of op(A) B at (i0, j0) into acc (op(A) = A or A').
+template <bool TA>
+__device__ __forceinline__ void mm4f_acc(int i0, int j0, int K, const float* A, int lda, const float* B, int ldb,
+                                         float (&acc)[4][4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+  for (int k = 0; k < K; ++k) {
+    float4 av;
+    if (TA) {
+      av = *reinterpret_cast<const float4*>(A + (size_t)k * lda + i0);
+    } else {
+      av.x = A[(size_t)i0 * lda + k];
+      av.y = A[(size_t)(i0 + 1) * lda + k];
+      av.z = A[(size_t)(i0 + 2) * lda + k];
+      av.w = A[(size_t)(i0 + 3) * lda + k];
+    }
+    const float4 bv = *reinterpret_cast<const float4*>(B + (size_t)k * ldb + j0);
+    const float ak[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      acc[a][0] = fmaf(ak[a], bv.x, acc[a][0]);
+      acc[a][1] = fmaf(ak[a], bv.y, acc[a][1]);
+      acc[a][2] = fmaf(ak[a], bv.z, acc[a][2]);
+      acc[a][3] = fmaf(ak[a], bv.w, acc[a][3]);
+    }
+  }
+}
+
+// C = epi(op(A) B) over M x N (multiples of 4) where C may alias A or B:
+// every tile a thread owns is computed into registers before any is stored.
+template <bool TA, typename Epi>
+__device__ __forceinline__ void mm4f_inplace(int M, int N, int K, const float* A, int lda, const float* B, int ldb,
+                                             Epi epi) {
+  const int tn = N >> 2, nt = (M >> 2) * tn;
+  float acc[kChainMaxTiles][4][4];
+#pragma unroll
+  for (int s = 0; s < kChainMaxTiles; ++s) {
+    const int tile = (int)threadIdx.x + s * (int)blockDim.x;
+    if (tile < nt) mm4f_acc<TA>((tile / tn) << 2, (tile % tn) << 2, K, A, lda, B, ldb, acc[s]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < kChainMaxTiles; ++s) {
+    const int tile = (int)threadIdx.x + s * (int)blockDim.x;
+    if (tile < nt) {
+      const int i0 = (tile / tn) << 2, j0 = (tile % tn) << 2;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) epi(i0 + a, j0 + b, acc[s][a][b]);
+    }
+  }
+  __syncthreads();
+}
+
+// Y <- L^-1 Y in place (L lower n x n, n a multiple of 4, rd[i] = 1 / L[i][i];
+// Y n x nc), by 4-row blocks: the diagonal block solved per column, then a
+// rank-4 downdate of the rows below. Ends with a barrier.
+__device__ inline void trsm_lower_blk4(int n, const float* L, int ldl, const float* rd, int nc, float* Y, int ldy) {
+  const int t = threadIdx.x, nthr = blockDim.x;
+  for (int b = 0; b < n; b += 4) {
+    const float* Lb = L + (size_t)b * ldl + b;
+    for (int c = t; c < nc; c += nthr) {
+      float* y = Y + (size_t)b * ldy + c;
+      const float y0 = y[0] * rd[b];
+      const float y1 = (y[ldy] - Lb[ldl] * y0) * rd[b + 1];
+      const float y2 = (y[2 * ldy] - Lb[2 * ldl] * y0 - Lb[2 * ldl + 1] * y1) * rd[b + 2];
+      const float y3 = (y[3 * ldy] - Lb[3 * ldl] * y0 - Lb[3 * ldl + 1] * y1 - Lb[3 * ldl + 2] * y2) * rd[b + 3];
+      y[0] = y0;
+      y[ldy] = y1;
+      y[2 * ldy] = y2;
+      y[3 * ldy] = y3;
+    }
+    __syncthreads();
+    const int rows = n - b - 4;
+    for (int e = t; e < rows * nc; e += nthr) {
+      const int i = b + 4 + e / nc, c = e % nc;
+      const float4 l = *reinterpret_cast<const float4*>(L + (size_t)i * ldl + b);
+      float v = Y[(size_t)i * ldy + c];
+      v -= l.x * Y[(size_t)b * ldy + c];
+      v -= l.y * Y[(size_t)(b + 1) * ldy + c];
+      v -= l.z * Y[(size_t)(b + 2) * ldy + c];
+      v -= l.w * Y[(size_t)(b + 3) * ldy + c];
+      Y[(size_t)i * ldy + c] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kChainF32Block, 1) link_chain_f32_kernel(ProbTable tab) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_flag;
+  const ProbDesc& pd = tab.single;
+  if (cta_should_exit(pd, &s_flag)) return;
+  const int n = pd.n, K = pd.nseg, ld = n + 4, n1 = n + 1;
+  const long long nn = (long long)n * n;
+  const WsLayout wl = ws_layout(n, K);
+  double* ws = pd.ws;
+  const long long sstride = 3 * nn + 2 * n;
+  float* X = reinterpret_cast<float*>(smem);  // Pi_{j+1} -> C -> I + C'Tm -> Ld -> Pi_j
+  float* Y = X + (size_t)n * ld;              // [Z | v] -> [E | e] -> [F | t]
+  float* Wb = Y + (size_t)n * ld;             // -W -> Tm
+  float* scr = Wb + (size_t)n * ld;           // Cholesky scratch
+  float* rdv = scr + p4_scratch_floats(n);    // 1 / diag of the current factor
+  float* pin = rdv + n;                       // pi_{j+1}
+  float* pnew = pin + n;                      // pi_j under construction
+  float* vv = pnew + n;                       // v_j
+  const int t = threadIdx.x, nthr = blockDim.x;
+  {  // the last segment carries the global value function at its start
+    const double* S = ws + wl.summ + (long long)(K - 1) * sstride;
+    double* Pi = ws + wl.Pi + (long long)(K - 1) * nn;
+    double* pi = ws + wl.pi + (long long)(K - 1) * n;
+    for (int e = t; e < nn; e += nthr) {
+      Pi[e] = S[e];
+      X[(size_t)(e / n) * ld + e % n] = static_cast<float>(S[e]);
+    }
+    for (int i = t; i < n; i += nthr) {
+      pi[i] = S[3 * nn + i];
+      pin[i] = static_cast<float>(S[3 * nn + i]);
+    }
+  }
+  __syncthreads();
+  for (int j = K - 2; j >= 0; --j) {
+    const double* S = ws + wl.summ + (long long)j * sstride;
+    const double* Pseg = S;
+    const double* Z = S + nn;
+    const double* Wneg = S + 2 * nn;  // -W_j
+    const double* ps = S + 3 * nn;
+    const double* w = S + 3 * nn + n;
+    // v_j = w_j + (-W_j) pi_{j+1}; stage [Z_j | v_j | 0] and -W_j
+    for (int i = t; i < n; i += nthr) {
+      float a = static_cast<float>(w[i]);
+      for (int k = 0; k < n; ++k) a = fmaf(static_cast<float>(Wneg[(size_t)i * n + k]), pin[k], a);
+      vv[i] = a;
+    }
+    for (int e = t; e < nn; e += nthr) {
+      const int i = e / n, k = e - i * n;
+      Y[(size_t)i * ld + k] = static_cast<float>(Z[e]);
+      Wb[(size_t)i * ld + k] = static_cast<float>(Wneg[e]);
+    }
+    if (t == 0) s_flag = 0;
+    __syncthreads();
+    for (int i = t; i < n; i += nthr) {
+      Y[(size_t)i * ld + n] = vv[i];
+      Y[(size_t)i * ld + n + 1] = 0.0f;
+      Y[(size_t)i * ld + n + 2] = 0.0f;
+      Y[(size_t)i * ld + n + 3] = 0.0f;
+      float a = static_cast<float>(ps[i]);  // pi_j = p_j + Z_j'pi_{j+1} + F't, first two terms
+      for (int k = 0; k < n; ++k) a = fmaf(Y[(size_t)k * ld + i], pin[k], a);
+      pnew[i] = a;
+    }
+    cta_chol_p4<4, 8>(n, X, ld, &s_flag, scr, rdv);  // C
+    if (s_flag) {
+      if (t == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
+      return;
+    }
+    // Tm = W C = -(-W) C ;  [E | e] = C'[Z | v]
+    mm4f_inplace<false>(n, n, n, Wb, ld, X, ld, [&](int i, int k, float v) { Wb[(size_t)i * ld + k] = -v; });
+    mm4f_inplace<true>(n, n + 4, n, X, ld, Y, ld, [&](int i, int k, float v) { Y[(size_t)i * ld + k] = v; });
+    {
+      double* gT = ws + wl.lkTm + (long long)j * nn;
+      for (int e = t; e < nn; e += nthr) gT[e] = static_cast<double>(Wb[(size_t)(e / n) * ld + e % n]);
+      double* gV = ws + wl.lkV + (long long)j * n;
+      for (int i = t; i < n; i += nthr) gV[i] = static_cast<double>(vv[i]);
+    }
+    // X = I + C'Tm, then Ld = chol(X)
+    mm4f_inplace<true>(n, n, n, X, ld, Wb, ld,
+                       [&](int i, int k, float v) { X[(size_t)i * ld + k] = v + (i == k ? 1.0f : 0.0f); });
+    cta_chol_p4<4, 8>(n, X, ld, &s_flag, scr, rdv);
+    if (s_flag) {
+      if (t == 0) raise_status(pd.status, LQR_ERR_NOT_PD, -1 - j);
+      return;
+    }
+    {
+      double* gL = ws + wl.lkLd + (long long)j * nn;
+      for (int e = t; e < nn; e += nthr) gL[e] = static_cast<double>(X[(size_t)(e / n) * ld + e % n]);
+      double* gR = ws + wl.lkRd + (long long)j * n;
+      for (int i = t; i < n; i += nthr) gR[i] = static_cast<double>(rdv[i]);
+    }
+    // [F | t] = Ld^-1 [E | e]
+    trsm_lower_blk4(n, X, ld, rdv, n1, Y, ld);
+    {
+      double* gF = ws + wl.lkF + (long long)j * n * n1;
+      for (int e = t; e < n * n1; e += nthr) gF[e] = static_cast<double>(Y[(size_t)(e / n1) * ld + e % n1]);
+    }
+    // Pi_j = P_j + F'F (into X: Ld is stored), pi_j += F't
+    cta_mm4f<true>(n, n, n, Y, ld, Y, ld, [&](int i, int k, float v) {
+      X[(size_t)i * ld + k] = v + static_cast<float>(Pseg[(size_t)i * n + k]);
+    });
+    for (int i = t; i < n; i += nthr) {
+      float a = pnew[i];
+      for (int k = 0; k < n; ++k) a = fmaf(Y[(size_t)k * ld + i], Y[(size_t)k * ld + n], a);
+      pnew[i] = a;
+    }
+    __syncthreads();
+    {
+      double* Pj = ws + wl.Pi + (long long)j * nn;
+      double* pj = ws + wl.pi + (long long)j * n;
+      for (int e = t; e < nn; e += nthr) {
+        const int i = e / n, k = e - i * n;
+        if (k < i) continue;
+        const float a = 0.5f * (X[(size_t)i * ld + k] + X[(size_t)k * ld + i]);
+        X[(size_t)i * ld + k] = a;
+        X[(size_t)k * ld + i] = a;
+        Pj[(size_t)i * n + k] = a;
+        Pj[(size_t)k * n + i] = a;
+      }
+      for (int i = t; i < n; i += nthr) {
+        pj[i] = static_cast<double>(pnew[i]);
+        pin[i] = pnew[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // The link states: z_0 = x0, z_{j+1} = Gam_j z_j + gam_j (one CTA, serial, O(K n^2)).
 __global__ void __launch_bounds__(kBlock) link_forward_kernel(ProbTable tab, int x0_is_float) {
   __shared__ int s_flag;
@@ -555,11 +793,13 @@ static cudaError_t launch_dual_cluster(const ProbTable& tab, int nprob, int x0_i
 }
 
 // link method of the last single-problem solve: -1 none yet, 0 single CTA,
-// 8/16 cluster chain width, 1000 + levels for the FP32 scan
+// 2 single-CTA FP32 chain, 8/16 cluster chain width, 1000 + levels for the FP32 scan
 static int g_link_cluster = -1;
 cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_is_float, cudaStream_t st,
                                         int* nlaunch);
-static int g_link_fp32 = 0;  // set per call by launch_link_solve_dual
+// set per call by launch_link_solve_dual: 0 FP64, 1 FP32, 2 FP64 where the cluster
+// chain holds the problem and the single-CTA FP32 chain beyond it
+static int g_link_fp32 = 0;
 
 int link_cluster_width() { return g_link_cluster; }
 
@@ -569,7 +809,7 @@ cudaError_t launch_link_solve_dual(const ProbTable& tab, int nprob, int x0_is_fl
   g_link_fp32 = link_fp32;
   cudaError_t r = cudaErrorNotSupported;
   int nl = 0;
-  if (link_fp32 && method != LQR_LINK_CHAIN) {
+  if (link_fp32 == 1 && method != LQR_LINK_CHAIN) {
     r = launch_link_scan(tab, x0_is_float, st, &nl);
     if (r == cudaSuccess) g_link_cluster = 1000 + nl - 3;
     if (r == cudaErrorNotSupported && method == LQR_LINK_SCAN) return r;
@@ -606,7 +846,7 @@ cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_
   {
     const int n = tab.single.n;
     const size_t nn = (size_t)n * n, n1 = (size_t)n + 1;
-    const size_t es = g_link_fp32 ? sizeof(float) : sizeof(double);
+    const size_t es = g_link_fp32 == 1 ? sizeof(float) : sizeof(double);
     // C, Tm, Ld, E (n x (n+1)), v | staged -W, [Z | v], w, p, pi
     const size_t cbytes = es * (3 * nn + n * n1 + n + nn + n * n1 + 3 * (size_t)n);
     int optin = 0, dev = 0;
@@ -614,21 +854,21 @@ cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (n >= 16 && tab.single.nseg > 1 && cbytes <= (size_t)optin - kStaticSmemReserve) {
       int width = 16;
-      cudaError_t e = g_link_fp32 ? launch_dual_cluster<16, float>(tab, nprob, x0_is_float, cbytes, st)
+      cudaError_t e = g_link_fp32 == 1 ? launch_dual_cluster<16, float>(tab, nprob, x0_is_float, cbytes, st)
                                   : launch_dual_cluster<16, double>(tab, nprob, x0_is_float, cbytes, st);
       if (e != cudaSuccess) {
         cudaGetLastError();  // 16-CTA clusters not available: portable width
         width = 8;
-        e = g_link_fp32 ? launch_dual_cluster<8, float>(tab, nprob, x0_is_float, cbytes, st)
+        e = g_link_fp32 == 1 ? launch_dual_cluster<8, float>(tab, nprob, x0_is_float, cbytes, st)
                         : launch_dual_cluster<8, double>(tab, nprob, x0_is_float, cbytes, st);
       }
       if (e == cudaSuccess) {
         g_link_cluster = width;
         const size_t pbytes = es * (n * n1 + 2 * nn + n);
-        const void* post = g_link_fp32 ? (const void*)link_post_kernel<float> : (const void*)link_post_kernel<double>;
+        const void* post = g_link_fp32 == 1 ? (const void*)link_post_kernel<float> : (const void*)link_post_kernel<double>;
         e = raise_dyn_smem(post, pbytes);
         if (e != cudaSuccess) return e;
-        if (g_link_fp32)
+        if (g_link_fp32 == 1)
           link_post_kernel<float><<<tab.single.nseg - 1, kBlock, pbytes, st>>>(tab);
         else
           link_post_kernel<double><<<tab.single.nseg - 1, kBlock, pbytes, st>>>(tab);
@@ -637,6 +877,26 @@ cudaError_t launch_link_solve_dual_impl(const ProbTable& tab, int nprob, int x0_
         return cudaGetLastError();
       }
       cudaGetLastError();
+    }
+  }
+  {  // FP32: the single-CTA FP32 chain with its work matrices in shared memory
+    const int n = tab.single.n, K = tab.single.nseg;
+    const size_t fbytes = sizeof(float) * (size_t)chain_f32_smem_floats(n);
+    int optin = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (g_link_fp32 && n >= 8 && n % 8 == 0 && n <= 128 && K > 1 && fbytes <= (size_t)optin - kStaticSmemReserve) {
+      const int n1 = n + 1;
+      const size_t pbytes = sizeof(float) * ((size_t)n * n1 + 2 * (size_t)n * n + n);
+      cudaError_t e = raise_dyn_smem((const void*)link_chain_f32_kernel, fbytes);
+      if (e == cudaSuccess) e = raise_dyn_smem((const void*)link_post_kernel<float>, pbytes);
+      if (e != cudaSuccess) return e;
+      link_chain_f32_kernel<<<1, kChainF32Block, fbytes, st>>>(tab);
+      link_post_kernel<float><<<K - 1, kBlock, pbytes, st>>>(tab);
+      link_forward_kernel<<<1, kBlock, 0, st>>>(tab, x0_is_float);
+      *nlaunch = 3;
+      g_link_cluster = 2;
+      return cudaGetLastError();
     }
   }
   g_link_cluster = 0;

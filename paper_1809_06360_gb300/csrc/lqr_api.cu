@@ -303,7 +303,11 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
     // the boundary-coupling solve runs in FP64 except in the all-FP32 mode
     if (dual) {
       int nl = 0;
-      e = launch_link_solve_dual(tab, 1, x0f, st, prec == LQR_FP32 ? 1 : 0, o->link, &nl);
+      // FP32 in the all-FP32 path; FP64 in the mixed modes where the cluster
+      // chain holds the problem (n <= 67), beyond it the FP32 chain (an FP64
+      // link step at n = 128 takes 4.4 ms on one SM)
+      e = launch_link_solve_dual(tab, 1, x0f, st, prec == LQR_FP32 ? 1 : (prec == LQR_MIXED_TF32 ? 2 : 0), o->link,
+                                 &nl);
       *launches += nl;
       if (e == cudaErrorNotSupported) return LQR_ERR_UNSUPPORTED;
     } else {

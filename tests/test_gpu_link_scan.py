@@ -101,3 +101,35 @@ def test_scan_unsupported_requests(solver):
     assert solver.report()["status"] == 0
     ref = oracle.riccati(big)
     assert oracle.rel_err(out["x"].double().cpu().numpy(), ref["x"]) < 1e-3
+
+
+@pytest.mark.parametrize("n,m,T,K", [(88, 24, 264, 11), (96, 8, 192, 4), (128, 64, 256, 16)])
+def test_fp32_chain_beyond_the_scan(solver, n, m, T, K):
+    """n beyond the scan's and the cluster chain's shared-memory plans (n a
+    multiple of 8, up to 128): the single-CTA FP32 chain (serial link steps
+    in shared memory) with the parallel feedback post-pass and the link-state
+    chain, 3 launches; the whole solve stays in the FP32 bound against the
+    oracle."""
+    prob = workloads.make_problem(n, m, T, seed=4343 + n + K, rho_max=1.02)
+    ref = oracle.riccati(prob)
+    out, rep = run(solver, prob, K, "auto")
+    e = {k: oracle.rel_err(out[k], ref[k]) for k in KEYS + ("P",)}
+    print("fp32 chain n=%d m=%d K=%d errors %s" % (n, m, K, e))
+    for k in ("K", "k", "x", "u", "P"):
+        assert e[k] < 1e-3, (k, e)
+    # sweep, chain + post-pass + link states, policy sweep, rollout, finalize
+    assert solver.last_launch_count() == 1 + 3 + 3, solver.last_launch_count()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "mixed_fp32"])
+def test_fp32_chain_under_refinement(solver, prec):
+    """The mixed modes at n = 128 take the FP32 chain for the link solve; FP64
+    refinement brings x, u, lambda to the oracle at 1e-9."""
+    prob = workloads.make_problem(128, 64, 256, seed=4444, rho_max=1.02)
+    ref = oracle.riccati(prob)
+    out = solver.solve(to_dev(prob, torch.float64), num_segments=16, prec=prec, max_refine=8, tol=1e-11)
+    rep = solver.report()
+    assert rep["status"] == 0, rep
+    for k in ("x", "u", "lam"):
+        err = oracle.rel_err(out[k].cpu().numpy(), ref[k])
+        assert err < 1e-9, (prec, k, err, rep)
