@@ -83,10 +83,24 @@ __host__ __device__ inline CorrSlot corr_slot(int n, int m) {
 
 }  // namespace
 
-size_t corr_seg_smem_bytes(int n, int m) { return sizeof(float) * (2 * (size_t)corr_slot(n, m).size + 4 * n + 2 * m); }
-size_t corr_psi_smem_bytes(int n, int m) {
+size_t corr_seg_smem_bytes(int n, int m, int slots) {
+  return sizeof(float) * ((size_t)slots * corr_slot(n, m).size + 4 * n + 2 * m);
+}
+size_t corr_psi_smem_bytes(int n, int m, int psi_global) {
   const size_t N = (n + 3) & ~3, M = (m + 3) & ~3;
-  return sizeof(float) * (3 * N * (N + 4) + N * (M + 4) + M * (N + 4));
+  return sizeof(float) * (3 * N * (N + 4) + (psi_global ? 0 : N * (M + 4) + M * (N + 4)));
+}
+void corr_plan(int n, int m, long long smem_budget, int* slots, int* psi_global) {
+  *slots = 0;
+  *psi_global = 0;
+  if ((long long)corr_link_smem_bytes(n) > smem_budget) return;
+  if ((long long)corr_psi_smem_bytes(n, m, 0) > smem_budget) {
+    // B_t, K_t straight from global memory: float4 rows need n, m multiples of 4
+    if (n % 4 != 0 || m % 4 != 0 || (long long)corr_psi_smem_bytes(n, m, 1) > smem_budget) return;
+    *psi_global = 1;
+  }
+  if ((long long)corr_seg_smem_bytes(n, m, 2) <= smem_budget) *slots = 2;
+  else if ((long long)corr_seg_smem_bytes(n, m, 1) <= smem_budget) *slots = 1;
 }
 size_t corr_link_smem_bytes(int n) {
   return sizeof(float) * ((size_t)kLinkDepth * n * (n + 1) + (1 + kLinkSplit) * (size_t)n);
@@ -105,23 +119,27 @@ __global__ void __launch_bounds__(kCorrBlock) corr_psi_kernel(CorrArgs a) {
   float* X = csm;            // Psi so far
   float* Y = X + N * LD;     // free: A_t, then Phi_t Psi
   float* Phi = Y + N * LD;
-  float* Bs = Phi + N * LD;  // N x LDm
+  float* Bs = Phi + N * LD;  // N x LDm (unless read from global memory)
   float* Ks = Bs + N * LDm;  // M x LD
-  const int total = 3 * N * LD + N * LDm + M * LD;
+  const int total = 3 * N * LD + (a.psi_global ? 0 : N * LDm + M * LD);
   for (int x = threadIdx.x; x < total; x += blockDim.x) csm[x] = 0.0f;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[i * LD + i] = 1.0f;
   const long long nn = (long long)n * n, nm = (long long)n * m;
   for (int t = b; t < e; ++t) {
     copy_pad(Y, LD, a.A + nn * t, n, n);
-    copy_pad(Bs, LDm, a.B + nm * t, n, m);
-    copy_pad(Ks, LD, a.K + nm * t, m, n);
+    if (!a.psi_global) {
+      copy_pad(Bs, LDm, a.B + nm * t, n, m);
+      copy_pad(Ks, LD, a.K + nm * t, m, n);
+    }
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();  // stage data in; the previous stage's products are finished
-    cta_mm4f<false>(N, N, M, Bs, LDm, Ks, LD, [&](int i, int l, float v) {
-      Phi[i * LD + l] = (i < n && l < n) ? v + Y[i * LD + l] : 0.0f;
-    });
+    auto phi = [&](int i, int l, float v) { Phi[i * LD + l] = (i < n && l < n) ? v + Y[i * LD + l] : 0.0f; };
+    if (a.psi_global)  // n, m multiples of 4: the unpadded rows of B_t and K_t
+      cta_mm4f<false>(N, N, M, a.B + nm * t, m, a.K + nm * t, n, phi);
+    else
+      cta_mm4f<false>(N, N, M, Bs, LDm, Ks, LD, phi);
     __syncthreads();
     cta_mm4f<false>(N, N, N, Phi, LD, X, LD, [&](int i, int l, float v) { Y[i * LD + l] = v; });
     __syncthreads();
@@ -147,13 +165,15 @@ __global__ void __launch_bounds__(kCorrBlock) corr_back_kernel(CorrArgs a, int m
   if (e <= b) return;  // an empty segment (uniform over the CTA)
   const CorrSlot L = corr_slot(n, m);
   float* ring = csm;
-  float* p = ring + 2 * L.size;
+  float* p = ring + (a.slots > 1 ? 2 : 1) * L.size;
   float* s = p + n;
   float* gx = s + n;
   float* gu = gx + n;
   const long long nn = (long long)n * n, nm = (long long)n * m, mm = (long long)m * m;
+  const int two = a.slots > 1;
+  auto slot = [&](int t) { return ring + (two ? ((e - 1 - t) & 1) : 0) * L.size; };
   auto issue = [&](int t) {
-    float* sl = ring + ((e - 1 - t) & 1) * L.size;
+    float* sl = slot(t);
     copy_pad(sl + L.oA, L.ldn, a.A + nn * t, n, n);
     copy_pad(sl + L.oB, L.ldm, a.B + nm * t, n, m);
     copy_pad(sl + L.oK, L.ldn, a.K + nm * t, m, n);
@@ -164,15 +184,19 @@ __global__ void __launch_bounds__(kCorrBlock) corr_back_kernel(CorrArgs a, int m
     copy_vec(sl + L.or_, a.cr + (long long)m * t, m);
     cp_async_commit();
   };
-  issue(e - 1);
+  if (two) issue(e - 1);
   for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = (mode == 0) ? 0.0f : a.pb[(long long)n * (j + 1) + i];
   if (mode == 1 && j == a.nseg - 1)
     for (int i = threadIdx.x; i < n; i += blockDim.x) a.dp[(long long)n * T + i] = a.pb[(long long)n * a.nseg + i];
   for (int t = e - 1; t >= b; --t) {
-    const float* sl = ring + ((e - 1 - t) & 1) * L.size;
+    const float* sl = slot(t);
+    if (!two) {  // one slot: the previous stage has finished with it
+      __syncthreads();
+      issue(t);
+    }
     cp_async_wait<0>();
     __syncthreads();  // stage t in its slot; p of stage t + 1 complete
-    if (t - 1 >= b) issue(t - 1);
+    if (two && t - 1 >= b) issue(t - 1);
     const float* As = sl + L.oA;
     const float* Bs = sl + L.oB;
     const float* Ks = sl + L.oK;
@@ -231,12 +255,14 @@ __global__ void __launch_bounds__(kCorrBlock) corr_fwd_kernel(CorrArgs a, int mo
   if (e <= b) return;  // an empty segment (uniform over the CTA)
   const CorrSlot L = corr_slot(n, m);
   float* ring = csm;
-  float* x0 = ring + 2 * L.size;  // two state buffers
+  float* x0 = ring + (a.slots > 1 ? 2 : 1) * L.size;  // two state buffers
   float* x1 = x0 + n;
   float* u = x1 + n;
   const long long nn = (long long)n * n, nm = (long long)n * m;
+  const int two = a.slots > 1;
+  auto slot = [&](int t) { return ring + (two ? ((t - b) & 1) : 0) * L.size; };
   auto issue = [&](int t) {
-    float* sl = ring + ((t - b) & 1) * L.size;
+    float* sl = slot(t);
     copy_pad(sl + L.oA, L.ldn, a.A + nn * t, n, n);
     copy_pad(sl + L.oB, L.ldm, a.B + nm * t, n, m);
     copy_pad(sl + L.oK, L.ldn, a.K + nm * t, m, n);
@@ -248,15 +274,19 @@ __global__ void __launch_bounds__(kCorrBlock) corr_fwd_kernel(CorrArgs a, int mo
     copy_vec(sl + L.ok, a.dk + (long long)m * t, m);
     cp_async_commit();
   };
-  issue(b);
+  if (two) issue(b);
   for (int i = threadIdx.x; i < n; i += blockDim.x) x0[i] = (mode == 0) ? 0.0f : a.xb[(long long)n * j + i];
   float* xc = x0;
   float* xn = x1;
   for (int t = b; t < e; ++t) {
-    const float* sl = ring + ((t - b) & 1) * L.size;
+    const float* sl = slot(t);
+    if (!two) {  // one slot: the previous stage has finished with it
+      __syncthreads();
+      issue(t);
+    }
     cp_async_wait<0>();
     __syncthreads();  // stage t in its slot; x~_t complete
-    if (t + 1 < e) issue(t + 1);
+    if (two && t + 1 < e) issue(t + 1);
     const float* As = sl + L.oA;
     const float* Bs = sl + L.oB;
     const float* Ks = sl + L.oK;
@@ -361,7 +391,7 @@ __global__ void __launch_bounds__(kCorrBlock) corr_link_kernel(CorrArgs a, int d
 }
 
 cudaError_t launch_corr_psi(const CorrArgs& a, cudaStream_t st) {
-  const size_t bytes = corr_psi_smem_bytes(a.n, a.m);
+  const size_t bytes = corr_psi_smem_bytes(a.n, a.m, a.psi_global);
   cudaError_t e = raise_dyn_smem((const void*)corr_psi_kernel, bytes);
   if (e != cudaSuccess) return e;
   corr_psi_kernel<<<a.nseg, kCorrBlock, bytes, st>>>(a);
@@ -370,7 +400,7 @@ cudaError_t launch_corr_psi(const CorrArgs& a, cudaStream_t st) {
 
 // one correction: eps, backward links, p and k~, delta, forward links, x~ u~ lambda~
 cudaError_t launch_correction(const CorrArgs& a, cudaStream_t st, int* launches) {
-  const size_t sb = corr_seg_smem_bytes(a.n, a.m), lb = corr_link_smem_bytes(a.n);
+  const size_t sb = corr_seg_smem_bytes(a.n, a.m, a.slots), lb = corr_link_smem_bytes(a.n);
   cudaError_t e = raise_dyn_smem((const void*)corr_back_kernel, sb);
   if (e == cudaSuccess) e = raise_dyn_smem((const void*)corr_fwd_kernel, sb);
   if (e == cudaSuccess) e = raise_dyn_smem((const void*)corr_link_kernel, lb);

@@ -366,9 +366,9 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   // when the FP32 fast sweeps run and the correction kernels' plans fit; otherwise
   // every correction is a whole FP32 solve.
   const long long budget = h->smem_optin - kStaticSmemReserve;
-  const bool reuse = !summary_only && sp.rbase >= 0 && o->max_refine > 0 && fast_sweep_supported(n, m, budget) &&
-                     (long long)corr_seg_smem_bytes(n, m) <= budget && (long long)corr_psi_smem_bytes(n, m) <= budget &&
-                     (long long)corr_link_smem_bytes(n) <= budget;
+  int cslots = 0, cpsi_global = 0;
+  corr_plan(n, m, budget, &cslots, &cpsi_global);
+  const bool reuse = !summary_only && sp.rbase >= 0 && o->max_refine > 0 && cslots > 0;
   const bool keep_P = want_P || reuse;
   // FP32 working arrays (each 256-byte aligned)
   size_t off = 0;
@@ -469,6 +469,7 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
       ca.dk = f + odk; ca.dp = f + odp; ca.dx = f + odx; ca.du = f + odu; ca.dl = f + odl;
       ca.skip = skip; ca.status = h->d_status;
       ca.n = n; ca.m = m; ca.T = T; ca.nseg = K;
+      ca.slots = cslots; ca.psi_global = cpsi_global;
       if (launch_corr_psi(ca, st) != cudaSuccess) return LQR_ERR_CUDA;
       ++launches;
     }

@@ -217,6 +217,8 @@ struct CorrArgs {
   const int* skip;                     // set: converged, every kernel returns at once
   int* status;
   int n, m, T, nseg;
+  int slots;       // stage-data ring slots of the segment passes (2: prefetch, 1: no prefetch)
+  int psi_global;  // 1: the closed-loop maps read B_t, K_t from global memory
 };
 
 // ---------------------------------------------------------------------------
@@ -238,9 +240,12 @@ long long fast_sweep_smem_bytes(int n, int m);
 // the FP32 fast sweeps (and with them the kept M_uu^-1) apply to (n, m)
 bool fast_sweep_supported(int n, int m, long long smem_budget);
 // refinement corrections that reuse the factorisation (correct.cu)
-size_t corr_seg_smem_bytes(int n, int m);
-size_t corr_psi_smem_bytes(int n, int m);
+size_t corr_seg_smem_bytes(int n, int m, int slots);
+size_t corr_psi_smem_bytes(int n, int m, int psi_global);
 size_t corr_link_smem_bytes(int n);
+// the plan of the correction kernels for (n, m) within the shared-memory
+// budget (slots 0: they do not apply)
+void corr_plan(int n, int m, long long smem_budget, int* slots, int* psi_global);
 cudaError_t launch_corr_psi(const CorrArgs& a, cudaStream_t st);
 cudaError_t launch_correction(const CorrArgs& a, cudaStream_t st, int* launches);
 

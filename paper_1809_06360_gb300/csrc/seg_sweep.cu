@@ -295,6 +295,11 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
             gK[nm * t + e] = static_cast<TS>(-F[(size_t)(e / n) * ldF + (e % n)]);
         if (gk)
           for (int a = threadIdx.x; a < m; a += blockDim.x) gk[(size_t)m * t + a] = static_cast<TS>(-F[(size_t)a * ldF + cmu]);
+        if (pd.Minv && Linv && sizeof(TS) == 4) {
+          // M_uu^-1 = L^-T L^-1, kept for refinement corrections that reuse the factorisation
+          cta_mm_auto<true, false, TC>(m, m, m, Linv, m, Linv, m,
+                                       EpiStore<TS>{static_cast<TS*>(pd.Minv) + (size_t)m * m * t, m, 1.0});
+        }
       } else {
         cta_copy<TC>(n, n, T1, ldAB, Vzx, n);
       }

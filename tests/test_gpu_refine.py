@@ -149,16 +149,24 @@ def _launches_per_correction(solver, prob, K):
 
 
 def test_mixed_fp32_correction_paths(solver):
-    """Which correction path a shape takes. n=64, m=32: corrections reuse the
-    solve's K_t, P_t and M_uu^-1 (residual, finalize, conversion, six vector
-    passes, update: 10 kernels each). n=72, m=32: the FP32 fast sweep's plan
-    does not fit in shared memory, so each correction is a whole FP32 solve
-    (more kernels); both reach the oracle at 1e-9."""
-    reuse = workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02)
-    assert _launches_per_correction(solver, reuse, 16) == 10
-    fallback = workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02)
-    assert _launches_per_correction(solver, fallback, 16) > 10
-    for prob, K in ((reuse, 16), (fallback, 16)):
+    """Which correction path a shape takes. Where the correction kernels' plans
+    fit (n=64, m=32: two stage-data slots and the fast sweep; n=72 and n=128:
+    the generic FP32 sweep, which also keeps M_uu^-1; n=128 with one slot and
+    the closed-loop maps reading B_t, K_t from global memory), corrections
+    reuse the solve's K_t, P_t and M_uu^-1 (residual, finalize, conversion, six
+    vector passes, update: 10 kernels each). n=136: beyond the link-chain plan
+    of the corrections, so each correction is a whole FP32 solve (residual,
+    finalize, conversion and update around the kernels of a plain FP32 solve
+    of that shape). All reach the oracle at 1e-9."""
+    cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, True),
+             (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, True),
+             (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, True),
+             (workloads.make_problem(136, 8, 160, seed=614, rho_max=1.02), 4, False)]
+    for prob, K, reuse in cases:
+        per = _launches_per_correction(solver, prob, K)
+        solver.solve(to_dev(prob, torch.float32), num_segments=K, prec="fp32")
+        plain = solver.last_launch_count()
+        assert per == (10 if reuse else 4 + plain), (prob["B"].shape, per, plain)
         ref = oracle.riccati(prob)
         out = host(solver.solve(to_dev(prob), num_segments=K, prec="mixed_fp32", max_refine=8, tol=1e-11))
         rep = solver.report()
