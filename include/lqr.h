@@ -244,6 +244,20 @@ lqr_status lqr_backward_batched(lqr_handle *h, int nprob, const lqr_problem *pro
 lqr_status lqr_kkt_residual_noalloc(const lqr_problem *prob, const lqr_solution *sol, lqr_precision prec,
                                     double *out, void *stream);
 
+/* Self-test of the tensor-core product unit the segment sweeps use on device
+ * `device` (the tcgen05 TF32 products of Section II-B's stage terms, in the
+ * operand forms the sweep issues: A from shared memory and from tensor
+ * memory, 128-row tiles at row offsets 0 and 64, N = 64, 128, 192, and
+ * accumulation with a negated A), against CUDA-core FP32 products of the same
+ * operands, one CTA on deterministic data. errs (host, 5 doubles) receives
+ * four normwise relative differences and a wait flag: [0] shared x shared
+ * (N = 128), [1] tensor-memory A (N = 192), [2] tensor-memory A (N = 64, the
+ * rows from 128 on), [3] |X - X| / |X| with the second product negated,
+ * [4] 1 if a bounded completion wait ran out (then LQR_ERR_TIMEOUT).
+ * TF32 operands carry 10 mantissa bits, so [0]-[2] are of order 1e-3 and
+ * [3] of order 1e-6. Synchronous; allocates and frees a small device buffer. */
+lqr_status lqr_tc_selftest(int device, double* errs);
+
 /* Step A1 alone: the per-segment parametric backward sweeps (Section II-B,
  * Eq. 9-16). Writes K summaries of LQR_SUMMARY_DOUBLES(n) doubles each to the
  * device array `summaries` (FP64). */

@@ -30,7 +30,7 @@ SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
 EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
-           "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc")
+           "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -91,6 +91,7 @@ def load(path: str | None = None):
                                       c_void_p]
     lib.lqr_report_batched.argtypes = [c_void_p, c_void_p, c_int, P(c_int), P(c_double)]
     lib.lqr_kkt_residual_noalloc.argtypes = [P(lqr_problem), P(lqr_solution), c_int, c_void_p, c_void_p]
+    lib.lqr_tc_selftest.argtypes = [c_int, P(c_double)]
     lib.lqr_backward.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p, c_void_p,
                                  P(lqr_problem), c_void_p]
     lib.lqr_backward_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution),
@@ -98,7 +99,7 @@ def load(path: str | None = None):
     for name in ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
-                 "lqr_backward_batched", "lqr_kkt_residual_noalloc"):
+                 "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -197,6 +198,13 @@ def lqr_backward_batched(h: int, probs, opts: lqr_opts, sols, gxs, gus, grads, s
     gu = (c_void_p * n)(*gus)
     _check(load().lqr_backward_batched(h, n, parr, ctypes.byref(opts), sarr, gx, gu, garr, stream or None),
            "lqr_backward_batched")
+
+
+def lqr_tc_selftest(device: int = 0) -> list[float]:
+    """The tensor-core product unit against CUDA-core products (include/lqr.h)."""
+    errs = (c_double * 5)()
+    _check(load().lqr_tc_selftest(device, errs), "lqr_tc_selftest")
+    return [errs[i] for i in range(5)]
 
 
 def lqr_profile_enable(h: int, enable: bool) -> None:
