@@ -253,12 +253,14 @@ void prof_mark(lqr_handle* h, int k, cudaStream_t st) {
 // `profile` marks the phase boundaries of this pipeline.
 lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan& sp, const lqr_opts* o,
                             bool want_traj, bool want_lam, int store_P, bool summary_only, bool profile,
-                            cudaStream_t st, int* launches) {
+                            cudaStream_t st, int* launches, bool tensor_cores = false) {
   const long long budget = h->smem_optin - kStaticSmemReserve;
   const int prec = o->prec;
   const bool dual = (o->form != LQR_FORM_CONSTRAINED);
   cudaError_t e;
   auto sweep = [&](int phase, cudaStream_t sst) {
+    if (tensor_cores && phase == 1 && prec == LQR_FP32 && dual && tc_sweep_supported(tab.single.n, tab.single.m))
+      return launch_seg_sweep_tc(tab, sp.K, store_P, sst);
     if (prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, sp.K, phase, sp.smem, budget, store_P, sst);
     if (prec == LQR_MIXED_TF32) return launch_seg_sweep<double, float>(tab, sp.K, phase, sp.smem, budget, store_P, sst);
     if (dual) {
@@ -353,7 +355,7 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
 // LQR_MIXED_FP32: the FP32 path on an FP32 copy of the data, solution kept in
 // FP64, FP64 residual and refinement corrections by the FP32 path.
 lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const lqr_solution* s,
-                             cudaStream_t st, bool summary_only, SolvePlan* sp_out) {
+                             cudaStream_t st, bool summary_only, SolvePlan* sp_out, bool tensor_cores = false) {
   SolvePlan sp;
   lqr_status rs = plan_solve(h, p, o, &sp);
   if (rs != LQR_OK) return rs;
@@ -422,7 +424,7 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
   if (cudaMemsetAsync(h->d_report, 0, 4 * sizeof(double), st) != cudaSuccess) return LQR_ERR_CUDA;
   rs = enqueue_pipeline(h, tab, sp, &o32, !summary_only, !summary_only, keep_P ? 1 : 0, summary_only, true, st,
-                        &launches);
+                        &launches, tensor_cores);
   if (rs != LQR_OK) return rs;
   if (!summary_only) {
     ConvTable<float, double> ct;
@@ -489,7 +491,8 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
       if (reuse) {
         if (launch_correction(ca, st, &launches) != cudaSuccess) return LQR_ERR_CUDA;
       } else {
-        rs = enqueue_pipeline(h, ctab, sp, &o32, true, true, want_P ? 1 : 0, false, false, st, &launches);
+        rs = enqueue_pipeline(h, ctab, sp, &o32, true, true, want_P ? 1 : 0, false, false, st, &launches,
+                              tensor_cores);
         if (rs != LQR_OK) return rs;
       }
       if (launch_refine_update_f32(main, f + odk, f + odx, f + odu, f + odl, want_P ? f + odp : nullptr, skip, st) !=
@@ -520,6 +523,10 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
 lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const lqr_solution* s,
                      cudaStream_t st, bool summary_only, SolvePlan* sp_out) {
   if (o->prec == LQR_MIXED_FP32) return run_solve_mixed32(h, p, o, s, st, summary_only, sp_out);
+  // the mixed TF32 mode on the tensor-core plan: an FP32 copy of the data, the
+  // policy sweeps on the tensor cores (FP64 factor of M_uu), FP64 refinement
+  if (o->prec == LQR_MIXED_TF32 && o->form == LQR_FORM_MULTIPLIER && tc_sweep_supported(p->n, p->m))
+    return run_solve_mixed32(h, p, o, s, st, summary_only, sp_out, true);
   SolvePlan sp;
   lqr_status rs = plan_solve(h, p, o, &sp);
   if (rs != LQR_OK) return rs;

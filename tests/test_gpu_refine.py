@@ -246,14 +246,15 @@ def config2():
 @pytest.mark.parametrize("prec", ["mixed", "mixed_fp32"])
 def test_config2_refined(solver, config2, prec):
     """The mixed-precision workload n=128, m=64, T=1024, K=64: FP64 data, FP32
-    segment sweeps (in the mixed mode with the FP64 Cholesky factor of
-    R + B'PB), FP64 KKT residual and refinement to |r|/|b| <= 1e-8. x, u and
+    segment sweeps (the mixed TF32 mode: policy sweeps on the tensor cores with
+    TF32 products and the FP64 Cholesky factor of R + B'PB), FP64 KKT residual
+    and refinement to |r|/|b| <= 1e-8. x, u and
     lambda reach the oracle at 1e-9; K_t, k_t, P_t and p_t are not unknowns of
     the KKT system: K, k and P keep the accuracy of the FP32 sweeps (bound
     1e-4), p_t carries that of the FP32 link chain through the boundary values
     pi_j it starts from (bound 1e-3), all stated per quantity."""
     prob, ref = config2
-    out = host(solver.solve(to_dev(prob), num_segments=64, prec=prec, max_refine=8, tol=1e-8,
+    out = host(solver.solve(to_dev(prob), num_segments=64, prec=prec, max_refine=12, tol=1e-8,
                             want=("K", "k", "x", "u", "lam", "P", "p")))
     rep = solver.report()
     assert rep["status"] == 0, rep
@@ -263,7 +264,9 @@ def test_config2_refined(solver, config2, prec):
     assert rep["kkt_rel"] <= 1e-8
     for k in ("x", "u", "lam"):
         assert errs[k] < 1e-9, errs
+    # the mixed TF32 mode runs the policy sweeps on the tensor cores: TF32 class
+    bound_mat, bound_p = (3e-2, 3e-2) if prec == "mixed" else (1e-4, 1e-3)
     for k in ("K", "k", "P"):
-        assert errs[k] < 1e-4, errs
-    assert errs["p"] < 1e-3, errs
+        assert errs[k] < bound_mat, errs
+    assert errs["p"] < bound_p, errs
     assert abs(rep["cost"] - ref["cost"]) <= 1e-10 * abs(ref["cost"])
