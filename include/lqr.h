@@ -130,6 +130,10 @@ typedef struct {
   int residual;       /* 1 = compute the FP64 KKT residual of the returned solution
                          (needs x, u, lam); implied by max_refine > 0              */
   lqr_link link;      /* link-system solver, see lqr_link (0 = automatic)         */
+  long long spin_limit; /* polls (about 32 ns apart) of a bounded device wait (the
+                         tensor-core sweep's waits for its own products) before it
+                         gives up with LQR_ERR_TIMEOUT, releases its tensor memory and
+                         returns; 0 = 2^26 (about two seconds)                       */
 } lqr_opts;
 
 /* Scalars of the last solve, read back by lqr_report(). */
@@ -181,15 +185,27 @@ lqr_status lqr_solve(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opt
 lqr_status lqr_solve_host(lqr_handle *h, const lqr_problem *prob_host, const lqr_opts *opts,
                           const lqr_solution *sol_host, void *stream);
 
-/* Many independent problems of uneven n, m, T in one solve (a batch): one
- * launch per step over all (problem, segment) units, with the segment count
- * of each problem chosen from the batch shape (one segment per problem when
- * the batch has at least one problem per SM) unless opts->num_segments > 0
- * fixes it. probs and sols are HOST arrays of nprob entries whose pointers are
- * device arrays (layout above); all problems share opts (precision, form
+/* Many independent problems of uneven n, m, T in one solve (a batch). Two
+ * schedules:
+ *  - persistent: one launch; resident CTAs take the problems from a queue
+ *    ordered by decreasing work (longest first) and solve each one whole as
+ *    one segment (Riccati sweep, rollout, multipliers, objective). Used for
+ *    LQR_FP32 multiplier-form batches that request x and u and fit the FP32
+ *    sweep and rollout plans (n up to about 64, m up to 32), with
+ *    opts->num_segments 0 or 1;
+ *  - per step: one launch per step over all (problem, segment) units, the
+ *    segment count of each problem from the batch shape (one segment per
+ *    problem when the batch has at least one problem per SM, else about two
+ *    units per SM) unless opts->num_segments > 0 fixes it.
+ * With opts->num_segments = 0 and both schedules possible, the first batch of
+ * a shape bucket (problem count and largest horizon by powers of two, largest
+ * n and m) is solved with each schedule and timed (that call synchronises
+ * `stream`); the handle keeps the faster schedule for the bucket.
+ * probs and sols are HOST arrays of nprob entries whose pointers are device
+ * arrays (layout above); all problems share opts (precision, form
  * LQR_FORM_MULTIPLIER; no refinement). segments (host, nprob ints, or NULL)
- * receives the segment count used per problem. Asynchronous on `stream`;
- * the host arrays may be reused as soon as the call returns. */
+ * receives the segment count used per problem. Otherwise asynchronous on
+ * `stream`; the host arrays may be reused as soon as the call returns. */
 lqr_status lqr_solve_batched(lqr_handle *h, int nprob, const lqr_problem *probs, const lqr_opts *opts,
                              const lqr_solution *sols, int *segments, void *stream);
 
@@ -258,6 +274,14 @@ lqr_status lqr_kkt_residual_noalloc(const lqr_problem *prob, const lqr_solution 
  * [3] of order 1e-6. Synchronous; allocates and frees a small device buffer. */
 lqr_status lqr_tc_selftest(int device, double* errs);
 
+/* The FP64 pivot reciprocal of the FP64 factorisations (the pivots of the
+ * Cholesky / LDL' factors of R + B'PB and of the link blocks, Section II-B),
+ * y[i] = 1 / d[i] from the FP32 hardware reciprocal refined by two
+ * Newton-Raphson steps y <- y + y (1 - d y) (the division itself outside the
+ * FP32 exponent range), exported so that its accuracy can be checked against
+ * IEEE division. d, y: DEVICE arrays of count doubles. Asynchronous on stream. */
+lqr_status lqr_rcp_newton_check(const double* d, double* y, int count, void* stream);
+
 /* Step A1 alone: the per-segment parametric backward sweeps (Section II-B,
  * Eq. 9-16). Writes K summaries of LQR_SUMMARY_DOUBLES(n) doubles each to the
  * device array `summaries` (FP64). */
@@ -270,7 +294,8 @@ lqr_status lqr_report(lqr_handle *h, void *stream, lqr_report_t *out);
 /* Human-readable name of a status code (static string). */
 const char *lqr_status_string(lqr_status s);
 
-/* Number of kernels the last lqr_solve / lqr_segment_summaries call enqueued. */
+/* Number of kernels the last lqr_solve / lqr_segment_summaries /
+ * lqr_solve_batched call enqueued. */
 int lqr_last_launch_count(const lqr_handle *h);
 
 /* Phase profiling with CUDA events recorded on the solve's own stream.

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "lqr_internal.cuh"
@@ -86,6 +87,12 @@ struct lqr_handle {
   // LQR_MIXED_FP32: FP32 copy of the data, FP32 solution and correction buffers
   unsigned char* f32 = nullptr;
   size_t f32_bytes = 0;
+  // batch-schedule autotuner: per batch-shape bucket, 1 = the persistent
+  // one-segment schedule was measured faster than the per-step launches
+  struct TuneEntry { int key[4]; int persistent; float ms[2]; };
+  TuneEntry tune[64];
+  int ntune = 0;
+  int last_schedule = 0;  // schedule of the last batched solve: 0 per-step launches, 1 persistent
 };
 
 namespace {
@@ -165,6 +172,7 @@ lqr_status validate(const lqr_problem* p, const lqr_opts* o, const lqr_solution*
     return LQR_ERR_INVALID_ARG;
   if (o->max_refine > 0 && o->prec == LQR_FP32) return LQR_ERR_UNSUPPORTED;  // refinement needs FP64 data
   if (o->link != LQR_LINK_AUTO && o->link != LQR_LINK_CHAIN && o->link != LQR_LINK_SCAN) return LQR_ERR_INVALID_ARG;
+  if (o->spin_limit < 0) return LQR_ERR_INVALID_ARG;
   if (o->link == LQR_LINK_SCAN && ((o->prec != LQR_FP32 && o->prec != LQR_MIXED_FP32) || o->form != LQR_FORM_MULTIPLIER))
     return LQR_ERR_UNSUPPORTED;
   return LQR_OK;
@@ -260,7 +268,7 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
   cudaError_t e;
   auto sweep = [&](int phase, cudaStream_t sst) {
     if (tensor_cores && phase == 1 && prec == LQR_FP32 && dual && tc_sweep_supported(tab.single.n, tab.single.m))
-      return launch_seg_sweep_tc(tab, sp.K, store_P, sst);
+      return launch_seg_sweep_tc(tab, sp.K, store_P, o->spin_limit, sst);
     if (prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, sp.K, phase, sp.smem, budget, store_P, sst);
     if (prec == LQR_MIXED_TF32) return launch_seg_sweep<double, float>(tab, sp.K, phase, sp.smem, budget, store_P, sst);
     if (dual) {
@@ -623,8 +631,8 @@ int batch_segments(const lqr_handle* h, int nprob, const lqr_problem* probs, int
   return K;
 }
 
-lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const lqr_opts* o,
-                       const lqr_solution* sols, int* segments_out, cudaStream_t st) {
+lqr_status run_batched_impl(lqr_handle* h, int nprob, const lqr_problem* probs, const lqr_opts* o,
+                            const lqr_solution* sols, int* segments_out, cudaStream_t st, bool persistent) {
   long long total_T = 0;
   int nmax = 0, mmax = 0;
   for (int i = 0; i < nprob; ++i) {
@@ -643,7 +651,7 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
   if (!items) return LQR_ERR_OOM;
   for (int i = 0; i < nprob; ++i) {
     const lqr_problem& p = probs[i];
-    const int K = batch_segments(h, nprob, probs, i, total_T, o->num_segments);
+    const int K = persistent ? 1 : batch_segments(h, nprob, probs, i, total_T, o->num_segments);
     if (K > 1 && p.T / K < min_segment_len(p.n, p.m)) { free(items); return LQR_ERR_SEGMENT_INFEASIBLE; }
     long long scratch = 0, smem = 0;
     if (o->prec == LQR_FP64) smem = sweep_smem_needed<double, double>(p.n, p.m, budget, cons, &scratch);
@@ -662,11 +670,14 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
   lqr_status rs = grow(&h->ws, &h->ws_bytes, sizeof(double) * (size_t)ws_total + 256);
   if (rs != LQR_OK) { free(items); return rs; }
   // device table: descriptors | unit map | status (2 ints each) | report (4 doubles each)
+  // device table: descriptors | unit map | LPT order | status (2 ints each) |
+  // report (4 doubles each) | ticket of the persistent schedule
   const size_t desc_bytes = sizeof(ProbDesc) * (size_t)nprob;
-  const size_t unit_bytes = sizeof(int) * (size_t)nunits;
+  const size_t unit_bytes = sizeof(int) * (size_t)nunits + sizeof(int) * (size_t)nprob;
   const size_t stat_off = (desc_bytes + unit_bytes + 255) & ~(size_t)255;
   const size_t rep_off = (stat_off + sizeof(int) * 2 * (size_t)nprob + 255) & ~(size_t)255;
-  const size_t table_bytes = rep_off + sizeof(double) * 4 * (size_t)nprob;
+  const size_t tick_off = (rep_off + sizeof(double) * 4 * (size_t)nprob + 255) & ~(size_t)255;
+  const size_t table_bytes = tick_off + 256;
   rs = grow(&h->bdev, &h->bdev_bytes, table_bytes);
   if (rs != LQR_OK) { free(items); return rs; }
   if (h->bhost_bytes < desc_bytes + unit_bytes) {
@@ -706,6 +717,19 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
     hd[i] = d;
     for (int j = 0; j < items[i].K; ++j) hu[u++] = i;
   }
+  // longest processing time first: the queue order of the persistent schedule
+  int* horder = hu + u;
+  {
+    for (int i = 0; i < nprob; ++i) horder[i] = i;
+    double* work = (double*)malloc(sizeof(double) * (size_t)nprob);
+    if (!work) { free(items); return LQR_ERR_OOM; }
+    for (int i = 0; i < nprob; ++i) {
+      const double n = probs[i].n, m = probs[i].m;
+      work[i] = (double)probs[i].T * (4 * n * n * n + 6 * n * n * m + 4 * n * m * m + 2 * m * m * m);
+    }
+    std::sort(horder, horder + nprob, [&](int a, int b) { return work[a] > work[b] || (work[a] == work[b] && a < b); });
+    free(work);
+  }
   free(items);
   if (cudaMemcpyAsync(h->bdev, h->bhost, desc_bytes + unit_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return LQR_ERR_CUDA;
@@ -727,6 +751,22 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
     if (!sols[i].x || !sols[i].u) all_xu = 0;
   }
   cudaError_t e;
+  h->last_schedule = persistent ? 1 : 0;
+  if (persistent) {
+    prof_mark(h, LQR_PHASE_SWEEP, st);
+    e = launch_batch_persistent(tab, reinterpret_cast<const int*>(h->bdev + desc_bytes) + nunits,
+                                reinterpret_cast<int*>(h->bdev + tick_off), want_lam ? 1 : 0, nmax, mmax, store_P,
+                                h->num_sms, st);
+    if (e != cudaSuccess) return LQR_ERR_CUDA;
+    for (int k = LQR_PHASE_LINK; k <= LQR_NUM_PHASES; ++k) prof_mark(h, k, st);
+    if (h->prof_on && h->prof_count < lqr_handle::kMaxProfiled) ++h->prof_count;
+    h->last_batch = nprob;
+    h->bstatus_off = stat_off;
+    h->breport_off = rep_off;
+    h->last_launches = 1;
+    h->last_K = nunits;
+    return LQR_OK;
+  }
   auto sweep = [&](int phase) {
     if (o->prec == LQR_FP64) return launch_seg_sweep<double, double>(tab, nunits, phase, smem_max, budget, store_P, st);
     if (o->prec == LQR_MIXED_TF32)
@@ -771,6 +811,69 @@ lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const
   h->breport_off = rep_off;
   h->last_launches = launches;
   h->last_K = nunits;
+  return LQR_OK;
+}
+
+int log2_bucket(long long v) {
+  int b = 0;
+  while (v > 1) { v >>= 1; ++b; }
+  return b;
+}
+
+// The batch schedule (step A10). Batches of FP32 multiplier-form problems that
+// want trajectories and fit the FP32 sweep and rollout plans can run as one
+// persistent launch of one-segment problems; otherwise, or when the per-step
+// launches (with the segment split of batch_segments) were measured faster for
+// this batch shape, one launch per step. The autotuner times both schedules on
+// the first batch of a shape bucket (problem count, largest n, m, horizon: the
+// call synchronises the stream then) and keeps the faster in the handle.
+lqr_status run_batched(lqr_handle* h, int nprob, const lqr_problem* probs, const lqr_opts* o,
+                       const lqr_solution* sols, int* segments_out, cudaStream_t st) {
+  int nmax = 0, mmax = 0, Tmax = 0;
+  bool all_xu = true;
+  for (int i = 0; i < nprob; ++i) {
+    if (probs[i].n > nmax) nmax = probs[i].n;
+    if (probs[i].m > mmax) mmax = probs[i].m;
+    if (probs[i].T > Tmax) Tmax = probs[i].T;
+    if (!sols[i].x || !sols[i].u) all_xu = false;
+  }
+  const long long budget = h->smem_optin - kStaticSmemReserve;
+  const bool eligible = o->prec == LQR_FP32 && o->form == LQR_FORM_MULTIPLIER && o->num_segments <= 1 && all_xu &&
+                        batch_persistent_supported(nmax, mmax, budget);
+  if (!eligible) return run_batched_impl(h, nprob, probs, o, sols, segments_out, st, false);
+  if (o->num_segments == 1) return run_batched_impl(h, nprob, probs, o, sols, segments_out, st, true);
+  const int key[4] = {log2_bucket(nprob), nmax, mmax, log2_bucket(Tmax)};
+  for (int i = 0; i < h->ntune; ++i)
+    if (memcmp(h->tune[i].key, key, sizeof(key)) == 0)
+      return run_batched_impl(h, nprob, probs, o, sols, segments_out, st, h->tune[i].persistent != 0);
+  // measure both schedules on this batch (each once to warm up, once timed)
+  cudaEvent_t ev[2];
+  if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) return LQR_ERR_CUDA;
+  float ms[2] = {0.f, 0.f};
+  lqr_status rs = LQR_OK;
+  for (int cand = 0; cand < 2 && rs == LQR_OK; ++cand) {
+    for (int rep = 0; rep < 2 && rs == LQR_OK; ++rep) {
+      if (rep == 1) cudaEventRecord(ev[0], st);
+      rs = run_batched_impl(h, nprob, probs, o, sols, segments_out, st, cand == 1);
+      if (rep == 1) cudaEventRecord(ev[1], st);
+    }
+    if (rs == LQR_OK && (cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms[cand], ev[0], ev[1]) != cudaSuccess))
+      rs = LQR_ERR_CUDA;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rs != LQR_OK) return rs;
+  const int pick = ms[1] <= ms[0] ? 1 : 0;
+  if (h->ntune < 64) {
+    lqr_handle::TuneEntry& te = h->tune[h->ntune++];
+    memcpy(te.key, key, sizeof(key));
+    te.persistent = pick;
+    te.ms[0] = ms[0];
+    te.ms[1] = ms[1];
+  }
+  // the outputs of the last (persistent) run stand; rerun only if the other schedule won
+  if (pick == 0) return run_batched_impl(h, nprob, probs, o, sols, segments_out, st, false);
   return LQR_OK;
 }
 

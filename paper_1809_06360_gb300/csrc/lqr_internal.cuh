@@ -237,10 +237,17 @@ cudaError_t launch_link_solve(const ProbTable& tab, int nprob, int x0_is_float, 
 cudaError_t launch_seg_sweep_f32(const ProbTable& tab, int nunits, int phase, int nmax, int mmax,
                                  long long smem_budget, int store_P, cudaStream_t st);
 long long fast_sweep_smem_bytes(int n, int m);
+long long rollout_f32_smem_bytes(int nmax, int mmax);
+// Step A10 in one persistent launch for batches of one-segment problems
+// (batch_persistent.cu): CTAs take problems from the LPT-ordered queue `order`
+// through the zeroed int `ticket`.
+bool batch_persistent_supported(int nmax, int mmax, long long smem_budget);
+cudaError_t launch_batch_persistent(const ProbTable& tab, const int* order, int* ticket, int want_lam, int nmax,
+                                    int mmax, int store_P, int num_sms, cudaStream_t st);
 // The policy sweep (step A4) with TF32 tensor-core stage products and the FP64
 // Cholesky factor of M_uu (seg_sweep_tc.cu), FP32 data, 64 < n <= 128, m <= 64.
 bool tc_sweep_supported(int n, int m);
-cudaError_t launch_seg_sweep_tc(const ProbTable& tab, int nunits, int store_P, cudaStream_t st);
+cudaError_t launch_seg_sweep_tc(const ProbTable& tab, int nunits, int store_P, long long spin_limit, cudaStream_t st);
 // the FP32 fast sweeps (and with them the kept M_uu^-1) apply to (n, m)
 bool fast_sweep_supported(int n, int m, long long smem_budget);
 // refinement corrections that reuse the factorisation (correct.cu)

@@ -29,7 +29,7 @@ namespace {
 
 constexpr int kTcBlock = 512;
 constexpr int NP = 128, MP = 64, NMP = NP + MP;  // padded n, m
-constexpr long long kTcSpin = 1LL << 26;         // polls of a completion wait before LQR_ERR_TIMEOUT
+constexpr long long kTcSpin = 1LL << 26;         // polls of a completion wait (32 ns apart) before LQR_ERR_TIMEOUT
 
 // Shared-memory plan (bytes from a 1024-byte-aligned base).
 constexpr uint32_t kOffAB = 0;                       // [A|B]': 192 rows x 128 K, swizzled
@@ -46,9 +46,11 @@ constexpr uint32_t kSmemBytes = kOffVec + kVecFloats * 4 + 1024;  // + alignment
 // TMEM columns
 constexpr uint32_t kTRa = 0, kTRb = 128, kTAA = 256, kTBB = 448, kTH = 0;
 
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& phase) {
-  const bool ok = tc::mbar_wait(bar, phase & 1u, kTcSpin);
-  ++phase;
+// Waits for the next completion of the mbarrier; the phase advances only when
+// it arrived, so that after a timeout `phase` still names the pending one.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t& phase, long long limit) {
+  const bool ok = tc::mbar_wait(bar, phase & 1u, limit);
+  if (ok) ++phase;
   tc::fence_after_sync();
   return ok;
 }
@@ -68,13 +70,14 @@ __device__ inline void trinv_f64_to_f32(int d, const double* L, int ldl, const d
   }
   for (int i = t; i < d; i += nthr) rdf[i] = (float)rd[i];
   __syncthreads();
+  // thread -> (row offset t / 64, column t % 64): 8 rows of 64 columns per pass
+  const int c = t & 63, r0 = t >> 6, rstep = nthr >> 6;
   for (int k = 0; k < d; ++k) {
-    for (int c = t; c <= k; c += nthr) X[k * ldx + c] *= rdf[k];
+    if (r0 == 0 && c <= k) X[k * ldx + c] *= rdf[k];
     __syncthreads();
-    const int rows = d - 1 - k, cols = k + 1;
-    for (int e = t; e < rows * cols; e += nthr) {
-      const int i = k + 1 + e / cols, c = e - (e / cols) * cols;
-      X[i * ldx + c] = fmaf(-Lf[i * ldx + k], X[k * ldx + c], X[i * ldx + c]);
+    if (c <= k) {
+      const float xk = X[k * ldx + c];
+      for (int i = k + 1 + r0; i < d; i += rstep) X[i * ldx + c] = fmaf(-Lf[i * ldx + k], xk, X[i * ldx + c]);
     }
     __syncthreads();
   }
@@ -84,7 +87,7 @@ __device__ inline void trinv_f64_to_f32(int d, const double* L, int ldl, const d
 
 bool tc_sweep_supported(int n, int m) { return n > 64 && n <= NP && m >= 1 && m <= MP; }
 
-__global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab, int store_P) {
+__global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab, int store_P, long long spin) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t s_bar;
   __shared__ uint32_t s_tmem;
@@ -148,7 +151,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
   const uint32_t aAB = tc::smem_addr(sAB), aV = tc::smem_addr(sV), aMux = tc::smem_addr(sMux),
                  aHx = tc::smem_addr(sHx), aMinv = tc::smem_addr(sMinv);
   uint32_t phase = 0;
-  int fail = 0;  // 0, LQR_ERR_TIMEOUT or LQR_ERR_NOT_PD (CTA-uniform once decided)
+  int fail = 0;     // 0, LQR_ERR_TIMEOUT or LQR_ERR_NOT_PD (CTA-uniform once decided)
+  int my_wait = 0;  // this thread's own wait ran out
 
   // stage data of stage s: [A|B]' element by element into the K-major tile
   // (lane -> 8 rows x 4 K positions of one 32-wide K block: conflict-free
@@ -233,8 +237,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
         else mu[r - NP] = a + rs[r - NP];
       }
     }
-    if (!wait_phase(&s_bar, phase)) fail = LQR_ERR_TIMEOUT;
-    if (__syncthreads_or(fail)) {
+    if (!wait_phase(&s_bar, phase, spin)) my_wait = 1;
+    if (__syncthreads_or(my_wait)) {
       fail = LQR_ERR_TIMEOUT;
       break;
     }
@@ -247,8 +251,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
       }
       tc::commit(&s_bar);
     }
-    if (!wait_phase(&s_bar, phase)) fail = LQR_ERR_TIMEOUT;
-    if (__syncthreads_or(fail)) {
+    if (!wait_phase(&s_bar, phase, spin)) my_wait = 1;
+    if (__syncthreads_or(my_wait)) {
       fail = LQR_ERR_TIMEOUT;
       break;
     }
@@ -260,7 +264,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int b = 16 * grp + q;
-        double val = (a < m && b < m) ? (double)v[q] + (double)gR[mm * st + (long long)a * m + b] : 0.0;
+        // R read transposed (coalesced over the lanes): M_uu is symmetrised below
+        double val = (a < m && b < m) ? (double)(v[q] + gR[mm * st + (long long)b * m + a]) : 0.0;
         L64[a * MP + b] = val;
       }
     }
@@ -339,8 +344,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) vx[i] = mx[i] - s;
     }
-    if (!wait_phase(&s_bar, phase)) fail = LQR_ERR_TIMEOUT;
-    if (__syncthreads_or(fail)) {
+    if (!wait_phase(&s_bar, phase, spin)) my_wait = 1;
+    if (__syncthreads_or(my_wait)) {
       fail = LQR_ERR_TIMEOUT;
       break;
     }
@@ -366,8 +371,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
         tc::mma_ss(tm + kTAA, tc::sdesc_k(aMux, NP, s), tc::sdesc_k(aHx, NP, s), tc::idesc_tf32(128, NP, true), 1);
       tc::commit(&s_bar);
     }
-    if (!wait_phase(&s_bar, phase)) fail = LQR_ERR_TIMEOUT;
-    if (__syncthreads_or(fail)) {
+    if (!wait_phase(&s_bar, phase, spin)) my_wait = 1;
+    if (__syncthreads_or(my_wait)) {
       fail = LQR_ERR_TIMEOUT;
       break;
     }
@@ -382,7 +387,8 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int j = j0 + q;
-          const float qv = (i < n && j < n) ? gQ[nn * st + (long long)i * n + j] : 0.0f;
+          // Q read transposed (coalesced over the lanes): V_t is symmetrised below
+          const float qv = (i < n && j < n) ? gQ[nn * st + (long long)j * n + i] : 0.0f;
           tc::sw_at(sV, NP, i, j) = (i < n && j < n) ? v[q] + qv : 0.0f;
         }
       }
@@ -411,7 +417,9 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
   // ---- clean-up: a failed wait gets one more bounded wait for the tensor core -------
   if (fail == LQR_ERR_TIMEOUT) {
     if (t == 0) raise_status(pd.status, LQR_ERR_TIMEOUT, -1);
-    tc::mbar_wait(&s_bar, phase & 1u, kTcSpin);
+    // the threads whose wait ran out wait once more, with the default limit, for
+    // the pending products (a thread that saw them complete has nothing pending)
+    if (my_wait) tc::mbar_wait(&s_bar, phase & 1u, kTcSpin);
   }
   cp_async_wait<0>();
   tc::fence_before_sync();
@@ -420,10 +428,10 @@ __global__ void __launch_bounds__(kTcBlock, 1) seg_sweep_tc_kernel(ProbTable tab
   if (warp == 0) tc::tmem_dealloc(tm, 512);
 }
 
-cudaError_t launch_seg_sweep_tc(const ProbTable& tab, int nunits, int store_P, cudaStream_t st) {
+cudaError_t launch_seg_sweep_tc(const ProbTable& tab, int nunits, int store_P, long long spin_limit, cudaStream_t st) {
   cudaError_t e = raise_dyn_smem((const void*)seg_sweep_tc_kernel, kSmemBytes);
   if (e != cudaSuccess) return e;
-  seg_sweep_tc_kernel<<<nunits, kTcBlock, kSmemBytes, st>>>(tab, store_P);
+  seg_sweep_tc_kernel<<<nunits, kTcBlock, kSmemBytes, st>>>(tab, store_P, spin_limit > 0 ? spin_limit : kTcSpin);
   return cudaGetLastError();
 }
 

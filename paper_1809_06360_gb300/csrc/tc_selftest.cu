@@ -195,3 +195,19 @@ extern "C" lqr_status lqr_tc_selftest(int device, double* errs) {
   if (prev >= 0) cudaSetDevice(prev);
   return st;
 }
+
+namespace lqr {
+namespace {
+__global__ void rcp_newton_kernel(const double* d, double* y, int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) y[i] = rcp_newton(d[i]);
+}
+}  // namespace
+}  // namespace lqr
+
+extern "C" lqr_status lqr_rcp_newton_check(const double* d, double* y, int count, void* stream) {
+  if (!d || !y || count < 0) return LQR_ERR_INVALID_ARG;
+  if (count == 0) return LQR_OK;
+  const int grid = (count + 255) / 256 < 1024 ? (count + 255) / 256 : 1024;
+  rcp_newton_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(d, y, count);
+  return cudaGetLastError() == cudaSuccess ? LQR_OK : LQR_ERR_CUDA;
+}

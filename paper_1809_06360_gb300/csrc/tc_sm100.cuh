@@ -136,11 +136,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Waits for the phase with the given parity to complete; false when `limit`
-// polls (each a hardware-suspended try_wait) pass without it.
+// polls (non-blocking tests, 32 ns apart) pass without it.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
-  for (long long i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
+  for (long long i = 0; i < limit; ++i) {
+    if (mbar_test_wait(bar, parity)) return true;
+    __nanosleep(32);
+  }
   return false;
 }
 

@@ -30,7 +30,8 @@ SOLUTION_FIELDS = ("K", "k", "x", "u", "P", "p", "lam")
 EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
-           "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest")
+           "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
+           "lqr_rcp_newton_check")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -44,7 +45,8 @@ class lqr_solution(ctypes.Structure):
 
 class lqr_opts(ctypes.Structure):
     _fields_ = [("prec", c_int), ("num_segments", c_int), ("tol", c_double), ("max_refine", c_int),
-                ("debug_checks", c_int), ("form", c_int), ("residual", c_int), ("link", c_int)]
+                ("debug_checks", c_int), ("form", c_int), ("residual", c_int), ("link", c_int),
+                ("spin_limit", ctypes.c_longlong)]
 
 
 class lqr_report_t(ctypes.Structure):
@@ -92,6 +94,7 @@ def load(path: str | None = None):
     lib.lqr_report_batched.argtypes = [c_void_p, c_void_p, c_int, P(c_int), P(c_double)]
     lib.lqr_kkt_residual_noalloc.argtypes = [P(lqr_problem), P(lqr_solution), c_int, c_void_p, c_void_p]
     lib.lqr_tc_selftest.argtypes = [c_int, P(c_double)]
+    lib.lqr_rcp_newton_check.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
     lib.lqr_backward.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p, c_void_p,
                                  P(lqr_problem), c_void_p]
     lib.lqr_backward_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution),
@@ -99,7 +102,8 @@ def load(path: str | None = None):
     for name in ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve_host",
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
-                 "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest"):
+                 "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
+                 "lqr_rcp_newton_check"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -207,6 +211,10 @@ def lqr_tc_selftest(device: int = 0) -> list[float]:
     return [errs[i] for i in range(5)]
 
 
+def lqr_rcp_newton_check(d_ptr: int, y_ptr: int, count: int, stream: int | None) -> None:
+    _check(load().lqr_rcp_newton_check(d_ptr, y_ptr, count, stream or None), "lqr_rcp_newton_check")
+
+
 def lqr_profile_enable(h: int, enable: bool) -> None:
     _check(load().lqr_profile_enable(h, 1 if enable else 0), "lqr_profile_enable")
 
@@ -280,7 +288,7 @@ class Solver:
         return out
 
     def solve(self, prob, num_segments=0, prec="fp64", out=None, want=("K", "k", "x", "u", "lam"),
-              stream=None, tol=1e-8, max_refine=0, form="multiplier", residual=False, link="auto"):
+              stream=None, tol=1e-8, max_refine=0, form="multiplier", residual=False, link="auto", spin_limit=0):
         """Enqueue a solve on `stream` (torch stream; default current). Returns the output tensors."""
         if out is None:
             out = self.alloc_solution(prob, want)
@@ -288,7 +296,8 @@ class Solver:
         p = self.make_problem_struct(prob, ptr)
         s = lqr_solution(**{f: (out[f].data_ptr() if f in out else None) for f in SOLUTION_FIELDS})
         o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
-                     debug_checks=0, form=FORM[form], residual=1 if residual else 0, link=LINK[link])
+                     debug_checks=0, form=FORM[form], residual=1 if residual else 0, link=LINK[link],
+                     spin_limit=spin_limit)
         lqr_solve(self.h, p, o, s, self._stream(stream))
         return out
 

@@ -90,3 +90,38 @@ def test_autograd_batch_fp32(solver):
             worst = max(worst, oracle.rel_err(stacked[k].grad[i].double().cpu().numpy(), ref[k]))
     print("fp32 batched adjoint worst rel err %.2e" % worst)
     assert worst < 1e-3
+
+
+@pytest.fixture(scope="module")
+def config4():
+    return workloads.config4()
+
+
+def test_config4_differentiable_batch(solver, config4):
+    """The differentiable batch at full size: 256 problems n=32, m=8, T=256,
+    K=16 in FP32, loss sum |x_t|^2 + |u_t|^2 through torch.autograd
+    (lqr_batch: one batched forward solve, one batched adjoint solve). Four
+    problems spread over the batch are checked on sampled entries of every
+    gradient against FP64 central finite differences of the serial oracle
+    (h = 1e-6), at the FP32 bound 1e-3 of each array's largest gradient entry;
+    every problem's trajectory is checked against the oracle at the FP32 bound."""
+    from paper_1809_06360_gb300.autograd import lqr_batch
+    probs = config4
+    stacked = {k: torch.from_numpy(np.stack([p[k] for p in probs])).to("cuda:0", torch.float32).requires_grad_(True)
+               for k in FIELDS}
+    x, u = lqr_batch(*[stacked[k] for k in FIELDS], num_segments=16, prec="fp32")
+    ((x ** 2).sum() + (u ** 2).sum()).backward()
+    xs = x.detach().double().cpu().numpy()
+    us = u.detach().double().cpu().numpy()
+    for i, p in enumerate(probs):
+        ric = oracle.riccati(p, want_P=False)
+        assert oracle.rel_err(xs[i], ric["x"]) < 1e-3 and oracle.rel_err(us[i], ric["u"]) < 1e-3, i
+    for i in (0, 63, 128, 255):
+        fd = oracle.fd_gradient(probs[i], sq_loss, keys=("A", "B", "Q", "R", "q", "r", "x0", "c"), entries=4,
+                                h=1e-6, seed=i)
+        for k, v in fd.items():
+            g = stacked[k].grad[i].double().cpu().numpy()
+            mask = ~np.isnan(v)
+            scale = max(1e-12, np.abs(g).max())
+            err = np.abs(g[mask] - v[mask]).max() / scale
+            assert err < 1e-3, (i, k, err)

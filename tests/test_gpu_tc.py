@@ -66,3 +66,42 @@ def test_tensor_core_policy_sweep(solver, n, m, T, K):
     for k in ("x", "u", "lam"):
         assert e[k] < 1e-9, e
     assert e["K"] < 3e-2
+
+
+def test_rcp_newton_against_ieee_division(lib):
+    """The FP64 pivot reciprocal (FP32 seed + two Newton-Raphson steps) against
+    IEEE 1/d over magnitudes 1e-300 .. 1e300 and both signs: the seed has
+    about 23 correct bits, each step doubles them (46, then beyond the 53 of
+    FP64), so the result is within 1 ulp of the correctly rounded reciprocal;
+    outside the FP32 exponent range the division itself is used."""
+    import numpy as np
+    g = np.random.default_rng(3)
+    mant = g.uniform(1.0, 2.0, size=20000)
+    expo = g.integers(-996, 997, size=20000)
+    sign = np.where(g.random(20000) < 0.5, -1.0, 1.0)
+    d = sign * np.ldexp(mant, expo)
+    d = np.concatenate([d, [1.0, -1.0, 3.0, 1e-30 * 1.5, 1e30 / 1.5, 2.0 ** 126, 2.0 ** -125]])
+    dd = torch.from_numpy(d).cuda()
+    y = torch.empty_like(dd)
+    lib.lqr_rcp_newton_check(dd.data_ptr(), y.data_ptr(), dd.numel(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    ref = 1.0 / d
+    ulp = np.abs(got - ref) / np.spacing(np.abs(ref))
+    print("rcp_newton max ulp", ulp.max())
+    assert ulp.max() <= 1.0, ulp.max()
+
+
+def test_bounded_wait_times_out_and_recovers(solver):
+    """A spin limit of one poll makes the tensor-core sweep's completion waits
+    run out: the solve reports LQR_ERR_TIMEOUT (the kernel waits once more,
+    with the default limit, for its own tensor-core products, frees its tensor
+    memory and returns), and the next solve on the same handle succeeds."""
+    import workloads
+    prob = workloads.make_problem(128, 64, 128, seed=77, rho_max=1.02)
+    dev = _dev(prob)
+    solver.solve(dev, num_segments=8, prec="mixed", spin_limit=1)
+    rep = solver.report()
+    assert rep["status_name"] == "LQR_ERR_TIMEOUT", rep
+    solver.solve(dev, num_segments=8, prec="mixed", max_refine=10, tol=1e-11)
+    assert solver.report()["status"] == 0
