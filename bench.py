@@ -43,6 +43,19 @@ UNIT = "stages/s"
 SMS, SM_MHZ = 152, 2070.0
 PEAK_FP64_TFLOPS = SMS * 2 * 2 * SM_MHZ * 1e6 / 1e12      # 1.259
 PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MHZ * 1e6 / 1e12    # 80.5
+# dense TF32 tensor peak: the measured bf16 cuBLAS peak x the nominal TF32:BF16
+# ratio 1.1 : 2.25 PFLOP/s (dense)
+
+
+def _tf32_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)["bf16_tflops"] * 1.1 / 2.25
+    except (OSError, ValueError, KeyError):
+        return 1900.0 * 1.1 / 2.25
+
+
+PEAK_TF32_TFLOPS = _tf32_peak()
 
 # bytes per launch (read + write) measured by ncu on the default FP32 workload;
 # an entry is removed whenever its kernel changes
@@ -215,6 +228,31 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = WORKLOADS[args.config]
+    if wl.get("batch"):
+        import oracle
+        probs = wl["make"]()[:wl["ref_problems"]]
+        oracle.riccati(_prefix(probs[0], 2), want_P=False)
+        stages = sum(p["B"].shape[0] for p in probs)
+        for _ in range(args.warmup):
+            oracle.riccati(probs[0], want_P=False)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for p in probs:
+                oracle.riccati(p, want_P=False)
+        el = time.perf_counter() - t0
+        value = args.steps * stages / el
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic (seeded PCG64)",
+                          "config": {"workload": "%s (per step: the first %d problems, serial FP64 Riccati oracle "
+                                                 "on the host, forward solves)" % (wl["name"], len(probs))},
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                           "sample": "%d steps x %d problems (%d stages), one thread" %
+                                                     (args.steps, len(probs), stages)},
+                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+              flush=True)
+        return
     n, m, T = wl["n"], wl["m"], wl["T"]
     prob = wl["make"]()
     T_sample = min(wl["ref_stages"], T)
@@ -252,7 +290,140 @@ WORKLOADS = {
             unrefined="fp32"),
     0: dict(name="single LQR n=12 m=4 T=128", n=12, m=4, T=128, K=8, prec="fp64", make=workloads.config0,
             Kgrid=(1, 8, 16), fp64_K=(8,), cpu_stages=128, ref_stages=128, unrefined=None),
+    3: dict(name="uneven batch of 4096 LQR problems, T~U{32..512}, n in {8,16,32,48}, m~U{2..16}", batch=True,
+            make=workloads.config3, K=0, backward=False, ref_problems=64),
+    4: dict(name="differentiable batch of 256 LQR problems n=32 m=8 T=256, forward + adjoint, loss sum |x|^2+|u|^2",
+            batch=True, make=workloads.config4, K=16, backward=True, ref_problems=16),
 }
+
+
+def riccati_stage_flops(n: int, m: int) -> float:
+    """Algorithmic FLOPs of one plain Riccati stage as the FP32 sweep evaluates it
+    (V[A|B|c], [A|B]'V[A|B], the M_uu inverse, H and the downdate)."""
+    return 4 * n ** 3 + 6 * n ** 2 * m + 4 * n * m ** 2 + 2 * m ** 3
+
+
+def run_batch_bench(args, wl, rank, world, local):
+    """A batch workload: one step = one batched solve (the uneven batch) or one
+    batched forward solve plus one batched adjoint solve (the differentiable
+    batch), all problems, FP32."""
+    import torch
+    import torch.distributed as dist
+    from paper_1809_06360_gb300 import lqr
+
+    device = f"cuda:{local}"
+    probs_np = wl["make"]()
+    stages = sum(p["B"].shape[0] for p in probs_np)
+    dev = [{k: torch.from_numpy(v).to(device, torch.float32) for k, v in p.items()} for p in probs_np]
+    solver = lqr.Solver(local)
+    outs = [solver.alloc_solution(p, ("K", "k", "x", "u", "lam")) for p in dev]
+    stream = torch.cuda.current_stream()
+    K = args.segments or wl["K"]
+    back = wl["backward"]
+    gx = [torch.zeros_like(o["x"]) for o in outs] if back else None
+    gu = [torch.zeros_like(o["u"]) for o in outs] if back else None
+
+    def step():
+        solver.solve_batched(dev, prec="fp32", num_segments=K, outs=outs)
+        if back:
+            for o, a, b in zip(outs, gx, gu):  # dL/dx, dL/du of the loss sum |x|^2 + |u|^2
+                torch.mul(o["x"], 2.0, out=a)
+                torch.mul(o["u"], 2.0, out=b)
+            solver.backward_batched(dev, outs, gx, gu, prec="fp32", num_segments=K)
+
+    for _ in range(args.warmup):
+        step()
+    st, _ = solver.report_batched(len(dev))
+    if any(x != 0 for x in st):
+        raise SystemExit("batched solve failed: %s" % sorted(set(st)))
+    solver.solve_batched(dev, prec="fp32", num_segments=K, outs=outs)
+    fwd_launches = lqr.lqr_last_launch_count(solver.h)
+    step_launches = fwd_launches
+    if back:  # the adjoint's batched solve with its right-hand-side and gradient kernels
+        solver.backward_batched(dev, outs, gx, gu, prec="fp32", num_segments=K)
+        step_launches += lqr.lqr_last_launch_count(solver.h)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ms = _timed(stream, step, args.steps) * args.steps
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks([ms], world, device)[0]
+    value = whole_job_rate(stages, args.steps, world, ms / 1e3)
+    # roofline: the algorithmic FLOPs of the Riccati stages (the adjoint solve
+    # runs the same sweeps once more) over the device time of the step
+    flops = sum(p["B"].shape[0] * riccati_stage_flops(p["B"].shape[1], p["B"].shape[2]) for p in probs_np)
+    if back:
+        flops *= 2
+    ach = flops / (ms / args.steps / 1e3) / 1e12
+    sched = "one persistent launch" if fwd_launches == 1 else "per-step launches (%d)" % fwd_launches
+    roofline = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / PEAK_FP32_TFLOPS, "traffic": None,
+                "kernel": ("batch_persistent_kernel (A10: sweep, rollout and objective per problem)" if fwd_launches == 1
+                           else "seg_sweep_f32_kernel, link, rollout (per-step launches)") +
+                          (", then the batched adjoint solve" if back else ""),
+                "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2070 MHz", "work_flops_per_step": flops}
+    e2e = None
+    if not args.no_e2e:
+        # inputs copied in from pinned host memory and x, u read back, every step
+        pin = [{k: torch.from_numpy(v.astype(np.float32)).pin_memory() for k, v in p.items()} for p in probs_np]
+        hx = [torch.empty(o["x"].shape, dtype=torch.float32).pin_memory() for o in outs]
+        hu = [torch.empty(o["u"].shape, dtype=torch.float32).pin_memory() for o in outs]
+
+        def e2e_step():
+            for d, hp in zip(dev, pin):
+                for k in d:
+                    d[k].copy_(hp[k], non_blocking=True)
+            step()
+            for o, a, b in zip(outs, hx, hu):
+                a.copy_(o["x"], non_blocking=True)
+                b.copy_(o["u"], non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        n_e2e = max(2, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        el = max_over_ranks([time.perf_counter() - t0], world, device)[0]
+        e2e = {"value": whole_job_rate(stages, n_e2e, world, el), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(v.nbytes for hp in pin for v in hp.values())),
+               "d2h_bytes_per_step": int(sum(a.numel() * 4 + b.numel() * 4 for a, b in zip(hx, hu))),
+               "steps": n_e2e}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.riccati(_prefix(probs_np[0], 2), want_P=False)
+        t0, done, st_done = time.perf_counter(), 0, 0
+        while time.perf_counter() - t0 < 12.0 and done < len(probs_np):
+            oracle.riccati(probs_np[done], want_P=False)
+            st_done += probs_np[done]["B"].shape[0]
+            done += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": st_done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "the FP64 serial Riccati oracle (single thread, C) on the first %d problems of the batch "
+                         "(%d stages, forward solves only), %.1f s" % (done, st_done, el)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic (seeded PCG64), inputs resident in HBM",
+                "config": {"workload": wl["name"], "problems": len(probs_np), "stages": stages,
+                           "K": K if K else "chosen by the batch schedule", "schedule": sched,
+                           "precision": "FP32 data and sweeps",
+                           "l2": "inputs (%.2f GB FP32) larger than L2 (129 MB)" % (
+                               sum(v.nbytes for p in probs_np for v in p.values()) / 2e9),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": step_launches * args.steps}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
 
 def _timed(stream, fn, reps):
     """Mean device time (ms) of fn() over reps calls, CUDA events on stream."""
@@ -305,6 +476,9 @@ def main():
     build.build()
 
     wl = WORKLOADS[args.config]
+    if wl.get("batch"):
+        run_batch_bench(args, wl, rank, world, local)
+        return
     n, m, T = wl["n"], wl["m"], wl["T"]
     K = args.segments or wl["K"]
     prec = args.prec or wl["prec"]
@@ -371,18 +545,27 @@ def main():
     fast = prec in ("fp32", "mixed_fp32") and args.form == "multiplier" and n <= 64
     es = 4 if prec in ("fp32", "mixed_fp32") else 8
     sweep_k = "seg_sweep_f32_kernel" if fast else "seg_sweep_kernel"
+    fp32_link = prec in ("fp32", "mixed_fp32") or (prec == "mixed" and n > 67)
     if fast and K > 1:
         link = {"kernel": "link_scan_kernel levels + feedback pass + link states (A3, FP32 scan)", "bound": "alu",
                 "unit": "TFLOP/s", "work": link_scan_flops(n, K), "peak": PEAK_FP32_TFLOPS}
+    elif fp32_link and n > 67:
+        link = {"kernel": "link_chain_f32_kernel + link_post_kernel<float> + link_forward_kernel (A3, FP32 chain)",
+                "bound": "alu", "unit": "TFLOP/s", "work": link_flops(n, K), "peak": PEAK_FP32_TFLOPS}
     else:
         link = {"kernel": ("link_solve_dual_cluster_kernel" if n <= 67 else "link_solve_dual_kernel") +
                           " (A3, FP64 block elimination)", "bound": "alu",
                 "unit": "TFLOP/s", "work": link_flops(n, K), "peak": PEAK_FP64_TFLOPS}
+    # the mixed TF32 mode runs the policy sweeps on the tensor cores for 64 < n <= 128, m <= 64
+    tc_policy = prec == "mixed" and 64 < n <= 128 and m <= 64
     phases = {
         "sweep": {"kernel": sweep_k + " phase 0 (A1)", "bound": "alu", "unit": "TFLOP/s",
                   "work": sweep_flops(n, m, T, K, "sweep"), "peak": alu_peak},
-        "policy": {"kernel": sweep_k + " phase 1 (A4)", "bound": "alu", "unit": "TFLOP/s",
-                   "work": sweep_flops(n, m, T, K, "policy"), "peak": alu_peak},
+        "policy": ({"kernel": "seg_sweep_tc_kernel (A4, tcgen05 TF32 products, FP64 factor of M_uu)",
+                    "bound": "tensor", "unit": "TFLOP/s", "work": sweep_flops(n, m, T, K, "policy"),
+                    "peak": PEAK_TF32_TFLOPS} if tc_policy else
+                   {"kernel": sweep_k + " phase 1 (A4)", "bound": "alu", "unit": "TFLOP/s",
+                    "work": sweep_flops(n, m, T, K, "policy"), "peak": alu_peak}),
         "link": link,
         "rollout": {"kernel": ("rollout_f32_kernel" if fast else "rollout_stream_kernel") + " + finalize (A5/A6)",
                     "bound": "hbm", "unit": "GB/s",
@@ -396,12 +579,17 @@ def main():
         d["frac"] = d["achieved"] / d["peak"]
     # per kernel function: the A1 and A4 sweeps are two launches of one kernel
     kern = {
-        sweep_k: {"kernel": sweep_k + " (A1 + A4, two launches per solve)", "bound": "alu", "unit": "TFLOP/s",
-                  "work": phases["sweep"]["work"] + phases["policy"]["work"],
-                  "ms": phases["sweep"]["ms"] + phases["policy"]["ms"], "peak": alu_peak, "launches": 2},
+        sweep_k: ({"kernel": sweep_k + " (A1)", "bound": "alu", "unit": "TFLOP/s",
+                   "work": phases["sweep"]["work"], "ms": phases["sweep"]["ms"], "peak": alu_peak, "launches": 1}
+                  if tc_policy else
+                  {"kernel": sweep_k + " (A1 + A4, two launches per solve)", "bound": "alu", "unit": "TFLOP/s",
+                   "work": phases["sweep"]["work"] + phases["policy"]["work"],
+                   "ms": phases["sweep"]["ms"] + phases["policy"]["ms"], "peak": alu_peak, "launches": 2}),
         "link": dict(phases["link"], launches=None),
         "rollout": dict(phases["rollout"], launches=2),
     }
+    if tc_policy:
+        kern["seg_sweep_tc_kernel"] = dict(phases["policy"], launches=1)
     for d in kern.values():
         d["achieved"] = (d["work"] / (d["ms"] / 1e3) / 1e12) if d["ms"] > 0 and d["unit"] == "TFLOP/s" else d["achieved"]
         d["frac"] = d["achieved"] / d["peak"]
@@ -415,6 +603,7 @@ def main():
                 "frac": dd["frac"], "traffic": traffic, "kernel": dd["kernel"],
                 "peak_source": ("derived: 152 SMs x 2 DFMA/clk x 2070 MHz" if dd["peak"] == PEAK_FP64_TFLOPS else
                                 "derived: 152 SMs x 128 FFMA/clk x 2070 MHz" if dd["peak"] == PEAK_FP32_TFLOPS else
+                                "measured bf16 x 1.1/2.25 (nominal TF32:BF16)" if dd["peak"] == PEAK_TF32_TFLOPS else
                                 "measured (MEASURED_PEAKS.json hbm_gbs)"),
                 "phases": {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in d.items()}
                            for k, d in phases.items()},

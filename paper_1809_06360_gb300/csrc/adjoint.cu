@@ -15,32 +15,70 @@
 //     dL/dB_t = lambda_{t+1} xi_u,t' + xi_l,t+1 u_t'
 // (xi_l = the multiplier part of xi, lambda = the forward multipliers).
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include "lqr_internal.cuh"
 
 namespace lqr {
 
-// Loads the adjoint problem's vector data: q~ = -gx, r~ = -gu, c~ = 0, x0~ = 0.
+// One problem's adjoint job: its dimensions, dL/dx and dL/du (null = 0), the
+// adjoint problem's vector data, the forward and adjoint solutions, and the
+// gradient outputs (null = not wanted).
+struct AdjJob {
+  int n, m, T;
+  const void *gx, *gu;
+  void *q, *r, *c, *x0;
+  const void *x, *u, *lam, *xix, *xiu, *xil;
+  void *dA, *dB, *dc, *dQ, *dR, *dS, *dq, *dr, *dx0;
+};
+
+// Loads the adjoint problem's vector data: q~ = -gx, r~ = -gu, c~ = 0, x0~ = 0
+// (blocks `blk` of `nblk` of the job).
 template <typename TS>
-__global__ void adjoint_rhs_kernel(int n, int m, int T, const TS* gx, const TS* gu, TS* q, TS* r, TS* c, TS* x0) {
+__device__ __forceinline__ void adjoint_rhs_job(const AdjJob& jb, int blk, int nblk) {
+  const int n = jb.n, m = jb.m, T = jb.T;
+  const TS* gx = static_cast<const TS*>(jb.gx);
+  const TS* gu = static_cast<const TS*>(jb.gu);
+  TS* q = static_cast<TS*>(jb.q);
+  TS* r = static_cast<TS*>(jb.r);
+  TS* c = static_cast<TS*>(jb.c);
+  TS* x0 = static_cast<TS*>(jb.x0);
   const size_t nx = (size_t)(T + 1) * n, nu = (size_t)T * m, nc = (size_t)T * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nx; e += (size_t)gridDim.x * blockDim.x) {
-    q[e] = gx ? static_cast<TS>(-gx[e]) : TS(0);
+  const size_t ne = nx > nu ? nx : nu;
+  for (size_t e = blk * (size_t)blockDim.x + threadIdx.x; e < ne; e += (size_t)nblk * blockDim.x) {
+    if (e < nx) q[e] = gx ? static_cast<TS>(-gx[e]) : TS(0);
     if (e < nu) r[e] = gu ? static_cast<TS>(-gu[e]) : TS(0);
     if (e < nc) c[e] = TS(0);
     if (e < (size_t)n) x0[e] = TS(0);
   }
 }
-
-// One CTA per stage (grid-stride); writes the gradients of stage t (and the
-// terminal / initial terms from the CTA of t = 0). Output pointers may be null.
 template <typename TS>
-__global__ void __launch_bounds__(kBlock) adjoint_grad_kernel(int n, int m, int T, const TS* x, const TS* u,
-                                                              const TS* lam, const TS* xix, const TS* xiu,
-                                                              const TS* xil, TS* dA, TS* dB, TS* dc, TS* dQ, TS* dR,
-                                                              TS* dS, TS* dq, TS* dr, TS* dx0) {
+__global__ void adjoint_rhs_kernel(AdjJob jb) { adjoint_rhs_job<TS>(jb, blockIdx.x, gridDim.x); }
+template <typename TS>
+__global__ void adjoint_rhs_batched_kernel(const AdjJob* jobs) { adjoint_rhs_job<TS>(jobs[blockIdx.y], blockIdx.x, gridDim.x); }
+
+// Stages dealt over blocks `blk` of `nblk` of the job; the terminal and initial
+// terms by block 0.
+template <typename TS>
+__device__ __forceinline__ void adjoint_grad_job(const AdjJob& jb, int blk, int nblk) {
+  const int n = jb.n, m = jb.m, T = jb.T;
+  const TS* x = static_cast<const TS*>(jb.x);
+  const TS* u = static_cast<const TS*>(jb.u);
+  const TS* lam = static_cast<const TS*>(jb.lam);
+  const TS* xix = static_cast<const TS*>(jb.xix);
+  const TS* xiu = static_cast<const TS*>(jb.xiu);
+  const TS* xil = static_cast<const TS*>(jb.xil);
+  TS* dA = static_cast<TS*>(jb.dA);
+  TS* dB = static_cast<TS*>(jb.dB);
+  TS* dc = static_cast<TS*>(jb.dc);
+  TS* dQ = static_cast<TS*>(jb.dQ);
+  TS* dR = static_cast<TS*>(jb.dR);
+  TS* dS = static_cast<TS*>(jb.dS);
+  TS* dq = static_cast<TS*>(jb.dq);
+  TS* dr = static_cast<TS*>(jb.dr);
+  TS* dx0 = static_cast<TS*>(jb.dx0);
   const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
-  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+  for (int t = blk; t < T; t += nblk) {
     const TS* xt = x + (size_t)n * t;
     const TS* ut = u + (size_t)m * t;
     const TS* ln = lam + (size_t)n * (t + 1);
@@ -79,7 +117,7 @@ __global__ void __launch_bounds__(kBlock) adjoint_grad_kernel(int n, int m, int 
     if (dr)
       for (int a = threadIdx.x; a < m; a += blockDim.x) dr[(size_t)m * t + a] = static_cast<TS>(-(double)au[a]);
   }
-  if (blockIdx.x == 0) {
+  if (blk == 0) {
     const TS* xT = x + (size_t)n * T;
     const TS* aT = xix + (size_t)n * T;
     if (dQ)
@@ -93,25 +131,61 @@ __global__ void __launch_bounds__(kBlock) adjoint_grad_kernel(int n, int m, int 
     }
   }
 }
+template <typename TS>
+__global__ void __launch_bounds__(kBlock) adjoint_grad_kernel(AdjJob jb) { adjoint_grad_job<TS>(jb, blockIdx.x, gridDim.x); }
+template <typename TS>
+__global__ void __launch_bounds__(kBlock) adjoint_grad_batched_kernel(const AdjJob* jobs) {
+  adjoint_grad_job<TS>(jobs[blockIdx.y], blockIdx.x, gridDim.x);
+}
 
 template <typename TS>
 cudaError_t launch_adjoint_rhs(int n, int m, int T, const void* gx, const void* gu, void* q, void* r, void* c,
                                void* x0, cudaStream_t st) {
-  adjoint_rhs_kernel<TS><<<2 * device_sm_count(), 256, 0, st>>>(n, m, T, static_cast<const TS*>(gx), static_cast<const TS*>(gu),
-                                                  static_cast<TS*>(q), static_cast<TS*>(r), static_cast<TS*>(c),
-                                                  static_cast<TS*>(x0));
+  AdjJob jb;
+  memset(&jb, 0, sizeof(jb));
+  jb.n = n; jb.m = m; jb.T = T; jb.gx = gx; jb.gu = gu; jb.q = q; jb.r = r; jb.c = c; jb.x0 = x0;
+  adjoint_rhs_kernel<TS><<<2 * device_sm_count(), 256, 0, st>>>(jb);
   return cudaGetLastError();
 }
 
 template <typename TS>
 cudaError_t launch_adjoint_grad(int n, int m, int T, const void* x, const void* u, const void* lam, const void* xix,
                                 const void* xiu, const void* xil, const lqr_problem* g, cudaStream_t st) {
+  AdjJob jb;
+  memset(&jb, 0, sizeof(jb));
+  jb.n = n; jb.m = m; jb.T = T; jb.x = x; jb.u = u; jb.lam = lam; jb.xix = xix; jb.xiu = xiu; jb.xil = xil;
+  jb.dA = (void*)g->A; jb.dB = (void*)g->B; jb.dc = (void*)g->c; jb.dQ = (void*)g->Q; jb.dR = (void*)g->R;
+  jb.dS = (void*)g->S; jb.dq = (void*)g->q; jb.dr = (void*)g->r; jb.dx0 = (void*)g->x0;
   const int grid = T < 4 * device_sm_count() ? T : 4 * device_sm_count();
-  adjoint_grad_kernel<TS><<<grid, kBlock, 0, st>>>(
-      n, m, T, static_cast<const TS*>(x), static_cast<const TS*>(u), static_cast<const TS*>(lam),
-      static_cast<const TS*>(xix), static_cast<const TS*>(xiu), static_cast<const TS*>(xil),
-      (TS*)g->A, (TS*)g->B, (TS*)g->c, (TS*)g->Q, (TS*)g->R, (TS*)g->S, (TS*)g->q, (TS*)g->r, (TS*)g->x0);
+  adjoint_grad_kernel<TS><<<grid, kBlock, 0, st>>>(jb);
   return cudaGetLastError();
+}
+
+// The batched forms: one launch each over a device table of njobs jobs
+// (blocks per job on the x dimension, jobs on y).
+template <typename TS>
+cudaError_t launch_adjoint_rhs_batched(const void* jobs, int njobs, cudaStream_t st) {
+  dim3 grid(4, njobs);
+  adjoint_rhs_batched_kernel<TS><<<grid, 256, 0, st>>>(static_cast<const AdjJob*>(jobs));
+  return cudaGetLastError();
+}
+template <typename TS>
+cudaError_t launch_adjoint_grad_batched(const void* jobs, int njobs, int Tmax, cudaStream_t st) {
+  dim3 grid(Tmax < 32 ? Tmax : 32, njobs);
+  adjoint_grad_batched_kernel<TS><<<grid, kBlock, 0, st>>>(static_cast<const AdjJob*>(jobs));
+  return cudaGetLastError();
+}
+size_t adjoint_job_bytes() { return sizeof(AdjJob); }
+void adjoint_job_fill(void* dst, int n, int m, int T, const void* gx, const void* gu, void* q, void* r, void* c,
+                      void* x0, const void* x, const void* u, const void* lam, const void* xix, const void* xiu,
+                      const void* xil, const lqr_problem* g) {
+  AdjJob jb;
+  memset(&jb, 0, sizeof(jb));
+  jb.n = n; jb.m = m; jb.T = T; jb.gx = gx; jb.gu = gu; jb.q = q; jb.r = r; jb.c = c; jb.x0 = x0;
+  jb.x = x; jb.u = u; jb.lam = lam; jb.xix = xix; jb.xiu = xiu; jb.xil = xil;
+  jb.dA = (void*)g->A; jb.dB = (void*)g->B; jb.dc = (void*)g->c; jb.dQ = (void*)g->Q; jb.dR = (void*)g->R;
+  jb.dS = (void*)g->S; jb.dq = (void*)g->q; jb.dr = (void*)g->r; jb.dx0 = (void*)g->x0;
+  memcpy(dst, &jb, sizeof(jb));
 }
 
 template cudaError_t launch_adjoint_rhs<double>(int, int, int, const void*, const void*, void*, void*, void*, void*,
@@ -122,5 +196,9 @@ template cudaError_t launch_adjoint_grad<double>(int, int, int, const void*, con
                                                  const void*, const void*, const lqr_problem*, cudaStream_t);
 template cudaError_t launch_adjoint_grad<float>(int, int, int, const void*, const void*, const void*, const void*,
                                                 const void*, const void*, const lqr_problem*, cudaStream_t);
+template cudaError_t launch_adjoint_rhs_batched<double>(const void*, int, cudaStream_t);
+template cudaError_t launch_adjoint_rhs_batched<float>(const void*, int, cudaStream_t);
+template cudaError_t launch_adjoint_grad_batched<double>(const void*, int, int, cudaStream_t);
+template cudaError_t launch_adjoint_grad_batched<float>(const void*, int, int, cudaStream_t);
 
 }  // namespace lqr

@@ -951,41 +951,47 @@ lqr_status lqr_backward_batched(lqr_handle* h, int nprob, const lqr_problem* pro
   size_t es = 0;
   elem_size(opts->prec, &es);
   size_t total = 0;
-  for (int i = 0; i < nprob; ++i) total += adj_layout(0, probs[i].n, probs[i].m, probs[i].T, es).total;
-  lqr_status r = grow(&h->adj, &h->adj_bytes, total);
+  int Tmax = 0;
+  for (int i = 0; i < nprob; ++i) {
+    total += adj_layout(0, probs[i].n, probs[i].m, probs[i].T, es).total;
+    if (probs[i].T > Tmax) Tmax = probs[i].T;
+  }
+  // the job table of the adjoint's right-hand-side and gradient kernels follows the vectors
+  const size_t job_off = (total + 255) & ~(size_t)255;
+  const size_t jb = adjoint_job_bytes();
+  lqr_status r = grow(&h->adj, &h->adj_bytes, job_off + jb * (size_t)nprob);
   if (r != LQR_OK) return r;
   lqr_problem* ap = (lqr_problem*)malloc(sizeof(lqr_problem) * (size_t)nprob);
   lqr_solution* as = (lqr_solution*)malloc(sizeof(lqr_solution) * (size_t)nprob);
-  if (!ap || !as) { free(ap); free(as); return LQR_ERR_OOM; }
+  unsigned char* jobs = (unsigned char*)malloc(jb * (size_t)nprob);
+  if (!ap || !as || !jobs) { free(ap); free(as); free(jobs); return LQR_ERR_OOM; }
   size_t off = 0;
+  unsigned char* b = h->adj;
   for (int i = 0; i < nprob; ++i) {
     const lqr_problem& p = probs[i];
     const AdjLayout al = adj_layout(off, p.n, p.m, p.T, es);
     off += al.total;
-    unsigned char* b = h->adj;
-    cudaError_t e = (es == 8)
-        ? launch_adjoint_rhs<double>(p.n, p.m, p.T, grad_x ? grad_x[i] : nullptr, grad_u ? grad_u[i] : nullptr,
-                                     b + al.q, b + al.r, b + al.c, b + al.x0, st)
-        : launch_adjoint_rhs<float>(p.n, p.m, p.T, grad_x ? grad_x[i] : nullptr, grad_u ? grad_u[i] : nullptr,
-                                    b + al.q, b + al.r, b + al.c, b + al.x0, st);
-    if (e != cudaSuccess) { free(ap); free(as); return LQR_ERR_CUDA; }
     ap[i] = p;
     ap[i].q = b + al.q; ap[i].r = b + al.r; ap[i].c = b + al.c; ap[i].x0 = b + al.x0;
     memset(&as[i], 0, sizeof(lqr_solution));
     as[i].K = b + al.K; as[i].k = b + al.k; as[i].x = b + al.x; as[i].u = b + al.u; as[i].lam = b + al.l;
+    adjoint_job_fill(jobs + jb * i, p.n, p.m, p.T, grad_x ? grad_x[i] : nullptr, grad_u ? grad_u[i] : nullptr,
+                     b + al.q, b + al.r, b + al.c, b + al.x0, sols[i].x, sols[i].u, sols[i].lam, as[i].x, as[i].u,
+                     as[i].lam, &grads[i]);
   }
-  r = run_batched(h, nprob, ap, opts, as, nullptr, st);
+  // pageable source: the copy is staged before the call returns, so `jobs` may be freed
+  cudaError_t e = cudaMemcpyAsync(b + job_off, jobs, jb * (size_t)nprob, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = (es == 8) ? launch_adjoint_rhs_batched<double>(b + job_off, nprob, st)
+                  : launch_adjoint_rhs_batched<float>(b + job_off, nprob, st);
+  r = (e == cudaSuccess) ? run_batched(h, nprob, ap, opts, as, nullptr, st) : LQR_ERR_CUDA;
   if (r == LQR_OK) {
-    for (int i = 0; i < nprob; ++i) {
-      const lqr_problem& p = probs[i];
-      cudaError_t e = (es == 8)
-          ? launch_adjoint_grad<double>(p.n, p.m, p.T, sols[i].x, sols[i].u, sols[i].lam, as[i].x, as[i].u, as[i].lam,
-                                        &grads[i], st)
-          : launch_adjoint_grad<float>(p.n, p.m, p.T, sols[i].x, sols[i].u, sols[i].lam, as[i].x, as[i].u, as[i].lam,
-                                       &grads[i], st);
-      if (e != cudaSuccess) { r = LQR_ERR_CUDA; break; }
-    }
+    e = (es == 8) ? launch_adjoint_grad_batched<double>(b + job_off, nprob, Tmax, st)
+                  : launch_adjoint_grad_batched<float>(b + job_off, nprob, Tmax, st);
+    if (e != cudaSuccess) r = LQR_ERR_CUDA;
+    h->last_launches += 2;
   }
+  free(jobs);
   free(ap);
   free(as);
   return r;

@@ -309,6 +309,17 @@ template <typename TS>
 cudaError_t launch_adjoint_grad(int n, int m, int T, const void* x, const void* u, const void* lam, const void* xix,
                                 const void* xiu, const void* xil, const lqr_problem* g, cudaStream_t st);
 
+// the batched adjoint's per-problem jobs (adjoint.cu): adjoint_job_bytes() per
+// job, filled on the host, one launch each over a device table
+size_t adjoint_job_bytes();
+void adjoint_job_fill(void* dst, int n, int m, int T, const void* gx, const void* gu, void* q, void* r, void* c,
+                      void* x0, const void* x, const void* u, const void* lam, const void* xix, const void* xiu,
+                      const void* xil, const lqr_problem* g);
+template <typename TS>
+cudaError_t launch_adjoint_rhs_batched(const void* jobs, int njobs, cudaStream_t st);
+template <typename TS>
+cudaError_t launch_adjoint_grad_batched(const void* jobs, int njobs, int Tmax, cudaStream_t st);
+
 // refinement (refine.cu)
 // per-CTA objective partials of the residual pass: at most kMaxResidBlocks CTAs
 constexpr int kMaxResidBlocks = 1024;
