@@ -288,6 +288,28 @@ lqr_status lqr_rcp_newton_check(const double* d, double* y, int count, void* str
 lqr_status lqr_segment_summaries(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts,
                                  double *summaries, void *stream);
 
+/* The paper's own feedback policies (Section III-A), beside the serial ones
+ * lqr_solve returns. The constraint-explicit segment sweeps (Section II-B)
+ * give, for every stage t of segment j, u_t = Kx_t x_t + Kz_t x_term + k1_t
+ * with x_term the segment's end link point (Eq. 9-16; the last segment, which
+ * has a terminal cost and no end constraint, its plain Riccati policy with
+ * Kz = 0); the link solve gives the link points z_j (z_0 = x0).
+ *  smooth = 0: these unsmoothed segment policies. Applied with the link
+ *      points they reproduce the optimal trajectory; their gains differ from
+ *      the serial ones, as the segment ends are held at the link points.
+ *  smooth = 1: the smoothing pass: each segment j < K-1 re-swept without end
+ *      constraint from the next segment's cost to go J_{j+1}(x, z_{j+2}) (its
+ *      own end pinned at its link point; the last segment's value for
+ *      j = K-2): u_t = Kx_t x_t + k1_t, Kz = 0.
+ * prob and opts as for lqr_solve with opts->prec = LQR_FP64 and
+ * opts->form = LQR_FORM_CONSTRAINED (else LQR_ERR_UNSUPPORTED), no
+ * refinement. Outputs (DEVICE, FP64, caller-allocated): Kx [T][m][n],
+ * Kz [T][m][n] (NULL = not wanted), k1 [T][m], z [K+1][n] (NULL = not
+ * wanted; K the segment count used, lqr_report's num_segments).
+ * Asynchronous on `stream`; device conditions through lqr_report. */
+lqr_status lqr_segment_policies(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts, int smooth,
+                                void *Kx, void *Kz, void *k1, void *z, void *stream);
+
 /* Synchronise `stream` and read back the scalars of the last solve on h. */
 lqr_status lqr_report(lqr_handle *h, void *stream, lqr_report_t *out);
 

@@ -1103,6 +1103,75 @@ lqr_status lqr_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
   return run_solve(h, p, o, s, static_cast<cudaStream_t>(stream), false, nullptr);
 }
 
+lqr_status lqr_segment_policies(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, int smooth, void* Kx,
+                                void* Kz, void* k1, void* z, void* stream) {
+  if (!h || !Kx || !k1) return LQR_ERR_INVALID_ARG;
+  lqr_solution none;
+  memset(&none, 0, sizeof(none));
+  lqr_status v = validate(p, o, &none);
+  if (v != LQR_OK) return v;
+  if (o->prec != LQR_FP64 || o->form != LQR_FORM_CONSTRAINED || o->max_refine > 0) return LQR_ERR_UNSUPPORTED;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lqr_opts o2 = *o;
+  o2.residual = 0;
+  SolvePlan sp;
+  lqr_status rs = plan_solve(h, p, &o2, &sp);
+  if (rs != LQR_OK) return rs;
+  const int n = p->n, m = p->m, T = p->T, K = sp.K;
+  const size_t ldp = 2 * (size_t)n + 1;
+  const long long pol_off = ((sp.wl.total + (long long)K * sp.scratch_doubles) + 31) & ~31LL;
+  const size_t need = sizeof(double) * ((size_t)pol_off + (size_t)T * m * ldp) + 256;
+  rs = grow(&h->ws, &h->ws_bytes, need > sp.ws_need ? need : sp.ws_need);
+  if (rs != LQR_OK) return rs;
+  lqr_solution sol;
+  memset(&sol, 0, sizeof(sol));
+  if (smooth) { sol.K = Kx; sol.k = k1; }  // the policy sweeps write the smoothed gains
+  ProbTable tab;
+  memset(&tab, 0, sizeof(tab));
+  tab.single = make_desc(h, p, &sol, sp, (int)LQR_FORM_CONSTRAINED);
+  tab.nprob = 1;
+  double* segpol = reinterpret_cast<double*>(h->ws) + pol_off;
+  if (!smooth) tab.single.segpol = segpol;
+  const long long budget = h->smem_optin - kStaticSmemReserve;
+  int launches = 0;
+  if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
+  if (cudaMemsetAsync(h->d_report, 0, 4 * sizeof(double), st) != cudaSuccess) return LQR_ERR_CUDA;
+  // A1: the constraint-explicit segment sweeps (and the last segment's Riccati sweep)
+  if (launch_seg_sweep<double, double>(tab, K, 0, sp.smem, budget, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
+  ++launches;
+  // A3: the link points (block elimination of the primal link system)
+  if (launch_link_solve(tab, 1, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
+  ++launches;
+  if (smooth) {
+    tab.single.smooth = 1;
+    if (K > 1) {
+      if (launch_seg_sweep<double, double>(tab, K, 1, sp.smem, budget, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
+      ++launches;
+    }
+    if (Kz && cudaMemsetAsync(Kz, 0, sizeof(double) * (size_t)T * m * n, st) != cudaSuccess) return LQR_ERR_CUDA;
+  } else {
+    // [K_x | K_z | k_1] rows into the three outputs
+    const size_t pitch = sizeof(double) * ldp;
+    if (cudaMemcpy2DAsync(Kx, sizeof(double) * n, segpol, pitch, sizeof(double) * n, (size_t)T * m,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    if (Kz && cudaMemcpy2DAsync(Kz, sizeof(double) * n, segpol + n, pitch, sizeof(double) * n, (size_t)T * m,
+                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    if (cudaMemcpy2DAsync(k1, sizeof(double), segpol + 2 * n, pitch, sizeof(double), (size_t)T * m,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+  }
+  if (z && cudaMemcpyAsync(z, h->ws + sizeof(double) * sp.wl.z, sizeof(double) * (size_t)(K + 1) * n,
+                           cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return LQR_ERR_CUDA;
+  h->last_K = K;
+  h->last_launches = launches;
+  h->last_resid = 0;
+  return LQR_OK;
+}
+
 lqr_status lqr_segment_summaries(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, double* summaries,
                                  void* stream) {
   if (!h || !summaries) return LQR_ERR_INVALID_ARG;

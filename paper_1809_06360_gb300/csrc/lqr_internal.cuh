@@ -82,6 +82,8 @@ struct ProbDesc {
   int unit0;                  // first unit (segment) index of this problem in a launch
   int form;                   // lqr_form of the parametric sweeps
   void* Minv;                 // FP32 fast path: T x m x m M_uu^-1 of the policy stages, may be null
+  double* segpol;             // FP64 constrained sweep: T x m x (2n+1) segment policies [K_x | K_z | k_1], may be null
+  int smooth;                 // policy sweep started from the next segment's cost with its end pinned (Section III-A)
 };
 
 // Kernel-argument view of the problems of one launch: a single problem is

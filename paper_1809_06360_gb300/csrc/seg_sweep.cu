@@ -168,6 +168,20 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
                                       static_cast<double>(QT[(size_t)j * n + i])));
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) vx[i] = static_cast<TC>(gq[(size_t)n * T + i]);
+  } else if (pd.smooth) {
+    // the smoothing pass of Section III-A: the next segment's cost to go at its
+    // start with its own end pinned at its link point, J_{j+1}(x, z_{j+2}):
+    // V = Vxx^{j+1}, v = vx^{j+1} + Vzx^{j+1}' z_{j+2} (the last segment: its value)
+    const double* S1 = pd.ws + wl.summ + (long long)(seg + 1) * (3LL * n * n + 2 * n);
+    const double* z2 = pd.ws + wl.z + (long long)(seg + 2) * n;
+    const bool pinned = seg + 1 < K - 1;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Vxx[e] = static_cast<TC>(S1[e]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double a = S1[3 * nn + i];
+      if (pinned)
+        for (int k = 0; k < n; ++k) a += S1[nn + (size_t)k * n + i] * z2[k];
+      vx[i] = static_cast<TC>(a);
+    }
   } else {
     const double* Pi = pd.ws + wl.Pi + (long long)(seg + 1) * nn;
     const double* pi = pd.ws + wl.pi + (long long)(seg + 1) * n;
@@ -295,6 +309,15 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
             gK[nm * t + e] = static_cast<TS>(-F[(size_t)(e / n) * ldF + (e % n)]);
         if (gk)
           for (int a = threadIdx.x; a < m; a += blockDim.x) gk[(size_t)m * t + a] = static_cast<TS>(-F[(size_t)a * ldF + cmu]);
+        if (pd.segpol && mode == MODE_TERMINAL) {  // the last segment's policy [K_t | 0 | k_t]
+          const int ld = 2 * n + 1;
+          double* sp = pd.segpol + (size_t)m * ld * t;
+          for (int e = threadIdx.x; e < m * ld; e += blockDim.x) {
+            const int a = e / ld, j = e % ld;
+            sp[e] = j < n ? -static_cast<double>(F[(size_t)a * ldF + j])
+                          : (j < 2 * n ? 0.0 : -static_cast<double>(F[(size_t)a * ldF + cmu]));
+          }
+        }
         if (pd.Minv && Linv && sizeof(TS) == 4) {
           // M_uu^-1 = L^-T L^-1, kept for refinement corrections that reuse the factorisation
           cta_mm_auto<true, false, TC>(m, m, m, Linv, m, Linv, m,
@@ -302,6 +325,14 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
         }
       } else {
         cta_copy<TC>(n, n, T1, ldAB, Vzx, n);
+        if (pd.segpol && sizeof(TC) == 8) {
+          // the paper's segment policy [K_x | K_z | k_1] = -L^-T W (W = L^-1 [M_ux | M_zu' | m_u])
+          __syncthreads();
+          cta_trsm_lower_t<TC>(m, reinterpret_cast<const TC*>(L64), m, s_rdc, ldF, F, ldF);
+          __syncthreads();
+          double* sp = pd.segpol + (size_t)m * ldF * t;
+          for (int e = threadIdx.x; e < m * ldF; e += blockDim.x) sp[e] = -static_cast<double>(F[e]);
+        }
       }
       cta_symmetrize<TC>(n, Vxx, n);
       __syncthreads();
@@ -425,6 +456,11 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
         // G = Q_f [Y; W]
         cta_householder_apply(m, rr, AUG, ld2, vhead, beta, ldG, Gc, ldG, false);
         rr = 0;
+      }
+      __syncthreads();
+      if (pd.segpol) {  // the paper's segment policy of this constrained stage, u = G [x; z; 1]
+        double* sp = pd.segpol + (size_t)m * ldG * t;
+        for (int e = threadIdx.x; e < m * ldG; e += blockDim.x) sp[e] = Gc[e];
       }
       // ---- value update by substitution of u = G [x; z; 1] (Eq. 16, symmetric form)
       // E = F + M_uu G

@@ -31,7 +31,7 @@ EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
            "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
-           "lqr_rcp_newton_check")
+           "lqr_rcp_newton_check", "lqr_segment_policies")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -95,6 +95,8 @@ def load(path: str | None = None):
     lib.lqr_kkt_residual_noalloc.argtypes = [P(lqr_problem), P(lqr_solution), c_int, c_void_p, c_void_p]
     lib.lqr_tc_selftest.argtypes = [c_int, P(c_double)]
     lib.lqr_rcp_newton_check.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
+    lib.lqr_segment_policies.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_int, c_void_p, c_void_p, c_void_p,
+                                         c_void_p, c_void_p]
     lib.lqr_backward.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p, c_void_p,
                                  P(lqr_problem), c_void_p]
     lib.lqr_backward_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution),
@@ -103,7 +105,7 @@ def load(path: str | None = None):
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
                  "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
-                 "lqr_rcp_newton_check"):
+                 "lqr_rcp_newton_check", "lqr_segment_policies"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -354,6 +356,24 @@ class Solver:
         gu = [t.data_ptr() if t is not None else None for t in grads_u]
         lqr_backward_batched(self.h, ps, o, ss, gx, gu, gs, self._stream(stream))
         return grads
+
+    def segment_policies(self, prob, num_segments, smooth=False, stream=None):
+        """The paper's segment policies (lqr_segment_policies): dict Kx, Kz, k1, z (FP64 device tensors)."""
+        torch = _torch()
+        n, m, T = self._dims(prob)
+        dev = prob["A"].device
+        out = dict(Kx=torch.empty((T, m, n), dtype=torch.float64, device=dev),
+                   Kz=torch.empty((T, m, n), dtype=torch.float64, device=dev),
+                   k1=torch.empty((T, m), dtype=torch.float64, device=dev),
+                   z=torch.empty((num_segments + 1, n), dtype=torch.float64, device=dev))
+        p = self.make_problem_struct(prob, lambda t: t.data_ptr())
+        o = lqr_opts(prec=PRECISION["fp64"], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=FORM["constrained"], residual=0)
+        _check(load().lqr_segment_policies(self.h, ctypes.byref(p), ctypes.byref(o), 1 if smooth else 0,
+                                           out["Kx"].data_ptr(), out["Kz"].data_ptr(), out["k1"].data_ptr(),
+                                           out["z"].data_ptr(), self._stream(stream) or None),
+               "lqr_segment_policies")
+        return out
 
     def segment_summaries(self, prob, num_segments, prec="fp64", stream=None, form="multiplier"):
         torch = _torch()
