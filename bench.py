@@ -57,9 +57,12 @@ def _tf32_peak():
 
 PEAK_TF32_TFLOPS = _tf32_peak()
 
-# bytes per launch (read + write) measured by ncu on the default FP32 workload;
-# an entry is removed whenever its kernel changes
-NCU_TRAFFIC: dict = {}  # none taken for the kernels as they now stand
+# DRAM bytes per launch (read + write) measured by ncu for the kernel as it now
+# stands, keyed by (kernel, workload config, precision); an entry is removed
+# whenever its kernel changes. seg_sweep_f32_kernel on the long-horizon
+# workload in LQR_MIXED_FP32: A1 226.3 MB, A4 309.3 MB (it also writes K_t, P_t,
+# M_uu^-1), mean of the two launches (profiles/seg_sweep_f32_n64_m32_K38_and_traffic_K152.md)
+NCU_TRAFFIC: dict = {("seg_sweep_f32_kernel", 1, "mixed_fp32"): (226.3e6 + 309.3e6) / 2}
 
 
 def link_flops(n: int, K: int) -> float:
