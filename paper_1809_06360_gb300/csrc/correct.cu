@@ -334,60 +334,165 @@ __global__ void __launch_bounds__(kCorrBlock) corr_fwd_kernel(CorrArgs a, int mo
   }
 }
 
-// The link chains, one CTA. dir 0: pb[K] = q~_T, pb[j] = Psi_j'pb[j + 1] + eps_j
-// (j = K-1 .. 0). dir 1: xb[0] = x0~, xb[j + 1] = Psi_j xb[j] + delta_j. Psi_j
-// arrive through a ring of kLinkDepth slots, kLinkDepth - 1 links ahead; each
-// output of a step is summed by kLinkSplit threads over a quarter of l each
-// (output index fastest over the threads: conflict-free reads of Psi's rows and
-// columns at the odd row stride), the partial sums combined through shared memory.
+// A run of dependent link steps by one CTA. dir 0 (backward): links l = hi-1
+// down to lo, v <- M_l' v + off_l, out[l] = v. dir 1 (forward): links l = lo ..
+// hi-1, v <- M_l v + off_l, out[l + 1] = v. M_l (n x n) arrive through a ring of
+// kLinkDepth slots, kLinkDepth - 1 links ahead; each output of a step is summed
+// by kLinkSplit threads over a quarter of l each (output index fastest over the
+// threads: conflict-free reads of M's rows and columns at the odd row stride),
+// the partial sums combined through shared memory. v (shared) holds the start
+// value on entry and the end value on exit; out may be null.
+__device__ inline void chain_run(const float* mats, const float* offs, int lo, int hi, int dir, int n, float* v,
+                                 float* out, float* csm) {
+  const long long nn = (long long)n * n;
+  const int ldn = n + 1;
+  constexpr int kRows = kCorrBlock / kLinkSplit;  // outputs per pass of the thread block
+  float* ring = csm;
+  float* part = ring + kLinkDepth * n * ldn;  // [kLinkSplit][n]
+  const int q = (int)threadIdx.x / kRows, r0 = (int)threadIdx.x % kRows;
+  const int chunk = (n + kLinkSplit - 1) / kLinkSplit;
+  const int l0 = q * chunk < n ? q * chunk : n, l1 = (q + 1) * chunk < n ? (q + 1) * chunk : n;
+  const int cnt = hi - lo;
+  auto link_of = [&](int idx) { return dir == 0 ? hi - 1 - idx : lo + idx; };
+  auto issue = [&](int idx) {
+    if (idx < cnt) copy_pad(ring + (idx % kLinkDepth) * n * ldn, ldn, mats + nn * link_of(idx), n, n);
+    cp_async_commit();
+  };
+  for (int d = 0; d < kLinkDepth - 1; ++d) issue(d);
+  for (int idx = 0; idx < cnt; ++idx) {
+    issue(idx + kLinkDepth - 1);
+    cp_async_wait<kLinkDepth - 1>();
+    __syncthreads();  // M of this link in its slot; v complete
+    const float* Ms = ring + (idx % kLinkDepth) * n * ldn;
+    const int jl = link_of(idx);
+    for (int i = r0; i < n; i += kRows) {
+      float acc = 0.0f;
+      if (dir == 0)
+        for (int l = l0; l < l1; ++l) acc = fmaf(Ms[l * ldn + i], v[l], acc);
+      else
+        for (int l = l0; l < l1; ++l) acc = fmaf(Ms[i * ldn + l], v[l], acc);
+      part[q * n + i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float acc = offs[(long long)n * jl + i];
+#pragma unroll
+      for (int g = 0; g < kLinkSplit; ++g) acc += part[g * n + i];
+      v[i] = acc;
+      if (out) out[(long long)n * (dir == 0 ? jl : jl + 1) + i] = acc;
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+}
+
+// The single link chain, one CTA. dir 0: pb[K] = q~_T, pb[j] = Psi_j'pb[j + 1] + eps_j
+// (j = K-1 .. 0). dir 1: xb[0] = x0~, xb[j + 1] = Psi_j xb[j] + delta_j.
 __global__ void __launch_bounds__(kCorrBlock) corr_link_kernel(CorrArgs a, int dir) {
   extern __shared__ __align__(16) float csm[];
   __shared__ int s_flag;
   if (corr_exit(a, &s_flag)) return;
-  const int n = a.n, K = a.nseg, ldn = n + 1;
-  const long long nn = (long long)n * n;
-  constexpr int kRows = kCorrBlock / kLinkSplit;  // outputs per pass of the thread block
-  float* ring = csm;
-  float* v = ring + kLinkDepth * n * ldn;
-  float* part = v + n;  // [kLinkSplit][n]
-  const int q = (int)threadIdx.x / kRows, r0 = (int)threadIdx.x % kRows;
-  const int chunk = (n + kLinkSplit - 1) / kLinkSplit;
-  const int l0 = q * chunk < n ? q * chunk : n, l1 = (q + 1) * chunk < n ? (q + 1) * chunk : n;
-  auto link_of = [&](int idx) { return dir == 0 ? K - 1 - idx : idx; };
-  auto issue = [&](int idx) {
-    if (idx < K) copy_pad(ring + (idx % kLinkDepth) * n * ldn, ldn, a.Psi + nn * link_of(idx), n, n);
-    cp_async_commit();
-  };
-  for (int d = 0; d < kLinkDepth - 1; ++d) issue(d);
+  const int n = a.n, K = a.nseg;
+  float* v = csm + kLinkDepth * n * (n + 1) + kLinkSplit * n;
   float* out = dir == 0 ? a.pb : a.xb;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     v[i] = dir == 0 ? a.cq[(long long)n * a.T + i] : a.cx0[i];
     out[(long long)n * (dir == 0 ? K : 0) + i] = v[i];
   }
-  for (int idx = 0; idx < K; ++idx) {
-    issue(idx + kLinkDepth - 1);
-    cp_async_wait<kLinkDepth - 1>();
-    __syncthreads();  // Psi of this link in its slot; v complete
-    const float* Ps = ring + (idx % kLinkDepth) * n * ldn;
-    const int jl = link_of(idx);
-    for (int i = r0; i < n; i += kRows) {
-      float acc = 0.0f;
-      if (dir == 0)
-        for (int l = l0; l < l1; ++l) acc = fmaf(Ps[l * ldn + i], v[l], acc);
-      else
-        for (int l = l0; l < l1; ++l) acc = fmaf(Ps[i * ldn + l], v[l], acc);
-      part[q * n + i] = acc;
-    }
-    __syncthreads();
+  chain_run(a.Psi, dir == 0 ? a.eps : a.delta, 0, K, dir, n, v, out, csm);
+}
+
+// The two-level chain over groups of G links (a depth of about 2 G + K / G steps
+// instead of K). stage 0, one CTA per group: the group's own steps from zero give
+// its offset (e_g backward, d_g forward: pb_lo = Phi_g' pb_hi + e_g,
+// x_hi = Phi_g x_lo + d_g). stage 1, one CTA: the chain over the groups with the
+// group maps Phi_g = Psi_{hi-1} ... Psi_lo gives the group boundary values.
+// stage 2, one CTA per group: the group's steps from its boundary value write
+// every link value.
+__global__ void __launch_bounds__(kCorrBlock) corr_chain2_kernel(CorrArgs a, int dir, int stage) {
+  extern __shared__ __align__(16) float csm[];
+  __shared__ int s_flag;
+  if (corr_exit(a, &s_flag)) return;
+  const int n = a.n, K = a.nseg, G = a.G, ng = a.ng;
+  float* v = csm + kLinkDepth * n * (n + 1) + kLinkSplit * n;
+  const float* offs = dir == 0 ? a.eps : a.delta;
+  if (stage == 1) {
+    float* gv = dir == 0 ? a.gY : a.gX;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      float acc = dir == 0 ? a.eps[(long long)n * jl + i] : a.delta[(long long)n * jl + i];
-#pragma unroll
-      for (int g = 0; g < kLinkSplit; ++g) acc += part[g * n + i];
-      v[i] = acc;
-      out[(long long)n * (dir == 0 ? jl : jl + 1) + i] = acc;
+      v[i] = dir == 0 ? a.cq[(long long)n * a.T + i] : a.cx0[i];
+      gv[(long long)n * (dir == 0 ? ng : 0) + i] = v[i];
+    }
+    chain_run(a.Phi, dir == 0 ? a.ge : a.gd, 0, ng, dir, n, v, gv, csm);
+    return;
+  }
+  const int g = blockIdx.x;
+  const int lo = g * G, hi = (lo + G < K) ? lo + G : K;
+  float* out = nullptr;
+  if (stage == 0) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 0.0f;
+  } else {
+    const float* gv = dir == 0 ? a.gY : a.gX;
+    out = dir == 0 ? a.pb : a.xb;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      v[i] = gv[(long long)n * (dir == 0 ? g + 1 : g) + i];
+      if (dir == 0 && g == ng - 1) out[(long long)n * K + i] = v[i];  // pb[K] = q~_T
+      if (dir == 1 && g == 0) out[i] = v[i];                          // xb[0] = x0~
     }
   }
+  __syncthreads();
+  chain_run(a.Psi, offs, lo, hi, dir, n, v, out, csm);
+  if (stage == 0) {
+    float* go = dir == 0 ? a.ge : a.gd;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) go[(long long)n * g + i] = v[i];
+  }
+}
+
+// Phi_g = Psi_{hi-1} ... Psi_lo per group (once per solve): one CTA per group,
+// products on 4 x 4 register tiles (n padded to a multiple of 4, row stride N + 4).
+__global__ void __launch_bounds__(kCorrBlock) corr_group_maps_kernel(CorrArgs a) {
+  extern __shared__ __align__(16) float csm[];
+  __shared__ int s_flag;
+  if (corr_exit(a, &s_flag)) return;
+  const int n = a.n, K = a.nseg, G = a.G;
+  const int g = blockIdx.x;
+  const int lo = g * G, hi = (lo + G < K) ? lo + G : K;
+  const int N = (n + 3) & ~3, LD = N + 4;
+  float* X = csm;        // product so far
+  float* Y = X + N * LD;
+  float* M = Y + N * LD;  // Psi_j
+  for (int x = threadIdx.x; x < 3 * N * LD; x += blockDim.x) csm[x] = 0.0f;
+  __syncthreads();
+  const long long nn = (long long)n * n;
+  copy_pad(X, LD, a.Psi + nn * lo, n, n);
+  cp_async_commit();
+  for (int j = lo + 1; j < hi; ++j) {
+    copy_pad(M, LD, a.Psi + nn * j, n, n);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    cta_mm4f<false>(N, N, N, M, LD, X, LD, [&](int i, int l, float val) { Y[i * LD + l] = val; });
+    __syncthreads();
+    float* tmp = X;
+    X = Y;
+    Y = tmp;
+  }
   cp_async_wait<0>();
+  __syncthreads();
+  for (int x = threadIdx.x; x < n * n; x += blockDim.x) a.Phi[nn * g + x] = X[(x / n) * LD + x % n];
+}
+
+size_t corr_group_smem_bytes(int n) {
+  const size_t N = (n + 3) & ~3;
+  return sizeof(float) * 3 * N * (N + 4);
+}
+
+cudaError_t launch_corr_groups(const CorrArgs& a, cudaStream_t st) {
+  if (a.ng <= 0) return cudaSuccess;
+  const size_t bytes = corr_group_smem_bytes(a.n);
+  cudaError_t e = raise_dyn_smem((const void*)corr_group_maps_kernel, bytes);
+  if (e != cudaSuccess) return e;
+  corr_group_maps_kernel<<<a.ng, kCorrBlock, bytes, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_corr_psi(const CorrArgs& a, cudaStream_t st) {
@@ -405,13 +510,29 @@ cudaError_t launch_correction(const CorrArgs& a, cudaStream_t st, int* launches)
   if (e == cudaSuccess) e = raise_dyn_smem((const void*)corr_fwd_kernel, sb);
   if (e == cudaSuccess) e = raise_dyn_smem((const void*)corr_link_kernel, lb);
   if (e != cudaSuccess) return e;
+  if (a.ng > 0) {
+    e = raise_dyn_smem((const void*)corr_chain2_kernel, lb);
+    if (e != cudaSuccess) return e;
+  }
+  // a link chain: one CTA over all K links, or the two-level form over groups
+  auto chain = [&](int dir) {
+    if (a.ng > 0) {
+      corr_chain2_kernel<<<a.ng, kCorrBlock, lb, st>>>(a, dir, 0);
+      corr_chain2_kernel<<<1, kCorrBlock, lb, st>>>(a, dir, 1);
+      corr_chain2_kernel<<<a.ng, kCorrBlock, lb, st>>>(a, dir, 2);
+      if (launches) *launches += 3;
+    } else {
+      corr_link_kernel<<<1, kCorrBlock, lb, st>>>(a, dir);
+      if (launches) *launches += 1;
+    }
+  };
   corr_back_kernel<<<a.nseg, kCorrBlock, sb, st>>>(a, 0);
-  corr_link_kernel<<<1, kCorrBlock, lb, st>>>(a, 0);
+  chain(0);
   corr_back_kernel<<<a.nseg, kCorrBlock, sb, st>>>(a, 1);
   corr_fwd_kernel<<<a.nseg, kCorrBlock, sb, st>>>(a, 0);
-  corr_link_kernel<<<1, kCorrBlock, lb, st>>>(a, 1);
+  chain(1);
   corr_fwd_kernel<<<a.nseg, kCorrBlock, sb, st>>>(a, 1);
-  if (launches) *launches += 6;
+  if (launches) *launches += 4;
   return cudaGetLastError();
 }
 

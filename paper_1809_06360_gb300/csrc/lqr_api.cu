@@ -395,6 +395,16 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   const size_t oMi = reuse ? take((size_t)T * mm) : 0, oPsi = reuse ? take((size_t)K * nn) : 0,
                oeps = reuse ? take((size_t)K * n) : 0, odel = reuse ? take((size_t)K * n) : 0,
                opb = reuse ? take((size_t)(K + 1) * n) : 0, oxb = reuse ? take((size_t)(K + 1) * n) : 0;
+  // two-level correction link chains for long chains: groups of about sqrt(K) links
+  int cG = 0, cng = 0;
+  if (reuse && K >= 32 && (long long)corr_group_smem_bytes(n) <= budget) {
+    cG = 1;
+    while (cG * cG < K) ++cG;
+    cng = (K + cG - 1) / cG;
+  }
+  const size_t oPhi = cng ? take((size_t)cng * nn) : 0, oge = cng ? take((size_t)cng * n) : 0,
+               ogd = cng ? take((size_t)cng * n) : 0, ogY = cng ? take((size_t)(cng + 1) * n) : 0,
+               ogX = cng ? take((size_t)(cng + 1) * n) : 0;
   rs = grow(&h->f32, &h->f32_bytes, sizeof(float) * off);
   if (rs != LQR_OK) return rs;
   float* f = reinterpret_cast<float*>(h->f32);
@@ -480,12 +490,20 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
       ca.skip = skip; ca.status = h->d_status;
       ca.n = n; ca.m = m; ca.T = T; ca.nseg = K;
       ca.slots = cslots; ca.psi_global = cpsi_global;
+      ca.G = cG; ca.ng = cng;
+      if (cng) { ca.Phi = f + oPhi; ca.ge = f + oge; ca.gd = f + ogd; ca.gY = f + ogY; ca.gX = f + ogX; }
       if (launch_corr_psi(ca, st) != cudaSuccess) return LQR_ERR_CUDA;
       ++launches;
+      if (cng) {
+        if (launch_corr_groups(ca, st) != cudaSuccess) return LQR_ERR_CUDA;
+        ++launches;
+      }
     }
     for (int it = 0; it < o->max_refine; ++it) {
-      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st) !=
-          cudaSuccess)
+      // the first pass also takes |KKT|_inf, so that the pass that finds the
+      // solution converged has the whole backward error
+      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st,
+                                      it == 0 ? 1 : 0) != cudaSuccess)
         return LQR_ERR_CUDA;
       if (launch_residual_finalize(main, acc, o->tol, skip, 0, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
       ConvTable<double, float> ct;
@@ -508,9 +526,10 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
         return LQR_ERR_CUDA;
       ++launches;
     }
-    if (launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st) != cudaSuccess)
+    // final residual and objective, skipped on the device once refinement has converged
+    if (launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, skip, st) != cudaSuccess)
       return LQR_ERR_CUDA;
-    if (launch_residual_finalize(main, acc, o->tol, nullptr, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
+    if (launch_residual_finalize(main, acc, o->tol, skip, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
         cudaSuccess)
       return LQR_ERR_CUDA;
     launches += 2;
@@ -573,8 +592,10 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
     ctab.single.skip = skip;
     ctab.nprob = 1;
     for (int it = 0; it < o->max_refine; ++it) {
-      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st) !=
-          cudaSuccess)
+      // the first pass also takes |KKT|_inf, so that the pass that finds the
+      // solution converged has the whole backward error
+      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st,
+                                      it == 0 ? 1 : 0) != cudaSuccess)
         return LQR_ERR_CUDA;
       if (launch_residual_finalize(main, acc, o->tol, skip, 0, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
       launches += 2;
@@ -585,12 +606,13 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
         return LQR_ERR_CUDA;
       ++launches;
     }
-    // final residual and objective of the returned solution (in the data's element type)
+    // final residual and objective of the returned solution (in the data's element
+    // type), skipped on the device once refinement has converged
     const cudaError_t er = (o->prec == LQR_FP32)
-        ? launch_kkt_residual<float>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st)
-        : launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+        ? launch_kkt_residual<float>(main, acc, nullptr, nullptr, nullptr, nullptr, skip, st)
+        : launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, skip, st);
     if (er != cudaSuccess) return LQR_ERR_CUDA;
-    if (launch_residual_finalize(main, acc, o->tol, nullptr, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
+    if (launch_residual_finalize(main, acc, o->tol, skip, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
         cudaSuccess)
       return LQR_ERR_CUDA;
     launches += 2;

@@ -221,6 +221,10 @@ struct CorrArgs {
   int n, m, T, nseg;
   int slots;       // stage-data ring slots of the segment passes (2: prefetch, 1: no prefetch)
   int psi_global;  // 1: the closed-loop maps read B_t, K_t from global memory
+  // two-level link chains (ng > 0): groups of G consecutive links, their maps
+  // Phi_g (ng n n), offsets e_g / d_g (ng n) and group boundary values Y, X ((ng+1) n)
+  float *Phi, *ge, *gd, *gY, *gX;
+  int G, ng;
 };
 
 // ---------------------------------------------------------------------------
@@ -261,6 +265,9 @@ size_t corr_link_smem_bytes(int n);
 void corr_plan(int n, int m, long long smem_budget, int* slots, int* psi_global);
 cudaError_t launch_corr_psi(const CorrArgs& a, cudaStream_t st);
 cudaError_t launch_correction(const CorrArgs& a, cudaStream_t st, int* launches);
+// the group maps of the two-level link chains (once per solve, after launch_corr_psi)
+cudaError_t launch_corr_groups(const CorrArgs& a, cudaStream_t st);
+size_t corr_group_smem_bytes(int n);
 
 // Element-type conversion of up to kMaxConv arrays in one launch (skip: when
 // non-null and set, nothing is done).
@@ -326,9 +333,12 @@ cudaError_t launch_adjoint_grad_batched(const void* jobs, int njobs, int Tmax, c
 // per-CTA objective partials of the residual pass: at most kMaxResidBlocks CTAs
 constexpr int kMaxResidBlocks = 1024;
 constexpr int kResidAccDoubles = 8 + kMaxResidBlocks;
+// knorm: also accumulate |KKT|_inf (1), not (0), or only when no correction
+// vectors are requested (-1). |KKT|_inf depends on the data alone: a pass that
+// computes it once keeps it in the accumulators until the solve's final pass.
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
-                                const int* skip, cudaStream_t st);
+                                const int* skip, cudaStream_t st, int knorm = -1);
 cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol, int* skip, int is_final,
                                      int check, cudaStream_t st);
 template <typename TS>

@@ -46,8 +46,8 @@ enum ResidSlot { RS_RNORM = 0, RS_KNORM, RS_WNORM, RS_BNORM, RS_COST, RS_COUNT }
 
 // One CTA per stage (grid-stride). Stage t < T, plus the terminal / initial
 // rows handled by the CTA that owns t = T-1 / t = 0.
-// want_knorm: also the |KKT| row sums of the backward error (the final pass);
-// the refinement passes only need |r| and |b|.
+// want_knorm: also the |KKT| row sums of the backward error (the final pass and
+// the first refinement pass); the other refinement passes only need |r| and |b|.
 template <typename TS>
 __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, double* acc, double* cq, double* cr,
                                                               double* cc, double* cx0, const int* skip, int want_knorm) {
@@ -330,7 +330,9 @@ __global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, 
                                          int is_final, int check_convergence) {
   if (threadIdx.x != 0) return;
   if (*(volatile int*)pd.status != 0) return;
-  if (!is_final && skip && *skip) return;  // already converged: keep the earlier numbers
+  // already converged: the solution has not changed since the pass that found
+  // it converged, whose numbers stand (the final pass was skipped as well)
+  if (skip && *skip) return;
   double cost = 0.0;
   for (int b = 0; b < nblocks; ++b) cost += acc[RS_COUNT + b];
   const double r = acc[RS_RNORM], k = acc[RS_KNORM], w = acc[RS_WNORM], bn = acc[RS_BNORM];
@@ -342,7 +344,9 @@ __global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, 
   if (!isfinite(eta) || !isfinite(cost)) raise_status(pd.status, LQR_ERR_NONFINITE, -1);
   if (skip && !is_final && rel <= tol) *skip = 1;
   if (is_final && check_convergence && !(rel <= tol)) raise_status(pd.status, LQR_ERR_NO_CONVERGENCE, -1);
-  for (int i = 0; i < RS_COUNT; ++i) acc[i] = 0.0;  // ready for the next pass
+  // ready for the next pass; |KKT|_inf, a function of the data, stays until the final pass
+  for (int i = 0; i < RS_COUNT; ++i)
+    if (i != RS_KNORM || is_final) acc[i] = 0.0;
 }
 
 // w <- w - delta for the outputs the correction solve refreshed.
@@ -382,9 +386,9 @@ int residual_grid(int T) {
 
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
-                                const int* skip, cudaStream_t st) {
-  // the refinement passes (correction vectors requested) skip the |KKT| row sums
-  const int want_knorm = (cq == nullptr) ? 1 : 0;
+                                const int* skip, cudaStream_t st, int knorm) {
+  // by default the refinement passes (correction vectors requested) skip the |KKT| row sums
+  const int want_knorm = knorm >= 0 ? knorm : (cq == nullptr) ? 1 : 0;
   const int nc = kkt_stage_cols(pd.n, pd.m);
   if (nc > 0) {
     const size_t base = sizeof(double) * kkt_stage_smem_doubles(pd.n, pd.m);  // <= 45056 B at n = m = 128
@@ -428,9 +432,9 @@ cudaError_t launch_refine_update(const ProbDesc& pd, const double* dk, const dou
 }
 
 template cudaError_t launch_kkt_residual<double>(const ProbDesc&, double*, double*, double*, double*, double*,
-                                                 const int*, cudaStream_t);
+                                                 const int*, cudaStream_t, int);
 template cudaError_t launch_kkt_residual<float>(const ProbDesc&, double*, double*, double*, double*, double*,
-                                                const int*, cudaStream_t);
+                                                const int*, cudaStream_t, int);
 template cudaError_t launch_refine_update<double>(const ProbDesc&, const double*, const double*, const double*,
                                                   const double*, const double*, const int*, cudaStream_t);
 template cudaError_t launch_refine_update<float>(const ProbDesc&, const double*, const double*, const double*,
