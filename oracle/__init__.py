@@ -20,6 +20,10 @@ segment_dual_summary(...) the same segment problem with its end-point constraint
                          G(x_s, mu) = 1/2 x_s'P x_s + mu'Z x_s - 1/2 mu'W mu + p'x_s + w'mu,
                          by a dense KKT solve with (x_s, mu) as parameters.
 kkt_residual(prob, ...)  the residual of Eq. 3 and its normwise backward error.
+ls_multipliers(...)      the multipliers of every segment problem from the
+                         over-determined stationarity system of Section II-B
+                         ("Lagrange Multipliers"), solved through its normal
+                         equations as the paper states.
 """
 from __future__ import annotations
 
@@ -316,6 +320,74 @@ def kkt_blocks_residual(prob: dict, x, u, lam):
     r0 = x[0] - x0
     rd = xn - np.einsum("tij,tj->ti", A, xt) - np.einsum("tij,tj->ti", B, u) - c
     return dict(rx=rx, ru=ru, rxT=rxT, r0=r0, rd=rd)
+
+
+def ls_multipliers(prob: dict, x, u, bounds) -> dict:
+    """Multipliers of the segment problems from the paper's least-squares
+    system (Section II-B, "Lagrange Multipliers"; Eq. mults, mu, multsglobal,
+    pseudoinverse), at the given trajectory (x, u).
+
+    Segment j covers stages bounds[j] .. bounds[j+1]-1 and is the problem of
+    the constraint-explicit section: x at its first stage fixed (multiplier
+    lambda_0), the dynamics (lambda_1..lambda_L), and for every segment but the
+    last its end state fixed (multiplier mu) with no terminal cost; the last
+    segment carries the terminal cost Q_T, q_T and no end constraint (the
+    splitting of Section II-A). With L stages, the stationarity conditions are
+      x rows, i < L:  lambda_i - A_t'lambda_{i+1} = g_i = -(Q_t x_t + S_t'u_t + q_t)
+      u rows, i < L:           -B_t'lambda_{i+1} = h_i = -(S_t x_t + R_t u_t + r_t)
+      end row:        lambda_L (+ mu)             = g_L
+    (t = bounds[j] + i; g_L = -(Q_T x_T + q_T) for the last segment, 0 else).
+    The matrix of this system (the paper's A') has full column rank; its
+    least-squares solution comes from the normal equations A A' lambda = A b,
+    assembled densely here and solved with numpy.linalg.solve.
+
+    Returns lam ((T+1) x n: lambda_t for t in segment j's stages from segment
+    j, lambda_T from the last segment), lam_end ((K-1) x n: each interior
+    segment's own lambda_L, the multiplier of the dynamics into the next
+    segment's first state) and mu ((K-1) x n)."""
+    A, B, Q, R, S, q, r = (prob[k] for k in ("A", "B", "Q", "R", "S", "q", "r"))
+    Q = _sym(Q)
+    R = _sym(R)
+    n, m, T = _dims(prob)
+    K = len(bounds) - 1
+    lam = np.zeros((T + 1, n))
+    lam_end = np.zeros((max(K - 1, 0), n))
+    mu = np.zeros((max(K - 1, 0), n))
+    for j in range(K):
+        b, e = bounds[j], bounds[j + 1]
+        L = e - b
+        last = (j == K - 1)
+        nunk = (L + 1) * n + (0 if last else n)
+        neq = L * (n + m) + n
+        At = np.zeros((neq, nunk))  # the paper's A': equations x unknowns
+        rhs = np.zeros(neq)
+
+        def lcol(i):
+            return slice(i * n, (i + 1) * n)
+
+        for i in range(L):
+            t = b + i
+            xr = slice(i * n, (i + 1) * n)
+            ur = slice(L * n + i * m, L * n + (i + 1) * m)
+            At[xr, lcol(i)] = np.eye(n)
+            At[xr, lcol(i + 1)] = -A[t].T
+            At[ur, lcol(i + 1)] = -B[t].T
+            rhs[xr] = -(Q[t] @ x[t] + S[t].T @ u[t] + q[t])
+            rhs[ur] = -(S[t] @ x[t] + R[t] @ u[t] + r[t])
+        er = slice(L * (n + m), L * (n + m) + n)
+        At[er, lcol(L)] = np.eye(n)
+        if last:
+            rhs[er] = -(Q[T] @ x[T] + q[T])
+        else:
+            At[er, (L + 1) * n:] = np.eye(n)
+        sol = np.linalg.solve(At.T @ At, At.T @ rhs)
+        lam[b:e] = sol[:L * n].reshape(L, n)
+        if last:
+            lam[T] = sol[L * n:(L + 1) * n]
+        else:
+            lam_end[j] = sol[L * n:(L + 1) * n]
+            mu[j] = sol[(L + 1) * n:]
+    return dict(lam=lam, lam_end=lam_end, mu=mu)
 
 
 def kkt_residual(prob: dict, x, u, lam) -> dict:
