@@ -300,6 +300,16 @@ WORKLOADS = {
 }
 
 
+def ls_mult_flops(n: int, m: int, T: int, K: int) -> float:
+    """Algorithmic FLOPs of the least-squares multipliers (block Cholesky of
+    the normal equations): per dynamics block A A' (2n^3), B B' (2n^2 m), the
+    coupling solve (n^3), its downdate (2n^3) and the n x n factor (n^3/3);
+    per interior segment the mu block (n^3 + 2n^3 + n^3/3); per segment its
+    first block (n^3/3). Vector work is O(n^2) and left out."""
+    return (T * (16.0 / 3.0 * n ** 3 + 2.0 * n * n * m) + (K - 1) * (10.0 / 3.0) * n ** 3
+            + K * n ** 3 / 3.0)
+
+
 def riccati_stage_flops(n: int, m: int) -> float:
     """Algorithmic FLOPs of one plain Riccati stage as the FP32 sweep evaluates it
     (V[A|B|c], [A|B]'V[A|B], the M_uu inverse, H and the downdate)."""
@@ -664,6 +674,23 @@ def main():
             extras["fp32_unrefined"] = {"stages_per_s": T / (t / 1e3), "ms_per_solve": t, "K": K,
                                         "kkt_backward_error": r["kkt_residual"], "kkt_rel_residual": r["kkt_rel"]}
             del d32, o32
+        # the multipliers from Section II-B's least-squares system at the FP64
+        # optimum (lqr_ls_multipliers: block Cholesky of the normal equations, FP64)
+        o64 = solver.alloc_solution(dev64, want=("x", "u", "lam"))
+        solver.solve(dev64, num_segments=K, prec="fp64", out=o64)
+        f = lambda: solver.ls_multipliers(dev64, o64["x"], o64["u"], K)
+        lsm = f()
+        torch.cuda.synchronize()
+        t = _timed(stream, f, 3)
+        work = ls_mult_flops(n, m, T, K)
+        ach = work / (t * 1e-3) / 1e12
+        extras["ls_multipliers"] = {
+            "kernel": "ls_mult_kernel (Section II-B least-squares multipliers, FP64 block Cholesky, one CTA per segment)",
+            "ms": t, "K": K, "bound": "alu", "unit": "TFLOP/s", "work": work, "achieved": ach,
+            "peak": PEAK_FP64_TFLOPS, "frac": ach / PEAK_FP64_TFLOPS,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
+            "rel_diff_vs_solve_lambda": float((lsm["lam"] - o64["lam"]).abs().max() / o64["lam"].abs().max())}
+        del o64, lsm
         del dev64
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timing

@@ -282,6 +282,32 @@ lqr_status lqr_tc_selftest(int device, double* errs);
  * IEEE division. d, y: DEVICE arrays of count doubles. Asynchronous on stream. */
 lqr_status lqr_rcp_newton_check(const double* d, double* y, int count, void* stream);
 
+/* The multipliers of every segment problem from the least-squares system of
+ * Section II-B ("Lagrange Multipliers"), at the trajectory (x, u) (the optimum
+ * lqr_solve returns, or any other): a check on the multipliers of Eq. 3 that
+ * lqr_solve returns (lambda_t = -(P_t x_t + p_t)).
+ * Segment j (the K-way split of lqr_partition; K = opts->num_segments, or the
+ * automatic count when 0) is the problem of the constraint-explicit section:
+ * its first state fixed, the dynamics, and for j < K-1 its end state fixed
+ * (multiplier mu_j) with no terminal cost; the last segment has the terminal
+ * cost. Its stationarity conditions in the multipliers are over-determined
+ * ((n + m) L + n equations, (L + 1) n (+ n) unknowns for L stages) and are
+ * solved in the least-squares sense through their block-tridiagonal normal
+ * equations (block Cholesky, one CTA per segment, FP64), as the paper states.
+ * At the optimum the system is consistent and the result is the exact
+ * multiplier vector; elsewhere it is the least-squares one.
+ * prob: FP64 device arrays as for lqr_solve; opts->prec = LQR_FP64, no
+ * refinement (else LQR_ERR_UNSUPPORTED). x [T+1][n], u [T][m]: DEVICE FP64.
+ * Outputs (DEVICE FP64, caller-allocated): lam [T+1][n] (lambda_t of the
+ * segment holding stage t; lambda_T from the last segment), lam_end [K-1][n]
+ * (segment j's own multiplier of the dynamics into its end state, which is
+ * segment j+1's lambda at its first stage), mu [K-1][n]; lam_end and mu may be
+ * NULL only when K = 1. Workspace: (longest segment + 2)(2n^2 + 2n) doubles per
+ * segment, owned by the handle. Asynchronous on `stream`; a block that is not
+ * positive definite is reported through lqr_report (LQR_ERR_NOT_PD). */
+lqr_status lqr_ls_multipliers(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts, const double *x,
+                              const double *u, double *lam, double *lam_end, double *mu, void *stream);
+
 /* Step A1 alone: the per-segment parametric backward sweeps (Section II-B,
  * Eq. 9-16). Writes K summaries of LQR_SUMMARY_DOUBLES(n) doubles each to the
  * device array `summaries` (FP64). */

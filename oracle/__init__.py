@@ -322,7 +322,7 @@ def kkt_blocks_residual(prob: dict, x, u, lam):
     return dict(rx=rx, ru=ru, rxT=rxT, r0=r0, rd=rd)
 
 
-def ls_multipliers(prob: dict, x, u, bounds) -> dict:
+def ls_multipliers(prob: dict, x, u, bounds, only=None) -> dict:
     """Multipliers of the segment problems from the paper's least-squares
     system (Section II-B, "Lagrange Multipliers"; Eq. mults, mu, multsglobal,
     pseudoinverse), at the given trajectory (x, u).
@@ -344,7 +344,8 @@ def ls_multipliers(prob: dict, x, u, bounds) -> dict:
     Returns lam ((T+1) x n: lambda_t for t in segment j's stages from segment
     j, lambda_T from the last segment), lam_end ((K-1) x n: each interior
     segment's own lambda_L, the multiplier of the dynamics into the next
-    segment's first state) and mu ((K-1) x n)."""
+    segment's first state) and mu ((K-1) x n). With `only` (segment indices),
+    just those segments are solved; the other entries stay zero."""
     A, B, Q, R, S, q, r = (prob[k] for k in ("A", "B", "Q", "R", "S", "q", "r"))
     Q = _sym(Q)
     R = _sym(R)
@@ -353,7 +354,7 @@ def ls_multipliers(prob: dict, x, u, bounds) -> dict:
     lam = np.zeros((T + 1, n))
     lam_end = np.zeros((max(K - 1, 0), n))
     mu = np.zeros((max(K - 1, 0), n))
-    for j in range(K):
+    for j in (range(K) if only is None else only):
         b, e = bounds[j], bounds[j + 1]
         L = e - b
         last = (j == K - 1)

@@ -1194,6 +1194,48 @@ lqr_status lqr_segment_policies(lqr_handle* h, const lqr_problem* p, const lqr_o
   return LQR_OK;
 }
 
+lqr_status lqr_ls_multipliers(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const double* x,
+                              const double* u, double* lam, double* lam_end, double* mu, void* stream) {
+  if (!h || !x || !u || !lam) return LQR_ERR_INVALID_ARG;
+  lqr_solution none;
+  memset(&none, 0, sizeof(none));
+  lqr_status v = validate(p, o, &none);
+  if (v != LQR_OK) return v;
+  if (o->prec != LQR_FP64 || o->max_refine > 0) return LQR_ERR_UNSUPPORTED;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lqr_opts o2 = *o;
+  o2.residual = 0;
+  SolvePlan sp;
+  lqr_status rs = plan_solve(h, p, &o2, &sp);
+  if (rs != LQR_OK) return rs;
+  const int n = p->n, m = p->m, T = p->T, K = sp.K;
+  if (K > 1 && (!lam_end || !mu)) return LQR_ERR_INVALID_ARG;
+  LsArgs a;
+  memset(&a, 0, sizeof(a));
+  a.A = static_cast<const double*>(p->A); a.B = static_cast<const double*>(p->B);
+  a.Q = static_cast<const double*>(p->Q); a.R = static_cast<const double*>(p->R);
+  a.S = static_cast<const double*>(p->S); a.q = static_cast<const double*>(p->q);
+  a.r = static_cast<const double*>(p->r);
+  a.x = x; a.u = u; a.lam = lam; a.lam_end = lam_end; a.mu = mu;
+  a.n = n; a.m = m; a.T = T; a.K = K;
+  a.status = h->d_status;
+  const long long budget = h->smem_optin - kStaticSmemReserve;
+  a.on_chip = (long long)ls_mult_smem_bytes(n, m, 1) <= budget ? 1 : 0;
+  if ((long long)ls_mult_smem_bytes(n, m, 0) > budget) return LQR_ERR_UNSUPPORTED;
+  a.scratch_per_seg = (ls_mult_scratch_doubles(n, T, K) + 31) & ~31LL;
+  rs = grow(&h->ws, &h->ws_bytes, sizeof(double) * (size_t)a.scratch_per_seg * K + 256);
+  if (rs != LQR_OK) return rs;
+  a.scratch = reinterpret_cast<double*>(h->ws);
+  if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
+  if (cudaMemsetAsync(h->d_report, 0, 4 * sizeof(double), st) != cudaSuccess) return LQR_ERR_CUDA;
+  if (launch_ls_mult(a, st) != cudaSuccess) return LQR_ERR_CUDA;
+  h->last_K = K;
+  h->last_launches = 1;
+  h->last_resid = 0;
+  return LQR_OK;
+}
+
 lqr_status lqr_segment_summaries(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, double* summaries,
                                  void* stream) {
   if (!h || !summaries) return LQR_ERR_INVALID_ARG;

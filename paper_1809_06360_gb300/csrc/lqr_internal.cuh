@@ -329,6 +329,20 @@ cudaError_t launch_adjoint_rhs_batched(const void* jobs, int njobs, cudaStream_t
 template <typename TS>
 cudaError_t launch_adjoint_grad_batched(const void* jobs, int njobs, int Tmax, cudaStream_t st);
 
+// least-squares multipliers of the segment problems (ls_mult.cu)
+struct LsArgs {
+  const double *A, *B, *Q, *R, *S, *q, *r, *x, *u;
+  double *lam, *lam_end, *mu;
+  double* scratch;             // per segment: (longest segment + 2) factor blocks
+  long long scratch_per_seg;   // doubles
+  int* status;
+  int n, m, T, K;
+  int on_chip;                 // 1: the working blocks in shared memory
+};
+size_t ls_mult_smem_bytes(int n, int m, int on_chip);
+long long ls_mult_scratch_doubles(int n, int T, int K);
+cudaError_t launch_ls_mult(const LsArgs& a, cudaStream_t st);
+
 // refinement (refine.cu)
 // per-CTA objective partials of the residual pass: at most kMaxResidBlocks CTAs
 constexpr int kMaxResidBlocks = 1024;

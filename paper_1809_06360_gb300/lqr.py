@@ -31,7 +31,7 @@ EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
            "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
-           "lqr_rcp_newton_check", "lqr_segment_policies")
+           "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -97,6 +97,8 @@ def load(path: str | None = None):
     lib.lqr_rcp_newton_check.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
     lib.lqr_segment_policies.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_int, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p]
+    lib.lqr_ls_multipliers.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, c_void_p]
     lib.lqr_backward.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p, c_void_p,
                                  P(lqr_problem), c_void_p]
     lib.lqr_backward_batched.argtypes = [c_void_p, c_int, P(lqr_problem), P(lqr_opts), P(lqr_solution),
@@ -105,7 +107,7 @@ def load(path: str | None = None):
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
                  "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
-                 "lqr_rcp_newton_check", "lqr_segment_policies"):
+                 "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -373,6 +375,28 @@ class Solver:
                                            out["Kx"].data_ptr(), out["Kz"].data_ptr(), out["k1"].data_ptr(),
                                            out["z"].data_ptr(), self._stream(stream) or None),
                "lqr_segment_policies")
+        return out
+
+    def ls_multipliers(self, prob, x, u, num_segments, stream=None):
+        """Segment multipliers from the least-squares system (lqr_ls_multipliers):
+        dict lam, lam_end, mu (FP64 device tensors)."""
+        torch = _torch()
+        n, m, T = self._dims(prob)
+        dev = prob["A"].device
+        K = max(num_segments, 1)
+        out = dict(lam=torch.empty((T + 1, n), dtype=torch.float64, device=dev),
+                   lam_end=torch.empty((max(K - 1, 1), n), dtype=torch.float64, device=dev),
+                   mu=torch.empty((max(K - 1, 1), n), dtype=torch.float64, device=dev))
+        p = self.make_problem_struct(prob, lambda t: t.data_ptr())
+        o = lqr_opts(prec=PRECISION["fp64"], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=FORM["multiplier"], residual=0)
+        _check(load().lqr_ls_multipliers(self.h, ctypes.byref(p), ctypes.byref(o), x.data_ptr(), u.data_ptr(),
+                                         out["lam"].data_ptr(), out["lam_end"].data_ptr(), out["mu"].data_ptr(),
+                                         self._stream(stream) or None),
+               "lqr_ls_multipliers")
+        if K == 1:
+            out["lam_end"] = out["lam_end"][:0]
+            out["mu"] = out["mu"][:0]
         return out
 
     def segment_summaries(self, prob, num_segments, prec="fp64", stream=None, form="multiplier"):
