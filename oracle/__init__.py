@@ -20,6 +20,10 @@ segment_dual_summary(...) the same segment problem with its end-point constraint
                          G(x_s, mu) = 1/2 x_s'P x_s + mu'Z x_s - 1/2 mu'W mu + p'x_s + w'mu,
                          by a dense KKT solve with (x_s, mu) as parameters.
 kkt_residual(prob, ...)  the residual of Eq. 3 and its normwise backward error.
+global_policy_from_segment(...) the global cost to go and policy at one stage
+                         from the end-constrained value of the rest of its segment
+                         and the global value at the segment end (Section II-B,
+                         Section III-A).
 ls_multipliers(...)      the multipliers of every segment problem from the
                          over-determined stationarity system of Section II-B
                          ("Lagrange Multipliers"), solved through its normal
@@ -227,8 +231,28 @@ def segment_summary(prob: dict, t0: int, t1: int) -> dict:
     vz = -nu_term[:, 0]
     w0 = sol[:nw, 0]
     v0 = 0.5 * w0 @ H @ w0 + g @ w0
+    u0 = sol[us(0)]  # the first control as an affine function of (x_s, z)
     return dict(Vxx=Vxx, Vzx=Vzx, Vzz=Vzz, vx=vx, vz=vz, v0=float(v0),
-                Vxz_from_init=-nu_init[:, 1 + n:])
+                Vxz_from_init=-nu_init[:, 1 + n:], Kx=u0[:, 1:1 + n], Kz=u0[:, 1 + n:], k1=u0[:, 0])
+
+
+def global_policy_from_segment(prob: dict, t: int, t1: int, P_end, p_end) -> dict:
+    """The global cost to go and policy at stage t from the end-constrained
+    problem on stages t..t1-1 (Eq. 8-9: its value J(x, z) and its first
+    control u_t = Kx x + Kz z + k1, by segment_summary) and the global value
+    1/2 z'P_end z + p_end'z at the end link point t1: the minimising end
+    state z* = -(Vzz + P_end)^-1 (Vzx x + vz + p_end) gives
+        P_t = Vxx - Vzx'(Vzz + P_end)^-1 Vzx,   p_t = vx - Vzx'(Vzz + P_end)^-1 (vz + p_end),
+        K_t = Kx - Kz (Vzz + P_end)^-1 Vzx,      k_t = k1 - Kz (Vzz + P_end)^-1 (vz + p_end)
+    (the per-stage reconstruction of the global policy from a segment's
+    parametric value, Section II-B with Section III-A's global value). Needs
+    t1 - t stages enough to reach every end state (a regular J)."""
+    sm = segment_summary(prob, t, t1)
+    Sm = sm["Vzz"] + np.asarray(P_end)
+    X = np.linalg.solve(Sm, np.column_stack([sm["Vzx"], sm["vz"] + np.asarray(p_end)]))
+    Xx, xv = X[:, :-1], X[:, -1]
+    return dict(P=sm["Vxx"] - sm["Vzx"].T @ Xx, p=sm["vx"] - sm["Vzx"].T @ xv,
+                K=sm["Kx"] - sm["Kz"] @ Xx, k=sm["k1"] - sm["Kz"] @ xv)
 
 
 def segment_dual_summary(prob: dict, t0: int, t1: int) -> dict:

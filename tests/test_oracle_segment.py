@@ -256,3 +256,21 @@ def test_dual_summary_composes_with_serial_value_function(n, m, T, t0, t1):
     p0 = d["p"] + d["Z"].T @ (P1 @ np.linalg.solve(M, d["w"] - d["W"] @ p1) + p1)
     assert oracle.rel_err(P0, ric["P"][t0]) < 1e-9
     assert oracle.rel_err(p0, ric["p"][t0]) < 1e-9
+
+
+@pytest.mark.parametrize("n,m,T,t1", [(3, 2, 14, 9), (4, 1, 16, 12), (2, 3, 8, 5), (5, 2, 18, 14)])
+def test_global_policy_from_segment_equals_serial(n, m, T, t1):
+    """The per-stage reconstruction of the global policy from the end-constrained
+    value of the rest of the segment and the global value at its end point
+    (the serial recursion's P, p at t1) is Bellman's split: it must return the
+    serial recursion's P_t, p_t, K_t, k_t at every stage from which the end
+    state is reachable (t1 - t >= ceil(n / m))."""
+    prob = workloads.make_problem(n, m, T, seed=40 + n * m + t1, cross=True)
+    ref = oracle.riccati(prob)
+    reach = -(-n // m)
+    scale = {k: np.abs(ref[k][:t1]).max() for k in ("P", "p", "K", "k")}
+    for t in range(0, t1 - reach + 1):
+        g = oracle.global_policy_from_segment(prob, t, t1, ref["P"][t1], ref["p"][t1])
+        for k in ("P", "p", "K", "k"):
+            assert np.abs(g[k] - ref[k][t]).max() < 1e-8 * scale[k], (t, k)
+
