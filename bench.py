@@ -300,6 +300,13 @@ WORKLOADS = {
 }
 
 
+def stage_policy_flops(n: int, m: int) -> float:
+    """Algorithmic FLOPs of one stage of the per-stage global-policy
+    reconstruction: the factor of Vzz + P_e (n^3/3), the two triangular solves
+    with n + 1 right-hand sides (2 n^2 (n + 1)), X'X (2n^3) and Kz Y (2 m n^2)."""
+    return n ** 3 / 3.0 + 2.0 * n * n * (n + 1) + 2.0 * n ** 3 + 2.0 * m * n * n
+
+
 def ls_mult_flops(n: int, m: int, T: int, K: int) -> float:
     """Algorithmic FLOPs of the least-squares multipliers (block Cholesky of
     the normal equations): per dynamics block A A' (2n^3), B B' (2n^2 m), the
@@ -623,6 +630,7 @@ def main():
                 "phase_ms_per_step": ph}
 
     extras = {}
+    gpp_answer = None
     if not args.no_extras:
         # the plain FP64 segment-parallel solve of the same workload on the same GPU,
         # at its best segment count
@@ -676,7 +684,7 @@ def main():
             del d32, o32
         # the multipliers from Section II-B's least-squares system at the FP64
         # optimum (lqr_ls_multipliers: block Cholesky of the normal equations, FP64)
-        o64 = solver.alloc_solution(dev64, want=("x", "u", "lam"))
+        o64 = solver.alloc_solution(dev64, want=("K", "k", "x", "u", "lam"))
         solver.solve(dev64, num_segments=K, prec="fp64", out=o64)
         f = lambda: solver.ls_multipliers(dev64, o64["x"], o64["u"], K)
         lsm = f()
@@ -691,6 +699,42 @@ def main():
             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz",
             "rel_diff_vs_solve_lambda": float((lsm["lam"] - o64["lam"]).abs().max() / o64["lam"].abs().max())}
         del o64, lsm
+        # the per-stage reconstruction of the global policy (constrained form, FP64)
+        # beside the sequential policy sweep of the FP64 constrained solve
+        f = lambda: solver.global_policy_parallel(dev64, K)
+        gpp = f()
+        torch.cuda.synchronize()
+        reps = 3
+        lqr.lqr_profile_enable(solver.h, True)
+        for _ in range(reps):
+            f()
+        ph, nprof = lqr.lqr_profile_read(solver.h)
+        lqr.lqr_profile_enable(solver.h, False)
+        oc = solver.alloc_solution(dev64, want=("K", "k", "x", "u"))
+        solver.solve(dev64, num_segments=K, prec="fp64", form="constrained", out=oc)
+        lqr.lqr_profile_enable(solver.h, True)
+        for _ in range(reps):
+            solver.solve(dev64, num_segments=K, prec="fp64", form="constrained", out=oc)
+        ph2, nprof2 = lqr.lqr_profile_read(solver.h)
+        lqr.lqr_profile_enable(solver.h, False)
+        del oc
+        reach = -(-n // m)
+        nst = sum(max(0, (j + 1) * T // K - j * T // K - (reach - 1)) for j in range(K - 1))
+        work = stage_policy_flops(n, m) * nst
+        ms_stage = ph["rollout"] / nprof
+        ach = work / (ms_stage * 1e-3) / 1e12
+        extras["global_policy_parallel"] = {
+            "kernel": "stage_policy_kernel (per-stage global P_t, K_t from the constrained segment values, FP64, "
+                      "one CTA per stage)",
+            "ms_total": sum(ph.values()) / nprof, "K": K,
+            "phase_ms": {"A1 constrained sweep": ph["sweep"] / nprof, "link": ph["link"] / nprof,
+                         "policy sweep of the segment ends": ph["policy"] / nprof, "per-stage kernel": ms_stage},
+            "sequential_policy_sweep_ms": ph2["policy"] / nprof2, "fp64_constrained_solve_ms": sum(ph2.values()) / nprof2,
+            "stages_in_parallel": nst, "bound": "alu", "unit": "TFLOP/s", "work": work, "achieved": ach,
+            "peak": PEAK_FP64_TFLOPS, "frac": ach / PEAK_FP64_TFLOPS,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2070 MHz"}
+        gpp_answer = {k: v.cpu().numpy() for k, v in gpp.items()}
+        del gpp
         del dev64
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timing
@@ -724,6 +768,9 @@ def main():
         if ref is not None:
             errors = {k: float(np.abs(answer[k] - ref[k]).max() / np.abs(ref[k]).max())
                       for k in ("K", "k", "x", "u", "lam")}
+            if gpp_answer is not None and "global_policy_parallel" in extras:
+                extras["global_policy_parallel"]["errors_vs_fp64_oracle"] = {
+                    k: float(np.abs(gpp_answer[k] - ref[k]).max() / np.abs(ref[k]).max()) for k in ("K", "k", "P", "p")}
 
     if rank == 0:
         config = {"workload": "%s, K=%d segments, %s" % (wl["name"], K, prec.upper()),

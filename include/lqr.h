@@ -282,6 +282,34 @@ lqr_status lqr_tc_selftest(int device, double* errs);
  * IEEE division. d, y: DEVICE arrays of count doubles. Asynchronous on stream. */
 lqr_status lqr_rcp_newton_check(const double* d, double* y, int count, void* stream);
 
+/* The global policy and cost to go of every stage reconstructed in parallel
+ * from the segments' parametric values (Section II-B with the global value of
+ * Section III-A), in place of the sequential policy sweep of step A4.
+ * The constraint-explicit sweeps give, at every stage t of segment j < K-1,
+ * the cost to go of the rest of the segment as a function of (x_t, z) (Eq. 9
+ * at stage t; z the segment's end state) and the stage's policy
+ * u_t = Kx x + Kz z + k1; the link solve gives the global value
+ * 1/2 z'P_e z + p_e'z at the segment's end. At every stage whose
+ * constraint_to_go has no rows left, independently (one CTA per stage):
+ *   P_t = Vxx - Vzx'(Vzz + P_e)^-1 Vzx,  p_t = vx - Vzx'(Vzz + P_e)^-1 (vz + p_e),
+ *   K_t = Kx - Kz (Vzz + P_e)^-1 Vzx,     k_t = k1 - Kz (Vzz + P_e)^-1 (vz + p_e).
+ * The few stages at each segment end whose constraint_to_go still has rows
+ * (about ceil(n/m)) come from the policy sweep started at the segment end, and
+ * the last segment's stages from its Riccati sweep. The result equals the
+ * serial recursion's up to rounding; P_t is a difference of terms that grow
+ * towards the segment end, so there the rounding error is larger than the
+ * sequential sweep's (the cancellation this reconstruction trades for its
+ * parallelism).
+ * prob and opts as for lqr_solve with opts->prec = LQR_FP64 and
+ * opts->form = LQR_FORM_CONSTRAINED, no refinement (else
+ * LQR_ERR_UNSUPPORTED). Outputs (DEVICE, FP64, caller-allocated): K [T][m][n],
+ * k [T][m], P [T+1][n][n] and p [T+1][n] (both NULL = not wanted).
+ * Workspace: T (m (2n+1) + 3n^2 + 2n) doubles beyond the solve's (plus
+ * T (2n^2 + n) when the per-stage factor does not fit in shared memory), owned
+ * by the handle. Asynchronous on `stream`; device conditions through lqr_report. */
+lqr_status lqr_global_policy_parallel(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts, void *K,
+                                      void *k, void *P, void *p, void *stream);
+
 /* The multipliers of every segment problem from the least-squares system of
  * Section II-B ("Lagrange Multipliers"), at the trajectory (x, u) (the optimum
  * lqr_solve returns, or any other): a check on the multipliers of Eq. 3 that
@@ -348,7 +376,9 @@ int lqr_last_launch_count(const lqr_handle *h);
 
 /* Phase profiling with CUDA events recorded on the solve's own stream.
  * Phases: the parametric segment sweeps (A1), the link solve (A3), the policy
- * sweeps (A4), rollout + multipliers + cost (A5/A6), refinement (A7/A8). */
+ * sweeps (A4), rollout + multipliers + cost (A5/A6), refinement (A7/A8).
+ * lqr_global_policy_parallel records A1, A3, the policy sweep of the segment
+ * ends (policy slot) and the per-stage reconstruction kernel (rollout slot). */
 #define LQR_NUM_PHASES 5
 enum { LQR_PHASE_SWEEP = 0, LQR_PHASE_LINK = 1, LQR_PHASE_POLICY = 2, LQR_PHASE_ROLLOUT = 3,
        LQR_PHASE_REFINE = 4 };

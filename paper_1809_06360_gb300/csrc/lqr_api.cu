@@ -1194,6 +1194,85 @@ lqr_status lqr_segment_policies(lqr_handle* h, const lqr_problem* p, const lqr_o
   return LQR_OK;
 }
 
+lqr_status lqr_global_policy_parallel(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, void* Kout,
+                                      void* kout, void* Pout, void* pout, void* stream) {
+  if (!h || !Kout || !kout || (Pout != nullptr) != (pout != nullptr)) return LQR_ERR_INVALID_ARG;
+  lqr_solution none;
+  memset(&none, 0, sizeof(none));
+  lqr_status v = validate(p, o, &none);
+  if (v != LQR_OK) return v;
+  if (o->prec != LQR_FP64 || o->form != LQR_FORM_CONSTRAINED || o->max_refine > 0) return LQR_ERR_UNSUPPORTED;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lqr_opts o2 = *o;
+  o2.residual = 0;
+  SolvePlan sp;
+  lqr_status rs = plan_solve(h, p, &o2, &sp);
+  if (rs != LQR_OK) return rs;
+  const int n = p->n, m = p->m, T = p->T, K = sp.K;
+  const long long nn = (long long)n * n;
+  const long long budget = h->smem_optin - kStaticSmemReserve;
+  const int on_chip = (long long)stage_policy_smem_bytes(n, 1) <= budget ? 1 : 0;
+  // workspace: the solve's, then the segment policies, the per-stage values and
+  // ranks, and (off chip) the per-stage factor buffers
+  const long long pol_off = ((sp.wl.total + (long long)K * sp.scratch_doubles) + 31) & ~31LL;
+  const long long sv_off = (pol_off + (long long)T * m * (2 * n + 1) + 31) & ~31LL;
+  const long long rk_off = (sv_off + (long long)T * (3 * nn + 2 * n) + 31) & ~31LL;
+  const long long sc_off = (rk_off + (T + 1) / 2 + 31) & ~31LL;
+  const long long end = sc_off + (on_chip ? 0 : (long long)T * (nn + (long long)n * (n + 1)));
+  const size_t need = sizeof(double) * (size_t)end + 256;
+  rs = grow(&h->ws, &h->ws_bytes, need > sp.ws_need ? need : sp.ws_need);
+  if (rs != LQR_OK) return rs;
+  double* base = reinterpret_cast<double*>(h->ws);
+  lqr_solution sol;
+  memset(&sol, 0, sizeof(sol));
+  sol.K = Kout; sol.k = kout; sol.P = Pout; sol.p = pout;
+  ProbTable tab;
+  memset(&tab, 0, sizeof(tab));
+  tab.single = make_desc(h, p, &sol, sp, (int)LQR_FORM_CONSTRAINED);
+  tab.single.segpol = base + pol_off;
+  tab.single.stageV = base + sv_off;
+  tab.single.stage_rank = reinterpret_cast<int*>(base + rk_off);
+  tab.nprob = 1;
+  const int store_P = (Pout && pout) ? 1 : 0;
+  int launches = 0;
+  if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
+  if (cudaMemsetAsync(h->d_report, 0, 4 * sizeof(double), st) != cudaSuccess) return LQR_ERR_CUDA;
+  // A1: the constraint-explicit segment sweeps, keeping every stage's cost to go,
+  // rank and policy (the last segment: its Riccati sweep, global already)
+  prof_mark(h, LQR_PHASE_SWEEP, st);
+  if (launch_seg_sweep<double, double>(tab, K, 0, sp.smem, budget, store_P, st) != cudaSuccess) return LQR_ERR_CUDA;
+  ++launches;
+  prof_mark(h, LQR_PHASE_LINK, st);
+  if (K > 1) {
+    // A3: the link points and the global value at each of them
+    if (launch_link_solve(tab, 1, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
+    ++launches;
+  }
+  prof_mark(h, LQR_PHASE_POLICY, st);
+  if (K > 1) {
+    // the stages whose constraint_to_go still has rows: the policy sweep from the
+    // segment end, stopping at the first stage of rank 0
+    if (launch_seg_sweep<double, double>(tab, K, 1, sp.smem, budget, store_P, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    ++launches;
+  }
+  prof_mark(h, LQR_PHASE_ROLLOUT, st);
+  if (K > 1) {
+    // every other stage of segments 0 .. K-2 at once
+    if (launch_stage_policy(tab.single, seg_begin(T, K, K - 1), on_chip, base + sc_off, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    ++launches;
+  }
+  prof_mark(h, LQR_PHASE_REFINE, st);
+  prof_mark(h, LQR_NUM_PHASES, st);
+  if (h->prof_on && h->prof_count < lqr_handle::kMaxProfiled) ++h->prof_count;
+  h->last_K = K;
+  h->last_launches = launches;
+  h->last_resid = 0;
+  return LQR_OK;
+}
+
 lqr_status lqr_ls_multipliers(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const double* x,
                               const double* u, double* lam, double* lam_end, double* mu, void* stream) {
   if (!h || !x || !u || !lam) return LQR_ERR_INVALID_ARG;

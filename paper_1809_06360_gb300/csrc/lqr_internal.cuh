@@ -84,6 +84,9 @@ struct ProbDesc {
   void* Minv;                 // FP32 fast path: T x m x m M_uu^-1 of the policy stages, may be null
   double* segpol;             // FP64 constrained sweep: T x m x (2n+1) segment policies [K_x | K_z | k_1], may be null
   int smooth;                 // policy sweep started from the next segment's cost with its end pinned (Section III-A)
+  double* stageV;             // FP64 constrained sweep: T x (3n^2 + 2n) per-stage [Vxx | Vzx | Vzz | vx | vz], may be null
+  int* stage_rank;            // T: rows of the constraint_to_go at each stage (with stageV); the policy
+                              // sweep stops at the first stage of rank 0 when set
 };
 
 // Kernel-argument view of the problems of one launch: a single problem is
@@ -328,6 +331,10 @@ template <typename TS>
 cudaError_t launch_adjoint_rhs_batched(const void* jobs, int njobs, cudaStream_t st);
 template <typename TS>
 cudaError_t launch_adjoint_grad_batched(const void* jobs, int njobs, int Tmax, cudaStream_t st);
+
+// per-stage reconstruction of the global policy (stage_policy.cu)
+size_t stage_policy_smem_bytes(int n, int on_chip);
+cudaError_t launch_stage_policy(const ProbDesc& pd, int nstages, int on_chip, double* scratch, cudaStream_t st);
 
 // least-squares multipliers of the segment problems (ls_mult.cu)
 struct LsArgs {

@@ -196,6 +196,9 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
 
   bool failed = false;
   for (int t = t1 - 1; t >= t0; --t) {
+    // with the per-stage reconstruction, the policy sweep only covers the stages
+    // whose constraint_to_go still has rows (the end of the segment)
+    if (mode == MODE_POLICY && pd.stage_rank && pd.stage_rank[t] == 0) break;
     // ---- (1) stage the dynamics [A_t | B_t | c_t] ---------------------------
     {
       const TS* At = gA + nn * t;
@@ -483,6 +486,23 @@ __global__ void __launch_bounds__(kBlock) seg_sweep_kernel(ProbTable tab, int ph
       cta_copy<TC>(n, n, T1, ldAB, Vzx, n);
       cta_symmetrize<TC>(n, Vxx, n);
       __syncthreads();
+    }
+    if (pd.stageV && param) {
+      // the cost to go at stage t as a function of (x_t, x_term) (Eq. 9 at stage
+      // t) and the rows of its constraint_to_go, for the per-stage reconstruction
+      // of the global policy
+      double* sv = pd.stageV + (size_t)t * (3 * nn + 2 * n);
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        sv[e] = static_cast<double>(Vxx[e]);
+        sv[nn + e] = static_cast<double>(Vzx[e]);
+        sv[2 * nn + e] = 0.5 * (static_cast<double>(Vzz[(size_t)i * n + j]) + static_cast<double>(Vzz[(size_t)j * n + i]));
+      }
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sv[3 * nn + i] = static_cast<double>(vx[i]);
+        sv[3 * nn + n + i] = static_cast<double>(vz[i]);
+      }
+      if (threadIdx.x == 0) pd.stage_rank[t] = rr;
     }
     if (store_P && gP && !param) {
       for (int e = threadIdx.x; e < n * n; e += blockDim.x) gP[nn * t + e] = static_cast<TS>(Vxx[e]);

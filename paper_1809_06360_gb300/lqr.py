@@ -31,7 +31,8 @@ EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve
            "lqr_segment_summaries", "lqr_report", "lqr_status_string", "lqr_last_launch_count",
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
            "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
-           "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers")
+           "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
+           "lqr_global_policy_parallel")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -97,6 +98,8 @@ def load(path: str | None = None):
     lib.lqr_rcp_newton_check.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
     lib.lqr_segment_policies.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_int, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p]
+    lib.lqr_global_policy_parallel.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_void_p, c_void_p,
+                                               c_void_p, c_void_p, c_void_p]
     lib.lqr_ls_multipliers.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_void_p, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p]
     lib.lqr_backward.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), P(lqr_solution), c_void_p, c_void_p,
@@ -107,7 +110,8 @@ def load(path: str | None = None):
                  "lqr_segment_summaries", "lqr_report", "lqr_last_launch_count", "lqr_profile_enable",
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
                  "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
-                 "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers"):
+                 "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
+           "lqr_global_policy_parallel"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -375,6 +379,28 @@ class Solver:
                                            out["Kx"].data_ptr(), out["Kz"].data_ptr(), out["k1"].data_ptr(),
                                            out["z"].data_ptr(), self._stream(stream) or None),
                "lqr_segment_policies")
+        return out
+
+    def global_policy_parallel(self, prob, num_segments, want_P=True, stream=None):
+        """Per-stage reconstruction of the global policy (lqr_global_policy_parallel):
+        dict K, k (and P, p) as FP64 device tensors."""
+        torch = _torch()
+        n, m, T = self._dims(prob)
+        dev = prob["A"].device
+        out = dict(K=torch.empty((T, m, n), dtype=torch.float64, device=dev),
+                   k=torch.empty((T, m), dtype=torch.float64, device=dev))
+        if want_P:
+            out["P"] = torch.empty((T + 1, n, n), dtype=torch.float64, device=dev)
+            out["p"] = torch.empty((T + 1, n), dtype=torch.float64, device=dev)
+        p = self.make_problem_struct(prob, lambda t: t.data_ptr())
+        o = lqr_opts(prec=PRECISION["fp64"], num_segments=num_segments, tol=0.0, max_refine=0, debug_checks=0,
+                     form=FORM["constrained"], residual=0)
+        _check(load().lqr_global_policy_parallel(self.h, ctypes.byref(p), ctypes.byref(o), out["K"].data_ptr(),
+                                                 out["k"].data_ptr(),
+                                                 out["P"].data_ptr() if want_P else None,
+                                                 out["p"].data_ptr() if want_P else None,
+                                                 self._stream(stream) or None),
+               "lqr_global_policy_parallel")
         return out
 
     def ls_multipliers(self, prob, x, u, num_segments, stream=None):
