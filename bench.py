@@ -736,6 +736,31 @@ def main():
         gpp_answer = {k: v.cpu().numpy() for k, v in gpp.items()}
         del gpp
         del dev64
+        # the trajectory-optimisation outer loop (Section I) on a nonlinear
+        # tracking model of the same size, its LQR subproblems in this mode
+        nlm = workloads.make_nl_model(n, m, T, seed=84, beta=0.05)
+        dm = {k: (torch.from_numpy(v).to(device, torch.float64) if isinstance(v, np.ndarray) else v)
+              for k, v in nlm.items()}
+
+        def sqp_run():
+            xs = torch.zeros((T + 1, n), dtype=torch.float64, device=device)
+            us = torch.zeros((T, m), dtype=torch.float64, device=device)
+            return solver.sqp_solve(dm, xs, us, max_iters=30, tol=1e-8, num_segments=K, prec="mixed_fp32",
+                                    max_refine=8, sub_tol=1e-10)
+        sqp_run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        so = sqp_run()
+        el = (time.perf_counter() - t0) * 1e3
+        extras["sqp_outer_loop"] = {
+            "model": "x' = A x + B u + 0.05 tanh(C x), tracking cost, n=%d m=%d T=%d, from x = u = 0" % (n, m, T),
+            "subproblem": "MIXED_FP32, K=%d, refined to rel 1e-10" % K,
+            "iterations": so["report"]["iters"], "converged": so["report"]["converged"],
+            "final_defect_l1": so["report"]["defect"], "final_cost": so["report"]["cost"],
+            "ms_total": el, "ms_per_iteration": el / so["report"]["iters"],
+            "stages_per_s_per_iteration": T * so["report"]["iters"] / (el / 1e3),
+            "step_lengths": [h["alpha"] for h in so["hist"]]}
+        del dm, so
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timing
     e2e = None

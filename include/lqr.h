@@ -282,6 +282,61 @@ lqr_status lqr_tc_selftest(int device, double* errs);
  * IEEE division. d, y: DEVICE arrays of count doubles. Asynchronous on stream. */
 lqr_status lqr_rcp_newton_check(const double* d, double* y, int count, void* stream);
 
+/* ---- Trajectory-optimisation outer loop --------------------------------------
+ * Section I: trajectory optimisation reduces to a sequence of LQR subproblems.
+ * lqr_sqp_solve runs Gauss-Newton multiple-shooting SQP on the nonlinear
+ * tracking model
+ *   x_{t+1} = A x_t + B u_t + beta tanh(C x_t),  x_0 = x0,
+ *   J = sum_t 1/2 (x_t - xref_t)'Q (x_t - xref_t) + 1/2 u_t'R u_t
+ *       + 1/2 (x_T - xref_T)'Q_T (x_T - xref_T),
+ * each iteration: the LQR subproblem in the step (dx, du) at the iterate
+ * (dynamics linearised at every stage, c_t the defect f(x_t, u_t) - x_{t+1},
+ * the objective's exact quadratic model; one kernel), its solution by the
+ * segment-parallel solver (the options in opts->sub), the l1 merit
+ * J + nu D (D the defects' l1 norm, nu = max(nu_min, 2 max|lambda|)) at the
+ * step lengths 0, 1, 1/2, ..., 1/128 (one kernel for all), the first length
+ * with Armijo decrease phi(a) <= phi(0) + 1e-4 a (g'd - nu D(0)) (the full
+ * step once |g'd - nu D(0)| <= 1e-12 max(1, |phi(0)|); 1/128 when none), and
+ * the step (one kernel). Stops after max_iters iterations or once
+ * a max|(dx, du)| <= tol max(1, max|(x, u)|) and D(a) <= tol.
+ * Model arrays: DEVICE FP64, row-major; Q, R, Q_T symmetric positive definite.
+ * x [T+1][n], u [T][m]: DEVICE FP64, the starting iterate on entry (need not
+ * satisfy the dynamics), the last iterate on return. lam [T+1][n], K [T][m][n],
+ * k [T][m]: DEVICE FP64 or NULL: the last subproblem's multipliers (those of
+ * the nonlinear problem at convergence) and feedback policy (the stabilising
+ * policy of Section I's model-predictive-control use). hist: HOST, NULL or
+ * max_iters * LQR_SQP_HIST doubles, per iteration (a, J(a), D(a), merit, step,
+ * nu). opts->sub.prec: LQR_FP64 or LQR_MIXED_FP32 (else LQR_ERR_UNSUPPORTED).
+ * Synchronous: returns after the loop (each iteration reads its merit values
+ * back). A failed subproblem returns its status. Workspace owned by the handle. */
+typedef struct {
+  int n, m, T;
+  const double *A, *B, *C; /* n x n, n x m, n x n */
+  double beta;
+  const double *Q, *R, *QT; /* n x n, m x m, n x n */
+  const double *xref;      /* [T+1][n] */
+  const double *x0;        /* [n] */
+} lqr_nl_model;
+
+typedef struct {
+  int max_iters;
+  double tol;
+  double nu_min;
+  lqr_opts sub;            /* options of every LQR subproblem solve */
+} lqr_sqp_opts;
+
+typedef struct {
+  int iters;               /* iterations taken */
+  int converged;           /* 1 when the stopping test held */
+  double cost, defect;     /* J and D at the returned iterate */
+  double alpha, step;      /* the last step length and a max|(dx, du)| */
+} lqr_sqp_report;
+
+#define LQR_SQP_HIST 6
+
+lqr_status lqr_sqp_solve(lqr_handle *h, const lqr_nl_model *model, const lqr_sqp_opts *opts, double *x, double *u,
+                         double *lam, double *K, double *k, lqr_sqp_report *report, double *hist, void *stream);
+
 /* The global policy and cost to go of every stage reconstructed in parallel
  * from the segments' parametric values (Section II-B with the global value of
  * Section III-A), in place of the sequential policy sweep of step A4.

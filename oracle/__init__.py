@@ -24,6 +24,11 @@ global_policy_from_segment(...) the global cost to go and policy at one stage
                          from the end-constrained value of the rest of its segment
                          and the global value at the segment end (Section II-B,
                          Section III-A).
+nl_dynamics / nl_jacobian / sqp(...)  the nonlinear tracking problem of the
+                         trajectory-optimisation outer loop (Section I: its
+                         subproblems are LQR problems) and a Gauss-Newton
+                         multiple-shooting SQP loop whose subproblems are solved
+                         by riccati().
 ls_multipliers(...)      the multipliers of every segment problem from the
                          over-determined stationarity system of Section II-B
                          ("Lagrange Multipliers"), solved through its normal
@@ -517,3 +522,99 @@ def fd_gradient(prob: dict, loss, keys=None, h: float = 1e-6, entries: int | Non
             grad.reshape(-1)[e] = (loss(riccati(p1)) - loss(riccati(p2))) / (2 * h)
         out[key] = grad
     return out
+
+
+# ---------------------------------------------------------------------------
+# The trajectory-optimisation outer loop (Section I: LQR as the subproblem)
+# ---------------------------------------------------------------------------
+
+def nl_dynamics(model: dict, x, u):
+    """f(x, u) = A x + B u + beta tanh(C x) (x, u may carry a leading stage axis)."""
+    A, B, C, beta = model["A"], model["B"], model["C"], model["beta"]
+    return x @ A.T + u @ B.T + beta * np.tanh(x @ C.T)
+
+
+def nl_jacobian(model: dict, x):
+    """df/dx = A + beta diag(1 - tanh(C x)^2) C (df/du = B), for a stack of states."""
+    A, C, beta = model["A"], model["C"], model["beta"]
+    th = np.tanh(x @ C.T)
+    return A[None] + beta * (1.0 - th ** 2)[..., :, None] * C[None]
+
+
+def nl_cost(model: dict, x, u) -> float:
+    """The tracking objective of the model at (x, u)."""
+    Q, R, QT, xr = model["Q"], model["R"], model["QT"], model["xref"]
+    e = x - xr
+    return float(0.5 * np.einsum("ti,ij,tj->", e[:-1], Q, e[:-1]) + 0.5 * np.einsum("ti,ij,tj->", u, R, u)
+                 + 0.5 * e[-1] @ QT @ e[-1])
+
+
+def sqp_subproblem(model: dict, x, u) -> dict:
+    """The LQR subproblem in the step (dx, du) at the iterate (x, u): dynamics
+    linearised at every stage (A_t = df/dx, B_t = B, c_t = f(x_t, u_t) - x_{t+1}),
+    the objective's exact quadratic model (its Hessians Q, R, Q_T and gradients
+    q_t = Q (x_t - xref_t), r_t = R u_t), dx_0 = x_init - x_0."""
+    T = u.shape[0]
+    n, m = model["B"].shape
+    Q, R, QT, xr = model["Q"], model["R"], model["QT"], model["xref"]
+    prob = dict(A=nl_jacobian(model, x[:T]), B=np.repeat(model["B"][None], T, 0),
+                c=nl_dynamics(model, x[:T], u) - x[1:],
+                Q=np.concatenate([np.repeat(Q[None], T, 0), QT[None]]), R=np.repeat(R[None], T, 0),
+                S=np.zeros((T, m, n)), q=np.concatenate([(x[:T] - xr[:T]) @ Q.T, ((x[T] - xr[T]) @ QT.T)[None]]),
+                r=u @ R.T, x0=model["x0"] - x[0])
+    return prob
+
+
+def sqp_merit_terms(model: dict, x, u, dx, du, alpha: float):
+    """Objective and l1 norm of the constraint defects (dynamics and initial
+    state) at the trial point (x + alpha dx, u + alpha du)."""
+    xa, ua = x + alpha * dx, u + alpha * du
+    d = np.abs(nl_dynamics(model, xa[:-1], ua) - xa[1:]).sum() + np.abs(xa[0] - model["x0"]).sum()
+    return nl_cost(model, xa, ua), float(d)
+
+
+SQP_ALPHAS = tuple(0.5 ** i for i in range(8))
+
+
+def sqp(model: dict, x, u, iters: int, tol: float = 1e-10, nu_min: float = 1.0) -> dict:
+    """Gauss-Newton multiple-shooting SQP for the nonlinear tracking problem:
+    at every iterate the LQR subproblem (sqp_subproblem) is solved by the serial
+    recursion (riccati), giving the step (dx, du) and the new multipliers
+    lambda; the step length is the first alpha of 1, 1/2, ..., 1/128 whose
+    l1 merit phi(alpha) = J + nu D (D the defects' l1 norm,
+    nu = max(nu_min, 2 max|lambda|)) satisfies the Armijo condition
+    phi(alpha) <= phi(0) + 1e-4 alpha (g'd - nu D(0)) (g'd the objective's
+    directional derivative), else the last one; the full step when the
+    predicted decrease |g'd - nu D(0)| is below 1e-12 max(1, |phi(0)|) (the
+    merit differences are then at rounding level). Stops after `iters`
+    iterations or once alpha max|(dx, du)| <= tol max(1, max|(x, u)|) (the
+    iterate before the step) and D(alpha) <= tol. Returns the iterate, the last multipliers and policy, and
+    per iteration the step length, merit and defects."""
+    x = np.array(x, dtype=np.float64)
+    u = np.array(u, dtype=np.float64)
+    hist = []
+    lam = K = k = None
+    for it in range(iters):
+        prob = sqp_subproblem(model, x, u)
+        sol = riccati(prob)
+        dx, du, lam, K, k = sol["x"], sol["u"], sol["lam"], sol["K"], sol["k"]
+        nu = max(nu_min, 2.0 * np.abs(lam).max())
+        gd = float(np.sum(prob["q"] * dx) + np.sum(prob["r"] * du))
+        J0, D0 = sqp_merit_terms(model, x, u, dx, du, 0.0)
+        phi0 = J0 + nu * D0
+        slope = gd - nu * D0
+        pick = None
+        for a in SQP_ALPHAS:
+            Ja, Da = sqp_merit_terms(model, x, u, dx, du, a)
+            pick = (a, Ja, Da)
+            if abs(slope) <= 1e-12 * max(1.0, abs(phi0)) or Ja + nu * Da <= phi0 + 1e-4 * a * slope:
+                break
+        a, Ja, Da = pick
+        scale = max(1.0, np.abs(x).max(), np.abs(u).max())
+        x = x + a * dx
+        u = u + a * du
+        step = a * max(np.abs(dx).max(), np.abs(du).max())
+        hist.append(dict(alpha=a, cost=Ja, defect=Da, merit=Ja + nu * Da, step=step, nu=nu))
+        if step <= tol * scale and Da <= tol:
+            break
+    return dict(x=x, u=u, lam=lam, K=K, k=k, hist=hist)

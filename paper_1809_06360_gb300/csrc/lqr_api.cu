@@ -87,6 +87,8 @@ struct lqr_handle {
   // LQR_MIXED_FP32: FP32 copy of the data, FP32 solution and correction buffers
   unsigned char* f32 = nullptr;
   size_t f32_bytes = 0;
+  unsigned char* nl = nullptr;  // the outer loop's subproblem data and merit partials
+  size_t nl_bytes = 0;
   // batch-schedule autotuner: per batch-shape bucket, 1 = the persistent
   // one-segment schedule was measured faster than the per-step launches
   struct TuneEntry { int key[4]; int persistent; float ms[2]; };
@@ -1103,6 +1105,7 @@ lqr_status lqr_destroy(lqr_handle* h) {
     for (int i = 0; i < lqr_handle::kMaxProfiled; ++i)
       for (int k = 0; k <= lqr_handle::kPhases; ++k) cudaEventDestroy(h->ev[i][k]);
   if (h->f32) cudaFree(h->f32);
+  if (h->nl) cudaFree(h->nl);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
@@ -1191,6 +1194,109 @@ lqr_status lqr_segment_policies(lqr_handle* h, const lqr_problem* p, const lqr_o
   h->last_K = K;
   h->last_launches = launches;
   h->last_resid = 0;
+  return LQR_OK;
+}
+
+lqr_status lqr_sqp_solve(lqr_handle* h, const lqr_nl_model* md, const lqr_sqp_opts* so, double* x, double* u,
+                         double* lam, double* Kout, double* kout, lqr_sqp_report* rep, double* hist, void* stream) {
+  if (!h || !md || !so || !x || !u || !rep) return LQR_ERR_INVALID_ARG;
+  memset(rep, 0, sizeof(*rep));
+  const int n = md->n, m = md->m, T = md->T;
+  if (n < 1 || m < 1 || T < 1 || n > 256 || m > 256) return LQR_ERR_INVALID_ARG;
+  if (!md->A || !md->B || !md->C || !md->Q || !md->R || !md->QT || !md->xref || !md->x0) return LQR_ERR_INVALID_ARG;
+  if (so->max_iters < 1 || !(so->tol >= 0.0) || !(so->nu_min >= 0.0)) return LQR_ERR_INVALID_ARG;
+  if (so->sub.prec != LQR_FP64 && so->sub.prec != LQR_MIXED_FP32) return LQR_ERR_UNSUPPORTED;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  // workspace: the subproblem's data, its solution where the caller gave none,
+  // the merit partials
+  size_t off = 0;
+  auto take = [&](size_t cnt) { const size_t a = off; off += (cnt + 31) & ~(size_t)31; return a; };
+  const size_t oA = take((size_t)T * nn), oB = take((size_t)T * nm), oc = take((size_t)T * n),
+               oQ = take((size_t)(T + 1) * nn), oR = take((size_t)T * mm), oq = take((size_t)(T + 1) * n),
+               or_ = take((size_t)T * m), ox0 = take(n), odx = take((size_t)(T + 1) * n), odu = take((size_t)T * m),
+               olam = lam ? 0 : take((size_t)(T + 1) * n), oK = Kout ? 0 : take((size_t)T * nm),
+               ok = kout ? 0 : take((size_t)T * m), opart = take((size_t)(T + 1) * kSqpOut), ores = take(kSqpOut);
+  lqr_status rs = grow(&h->nl, &h->nl_bytes, sizeof(double) * off);
+  if (rs != LQR_OK) return rs;
+  double* b = reinterpret_cast<double*>(h->nl);
+  NlModelDev dm;
+  dm.A = md->A; dm.B = md->B; dm.C = md->C; dm.Q = md->Q; dm.R = md->R; dm.QT = md->QT;
+  dm.xref = md->xref; dm.x0 = md->x0; dm.beta = md->beta; dm.n = n; dm.m = m; dm.T = T;
+  lqr_problem sp;
+  memset(&sp, 0, sizeof(sp));
+  sp.n = n; sp.m = m; sp.T = T;
+  sp.A = b + oA; sp.B = b + oB; sp.c = b + oc; sp.Q = b + oQ; sp.R = b + oR; sp.S = nullptr;
+  sp.q = b + oq; sp.r = b + or_; sp.x0 = b + ox0;
+  lqr_solution sol;
+  memset(&sol, 0, sizeof(sol));
+  double* dx = b + odx;
+  double* du = b + odu;
+  double* lm = lam ? lam : b + olam;
+  sol.K = Kout ? Kout : b + oK; sol.k = kout ? kout : b + ok;
+  sol.x = dx; sol.u = du; sol.lam = lm;
+  lqr_opts o = so->sub;
+  o.residual = 0;
+  rs = validate(&sp, &o, &sol);
+  if (rs != LQR_OK) return rs;
+  int launches = 0;
+  if (launch_sqp_fill(dm, b + oB, b + oQ, b + oR, st) != cudaSuccess) return LQR_ERR_CUDA;
+  ++launches;
+  double res[kSqpOut];
+  int status[2];
+  for (int it = 0; it < so->max_iters; ++it) {
+    // the LQR subproblem at the iterate, its solution, the merit of every candidate step
+    if (launch_sqp_linearize(dm, x, u, b + oA, b + oc, b + oq, b + or_, b + ox0, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    rs = run_solve(h, &sp, &o, &sol, st, false, nullptr);
+    if (rs != LQR_OK) return rs;
+    launches += 1 + h->last_launches;
+    if (launch_sqp_merit(dm, x, u, dx, du, b + oq, b + or_, lm, b + opart, b + ores, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    launches += 2;
+    if (cudaMemcpyAsync(res, b + ores, sizeof(res), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LQR_ERR_CUDA;
+    if (cudaMemcpyAsync(status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LQR_ERR_CUDA;
+    if (status[0] != 0) return static_cast<lqr_status>(status[0]);
+    const double* J = res;
+    const double* D = res + kSqpCand;
+    const double gd = res[2 * kSqpCand], lmax = res[2 * kSqpCand + 1], dxm = res[2 * kSqpCand + 2],
+                 dum = res[2 * kSqpCand + 3], xm = res[2 * kSqpCand + 4], um = res[2 * kSqpCand + 5];
+    // step length: the first of 1, 1/2, ..., 1/128 with sufficient decrease of
+    // the l1 merit J + nu D (Armijo), else the last; the full step once the
+    // predicted decrease is at rounding level
+    const double nu = fmax(so->nu_min, 2.0 * lmax);
+    const double phi0 = J[0] + nu * D[0], slope = gd - nu * D[0];
+    int a = 1;
+    for (; a < kSqpCand; ++a) {
+      const double al = sqp_alpha(a);
+      if (fabs(slope) <= 1e-12 * fmax(1.0, fabs(phi0)) || J[a] + nu * D[a] <= phi0 + 1e-4 * al * slope) break;
+    }
+    if (a == kSqpCand) a = kSqpCand - 1;
+    const double al = sqp_alpha(a);
+    const double scale = fmax(1.0, fmax(xm, um));
+    if (launch_sqp_update(x, u, dx, du, al, (long long)(T + 1) * n, (long long)T * m, st) != cudaSuccess)
+      return LQR_ERR_CUDA;
+    ++launches;
+    const double step = al * fmax(dxm, dum);
+    if (hist) {
+      double* hr = hist + (size_t)LQR_SQP_HIST * it;
+      hr[0] = al; hr[1] = J[a]; hr[2] = D[a]; hr[3] = J[a] + nu * D[a]; hr[4] = step; hr[5] = nu;
+    }
+    rep->iters = it + 1;
+    rep->cost = J[a];
+    rep->defect = D[a];
+    rep->alpha = al;
+    rep->step = step;
+    if (step <= so->tol * scale && D[a] <= so->tol) {
+      rep->converged = 1;
+      break;
+    }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LQR_ERR_CUDA;
+  h->last_launches = launches;
   return LQR_OK;
 }
 

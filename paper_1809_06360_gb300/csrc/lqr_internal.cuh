@@ -336,6 +336,24 @@ cudaError_t launch_adjoint_grad_batched(const void* jobs, int njobs, int Tmax, c
 size_t stage_policy_smem_bytes(int n, int on_chip);
 cudaError_t launch_stage_policy(const ProbDesc& pd, int nstages, int on_chip, double* scratch, cudaStream_t st);
 
+// the trajectory-optimisation outer loop (sqp.cu): model data on the device
+struct NlModelDev {
+  const double *A, *B, *C, *Q, *R, *QT, *xref, *x0;
+  double beta;
+  int n, m, T;
+};
+constexpr int kSqpCand = 9;                 // candidate step lengths: 0, 1, 1/2, ..., 1/128
+constexpr int kSqpOut = 2 * kSqpCand + 6;   // per stage: J(alpha), D(alpha), g'd, max|lam|, |dx|, |du|, |x|, |u|
+__host__ __device__ inline double sqp_alpha(int a) { return a == 0 ? 0.0 : ldexp(1.0, -(a - 1)); }
+cudaError_t launch_sqp_fill(const NlModelDev& md, double* Bt, double* Qt, double* Rt, cudaStream_t st);
+cudaError_t launch_sqp_linearize(const NlModelDev& md, const double* x, const double* u, double* At, double* c,
+                                 double* q, double* r, double* dx0, cudaStream_t st);
+cudaError_t launch_sqp_merit(const NlModelDev& md, const double* x, const double* u, const double* dx,
+                             const double* du, const double* q, const double* r, const double* lam, double* part,
+                             double* res, cudaStream_t st);
+cudaError_t launch_sqp_update(double* x, double* u, const double* dx, const double* du, double alpha, long long nx,
+                              long long nu, cudaStream_t st);
+
 // least-squares multipliers of the segment problems (ls_mult.cu)
 struct LsArgs {
   const double *A, *B, *Q, *R, *S, *q, *r, *x, *u;

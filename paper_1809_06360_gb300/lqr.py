@@ -32,7 +32,7 @@ EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
            "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
            "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
-           "lqr_global_policy_parallel")
+           "lqr_global_policy_parallel", "lqr_sqp_solve")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -53,6 +53,24 @@ class lqr_opts(ctypes.Structure):
 class lqr_report_t(ctypes.Structure):
     _fields_ = [("status", c_int), ("num_segments", c_int), ("refine_iters", c_int), ("bad_stage", c_int),
                 ("cost", c_double), ("kkt_residual", c_double), ("kkt_rel", c_double)]
+
+
+class lqr_nl_model(ctypes.Structure):
+    _fields_ = [("n", c_int), ("m", c_int), ("T", c_int), ("A", c_void_p), ("B", c_void_p), ("C", c_void_p),
+                ("beta", c_double), ("Q", c_void_p), ("R", c_void_p), ("QT", c_void_p), ("xref", c_void_p),
+                ("x0", c_void_p)]
+
+
+class lqr_sqp_opts(ctypes.Structure):
+    _fields_ = [("max_iters", c_int), ("tol", c_double), ("nu_min", c_double), ("sub", lqr_opts)]
+
+
+class lqr_sqp_report(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("converged", c_int), ("cost", c_double), ("defect", c_double),
+                ("alpha", c_double), ("step", c_double)]
+
+
+SQP_HIST = ("alpha", "cost", "defect", "merit", "step", "nu")
 
 
 class LqrError(RuntimeError):
@@ -98,6 +116,8 @@ def load(path: str | None = None):
     lib.lqr_rcp_newton_check.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
     lib.lqr_segment_policies.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_int, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p]
+    lib.lqr_sqp_solve.argtypes = [c_void_p, P(lqr_nl_model), P(lqr_sqp_opts), c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, P(lqr_sqp_report), P(c_double), c_void_p]
     lib.lqr_global_policy_parallel.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_void_p, c_void_p,
                                                c_void_p, c_void_p, c_void_p]
     lib.lqr_ls_multipliers.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_void_p, c_void_p, c_void_p,
@@ -111,7 +131,7 @@ def load(path: str | None = None):
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
                  "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
                  "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
-           "lqr_global_policy_parallel"):
+           "lqr_global_policy_parallel", "lqr_sqp_solve"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -380,6 +400,35 @@ class Solver:
                                            out["z"].data_ptr(), self._stream(stream) or None),
                "lqr_segment_policies")
         return out
+
+    def sqp_solve(self, model, x, u, max_iters=30, tol=1e-10, nu_min=1.0, num_segments=0, prec="fp64",
+                  max_refine=0, sub_tol=1e-10, stream=None):
+        """Trajectory-optimisation outer loop (lqr_sqp_solve). model: dict of FP64
+        device tensors A, B, C, Q, R, QT, xref, x0 and float beta; x, u: FP64
+        device tensors, updated in place. Returns dict x, u, lam, K, k, report
+        (dict), hist (list of per-iteration dicts)."""
+        torch = _torch()
+        n, m = model["B"].shape
+        T = u.shape[0]
+        dev = x.device
+        lam = torch.empty((T + 1, n), dtype=torch.float64, device=dev)
+        K = torch.empty((T, m, n), dtype=torch.float64, device=dev)
+        k = torch.empty((T, m), dtype=torch.float64, device=dev)
+        md = lqr_nl_model(n=n, m=m, T=T, A=model["A"].data_ptr(), B=model["B"].data_ptr(), C=model["C"].data_ptr(),
+                          beta=float(model["beta"]), Q=model["Q"].data_ptr(), R=model["R"].data_ptr(),
+                          QT=model["QT"].data_ptr(), xref=model["xref"].data_ptr(), x0=model["x0"].data_ptr())
+        sub = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=sub_tol, max_refine=max_refine,
+                       debug_checks=0, form=FORM["multiplier"], residual=0)
+        so = lqr_sqp_opts(max_iters=max_iters, tol=tol, nu_min=nu_min, sub=sub)
+        rep = lqr_sqp_report()
+        hist = (c_double * (len(SQP_HIST) * max_iters))()
+        _check(load().lqr_sqp_solve(self.h, ctypes.byref(md), ctypes.byref(so), x.data_ptr(), u.data_ptr(),
+                                    lam.data_ptr(), K.data_ptr(), k.data_ptr(), ctypes.byref(rep), hist,
+                                    self._stream(stream) or None),
+               "lqr_sqp_solve")
+        report = {f: getattr(rep, f) for f, _ in lqr_sqp_report._fields_}
+        hl = [dict(zip(SQP_HIST, hist[len(SQP_HIST) * i:len(SQP_HIST) * (i + 1)])) for i in range(rep.iters)]
+        return dict(x=x, u=u, lam=lam, K=K, k=k, report=report, hist=hl)
 
     def global_policy_parallel(self, prob, num_segments, want_P=True, stream=None):
         """Per-stage reconstruction of the global policy (lqr_global_policy_parallel):

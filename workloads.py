@@ -146,3 +146,33 @@ def time_invariant(n: int, m: int, T: int, seed: int, cross: bool = True) -> dic
     out["q"] = np.repeat(one["q"][:1], T + 1, axis=0)
     out["x0"] = g.standard_normal(n)
     return {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in out.items()}
+
+
+def make_nl_model(n: int, m: int, T: int, seed: int, beta: float = 0.2) -> dict:
+    """A seeded nonlinear tracking problem for the trajectory-optimisation outer
+    loop (the setting of the paper's Section I, whose subproblems are LQR):
+        x_{t+1} = A x_t + B u_t + beta tanh(C x_t),  x_0 = x_init,
+        cost  sum_t 1/2 (x_t - xref_t)'Q (x_t - xref_t) + 1/2 u_t'R u_t
+              + 1/2 (x_T - xref_T)'Q_T (x_T - xref_T).
+    Time-invariant A (I + 0.1 N(0,1)/sqrt(n), rescaled to rho(A) <= 1),
+    B ~ N(0,1)/sqrt(n), C ~ N(0,1)/sqrt(n); Q = L L'/n + I, Q_T = 10 Q,
+    R = M M'/m + 0.1 I; the reference is a sum of three random sinusoids per
+    state over the horizon (amplitudes 0.1 N(0,1)); x_init ~ N(0, I)."""
+    g = _rng(seed)
+    A = np.eye(n) + 0.1 * g.standard_normal((n, n)) / np.sqrt(n)
+    A = A / max(1.0, np.max(np.abs(np.linalg.eigvals(A))))
+    B = g.standard_normal((n, m)) / np.sqrt(n)
+    C = g.standard_normal((n, n)) / np.sqrt(n)
+    L = g.standard_normal((n, n))
+    Q = L @ L.T / n + np.eye(n)
+    M = g.standard_normal((m, m))
+    R = M @ M.T / m + 0.1 * np.eye(m)
+    t = np.arange(T + 1)[:, None] / max(T, 1)
+    xref = np.zeros((T + 1, n))
+    for _ in range(3):
+        amp = 0.1 * g.standard_normal(n)
+        freq = g.uniform(0.5, 4.0, n)
+        phase = g.uniform(0.0, 2 * np.pi, n)
+        xref += amp * np.sin(2 * np.pi * freq * t + phase)
+    x0 = g.standard_normal(n)
+    return dict(A=A, B=B, C=C, beta=float(beta), Q=Q, R=R, QT=10.0 * Q, xref=xref, x0=x0, T=T)
