@@ -21,6 +21,8 @@
 
 #include <cuda_runtime.h>
 
+#include "lqr_internal.cuh"
+
 namespace lqr {
 
 constexpr int kKktBlock = 256;  // threads per CTA of every kernel calling kkt_stage
@@ -202,12 +204,12 @@ __device__ __forceinline__ void kkt_sym_abs_rows(const TM* M, int d, int ld, dou
 
 // Stage t < T, called by all kKktBlock threads of a CTA (it synchronises the
 // CTA). Folds |rx|, |ru|, |rd|, the |KKT| row sums (KN), |w| and |b| into mx;
-// writes cq = -rx, cr = -ru, cc = rd when cq is given; returns this thread's
+// writes -rx, -ru, rd to out when out.q is given; returns this thread's
 // share of the stage objective x'(Qx/2 + q) + u'(Sx + Ru/2 + r). stash (KN,
 // optional, kkt_stash_doubles): shared memory for the symmetric row sums.
 template <int NC, bool KN, typename TS>
-__device__ double kkt_stage(const KktData<TS>& g, int t, double* sm, KktMax& mx, double* cq, double* cr,
-                            double* cc, double* stash = nullptr) {
+__device__ double kkt_stage(const KktData<TS>& g, int t, double* sm, KktMax& mx, const KktOut& out,
+                            double* stash = nullptr) {
   const int n = g.n, m = g.m;
   const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -307,9 +309,9 @@ __device__ double kkt_stage(const KktData<TS>& g, int t, double* sm, KktMax& mx,
     mx.w = fmax(mx.w, fmax(fabs(x), fabs(lt)));
     mx.b = fmax(mx.b, fmax(fabs(q), fabs(c)));
     if (KN) mx.k = fmax(mx.k, fmax(kx[i] + sxa + 1.0, 1.0 + kd[i]));
-    if (cq) {
-      cq[(size_t)n * t + i] = -rx;
-      cc[(size_t)n * t + i] = rd;
+    if (out.q) {
+      out.put(out.q, (size_t)n * t + i, -rx);
+      out.put(out.c, (size_t)n * t + i, rd);
     }
   }
   for (int a = threadIdx.x; a < m; a += kKktBlock) {
@@ -326,7 +328,7 @@ __device__ double kkt_stage(const KktData<TS>& g, int t, double* sm, KktMax& mx,
     mx.w = fmax(mx.w, fabs(ut[a]));
     mx.b = fmax(mx.b, fabs(r));
     if (KN) mx.k = fmax(mx.k, ku[a] + kr[a] + sua);
-    if (cr) cr[(size_t)m * t + a] = -ru;
+    if (out.q) out.put(out.r, (size_t)m * t + a, -ru);
   }
   __syncthreads();
   return cost;

@@ -501,21 +501,16 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
         ++launches;
       }
     }
+    // |KKT|_inf (data only) once, from the FP32 copy, so that whichever pass finds
+    // the solution converged has the whole backward error
+    if (launch_kkt_norm_f32(tab.single, acc, st) != cudaSuccess) return LQR_ERR_CUDA;
+    ++launches;
+    // the residual passes write the correction problem's vectors in FP32 directly
+    const KktOut cvec{(void*)cp.q, (void*)cp.r, (void*)cp.c, (void*)cp.x0, 1};
     for (int it = 0; it < o->max_refine; ++it) {
-      // the first pass also takes |KKT|_inf, so that the pass that finds the
-      // solution converged has the whole backward error
-      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st,
-                                      it == 0 ? 1 : 0) != cudaSuccess)
-        return LQR_ERR_CUDA;
+      if (launch_kkt_residual<double>(main, acc, cvec, skip, st, 0) != cudaSuccess) return LQR_ERR_CUDA;
       if (launch_residual_finalize(main, acc, o->tol, skip, 0, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
-      ConvTable<double, float> ct;
-      ct.count = 0;
-      ct.add(base + rl.cq, (void*)cp.q, (size_t)(T + 1) * n);
-      ct.add(base + rl.cr, (void*)cp.r, (size_t)T * m);
-      ct.add(base + rl.cc, (void*)cp.c, (size_t)T * n);
-      ct.add(base + rl.cx0, (void*)cp.x0, (size_t)n);
-      if (launch_convert(ct, skip, st) != cudaSuccess) return LQR_ERR_CUDA;
-      launches += 3;
+      launches += 2;
       if (reuse) {
         if (launch_correction(ca, st, &launches) != cudaSuccess) return LQR_ERR_CUDA;
       } else {
@@ -529,8 +524,7 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
       ++launches;
     }
     // final residual and objective, skipped on the device once refinement has converged
-    if (launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, skip, st) != cudaSuccess)
-      return LQR_ERR_CUDA;
+    if (launch_kkt_residual<double>(main, acc, KktOut{}, skip, st) != cudaSuccess) return LQR_ERR_CUDA;
     if (launch_residual_finalize(main, acc, o->tol, skip, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
         cudaSuccess)
       return LQR_ERR_CUDA;
@@ -596,9 +590,8 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
     for (int it = 0; it < o->max_refine; ++it) {
       // the first pass also takes |KKT|_inf, so that the pass that finds the
       // solution converged has the whole backward error
-      if (launch_kkt_residual<double>(main, acc, base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, skip, st,
-                                      it == 0 ? 1 : 0) != cudaSuccess)
-        return LQR_ERR_CUDA;
+      const KktOut out{base + rl.cq, base + rl.cr, base + rl.cc, base + rl.cx0, 0};
+      if (launch_kkt_residual<double>(main, acc, out, skip, st, it == 0 ? 1 : 0) != cudaSuccess) return LQR_ERR_CUDA;
       if (launch_residual_finalize(main, acc, o->tol, skip, 0, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
       launches += 2;
       rs = enqueue_pipeline(h, ctab, sp, o, true, true, store_P, false, false, st, &launches);
@@ -611,8 +604,8 @@ lqr_status run_solve(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, con
     // final residual and objective of the returned solution (in the data's element
     // type), skipped on the device once refinement has converged
     const cudaError_t er = (o->prec == LQR_FP32)
-        ? launch_kkt_residual<float>(main, acc, nullptr, nullptr, nullptr, nullptr, skip, st)
-        : launch_kkt_residual<double>(main, acc, nullptr, nullptr, nullptr, nullptr, skip, st);
+        ? launch_kkt_residual<float>(main, acc, KktOut{}, skip, st)
+        : launch_kkt_residual<double>(main, acc, KktOut{}, skip, st);
     if (er != cudaSuccess) return LQR_ERR_CUDA;
     if (launch_residual_finalize(main, acc, o->tol, skip, 1, (o->max_refine > 0 && o->tol > 0) ? 1 : 0, st) !=
         cudaSuccess)

@@ -368,6 +368,20 @@ size_t ls_mult_smem_bytes(int n, int m, int on_chip);
 long long ls_mult_scratch_doubles(int n, int T, int K);
 cudaError_t launch_ls_mult(const LsArgs& a, cudaStream_t st);
 
+// Destinations of the correction problem's vectors that a residual pass
+// writes (-rx, -ru, rd and x_0 - x0): FP64, or FP32 for the FP32 correction
+// solves of the mixed-precision refinement; q == nullptr: none.
+struct KktOut {
+  void *q, *r, *c, *x0;
+  int f32;
+  __device__ __forceinline__ void put(void* p, size_t i, double v) const {
+    if (f32)
+      static_cast<float*>(p)[i] = static_cast<float>(v);
+    else
+      static_cast<double*>(p)[i] = v;
+  }
+};
+
 // refinement (refine.cu)
 // per-CTA objective partials of the residual pass: at most kMaxResidBlocks CTAs
 constexpr int kMaxResidBlocks = 1024;
@@ -376,8 +390,10 @@ constexpr int kResidAccDoubles = 8 + kMaxResidBlocks;
 // vectors are requested (-1). |KKT|_inf depends on the data alone: a pass that
 // computes it once keeps it in the accumulators until the solve's final pass.
 template <typename TS>
-cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
-                                const int* skip, cudaStream_t st, int knorm = -1);
+cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& out, const int* skip, cudaStream_t st,
+                                int knorm = -1);
+// |KKT|_inf from the FP32 copy of the data (pd: the FP32 problem), once per mixed-precision solve
+cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st);
 cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol, int* skip, int is_final,
                                      int check, cudaStream_t st);
 template <typename TS>

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_noalloc_kernel(NoallocArg
   for (int t = blockIdx.x; t < T; t += gridDim.x) {
     double cost = 0.0;
     if constexpr (NC > 0) {
-      cost = kkt_stage<NC, true>(g, t, reinterpret_cast<double*>(smem), mx, nullptr, nullptr, nullptr);
+      cost = kkt_stage<NC, true>(g, t, reinterpret_cast<double*>(smem), mx, KktOut{});
     } else {
       const TS* At = gA + nn * t;
       const TS* Bt = gB + nm * t;

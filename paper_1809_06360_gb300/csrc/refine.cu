@@ -49,8 +49,8 @@ enum ResidSlot { RS_RNORM = 0, RS_KNORM, RS_WNORM, RS_BNORM, RS_COST, RS_COUNT }
 // want_knorm: also the |KKT| row sums of the backward error (the final pass and
 // the first refinement pass); the other refinement passes only need |r| and |b|.
 template <typename TS>
-__global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, double* acc, double* cq, double* cr,
-                                                              double* cc, double* cx0, const int* skip, int want_knorm) {
+__global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, double* acc, KktOut out, const int* skip,
+                                                              int want_knorm) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (skip && *(volatile const int*)skip) return;
   if (*(volatile int*)pd.status != 0) return;
@@ -183,16 +183,16 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, doubl
       rmax = fmax(rmax, fmax(fabs(rxv[i]), fabs(rdv[i])));
       wmax = fmax(wmax, fmax(fabs(xt[i]), fabs(lt[i])));
       bmax = fmax(bmax, fmax(fabs((double)gq[(size_t)n * t + i]), fabs((double)gc[(size_t)n * t + i])));
-      if (cq) {
-        cq[(size_t)n * t + i] = -rxv[i];
-        cc[(size_t)n * t + i] = rdv[i];
+      if (out.q) {
+        out.put(out.q, (size_t)n * t + i, -rxv[i]);
+        out.put(out.c, (size_t)n * t + i, rdv[i]);
       }
     }
     for (int a = threadIdx.x; a < m; a += blockDim.x) {
       rmax = fmax(rmax, fabs(ruv[a]));
       wmax = fmax(wmax, fabs(ut[a]));
       bmax = fmax(bmax, fabs((double)gr[(size_t)m * t + a]));
-      if (cr) cr[(size_t)m * t + a] = -ruv[a];
+      if (out.q) out.put(out.r, (size_t)m * t + a, -ruv[a]);
     }
     __syncthreads();
   }
@@ -215,9 +215,9 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, doubl
       kmax = fmax(kmax, absQ + 1.0);
       wmax = fmax(wmax, fmax(fabs(xT), fabs((double)gl[(size_t)n * T + i])));
       bmax = fmax(bmax, fmax(fabs((double)gq[(size_t)n * T + i]), fabs((double)gx0[i])));
-      if (cq) {
-        cq[(size_t)n * T + i] = -s;
-        cx0[i] = r0;
+      if (out.q) {
+        out.put(out.q, (size_t)n * T + i, -s);
+        out.put(out.x0, i, r0);
       }
     }
   }
@@ -251,8 +251,7 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, doubl
 // grid-stride over the stages like kkt_residual_kernel.
 template <int NC, bool KN, typename TS>
 __global__ void __launch_bounds__(kKktBlock, 2)
-    kkt_residual_stream_kernel(ProbDesc pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
-                               const int* skip, int use_stash) {
+    kkt_residual_stream_kernel(ProbDesc pd, double* acc, KktOut out, const int* skip, int use_stash) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (skip && *(volatile const int*)skip) return;
   if (*(volatile int*)pd.status != 0) return;
@@ -277,7 +276,7 @@ __global__ void __launch_bounds__(kKktBlock, 2)
   double* stash = use_stash ? sm + kkt_stage_smem_doubles(pd.n, pd.m) : nullptr;
   KktMax mx;
   double cost = 0.0;
-  for (int t = blockIdx.x; t < T; t += gridDim.x) cost += kkt_stage<NC, KN>(g, t, sm, mx, cq, cr, cc, stash);
+  for (int t = blockIdx.x; t < T; t += gridDim.x) cost += kkt_stage<NC, KN>(g, t, sm, mx, out, stash);
   // terminal row (Q_T x_T + q_T + lambda_T) and the initial row (x_0 - x0)
   if (blockIdx.x == 0) {
     const TS* QT = g.Q + (size_t)n * n * T;
@@ -297,9 +296,9 @@ __global__ void __launch_bounds__(kKktBlock, 2)
       if (KN) mx.k = fmax(mx.k, absQ + 1.0);
       mx.w = fmax(mx.w, fmax(fabs(xT), fabs((double)g.lam[(size_t)n * T + i])));
       mx.b = fmax(mx.b, fmax(fabs((double)g.q[(size_t)n * T + i]), fabs((double)gx0[i])));
-      if (cq) {
-        cq[(size_t)n * T + i] = -s;
-        cx0[i] = r0;
+      if (out.q) {
+        out.put(out.q, (size_t)n * T + i, -s);
+        out.put(out.x0, i, r0);
       }
     }
   }
@@ -385,10 +384,10 @@ int residual_grid(int T) {
 }
 
 template <typename TS>
-cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, double* cr, double* cc, double* cx0,
-                                const int* skip, cudaStream_t st, int knorm) {
+cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& out, const int* skip, cudaStream_t st,
+                                int knorm) {
   // by default the refinement passes (correction vectors requested) skip the |KKT| row sums
-  const int want_knorm = knorm >= 0 ? knorm : (cq == nullptr) ? 1 : 0;
+  const int want_knorm = knorm >= 0 ? knorm : (out.q == nullptr) ? 1 : 0;
   const int nc = kkt_stage_cols(pd.n, pd.m);
   if (nc > 0) {
     const size_t base = sizeof(double) * kkt_stage_smem_doubles(pd.n, pd.m);  // <= 45056 B at n = m = 128
@@ -401,7 +400,7 @@ cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, dou
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,              \
                                                   (int)bytes) != cudaSuccess)                                \
       return cudaGetLastError();                                                                             \
-    kkt_residual_stream_kernel<NC, KN, TS><<<g, kKktBlock, bytes, st>>>(pd, acc, cq, cr, cc, cx0, skip, KN); \
+    kkt_residual_stream_kernel<NC, KN, TS><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip, KN);            \
   } while (0)
     if (nc == 1) {
       if (want_knorm) LQR_RES_LAUNCH(1, true); else LQR_RES_LAUNCH(1, false);
@@ -414,7 +413,77 @@ cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, double* cq, dou
     return cudaGetLastError();
   }
   const size_t bytes = sizeof(double) * (6 * (size_t)pd.n + 3 * (size_t)pd.m);
-  kkt_residual_kernel<TS><<<residual_grid(pd.T), kBlock, bytes, st>>>(pd, acc, cq, cr, cc, cx0, skip, want_knorm);
+  kkt_residual_kernel<TS><<<residual_grid(pd.T), kBlock, bytes, st>>>(pd, acc, out, skip, want_knorm);
+  return cudaGetLastError();
+}
+
+// |KKT|_inf of Eq. 3's matrix (the largest absolute row sum, Q and R read
+// symmetrised) from the FP32 copy of the data, into the accumulators of the
+// residual passes: per stage the x rows (|Q_sym| row + |S| column + 1 + |A|
+// column), the u rows (|S| row + |R_sym| row + |B| column) and the dynamics
+// rows (1 + |A| row + |B| row); the terminal rows (|Q_T,sym| row + 1) and the
+// initial-condition rows (1). It depends on the data alone, so the mixed-
+// precision refinement takes it once per solve, in FP32 (it only scales the
+// reported backward error), instead of in an FP64 residual pass.
+__global__ void kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
+  if (*(volatile int*)pd.status != 0) return;
+  const int n = pd.n, m = pd.m, T = pd.T;
+  const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  const float* gA = static_cast<const float*>(pd.A);
+  const float* gB = static_cast<const float*>(pd.B);
+  const float* gQ = static_cast<const float*>(pd.Q);
+  const float* gR = static_cast<const float*>(pd.R);
+  const float* gS = static_cast<const float*>(pd.S);
+  float kmax = 1.0f;  // the initial-condition rows
+  for (int t = blockIdx.x; t < T; t += gridDim.x) {
+    const float* A = gA + nn * t;
+    const float* B = gB + nm * t;
+    const float* Q = gQ + nn * t;
+    const float* R = gR + mm * t;
+    const float* S = gS ? gS + nm * t : nullptr;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      float sx = 1.0f, sd = 1.0f;
+      for (int i = 0; i < n; ++i) {
+        sx += fabsf(A[(size_t)i * n + j]) + fabsf(0.5f * (Q[(size_t)j * n + i] + Q[(size_t)i * n + j]));
+        sd += fabsf(A[(size_t)j * n + i]);
+      }
+      for (int a = 0; a < m; ++a) {
+        if (S) sx += fabsf(S[(size_t)a * n + j]);
+        sd += fabsf(B[(size_t)j * m + a]);
+      }
+      kmax = fmaxf(kmax, fmaxf(sx, sd));
+    }
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+      float su = 0.0f;
+      for (int i = 0; i < n; ++i) {
+        su += fabsf(B[(size_t)i * m + a]);
+        if (S) su += fabsf(S[(size_t)a * n + i]);
+      }
+      for (int b = 0; b < m; ++b) su += fabsf(0.5f * (R[(size_t)a * m + b] + R[(size_t)b * m + a]));
+      kmax = fmaxf(kmax, su);
+    }
+  }
+  if (blockIdx.x == 0) {
+    const float* QT = gQ + nn * T;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      float s = 1.0f;
+      for (int i = 0; i < n; ++i) s += fabsf(0.5f * (QT[(size_t)j * n + i] + QT[(size_t)i * n + j]));
+      kmax = fmaxf(kmax, s);
+    }
+  }
+  double v = warp_max((double)kmax);
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+    atomic_max_nonneg(acc + RS_KNORM, fmax(v, red[0]));
+  }
+}
+
+cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st) {
+  kkt_norm_f32_kernel<<<residual_grid(pd.T), 256, 0, st>>>(pd, acc);
   return cudaGetLastError();
 }
 
@@ -431,10 +500,10 @@ cudaError_t launch_refine_update(const ProbDesc& pd, const double* dk, const dou
   return cudaGetLastError();
 }
 
-template cudaError_t launch_kkt_residual<double>(const ProbDesc&, double*, double*, double*, double*, double*,
-                                                 const int*, cudaStream_t, int);
-template cudaError_t launch_kkt_residual<float>(const ProbDesc&, double*, double*, double*, double*, double*,
-                                                const int*, cudaStream_t, int);
+template cudaError_t launch_kkt_residual<double>(const ProbDesc&, double*, const KktOut&, const int*, cudaStream_t,
+                                                 int);
+template cudaError_t launch_kkt_residual<float>(const ProbDesc&, double*, const KktOut&, const int*, cudaStream_t,
+                                                int);
 template cudaError_t launch_refine_update<double>(const ProbDesc&, const double*, const double*, const double*,
                                                   const double*, const double*, const int*, cudaStream_t);
 template cudaError_t launch_refine_update<float>(const ProbDesc&, const double*, const double*, const double*,

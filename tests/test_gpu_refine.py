@@ -153,26 +153,26 @@ def test_mixed_fp32_correction_paths(solver):
     fit (n=64, m=32: two stage-data slots and the fast sweep; n=72 and n=128:
     the generic FP32 sweep, which also keeps M_uu^-1; n=128 with one slot and
     the closed-loop maps reading B_t, K_t from global memory), corrections
-    reuse the solve's K_t, P_t and M_uu^-1 (residual, finalize, conversion, four
-    segment passes, two link chains, update: 10 kernels each when a chain is
-    one kernel). With K >= 32 segments each link chain runs in two levels
-    over groups of ceil(sqrt(K)) links (group offsets, the chain over the
-    groups, the fill: three kernels), 14 kernels per correction; K = 40 leaves
-    a short last group, K = 49 none. n=136: beyond the link-chain plan of the
-    corrections, so each correction is a whole FP32 solve (residual, finalize,
-    conversion and update around the kernels of a plain FP32 solve of that
-    shape). All reach the oracle at 1e-9."""
-    cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, 10),
-             (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, 10),
-             (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, 10),
-             (workloads.make_problem(64, 32, 400, seed=615, rho_max=1.02), 40, 14),
-             (workloads.make_problem(128, 64, 392, seed=616, rho_max=1.02), 49, 14),
+    reuse the solve's K_t, P_t and M_uu^-1 (residual pass writing the FP32
+    correction vectors, finalize, four segment passes, two link chains,
+    update: 9 kernels each when a chain is one kernel). With K >= 32 segments
+    each link chain runs in two levels over groups of ceil(sqrt(K)) links
+    (group offsets, the chain over the groups, the fill: three kernels), 13
+    kernels per correction; K = 40 leaves a short last group, K = 49 none.
+    n=136: beyond the link-chain plan of the corrections, so each correction is
+    a whole FP32 solve (residual, finalize and update around the kernels of a
+    plain FP32 solve of that shape). All reach the oracle at 1e-9."""
+    cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, 9),
+             (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, 9),
+             (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, 9),
+             (workloads.make_problem(64, 32, 400, seed=615, rho_max=1.02), 40, 13),
+             (workloads.make_problem(128, 64, 392, seed=616, rho_max=1.02), 49, 13),
              (workloads.make_problem(136, 8, 160, seed=614, rho_max=1.02), 4, None)]
     for prob, K, expect in cases:
         per = _launches_per_correction(solver, prob, K)
         solver.solve(to_dev(prob, torch.float32), num_segments=K, prec="fp32")
         plain = solver.last_launch_count()
-        assert per == (expect if expect is not None else 4 + plain), (prob["B"].shape, per, plain)
+        assert per == (expect if expect is not None else 3 + plain), (prob["B"].shape, per, plain)
         ref = oracle.riccati(prob)
         out = host(solver.solve(to_dev(prob), num_segments=K, prec="mixed_fp32", max_refine=8, tol=1e-11))
         rep = solver.report()
