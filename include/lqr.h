@@ -365,6 +365,20 @@ lqr_status lqr_sqp_solve(lqr_handle *h, const lqr_nl_model *model, const lqr_sqp
 lqr_status lqr_global_policy_parallel(lqr_handle *h, const lqr_problem *prob, const lqr_opts *opts, void *K,
                                       void *k, void *P, void *p, void *stream);
 
+/* The residual of the KKT system of Eq. 3 at (x, u, lambda), as the right-hand
+ * side of the correction solve of iterative refinement (Section II-C): with
+ * rx_t = Q_t x_t + S_t'u_t + q_t + lambda_t - A_t'lambda_{t+1},
+ * rx_T = Q_T x_T + q_T + lambda_T, ru_t = S_t x_t + R_t u_t + r_t - B_t'lambda_{t+1},
+ * rd_t = x_{t+1} - A_t x_t - B_t u_t - c_t, r0 = x_0 - x0 (Q, R read
+ * symmetrised), writes q~ = -rx [T+1][n], r~ = -ru [T][m], c~ = rd [T][n] and
+ * x0~ = r0 [n] (DEVICE FP64, caller-allocated). FP64 data and solution; the
+ * products run in double-FP32 arithmetic (each FP64 value split into an FP32
+ * pair, compensated accumulation: about 47 significant bits), the kernel of the
+ * mixed-precision refinement's early passes. n, m <= 128 (else
+ * LQR_ERR_UNSUPPORTED). Asynchronous on `stream`. */
+lqr_status lqr_kkt_residual_vectors(lqr_handle *h, const lqr_problem *prob, const lqr_solution *sol, double *q_out,
+                                    double *r_out, double *c_out, double *x0_out, void *stream);
+
 /* The multipliers of every segment problem from the least-squares system of
  * Section II-B ("Lagrange Multipliers"), at the trajectory (x, u) (the optimum
  * lqr_solve returns, or any other): a check on the multipliers of Eq. 3 that

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 
+#include "kkt_stage.cuh"
 #include "lqr_internal.cuh"
 
 using namespace lqr;
@@ -503,12 +504,17 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
     }
     // |KKT|_inf (data only) once, from the FP32 copy, so that whichever pass finds
     // the solution converged has the whole backward error
-    if (launch_kkt_norm_f32(tab.single, acc, st) != cudaSuccess) return LQR_ERR_CUDA;
-    ++launches;
+    if (o->max_refine > 0) {
+      if (launch_kkt_norm_f32(tab.single, acc, st) != cudaSuccess) return LQR_ERR_CUDA;
+      ++launches;
+    }
     // the residual passes write the correction problem's vectors in FP32 directly
     const KktOut cvec{(void*)cp.q, (void*)cp.r, (void*)cp.c, (void*)cp.x0, 1};
     for (int it = 0; it < o->max_refine; ++it) {
-      if (launch_kkt_residual<double>(main, acc, cvec, skip, st, 0) != cudaSuccess) return LQR_ERR_CUDA;
+      // the first pass (the residual of the FP32 solve, some 2^-24 of |KKT| |w|)
+      // in double-FP32 arithmetic (~2^-47 of it), the later ones in FP64
+      if (launch_kkt_residual<double>(main, acc, cvec, skip, st, 0, it == 0 ? 1 : 0) != cudaSuccess)
+        return LQR_ERR_CUDA;
       if (launch_residual_finalize(main, acc, o->tol, skip, 0, 0, st) != cudaSuccess) return LQR_ERR_CUDA;
       launches += 2;
       if (reuse) {
@@ -1368,6 +1374,36 @@ lqr_status lqr_global_policy_parallel(lqr_handle* h, const lqr_problem* p, const
   if (h->prof_on && h->prof_count < lqr_handle::kMaxProfiled) ++h->prof_count;
   h->last_K = K;
   h->last_launches = launches;
+  h->last_resid = 0;
+  return LQR_OK;
+}
+
+lqr_status lqr_kkt_residual_vectors(lqr_handle* h, const lqr_problem* p, const lqr_solution* s, double* qt,
+                                    double* rt, double* ct, double* x0t, void* stream) {
+  if (!h || !p || !s || !qt || !rt || !ct || !x0t) return LQR_ERR_INVALID_ARG;
+  if (!s->x || !s->u || !s->lam) return LQR_ERR_INVALID_ARG;
+  lqr_opts o;
+  memset(&o, 0, sizeof(o));
+  o.prec = LQR_FP64;
+  lqr_solution none;
+  memset(&none, 0, sizeof(none));
+  lqr_status v = validate(p, &o, &none);
+  if (v != LQR_OK) return v;
+  if (kkt_stage_cols(p->n, p->m) == 0) return LQR_ERR_UNSUPPORTED;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lqr_status rs = grow(&h->ws, &h->ws_bytes, sizeof(double) * kResidAccDoubles);
+  if (rs != LQR_OK) return rs;
+  double* acc = reinterpret_cast<double*>(h->ws);
+  SolvePlan sp;
+  memset(&sp, 0, sizeof(sp));
+  sp.K = 1;
+  ProbDesc d = make_desc(h, p, s, sp, (int)LQR_FORM_MULTIPLIER);
+  if (cudaMemsetAsync(h->d_status, 0, 2 * sizeof(int), st) != cudaSuccess) return LQR_ERR_CUDA;
+  if (cudaMemsetAsync(acc, 0, sizeof(double) * kResidAccDoubles, st) != cudaSuccess) return LQR_ERR_CUDA;
+  const KktOut out{qt, rt, ct, x0t, 0};
+  if (launch_kkt_residual<double>(d, acc, out, nullptr, st, 0, 1) != cudaSuccess) return LQR_ERR_CUDA;
+  h->last_launches = 1;
   h->last_resid = 0;
   return LQR_OK;
 }

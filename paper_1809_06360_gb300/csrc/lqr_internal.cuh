@@ -389,9 +389,11 @@ constexpr int kResidAccDoubles = 8 + kMaxResidBlocks;
 // knorm: also accumulate |KKT|_inf (1), not (0), or only when no correction
 // vectors are requested (-1). |KKT|_inf depends on the data alone: a pass that
 // computes it once keeps it in the accumulators until the solve's final pass.
+// df: 1 the double-FP32 kernel where it applies (FP64 data, correction vectors
+// requested, no |KKT| row sums, n, m <= 128), else the FP64 one.
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& out, const int* skip, cudaStream_t st,
-                                int knorm = -1);
+                                int knorm = -1, int df = 0);
 // |KKT|_inf from the FP32 copy of the data (pd: the FP32 problem), once per mixed-precision solve
 cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st);
 cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol, int* skip, int is_final,

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "kkt_stage.cuh"
+#include "kkt_stage_df.cuh"
 #include "lqr_internal.cuh"
 
 namespace lqr {
@@ -323,6 +324,77 @@ __global__ void __launch_bounds__(kKktBlock, 2)
   }
 }
 
+// The refinement pass for FP64 data in double-FP32 arithmetic (kkt_stage_df):
+// the stages as in kkt_residual_stream_kernel, without the |KKT| row sums; the
+// terminal and initial rows (O(n^2) once) in FP64.
+template <int NC>
+__global__ void __launch_bounds__(kKktBlock, NC >= 4 ? 3 : 4)  // 80 / 64 registers, no spills
+    kkt_residual_df_kernel(ProbDesc pd, double* acc, KktOut out, const int* skip) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (skip && *(volatile const int*)skip) return;
+  if (*(volatile int*)pd.status != 0) return;
+  const int n = pd.n, T = pd.T;
+  KktData<double> g;
+  g.x = static_cast<const double*>(pd.x);
+  g.u = static_cast<const double*>(pd.u);
+  g.lam = static_cast<const double*>(pd.lam);
+  g.A = static_cast<const double*>(pd.A);
+  g.B = static_cast<const double*>(pd.B);
+  g.c = static_cast<const double*>(pd.c);
+  g.Q = static_cast<const double*>(pd.Q);
+  g.R = static_cast<const double*>(pd.R);
+  g.S = static_cast<const double*>(pd.S);
+  g.q = static_cast<const double*>(pd.q);
+  g.r = static_cast<const double*>(pd.r);
+  g.n = pd.n;
+  g.m = pd.m;
+  const double* gx0 = static_cast<const double*>(pd.x0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* sm = reinterpret_cast<double*>(smem);
+  KktMax mx;
+  double cost = 0.0;
+  for (int t = blockIdx.x; t < T; t += gridDim.x) cost += kkt_stage_df<NC>(g, t, sm, mx, out);
+  if (blockIdx.x == 0) {
+    const double* QT = g.Q + (size_t)n * n * T;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double s = g.q[(size_t)n * T + i] + g.lam[(size_t)n * T + i];
+      double qx = 0.0;
+      for (int k = 0; k < n; ++k) {
+        s = fma(0.5 * (QT[(size_t)i * n + k] + QT[(size_t)k * n + i]), g.x[(size_t)n * T + k], s);
+        qx = fma(QT[(size_t)i * n + k], g.x[(size_t)n * T + k], qx);
+      }
+      const double xT = g.x[(size_t)n * T + i];
+      cost += xT * (0.5 * qx + g.q[(size_t)n * T + i]);
+      const double r0 = g.x[i] - gx0[i];
+      mx.r = fmax(mx.r, fmax(fabs(s), fabs(r0)));
+      mx.w = fmax(mx.w, fmax(fabs(xT), fabs(g.lam[(size_t)n * T + i])));
+      mx.b = fmax(mx.b, fmax(fabs(g.q[(size_t)n * T + i]), fabs(gx0[i])));
+      if (out.q) {
+        out.put(out.q, (size_t)n * T + i, -s);
+        out.put(out.x0, i, r0);
+      }
+    }
+  }
+  __shared__ double red[4][kKktWarps];
+  const double rm = warp_max(mx.r), wm = warp_max(mx.w), bm = warp_max(mx.b);
+  cost = warp_sum(cost);
+  if (lane == 0) {
+    red[0][warp] = rm; red[1][warp] = wm; red[2][warp] = bm; red[3][warp] = cost;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a[4] = {0, 0, 0, 0};
+    for (int w = 0; w < kKktWarps; ++w) {
+      for (int k = 0; k < 3; ++k) a[k] = fmax(a[k], red[k][w]);
+      a[3] += red[3][w];
+    }
+    atomic_max_nonneg(acc + RS_RNORM, a[0]);
+    atomic_max_nonneg(acc + RS_WNORM, a[1]);
+    atomic_max_nonneg(acc + RS_BNORM, a[2]);
+    acc[RS_COUNT + blockIdx.x] = a[3];
+  }
+}
+
 // Turns the accumulators into eta, rel and the cost; decides convergence.
 // report: [0] cost, [1] eta, [2] rel, [3] refinement iterations applied.
 __global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, double tol, int* skip,
@@ -385,10 +457,21 @@ int residual_grid(int T) {
 
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& out, const int* skip, cudaStream_t st,
-                                int knorm) {
+                                int knorm, int df) {
   // by default the refinement passes (correction vectors requested) skip the |KKT| row sums
   const int want_knorm = knorm >= 0 ? knorm : (out.q == nullptr) ? 1 : 0;
   const int nc = kkt_stage_cols(pd.n, pd.m);
+  if (df && nc > 0 && sizeof(TS) == 8 && !want_knorm && out.q) {
+    const size_t bytes = sizeof(double) * kkt_stage_df_smem_doubles(pd.n, pd.m);
+    const int g = residual_grid(pd.T);
+    if (nc == 1)
+      kkt_residual_df_kernel<1><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip);
+    else if (nc == 2)
+      kkt_residual_df_kernel<2><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip);
+    else
+      kkt_residual_df_kernel<4><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip);
+    return cudaGetLastError();
+  }
   if (nc > 0) {
     const size_t base = sizeof(double) * kkt_stage_smem_doubles(pd.n, pd.m);  // <= 45056 B at n = m = 128
     // the |KKT| pass stages Q_t and R_t in shared memory for their symmetric row sums
@@ -426,64 +509,89 @@ cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& o
 // precision refinement takes it once per solve, in FP32 (it only scales the
 // reported backward error), instead of in an FP64 residual pass.
 __global__ void kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
+  extern __shared__ __align__(16) float nsm[];
   if (*(volatile int*)pd.status != 0) return;
   const int n = pd.n, m = pd.m, T = pd.T;
+  const int d = n > m ? n : m, ld = d + 1;
   const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
   const float* gA = static_cast<const float*>(pd.A);
   const float* gB = static_cast<const float*>(pd.B);
   const float* gQ = static_cast<const float*>(pd.Q);
   const float* gR = static_cast<const float*>(pd.R);
   const float* gS = static_cast<const float*>(pd.S);
-  float kmax = 1.0f;  // the initial-condition rows
-  for (int t = blockIdx.x; t < T; t += gridDim.x) {
-    const float* A = gA + nn * t;
-    const float* B = gB + nm * t;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float* tile = nsm;            // a symmetric block, row stride d + 1
+  float* xr = tile + d * ld;    // x rows
+  float* dr = xr + n;           // dynamics rows
+  float* ur = dr + n;           // u rows
+  float kmax = 1.0f;            // the initial-condition rows
+  // row sums of |(M + M')/2| of the dd x dd block in the tile, added to out[i] (one writer per row)
+  auto sym_rows = [&](int dd, float* out) {
+    for (int i = warp; i < dd; i += nw) {
+      float s = 0.0f;
+      for (int k = lane; k < dd; k += 32) s += fabsf(0.5f * (tile[i * ld + k] + tile[k * ld + i]));
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) out[i] += s;
+    }
+  };
+  // |M| of a row-major R x C block: row sums into rows[], column sums into cols[]
+  // (rows to warps, columns to lanes: coalesced; shared-memory atomics)
+  auto abs_rows_cols = [&](const float* M, int R, int C, float* rows, float* cols) {
+    for (int i = warp; i < R; i += nw) {
+      float s = 0.0f;
+      for (int k = lane; k < C; k += 32) {
+        const float v = fabsf(M[(size_t)i * C + k]);
+        s += v;
+        atomicAdd(&cols[k], v);
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) atomicAdd(&rows[i], s);
+    }
+  };
+  for (int t = blockIdx.x; t <= T; t += gridDim.x) {
+    const bool term = (t == T);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      xr[i] = 1.0f;
+      dr[i] = 1.0f;
+    }
+    for (int a = threadIdx.x; a < m; a += blockDim.x) ur[a] = 0.0f;
     const float* Q = gQ + nn * t;
-    const float* R = gR + mm * t;
-    const float* S = gS ? gS + nm * t : nullptr;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      float sx = 1.0f, sd = 1.0f;
-      for (int i = 0; i < n; ++i) {
-        sx += fabsf(A[(size_t)i * n + j]) + fabsf(0.5f * (Q[(size_t)j * n + i] + Q[(size_t)i * n + j]));
-        sd += fabsf(A[(size_t)j * n + i]);
-      }
-      for (int a = 0; a < m; ++a) {
-        if (S) sx += fabsf(S[(size_t)a * n + j]);
-        sd += fabsf(B[(size_t)j * m + a]);
-      }
-      kmax = fmaxf(kmax, fmaxf(sx, sd));
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) tile[(e / n) * ld + e % n] = Q[e];
+    __syncthreads();
+    sym_rows(n, xr);  // x rows: |Q_sym| (the terminal rows: |Q_T,sym| + 1)
+    __syncthreads();
+    if (!term) {
+      abs_rows_cols(gA + nn * t, n, n, dr, xr);          // |A| rows (dynamics), columns (x rows)
+      abs_rows_cols(gB + nm * t, n, m, dr, ur);          // |B| rows (dynamics), columns (u rows)
+      if (gS) abs_rows_cols(gS + nm * t, m, n, ur, xr);  // |S| rows (u rows), columns (x rows)
+      const float* R = gR + mm * t;
+      for (int e = threadIdx.x; e < m * m; e += blockDim.x) tile[(e / m) * ld + e % m] = R[e];
+      __syncthreads();
+      sym_rows(m, ur);  // u rows: |R_sym|
+      __syncthreads();
     }
-    for (int a = threadIdx.x; a < m; a += blockDim.x) {
-      float su = 0.0f;
-      for (int i = 0; i < n; ++i) {
-        su += fabsf(B[(size_t)i * m + a]);
-        if (S) su += fabsf(S[(size_t)a * n + i]);
-      }
-      for (int b = 0; b < m; ++b) su += fabsf(0.5f * (R[(size_t)a * m + b] + R[(size_t)b * m + a]));
-      kmax = fmaxf(kmax, su);
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) kmax = fmaxf(kmax, term ? xr[i] : fmaxf(xr[i], dr[i]));
+    if (!term)
+      for (int a = threadIdx.x; a < m; a += blockDim.x) kmax = fmaxf(kmax, ur[a]);
+    __syncthreads();
   }
-  if (blockIdx.x == 0) {
-    const float* QT = gQ + nn * T;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      float s = 1.0f;
-      for (int i = 0; i < n; ++i) s += fabsf(0.5f * (QT[(size_t)j * n + i] + QT[(size_t)i * n + j]));
-      kmax = fmaxf(kmax, s);
-    }
-  }
-  double v = warp_max((double)kmax);
   __shared__ double red[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double v = warp_max((double)kmax);
   if (lane == 0) red[warp] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
-    atomic_max_nonneg(acc + RS_KNORM, fmax(v, red[0]));
+    double b = red[0];
+    for (int w = 1; w < nw; ++w) b = fmax(b, red[w]);
+    atomic_max_nonneg(acc + RS_KNORM, b);
   }
 }
 
 cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st) {
-  kkt_norm_f32_kernel<<<residual_grid(pd.T), 256, 0, st>>>(pd, acc);
+  const int d = pd.n > pd.m ? pd.n : pd.m;
+  const size_t bytes = sizeof(float) * ((size_t)d * (d + 1) + 2 * (size_t)pd.n + pd.m);
+  cudaError_t e = raise_dyn_smem((const void*)kkt_norm_f32_kernel, bytes);
+  if (e != cudaSuccess) return e;
+  kkt_norm_f32_kernel<<<residual_grid(pd.T + 1), 256, bytes, st>>>(pd, acc);
   return cudaGetLastError();
 }
 
@@ -501,9 +609,9 @@ cudaError_t launch_refine_update(const ProbDesc& pd, const double* dk, const dou
 }
 
 template cudaError_t launch_kkt_residual<double>(const ProbDesc&, double*, const KktOut&, const int*, cudaStream_t,
-                                                 int);
+                                                 int, int);
 template cudaError_t launch_kkt_residual<float>(const ProbDesc&, double*, const KktOut&, const int*, cudaStream_t,
-                                                int);
+                                                int, int);
 template cudaError_t launch_refine_update<double>(const ProbDesc&, const double*, const double*, const double*,
                                                   const double*, const double*, const int*, cudaStream_t);
 template cudaError_t launch_refine_update<float>(const ProbDesc&, const double*, const double*, const double*,

@@ -32,7 +32,7 @@ EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
            "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
            "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
-           "lqr_global_policy_parallel", "lqr_sqp_solve")
+           "lqr_global_policy_parallel", "lqr_sqp_solve", "lqr_kkt_residual_vectors")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
     lib.lqr_rcp_newton_check.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
     lib.lqr_segment_policies.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_int, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p]
+    lib.lqr_kkt_residual_vectors.argtypes = [c_void_p, P(lqr_problem), P(lqr_solution), c_void_p, c_void_p,
+                                             c_void_p, c_void_p, c_void_p]
     lib.lqr_sqp_solve.argtypes = [c_void_p, P(lqr_nl_model), P(lqr_sqp_opts), c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, P(lqr_sqp_report), P(c_double), c_void_p]
     lib.lqr_global_policy_parallel.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_void_p, c_void_p,
@@ -131,7 +133,7 @@ def load(path: str | None = None):
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
                  "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
                  "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
-           "lqr_global_policy_parallel", "lqr_sqp_solve"):
+                 "lqr_global_policy_parallel", "lqr_sqp_solve", "lqr_kkt_residual_vectors"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -399,6 +401,24 @@ class Solver:
                                            out["Kx"].data_ptr(), out["Kz"].data_ptr(), out["k1"].data_ptr(),
                                            out["z"].data_ptr(), self._stream(stream) or None),
                "lqr_segment_policies")
+        return out
+
+    def kkt_residual_vectors(self, prob, sol, stream=None):
+        """The correction solve's right-hand side at sol (lqr_kkt_residual_vectors):
+        dict q = -rx ((T+1) x n), r = -ru, c = rd, x0 = r0 (FP64 device tensors)."""
+        torch = _torch()
+        n, m, T = self._dims(prob)
+        dev = prob["A"].device
+        out = dict(q=torch.empty((T + 1, n), dtype=torch.float64, device=dev),
+                   r=torch.empty((T, m), dtype=torch.float64, device=dev),
+                   c=torch.empty((T, n), dtype=torch.float64, device=dev),
+                   x0=torch.empty((n,), dtype=torch.float64, device=dev))
+        p = self.make_problem_struct(prob, lambda t: t.data_ptr())
+        s = lqr_solution(**{f: (sol[f].data_ptr() if f in sol else None) for f in SOLUTION_FIELDS})
+        _check(load().lqr_kkt_residual_vectors(self.h, ctypes.byref(p), ctypes.byref(s), out["q"].data_ptr(),
+                                               out["r"].data_ptr(), out["c"].data_ptr(), out["x0"].data_ptr(),
+                                               self._stream(stream) or None),
+               "lqr_kkt_residual_vectors")
         return out
 
     def sqp_solve(self, model, x, u, max_iters=30, tol=1e-10, nu_min=1.0, num_segments=0, prec="fp64",

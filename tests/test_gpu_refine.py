@@ -155,13 +155,15 @@ def test_mixed_fp32_correction_paths(solver):
     the closed-loop maps reading B_t, K_t from global memory), corrections
     reuse the solve's K_t, P_t and M_uu^-1 (residual pass writing the FP32
     correction vectors, finalize, four segment passes, two link chains,
-    update: 9 kernels each when a chain is one kernel). With K >= 32 segments
-    each link chain runs in two levels over groups of ceil(sqrt(K)) links
-    (group offsets, the chain over the groups, the fill: three kernels), 13
-    kernels per correction; K = 40 leaves a short last group, K = 49 none.
-    n=136: beyond the link-chain plan of the corrections, so each correction is
-    a whole FP32 solve (residual, finalize and update around the kernels of a
-    plain FP32 solve of that shape). All reach the oracle at 1e-9."""
+    update: 9 kernels each when a chain is one kernel; the counted correction
+    is the second, whose residual pass runs in FP64, the first one's in
+    double-FP32). With K >= 32 segments each link chain runs in two levels
+    over groups of ceil(sqrt(K)) links (group offsets, the chain over the
+    groups, the fill: three kernels), 13 kernels per correction; K = 40 leaves
+    a short last group, K = 49 none. n=136: beyond the link-chain plan of the
+    corrections, so each correction is a whole FP32 solve (residual, finalize
+    and update around the kernels of a plain FP32 solve of that shape). All
+    reach the oracle at 1e-9."""
     cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, 9),
              (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, 9),
              (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, 9),

@@ -82,3 +82,33 @@ def test_residual_at_perturbed_point_matches_oracle(solver, n, m, T, cross, prec
     assert abs(eta - ref["eta"]) <= 1e-12 * ref["eta"], (eta, ref["eta"])
     assert abs(rel - ref["rel"]) <= 1e-12 * ref["rel"], (rel, ref["rel"])
     assert abs(cost - ref_cost) <= 1e-12 * max(abs(ref_cost), 1.0), (cost, ref_cost)
+
+
+@pytest.mark.parametrize("n,m,T,cross,perturb", [
+    (7, 3, 61, True, True), (30, 10, 700, False, True), (64, 32, 1300, True, True), (128, 64, 300, True, True),
+    (5, 9, 40, True, True), (33, 33, 20, False, True), (4, 2, 1, True, True), (64, 32, 512, True, False)])
+def test_residual_vectors_double_fp32(solver, n, m, T, cross, perturb):
+    """The residual blocks of Eq. 3 from the double-FP32 kernel of the refinement
+    (lqr_kkt_residual_vectors) against the oracle's FP64 blocks, element by
+    element, at points 1e-3 off the optimum and at the optimum itself: within
+    2e-13 of |KKT| |w| + |b| (the scale the backward error divides by; the
+    pairs keep about 47 bits, FP64 53)."""
+    prob = workloads.make_problem(n, m, T, seed=950 + n + m + T, cross=cross)
+    if not cross:
+        prob["S"] = np.zeros_like(prob["S"])
+    sol = _perturbed(prob, seed=n + 3 * T, prec="fp64") if perturb else {
+        k: v for k, v in oracle.riccati(prob).items() if k in ("x", "u", "lam")}
+    dev = {k: torch.from_numpy(v).to("cuda:0", torch.float64) for k, v in prob.items()}
+    if not cross:
+        dev["S"] = None
+    dsol = {k: torch.from_numpy(np.ascontiguousarray(v)).to("cuda:0", torch.float64) for k, v in sol.items()}
+    got = {k: v.cpu().numpy() for k, v in solver.kkt_residual_vectors(
+        {k: v for k, v in dev.items() if v is not None}, dsol).items()}
+    ref = oracle.kkt_blocks_residual(prob, sol["x"], sol["u"], sol["lam"])
+    nrm = oracle.kkt_residual(prob, sol["x"], sol["u"], sol["lam"])
+    scale = nrm["knorm"] * nrm["wnorm"] + nrm["bnorm"]
+    err = max(np.abs(got["q"][:T] + ref["rx"]).max(), np.abs(got["q"][T] + ref["rxT"]).max(),
+              np.abs(got["r"] + ref["ru"]).max(), np.abs(got["c"] - ref["rd"]).max(),
+              np.abs(got["x0"] - ref["r0"]).max())
+    print("n=%d m=%d T=%d residual %.2e error %.2e of scale %.2e" % (n, m, T, nrm["rnorm"], err, scale))
+    assert err <= 2e-13 * scale, (err, scale)
