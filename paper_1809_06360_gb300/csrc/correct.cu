@@ -47,10 +47,7 @@ __device__ __forceinline__ bool corr_exit(const CorrArgs& a, int* s_flag) {
 
 // rows x cols floats (row stride cols) into shared memory with row stride ldd
 __device__ __forceinline__ void copy_pad(float* dst, int ldd, const float* src, int rows, int cols) {
-  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-    const int i = e / cols, j = e - i * cols;
-    cp_async4(dst + i * ldd + j, src + e);
-  }
+  cta_for_rc(rows, cols, [&](int e, int i, int j) { cp_async4(dst + i * ldd + j, src + e); });
 }
 __device__ __forceinline__ void copy_vec(float* dst, const float* src, int cnt) {
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) cp_async4(dst + e, src + e);

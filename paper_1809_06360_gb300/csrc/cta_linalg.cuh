@@ -452,6 +452,27 @@ __device__ inline void cta_householder_apply(int nr, int p, const double* V, int
   }
 }
 
+// Calls f(e, i, j) for e = threadIdx.x, threadIdx.x + blockDim.x, ... < rows *
+// cols with (i, j) = (e / cols, e % cols): each thread steps its (i, j) by the
+// block's quotient and remainder, one division per call instead of one per
+// element (an integer division costs tens of instructions, a 64-bit one about a
+// hundred).
+template <typename F>
+__device__ __forceinline__ void cta_for_rc(int rows, int cols, F f) {
+  const int total = rows * cols, step = blockDim.x;
+  const int dq = step / cols, dr = step - dq * cols;
+  int i = threadIdx.x / cols, j = threadIdx.x - i * cols;
+  for (int e = threadIdx.x; e < total; e += step) {
+    f(e, i, j);
+    i += dq;
+    j += dr;
+    if (j >= cols) {
+      j -= cols;
+      ++i;
+    }
+  }
+}
+
 // --- asynchronous global -> shared copies (cp.async, sm_80+) ----------------
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));

@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(kScanBlock, 1) link_scan_kernel(ProbTable tab,
   __syncthreads();
   const double* Pfin = ws + wl.Pi + (long long)b * nn;
   const double* pfin = ws + wl.pi + (long long)b * n;
-  for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-    const int i = (int)(e / n), k = (int)(e - (long long)i * n);
+  for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) {
+    const int i = e / n, k = e - i * n;
     Cb[i * ldn + k] = bfin ? static_cast<float>(Pfin[e]) : eb[e];
     Za[i * ld1 + k] = ea[nn + e];
     Wa[i * ldn + k] = ea[2 * nn + e];
@@ -299,18 +299,12 @@ __global__ void __launch_bounds__(kBlock) link_scan_forward_kernel(ProbTable tab
     if (j < K - 1) {
       const float* src = sbase + (long long)j * es + nn;
       float* dst = Gr + (long long)(j % kFwdDepth) * n4 * ldg;
-      if (rows16) {
-        const int per = n / 4;
-        for (int e = threadIdx.x; e < n * per; e += blockDim.x) {
-          const int i = e / per, c = e - i * per;
+      if (rows16)
+        cta_for_rc(n, n / 4, [&](int, int i, int c) {
           cp_async16(dst + (long long)i * ldg + 4 * c, src + (long long)i * n + 4 * c);
-        }
-      } else {
-        for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-          const int i = (int)(e / n), k = (int)(e - (long long)i * n);
-          cp_async4(dst + (long long)i * ldg + k, src + e);
-        }
-      }
+        });
+      else
+        cta_for_rc(n, n, [&](int e, int i, int k) { cp_async4(dst + (long long)i * ldg + k, src + e); });
       const double* gs = pd.ws + wl.gam + (long long)j * n;
       double* gdst = gr + (j % kFwdDepth) * n4;
       for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async8(gdst + i, gs + i);

@@ -383,16 +383,16 @@ __device__ __forceinline__ void seg_sweep_f32_unit(const ProbTable& tab, int uni
     } else {
       // policy K_t = -H_x, k_t = -h
       if (gK)
-        for (long long e = threadIdx.x; e < nm; e += blockDim.x) {
-          const int a = (int)(e / n), j = (int)(e - (long long)a * n);
+        for (int e = threadIdx.x; e < (int)nm; e += blockDim.x) {
+          const int a = e / n, j = e - a * n;
           gK[nm * t + e] = -H[a * ldF + j];
         }
       if (gk)
         for (int a = threadIdx.x; a < m; a += blockDim.x) gk[(long long)m * t + a] = -H[a * ldF + 2 * N];
       if (pd.Minv) {  // M_uu^-1, kept for refinement corrections that reuse the factorisation
         float* gM = static_cast<float*>(pd.Minv) + mm * t;
-        for (long long e = threadIdx.x; e < mm; e += blockDim.x) {
-          const int a = (int)(e / m), b = (int)(e - (long long)a * m);
+        for (int e = threadIdx.x; e < (int)mm; e += blockDim.x) {
+          const int a = e / m, b = e - a * m;
           gM[e] = Muu[a * LM + b];
         }
       }
@@ -409,7 +409,10 @@ __device__ __forceinline__ void seg_sweep_f32_unit(const ProbTable& tab, int uni
     }
     if (store_P && gP && !param) {
       __syncthreads();
-      for (long long e = threadIdx.x; e < nn; e += blockDim.x) gP[nn * t + e] = V[(e / n) * LV + (e % n)];
+      for (int e = threadIdx.x; e < (int)nn; e += blockDim.x) {
+        const int i = e / n;
+        gP[nn * t + e] = V[i * LV + (e - i * n)];
+      }
       for (int i = threadIdx.x; i < n; i += blockDim.x) gp[(long long)n * t + i] = vx[i];
     }
   }
