@@ -90,6 +90,21 @@ struct lqr_handle {
   size_t f32_bytes = 0;
   unsigned char* nl = nullptr;  // the outer loop's subproblem data and merit partials
   size_t nl_bytes = 0;
+  // the refinement loop of the mixed modes as a CUDA graph: a WHILE node around
+  // one iteration, the condition set by the iteration's finalize kernel, so
+  // that the iterations after convergence are not launched at all. Rebuilt when
+  // the arguments of its kernels change (key); plain launches if a graph call fails.
+  static constexpr int kRKeyBytes = 1024;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t rgraph = nullptr;
+  cudaGraphExec_t rexec = nullptr;
+  unsigned char rkey[kRKeyBytes];
+  int rkey_valid = 0;
+  int rbody = 0;                  // kernels of the loop body
+  int rgraph_broken = 0;
+  // launches of the last solve that ran the graph: last_launches + rbody * *last_iters
+  const int* last_iters = nullptr;
+  cudaStream_t last_stream = nullptr;
   // batch-schedule autotuner: per batch-shape bucket, 1 = the persistent
   // one-segment schedule was measured faster than the per-step launches
   struct TuneEntry { int key[4]; int persistent; float ms[2]; };
@@ -258,6 +273,95 @@ ProbDesc make_desc(lqr_handle* h, const lqr_problem* p, const lqr_solution* s, c
 void prof_mark(lqr_handle* h, int k, cudaStream_t st) {
   if (!h->prof_on || h->prof_count >= lqr_handle::kMaxProfiled) return;
   cudaEventRecord(h->ev[h->prof_count][k], st);
+}
+
+// The arguments of the kernels of one refinement iteration (the key of the
+// cached graph: compared byte by byte, so built from a zeroed struct).
+struct RefineGraphArgs {
+  ProbDesc main;
+  CorrArgs ca;
+  KktOut cvec;
+  double* acc;
+  int* skip;
+  float* dp;
+  double tol;
+  int max_refine;
+};
+static_assert(sizeof(RefineGraphArgs) <= lqr_handle::kRKeyBytes, "graph key too large");
+
+// One refinement iteration of the mixed modes (reuse path) on stream s: the
+// residual pass (both forms, gated on the iteration count), the finalize that
+// counts the iteration and sets the loop condition, the correction and the
+// update. *cnt += kernels launched.
+static bool refine_iteration(const RefineGraphArgs& a, cudaGraphConditionalHandle cond, cudaStream_t s, int* cnt) {
+  const int n = a.main.n, m = a.main.m;
+  if (launch_kkt_residual<double>(a.main, a.acc, a.cvec, a.skip, s, 0, 3) != cudaSuccess) return false;
+  if (launch_residual_finalize_loop(a.main, a.acc, a.tol, a.skip, a.max_refine, cond, s) != cudaSuccess) return false;
+  *cnt += (kkt_stage_cols(n, m) > 0 ? 2 : 1) + 1;
+  if (launch_correction(a.ca, s, cnt) != cudaSuccess) return false;
+  if (launch_refine_update_f32(a.main, a.ca.dk, a.ca.dx, a.ca.du, a.ca.dl, a.dp, a.skip, s) != cudaSuccess) return false;
+  *cnt += 1;
+  return true;
+}
+
+static void refine_graph_drop(lqr_handle* h) {
+  if (h->rexec) cudaGraphExecDestroy(h->rexec);
+  if (h->rgraph) cudaGraphDestroy(h->rgraph);
+  h->rexec = nullptr;
+  h->rgraph = nullptr;
+  h->rkey_valid = 0;
+}
+
+// Launches the refinement loop as a graph on st (building it when the
+// arguments differ from the cached graph's). false: no graph (a graph call
+// failed; the caller launches the iterations itself from then on).
+static bool refine_graph_launch(lqr_handle* h, const RefineGraphArgs& a, cudaStream_t st) {
+  if (!h->rkey_valid || memcmp(h->rkey, &a, sizeof(a)) != 0) {
+    refine_graph_drop(h);
+    bool ok = (h->cap || cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess);
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle cond;
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+    cudaGraphNode_t node;
+    ok = ok && cudaGraphCreate(&g, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = cond;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    int body = 0;
+    if (ok) {
+      cudaGraph_t bg = np.conditional.phGraph_out[0];
+      ok = cudaStreamBeginCaptureToGraph(h->cap, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+      if (ok) {
+        const bool launched = refine_iteration(a, cond, h->cap, &body);
+        cudaGraph_t out = nullptr;
+        ok = cudaStreamEndCapture(h->cap, &out) == cudaSuccess && launched;
+      }
+    }
+    ok = ok && cudaGraphInstantiate(&h->rexec, g, 0) == cudaSuccess;
+    h->rgraph = g;
+    if (!ok) {
+      cudaGetLastError();  // clear a sticky launch error of the capture, if any
+      refine_graph_drop(h);
+      h->rgraph_broken = 1;
+      return false;
+    }
+    memcpy(h->rkey, &a, sizeof(a));
+    h->rkey_valid = 1;
+    h->rbody = body;
+  }
+  if (cudaGraphLaunch(h->rexec, st) != cudaSuccess) {
+    refine_graph_drop(h);
+    h->rgraph_broken = 1;
+    return false;
+  }
+  return true;
 }
 
 // Steps A1 (and, unless summary_only, A3, A4, A5/A6) for the problem in tab.
@@ -509,8 +613,24 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
       ++launches;
     }
     // the residual passes write the correction problem's vectors in FP32 directly
-    const KktOut cvec{(void*)cp.q, (void*)cp.r, (void*)cp.c, (void*)cp.x0, 1};
-    for (int it = 0; it < o->max_refine; ++it) {
+    KktOut cvec;
+    memset(&cvec, 0, sizeof(cvec));
+    cvec.q = (void*)cp.q; cvec.r = (void*)cp.r; cvec.c = (void*)cp.c; cvec.x0 = (void*)cp.x0; cvec.f32 = 1;
+    h->last_iters = nullptr;
+    bool looped = false;
+    if (reuse && o->max_refine > 0 && !h->rgraph_broken) {
+      // the loop as a graph: one iteration's kernels under a WHILE node
+      RefineGraphArgs ga;
+      memset(&ga, 0, sizeof(ga));
+      ga.main = main; ga.ca = ca; ga.cvec = cvec; ga.acc = acc; ga.skip = skip; ga.tol = o->tol;
+      ga.max_refine = o->max_refine; ga.dp = want_P ? f + odp : nullptr;
+      if (refine_graph_launch(h, ga, st)) {
+        looped = true;
+        h->last_iters = skip + 2;
+        h->last_stream = st;
+      }
+    }
+    for (int it = 0; it < o->max_refine && !looped; ++it) {
       // the first pass (the residual of the FP32 solve, some 2^-24 of |KKT| |w|)
       // in double-FP32 arithmetic (~2^-47 of it), the later ones in FP64
       if (launch_kkt_residual<double>(main, acc, cvec, skip, st, 0, it == 0 ? 1 : 0) != cudaSuccess)
@@ -1105,6 +1225,9 @@ lqr_status lqr_destroy(lqr_handle* h) {
       for (int k = 0; k <= lqr_handle::kPhases; ++k) cudaEventDestroy(h->ev[i][k]);
   if (h->f32) cudaFree(h->f32);
   if (h->nl) cudaFree(h->nl);
+  if (h->rexec) cudaGraphExecDestroy(h->rexec);
+  if (h->rgraph) cudaGraphDestroy(h->rgraph);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
@@ -1563,7 +1686,17 @@ const char* lqr_status_string(lqr_status s) {
   return "unknown status";
 }
 
-int lqr_last_launch_count(const lqr_handle* h) { return h ? h->last_launches : 0; }
+int lqr_last_launch_count(const lqr_handle* h) {
+  if (!h) return 0;
+  if (!h->last_iters) return h->last_launches;
+  // a refinement graph ran: its loop body ran as many times as the device counted
+  DeviceGuard g(h->device);
+  int iters = 0;
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess ||
+      cudaMemcpy(&iters, h->last_iters, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -1;
+  return h->last_launches + h->rbody * iters;
+}
 
 lqr_status lqr_profile_enable(lqr_handle* h, int enable) {
   if (!h) return LQR_ERR_INVALID_ARG;

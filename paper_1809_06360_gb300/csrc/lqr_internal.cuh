@@ -390,12 +390,19 @@ constexpr int kResidAccDoubles = 8 + kMaxResidBlocks;
 // vectors are requested (-1). |KKT|_inf depends on the data alone: a pass that
 // computes it once keeps it in the accumulators until the solve's final pass.
 // df: 1 the double-FP32 kernel where it applies (FP64 data, correction vectors
-// requested, no |KKT| row sums, n, m <= 128), else the FP64 one.
+// requested, no |KKT| row sums, n, m <= 128), else the FP64 one; 3 (the loop
+// body of a refinement graph) both, the double-FP32 one running in the first
+// iteration (skip[2] == 0) and the FP64 one in the later ones.
 template <typename TS>
 cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& out, const int* skip, cudaStream_t st,
                                 int knorm = -1, int df = 0);
 // |KKT|_inf from the FP32 copy of the data (pd: the FP32 problem), once per mixed-precision solve
 cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st);
+// The finalize of a refinement graph's loop body: also counts the iterations
+// in skip[2] and sets the loop condition `cond` (continue while not converged,
+// no error and fewer than `loop` iterations).
+cudaError_t launch_residual_finalize_loop(const ProbDesc& pd, double* acc, double tol, int* skip, int loop,
+                                          cudaGraphConditionalHandle cond, cudaStream_t st);
 cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol, int* skip, int is_final,
                                      int check, cudaStream_t st);
 template <typename TS>

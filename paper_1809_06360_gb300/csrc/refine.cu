@@ -252,9 +252,10 @@ __global__ void __launch_bounds__(kBlock) kkt_residual_kernel(ProbDesc pd, doubl
 // grid-stride over the stages like kkt_residual_kernel.
 template <int NC, bool KN, typename TS>
 __global__ void __launch_bounds__(kKktBlock, 2)
-    kkt_residual_stream_kernel(ProbDesc pd, double* acc, KktOut out, const int* skip, int use_stash) {
+    kkt_residual_stream_kernel(ProbDesc pd, double* acc, KktOut out, const int* skip, int use_stash, int gate) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (skip && *(volatile const int*)skip) return;
+  if (gate && (((volatile const int*)skip)[2] == 0) != (gate == 1)) return;  // not this iteration's form
   if (*(volatile int*)pd.status != 0) return;
   const int n = pd.n, T = pd.T;
   KktData<TS> g;
@@ -329,9 +330,10 @@ __global__ void __launch_bounds__(kKktBlock, 2)
 // terminal and initial rows (O(n^2) once) in FP64.
 template <int NC>
 __global__ void __launch_bounds__(kKktBlock, NC >= 4 ? 3 : 4)  // 80 / 64 registers, no spills
-    kkt_residual_df_kernel(ProbDesc pd, double* acc, KktOut out, const int* skip) {
+    kkt_residual_df_kernel(ProbDesc pd, double* acc, KktOut out, const int* skip, int gate) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (skip && *(volatile const int*)skip) return;
+  if (gate && (((volatile const int*)skip)[2] == 0) != (gate == 1)) return;  // not this iteration's form
   if (*(volatile int*)pd.status != 0) return;
   const int n = pd.n, T = pd.T;
   KktData<double> g;
@@ -397,9 +399,8 @@ __global__ void __launch_bounds__(kKktBlock, NC >= 4 ? 3 : 4)  // 80 / 64 regist
 
 // Turns the accumulators into eta, rel and the cost; decides convergence.
 // report: [0] cost, [1] eta, [2] rel, [3] refinement iterations applied.
-__global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, double tol, int* skip,
-                                         int is_final, int check_convergence) {
-  if (threadIdx.x != 0) return;
+__device__ void finalize_body(ProbDesc pd, double* acc, int nblocks, double tol, int* skip, int is_final,
+                              int check_convergence) {
   if (*(volatile int*)pd.status != 0) return;
   // already converged: the solution has not changed since the pass that found
   // it converged, whose numbers stand (the final pass was skipped as well)
@@ -418,6 +419,23 @@ __global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, 
   // ready for the next pass; |KKT|_inf, a function of the data, stays until the final pass
   for (int i = 0; i < RS_COUNT; ++i)
     if (i != RS_KNORM || is_final) acc[i] = 0.0;
+}
+
+// In the refinement loop of a graph (loop: max iterations > 0): skip[2] counts
+// the iterations and the loop's condition is set to continue while the
+// solution has not converged, no error was raised and the count is below the
+// maximum.
+__global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, double tol, int* skip,
+                                         int is_final, int check_convergence, int loop,
+                                         cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0) return;
+  finalize_body(pd, acc, nblocks, tol, skip, is_final, check_convergence);
+  if (loop > 0) {
+    const int it = skip[2] + 1;
+    skip[2] = it;
+    const bool go = skip[0] == 0 && *(volatile int*)pd.status == 0 && it < loop;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+  }
 }
 
 // w <- w - delta for the outputs the correction solve refreshed.
@@ -461,16 +479,19 @@ cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& o
   // by default the refinement passes (correction vectors requested) skip the |KKT| row sums
   const int want_knorm = knorm >= 0 ? knorm : (out.q == nullptr) ? 1 : 0;
   const int nc = kkt_stage_cols(pd.n, pd.m);
-  if (df && nc > 0 && sizeof(TS) == 8 && !want_knorm && out.q) {
+  const bool df_ok = nc > 0 && sizeof(TS) == 8 && !want_knorm && out.q;
+  // df = 3 (a graph's loop body): both forms, gated on the iteration count skip[2]
+  const int gate_df = (df == 3 && df_ok && skip) ? 1 : 0, gate_fp64 = gate_df ? 2 : 0;
+  if (df && df_ok) {
     const size_t bytes = sizeof(double) * kkt_stage_df_smem_doubles(pd.n, pd.m);
     const int g = residual_grid(pd.T);
     if (nc == 1)
-      kkt_residual_df_kernel<1><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip);
+      kkt_residual_df_kernel<1><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip, gate_df);
     else if (nc == 2)
-      kkt_residual_df_kernel<2><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip);
+      kkt_residual_df_kernel<2><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip, gate_df);
     else
-      kkt_residual_df_kernel<4><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip);
-    return cudaGetLastError();
+      kkt_residual_df_kernel<4><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip, gate_df);
+    if (!gate_df) return cudaGetLastError();
   }
   if (nc > 0) {
     const size_t base = sizeof(double) * kkt_stage_smem_doubles(pd.n, pd.m);  // <= 45056 B at n = m = 128
@@ -483,7 +504,7 @@ cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& o
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,              \
                                                   (int)bytes) != cudaSuccess)                                \
       return cudaGetLastError();                                                                             \
-    kkt_residual_stream_kernel<NC, KN, TS><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip, KN);            \
+    kkt_residual_stream_kernel<NC, KN, TS><<<g, kKktBlock, bytes, st>>>(pd, acc, out, skip, KN, gate_fp64); \
   } while (0)
     if (nc == 1) {
       if (want_knorm) LQR_RES_LAUNCH(1, true); else LQR_RES_LAUNCH(1, false);
@@ -595,9 +616,16 @@ cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st
   return cudaGetLastError();
 }
 
+cudaError_t launch_residual_finalize_loop(const ProbDesc& pd, double* acc, double tol, int* skip, int loop,
+                                          cudaGraphConditionalHandle cond, cudaStream_t st) {
+  residual_finalize_kernel<<<1, 32, 0, st>>>(pd, acc, residual_grid(pd.T), tol, skip, 0, 0, loop, cond);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_residual_finalize(const ProbDesc& pd, double* acc, double tol, int* skip, int is_final,
                                      int check, cudaStream_t st) {
-  residual_finalize_kernel<<<1, 32, 0, st>>>(pd, acc, residual_grid(pd.T), tol, skip, is_final, check);
+  residual_finalize_kernel<<<1, 32, 0, st>>>(pd, acc, residual_grid(pd.T), tol, skip, is_final, check, 0,
+                                             cudaGraphConditionalHandle{});
   return cudaGetLastError();
 }
 

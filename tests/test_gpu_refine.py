@@ -153,22 +153,23 @@ def test_mixed_fp32_correction_paths(solver):
     fit (n=64, m=32: two stage-data slots and the fast sweep; n=72 and n=128:
     the generic FP32 sweep, which also keeps M_uu^-1; n=128 with one slot and
     the closed-loop maps reading B_t, K_t from global memory), corrections
-    reuse the solve's K_t, P_t and M_uu^-1 (residual pass writing the FP32
-    correction vectors, finalize, four segment passes, two link chains,
-    update: 9 kernels each when a chain is one kernel; the counted correction
-    is the second, whose residual pass runs in FP64, the first one's in
-    double-FP32). With K >= 32 segments each link chain runs in two levels
-    over groups of ceil(sqrt(K)) links (group offsets, the chain over the
-    groups, the fill: three kernels), 13 kernels per correction; K = 40 leaves
-    a short last group, K = 49 none. n=136: beyond the link-chain plan of the
-    corrections, so each correction is a whole FP32 solve (residual, finalize
-    and update around the kernels of a plain FP32 solve of that shape). All
-    reach the oracle at 1e-9."""
-    cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, 9),
-             (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, 9),
-             (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, 9),
-             (workloads.make_problem(64, 32, 400, seed=615, rho_max=1.02), 40, 13),
-             (workloads.make_problem(128, 64, 392, seed=616, rho_max=1.02), 49, 13),
+    reuse the solve's K_t, P_t and M_uu^-1 and the refinement loop runs as a
+    CUDA graph whose loop body is one iteration: the residual pass writing the
+    FP32 correction vectors (two kernels, double-FP32 and FP64, gated on the
+    iteration count), finalize, four segment passes, two link chains, update:
+    10 kernels per executed iteration when a chain is one kernel. With K >= 32
+    segments each link chain runs in two levels over groups of ceil(sqrt(K))
+    links (group offsets, the chain over the groups, the fill: three kernels),
+    14 kernels per iteration; K = 40 leaves a short last group, K = 49 none.
+    n=136: beyond the link-chain plan of the corrections and the register plan
+    of the residual kernels, so each correction is a whole FP32 solve launched
+    from the host (residual, finalize and update around the kernels of a plain
+    FP32 solve of that shape). All reach the oracle at 1e-9."""
+    cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, 10),
+             (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, 10),
+             (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, 10),
+             (workloads.make_problem(64, 32, 400, seed=615, rho_max=1.02), 40, 14),
+             (workloads.make_problem(128, 64, 392, seed=616, rho_max=1.02), 49, 14),
              (workloads.make_problem(136, 8, 160, seed=614, rho_max=1.02), 4, None)]
     for prob, K, expect in cases:
         per = _launches_per_correction(solver, prob, K)
@@ -181,6 +182,32 @@ def test_mixed_fp32_correction_paths(solver):
         assert rep["status"] == 0, rep
         for k in ("x", "u", "lam"):
             assert oracle.rel_err(out[k], ref[k]) < 1e-9, (prob["B"].shape, k, oracle.rel_err(out[k], ref[k]))
+
+
+def test_refinement_graph_stops_at_convergence(solver):
+    """The refinement loop of the mixed modes runs as a graph whose WHILE node
+    stops once the finalize kernel finds the solution converged: a cap of 8
+    iterations launches exactly the kernels a cap of 3 does (two corrections
+    and the pass that finds convergence), and the answer is the same bit for
+    bit; a third problem in between (other arguments: the graph is rebuilt)
+    does not disturb either."""
+    prob = workloads.make_problem(64, 32, 512, seed=617, rho_max=1.02)
+    other = workloads.make_problem(32, 8, 300, seed=618, rho_max=1.02)
+    dev = to_dev(prob)
+    res = {}
+    for cap in (3, 8, 8, 3):
+        out = host(solver.solve(dev, num_segments=32, prec="mixed_fp32", max_refine=cap, tol=1e-10))
+        rep = solver.report()
+        assert rep["status"] == 0 and rep["refine_iters"] == 2, rep
+        res.setdefault(cap, []).append((solver.last_launch_count(), out))
+        host(solver.solve(to_dev(other), num_segments=8, prec="mixed_fp32", max_refine=cap, tol=1e-10))
+        assert solver.report()["status"] == 0
+    counts = {cap: [c for c, _ in v] for cap, v in res.items()}
+    assert counts[3][0] == counts[3][1] == counts[8][0] == counts[8][1], counts
+    for k in ("x", "u", "lam", "k"):
+        assert np.array_equal(res[3][0][1][k], res[8][0][1][k]), k
+    ref = oracle.riccati(prob)
+    assert oracle.rel_err(res[8][1][1]["x"], ref["x"]) < 1e-9
 
 
 @pytest.mark.parametrize("K", [64, 152])
