@@ -60,7 +60,7 @@ PEAK_TF32_TFLOPS = _tf32_peak()
 # DRAM bytes per launch (read + write) measured by ncu for the kernel as it now
 # stands, keyed by (kernel, workload config, precision); an entry is removed
 # whenever its kernel changes. seg_sweep_f32_kernel on the long-horizon
-# workload in LQR_MIXED_FP32: A1 226.3 MB, A4 309.3 MB (it also writes K_t, P_t,
+# workload in LQR_MIXED_FP32: A1 227.6 MB, A4 309.4 MB (it also writes K_t, P_t,
 # M_uu^-1), mean of the two launches (profiles/seg_sweep_f32_n64_m32_T4096_K152.md)
 NCU_TRAFFIC: dict = {("seg_sweep_f32_kernel", 1, "mixed_fp32"): (227.6e6 + 309.4e6) / 2}
 
