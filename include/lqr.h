@@ -282,6 +282,13 @@ lqr_status lqr_tc_selftest(int device, double* errs);
  * IEEE division. d, y: DEVICE arrays of count doubles. Asynchronous on stream. */
 lqr_status lqr_rcp_newton_check(const double* d, double* y, int count, void* stream);
 
+/* FP64 -> FP32 conversion of `count` values (DEVICE arrays), rounding to
+ * nearest with ties to even as IEEE prescribes, computed with integer
+ * operations on the bit patterns (the conversion instruction would occupy the
+ * FP64 pipe): the kernel that makes the FP32 working copies of the mixed
+ * modes. Asynchronous on `stream`. */
+lqr_status lqr_convert_f64_to_f32(const double *src, float *dst, long long count, void *stream);
+
 /* ---- Trajectory-optimisation outer loop --------------------------------------
  * Section I: trajectory optimisation reduces to a sequence of LQR subproblems.
  * lqr_sqp_solve runs Gauss-Newton multiple-shooting SQP on the nonlinear

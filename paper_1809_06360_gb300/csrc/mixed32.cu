@@ -7,6 +7,47 @@
 
 namespace lqr {
 
+// FP64 -> FP32 with rounding to nearest, ties to even (IEEE), by integer
+// operations on the bit pattern: the conversion instruction would hold the
+// sub-partition's FP64 pipe for 64 cycles per warp. Normal results round the
+// 52-bit significand at bit 29; results below the normal range are formed as
+// multiples of 2^-149 the same way; beyond the range infinity; NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+  const int e = static_cast<int>((b >> 52) & 0x7FF);
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  unsigned int r;
+  if (e >= 897 && e <= 1150) {
+    const unsigned int m24 = static_cast<unsigned int>(mant >> 29);
+    const unsigned int rem = static_cast<unsigned int>(mant & 0x1FFFFFFFull);
+    const unsigned int up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (m24 & 1u));
+    r = ((static_cast<unsigned int>(e - 896) << 23) | m24) + up;
+  } else if (e > 1150) {
+    r = 0x7F800000u | ((e == 0x7FF && mant) ? 0x400000u : 0u);
+  } else {
+    const int shift = 926 - e;  // >= 30
+    if (shift >= 54) {
+      r = 0u;
+    } else {
+      const unsigned long long F = mant | (1ull << 52);
+      const unsigned int q = static_cast<unsigned int>(F >> shift);
+      const unsigned long long rem = F & ((1ull << shift) - 1), half = 1ull << (shift - 1);
+      r = q + static_cast<unsigned int>((rem > half) | ((rem == half) & (q & 1u)));
+    }
+  }
+  return __uint_as_float(sign | r);
+}
+
+template <typename S, typename D>
+__device__ __forceinline__ D convert_one(S v) {
+  return static_cast<D>(v);
+}
+template <>
+__device__ __forceinline__ float convert_one<double, float>(double v) {
+  return f64_to_f32_rn(v);
+}
+
 // Up to kMaxConv arrays converted in one launch; grid-stride over each.
 template <typename S, typename D>
 __global__ void convert_kernel(ConvTable<S, D> tab, const int* skip) {
@@ -17,7 +58,7 @@ __global__ void convert_kernel(ConvTable<S, D> tab, const int* skip) {
     D* dst = tab.dst[a];
     const size_t n = tab.n[a];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride)
-      dst[e] = static_cast<D>(src[e]);
+      dst[e] = convert_one<S, D>(src[e]);
   }
 }
 
@@ -63,6 +104,19 @@ cudaError_t launch_refine_update_f32(const ProbDesc& pd, const float* dk, const 
 }
 
 template cudaError_t launch_convert<double, float>(const ConvTable<double, float>&, const int*, cudaStream_t);
+
+}  // namespace lqr
+
+extern "C" lqr_status lqr_convert_f64_to_f32(const double* src, float* dst, long long count, void* stream) {
+  if (count < 0 || (count > 0 && (!src || !dst))) return LQR_ERR_INVALID_ARG;
+  if (count == 0) return LQR_OK;
+  lqr::ConvTable<double, float> ct;
+  ct.count = 0;
+  ct.add(src, dst, static_cast<size_t>(count));
+  return lqr::launch_convert(ct, nullptr, static_cast<cudaStream_t>(stream)) == cudaSuccess ? LQR_OK : LQR_ERR_CUDA;
+}
+
+namespace lqr {
 template cudaError_t launch_convert<float, double>(const ConvTable<float, double>&, const int*, cudaStream_t);
 
 }  // namespace lqr

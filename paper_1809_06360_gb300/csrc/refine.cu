@@ -545,8 +545,10 @@ __global__ void kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
   float* xr = tile + d * ld;    // x rows
   float* dr = xr + n;           // dynamics rows
   float* ur = dr + n;           // u rows
+  float* part = ur + m;         // [nw][d] column sums of each warp's rows
   float kmax = 1.0f;            // the initial-condition rows
-  // row sums of |(M + M')/2| of the dd x dd block in the tile, added to out[i] (one writer per row)
+  // row sums of |(M + M')/2| of the dd x dd block in the tile, added to out[i] by
+  // lane 0 of warp i % nw
   auto sym_rows = [&](int dd, float* out) {
     for (int i = warp; i < dd; i += nw) {
       float s = 0.0f;
@@ -555,18 +557,38 @@ __global__ void kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
       if (lane == 0) out[i] += s;
     }
   };
-  // |M| of a row-major R x C block: row sums into rows[], column sums into cols[]
-  // (rows to warps, columns to lanes: coalesced; shared-memory atomics)
-  auto abs_rows_cols = [&](const float* M, int R, int C, float* rows, float* cols) {
+  // |M| of a row-major R x C block (C <= 256): row sums added to rows[i] by lane 0
+  // of warp i % nw; column sums of the warp's rows into part[warp][.] (columns to
+  // lanes, coalesced, in registers)
+  auto abs_pass = [&](const float* M, int R, int C, float* rows) {
+    float cs[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cs[c] = 0.0f;
     for (int i = warp; i < R; i += nw) {
       float s = 0.0f;
-      for (int k = lane; k < C; k += 32) {
-        const float v = fabsf(M[(size_t)i * C + k]);
-        s += v;
-        atomicAdd(&cols[k], v);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = lane + 32 * c;
+        if (k < C) {
+          const float v = fabsf(M[(size_t)i * C + k]);
+          s += v;
+          cs[c] += v;
+        }
       }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) atomicAdd(&rows[i], s);
+      if (lane == 0) rows[i] += s;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int k = lane + 32 * c;
+      if (k < C) part[warp * d + k] = cs[c];
+    }
+  };
+  auto add_parts = [&](int C, float* cols) {  // after a barrier
+    for (int k = threadIdx.x; k < C; k += blockDim.x) {
+      float s = 0.0f;
+      for (int w = 0; w < nw; ++w) s += part[w * d + k];
+      cols[k] += s;
     }
   };
   for (int t = blockIdx.x; t <= T; t += gridDim.x) {
@@ -577,20 +599,30 @@ __global__ void kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
     }
     for (int a = threadIdx.x; a < m; a += blockDim.x) ur[a] = 0.0f;
     const float* Q = gQ + nn * t;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) tile[(e / n) * ld + e % n] = Q[e];
+    cta_for_rc(n, n, [&](int e, int i, int j) { tile[i * ld + j] = Q[e]; });
     __syncthreads();
     sym_rows(n, xr);  // x rows: |Q_sym| (the terminal rows: |Q_T,sym| + 1)
-    __syncthreads();
     if (!term) {
-      abs_rows_cols(gA + nn * t, n, n, dr, xr);          // |A| rows (dynamics), columns (x rows)
-      abs_rows_cols(gB + nm * t, n, m, dr, ur);          // |B| rows (dynamics), columns (u rows)
-      if (gS) abs_rows_cols(gS + nm * t, m, n, ur, xr);  // |S| rows (u rows), columns (x rows)
+      abs_pass(gA + nn * t, n, n, dr);  // |A|: rows (dynamics), columns (x rows)
+      __syncthreads();
+      add_parts(n, xr);
+      __syncthreads();
+      abs_pass(gB + nm * t, n, m, dr);  // |B|: rows (dynamics), columns (u rows)
+      __syncthreads();
+      add_parts(m, ur);
+      __syncthreads();
+      if (gS) {
+        abs_pass(gS + nm * t, m, n, ur);  // |S|: rows (u rows), columns (x rows)
+        __syncthreads();
+        add_parts(n, xr);
+        __syncthreads();
+      }
       const float* R = gR + mm * t;
-      for (int e = threadIdx.x; e < m * m; e += blockDim.x) tile[(e / m) * ld + e % m] = R[e];
+      cta_for_rc(m, m, [&](int e, int i, int j) { tile[i * ld + j] = R[e]; });
       __syncthreads();
       sym_rows(m, ur);  // u rows: |R_sym|
-      __syncthreads();
     }
+    __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) kmax = fmaxf(kmax, term ? xr[i] : fmaxf(xr[i], dr[i]));
     if (!term)
       for (int a = threadIdx.x; a < m; a += blockDim.x) kmax = fmaxf(kmax, ur[a]);
@@ -609,7 +641,7 @@ __global__ void kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
 
 cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st) {
   const int d = pd.n > pd.m ? pd.n : pd.m;
-  const size_t bytes = sizeof(float) * ((size_t)d * (d + 1) + 2 * (size_t)pd.n + pd.m);
+  const size_t bytes = sizeof(float) * ((size_t)d * (d + 1) + 2 * (size_t)pd.n + pd.m + 8 * (size_t)d);
   cudaError_t e = raise_dyn_smem((const void*)kkt_norm_f32_kernel, bytes);
   if (e != cudaSuccess) return e;
   kkt_norm_f32_kernel<<<residual_grid(pd.T + 1), 256, bytes, st>>>(pd, acc);

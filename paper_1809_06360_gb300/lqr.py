@@ -32,7 +32,8 @@ EXPORTS = ("lqr_create", "lqr_destroy", "lqr_partition", "lqr_solve", "lqr_solve
            "lqr_profile_enable", "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched",
            "lqr_backward", "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
            "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
-           "lqr_global_policy_parallel", "lqr_sqp_solve", "lqr_kkt_residual_vectors")
+           "lqr_global_policy_parallel", "lqr_sqp_solve", "lqr_kkt_residual_vectors",
+           "lqr_convert_f64_to_f32")
 PHASES = ("sweep", "link", "policy", "rollout", "refine")
 
 
@@ -116,6 +117,7 @@ def load(path: str | None = None):
     lib.lqr_rcp_newton_check.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
     lib.lqr_segment_policies.argtypes = [c_void_p, P(lqr_problem), P(lqr_opts), c_int, c_void_p, c_void_p, c_void_p,
                                          c_void_p, c_void_p]
+    lib.lqr_convert_f64_to_f32.argtypes = [c_void_p, c_void_p, ctypes.c_longlong, c_void_p]
     lib.lqr_kkt_residual_vectors.argtypes = [c_void_p, P(lqr_problem), P(lqr_solution), c_void_p, c_void_p,
                                              c_void_p, c_void_p, c_void_p]
     lib.lqr_sqp_solve.argtypes = [c_void_p, P(lqr_nl_model), P(lqr_sqp_opts), c_void_p, c_void_p, c_void_p,
@@ -133,7 +135,8 @@ def load(path: str | None = None):
                  "lqr_profile_read", "lqr_solve_batched", "lqr_report_batched", "lqr_backward",
                  "lqr_backward_batched", "lqr_kkt_residual_noalloc", "lqr_tc_selftest",
                  "lqr_rcp_newton_check", "lqr_segment_policies", "lqr_ls_multipliers",
-                 "lqr_global_policy_parallel", "lqr_sqp_solve", "lqr_kkt_residual_vectors"):
+                 "lqr_global_policy_parallel", "lqr_sqp_solve", "lqr_kkt_residual_vectors",
+                 "lqr_convert_f64_to_f32"):
         getattr(lib, name).restype = c_int
     _lib = lib
     return lib
@@ -243,6 +246,10 @@ def lqr_tc_selftest(device: int = 0) -> list[float]:
 
 def lqr_rcp_newton_check(d_ptr: int, y_ptr: int, count: int, stream: int | None) -> None:
     _check(load().lqr_rcp_newton_check(d_ptr, y_ptr, count, stream or None), "lqr_rcp_newton_check")
+
+
+def lqr_convert_f64_to_f32(src: int, dst: int, count: int, stream: int | None = None) -> None:
+    _check(load().lqr_convert_f64_to_f32(src, dst, count, stream), "lqr_convert_f64_to_f32")
 
 
 def lqr_profile_enable(h: int, enable: bool) -> None:

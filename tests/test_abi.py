@@ -24,7 +24,7 @@ def _declared():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(lqr_[a-z_]+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(lqr_[a-z0-9_]+)\s*\(", src, re.M))
     return names
 
 

@@ -112,3 +112,32 @@ def test_residual_vectors_double_fp32(solver, n, m, T, cross, perturb):
               np.abs(got["x0"] - ref["r0"]).max())
     print("n=%d m=%d T=%d residual %.2e error %.2e of scale %.2e" % (n, m, T, nrm["rnorm"], err, scale))
     assert err <= 2e-13 * scale, (err, scale)
+
+
+def test_convert_f64_to_f32_rounds_to_nearest_even(solver):
+    """The integer-operation FP64 -> FP32 conversion of the mixed modes'
+    working copies (lqr_convert_f64_to_f32) against IEEE rounding (numpy's),
+    bit for bit: magnitudes over the whole FP32 range and beyond, halfway
+    cases (ties to even), subnormal results, overflow to infinity, signed
+    zeros, infinities and NaN."""
+    from paper_1809_06360_gb300 import lqr
+    import warnings
+    g = np.random.default_rng(11)
+    v = g.standard_normal(300000) * 10.0 ** g.integers(-50, 50, 300000)
+    f = g.standard_normal(5000).astype(np.float32)
+    ties = (f.astype(np.float64) + np.nextafter(f, np.float32(np.inf)).astype(np.float64)) / 2
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 3.4028235677973366e38, 3.4028235e38 * 1.0000001,
+                        2.0 ** -149, 2.0 ** -150, 2.0 ** -150 * 1.0000001, 1.1754942e-38, 2.0 ** -126 * (1 - 2 ** -25),
+                        1e-300, -1e300, 1.0, -1.5])
+    d = np.concatenate([v, ties, special])
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty(d.shape, dtype=torch.float32, device="cuda")
+    lqr.lqr_convert_f64_to_f32(dd.data_ptr(), out.data_ptr(), d.size, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        want = d.astype(np.float32)
+    nan = np.isnan(want)
+    assert np.isnan(out.cpu().numpy()[nan]).all()
+    assert np.array_equal(got[~nan], want.view(np.uint32)[~nan]), np.flatnonzero(got[~nan] != want.view(np.uint32)[~nan])[:5]
