@@ -499,8 +499,10 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   const size_t ocq = take((size_t)(T + 1) * n), ocr = take((size_t)T * m), occ = take((size_t)T * n),
                ocx0 = take(n), odk = take((size_t)T * m), odx = take((size_t)(T + 1) * n), odu = take((size_t)T * m),
                odl = take((size_t)(T + 1) * n), odp = keep_P ? take((size_t)(T + 1) * n) : 0;
-  const size_t oMi = reuse ? take((size_t)T * mm) : 0, oPsi = reuse ? take((size_t)K * nn) : 0,
-               oeps = reuse ? take((size_t)K * n) : 0, odel = reuse ? take((size_t)K * n) : 0,
+  const size_t cld = (size_t)corr_ld(n), blk = (size_t)(n + 1) * cld;
+  const size_t oMi = reuse ? take((size_t)T * mm) : 0, oPhit = reuse ? take((size_t)T * blk) : 0,
+               oPhiTt = reuse ? take((size_t)T * blk) : 0, oPsi = reuse ? take((size_t)K * blk) : 0,
+               oPsiT = reuse ? take((size_t)K * blk) : 0, opcv = reuse ? take((size_t)T * cld) : 0,
                opb = reuse ? take((size_t)(K + 1) * n) : 0, oxb = reuse ? take((size_t)(K + 1) * n) : 0;
   // two-level correction link chains for long chains: groups of about sqrt(K) links
   int cG = 0, cng = 0;
@@ -509,9 +511,8 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
     while (cG * cG < K) ++cG;
     cng = (K + cG - 1) / cG;
   }
-  const size_t oPhi = cng ? take((size_t)cng * nn) : 0, oge = cng ? take((size_t)cng * n) : 0,
-               ogd = cng ? take((size_t)cng * n) : 0, ogY = cng ? take((size_t)(cng + 1) * n) : 0,
-               ogX = cng ? take((size_t)(cng + 1) * n) : 0;
+  const size_t oTh = cng ? take((size_t)cng * blk) : 0, oThT = cng ? take((size_t)cng * blk) : 0,
+               ogY = cng ? take((size_t)(cng + 1) * n) : 0, ogX = cng ? take((size_t)(cng + 1) * n) : 0;
   rs = grow(&h->f32, &h->f32_bytes, sizeof(float) * off);
   if (rs != LQR_OK) return rs;
   float* f = reinterpret_cast<float*>(h->f32);
@@ -592,13 +593,14 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
     if (reuse) {
       ca.A = f + oA; ca.B = f + oB; ca.K = f + oK; ca.P = f + oP; ca.Minv = f + oMi;
       ca.cq = f + ocq; ca.cr = f + ocr; ca.cc = f + occ; ca.cx0 = f + ocx0;
-      ca.Psi = f + oPsi; ca.eps = f + oeps; ca.delta = f + odel; ca.pb = f + opb; ca.xb = f + oxb;
+      ca.Phit = f + oPhit; ca.PhiTt = f + oPhiTt; ca.Psi = f + oPsi; ca.PsiT = f + oPsiT; ca.pcv = f + opcv;
+      ca.pb = f + opb; ca.xb = f + oxb;
       ca.dk = f + odk; ca.dp = f + odp; ca.dx = f + odx; ca.du = f + odu; ca.dl = f + odl;
       ca.skip = skip; ca.status = h->d_status;
       ca.n = n; ca.m = m; ca.T = T; ca.nseg = K;
       ca.slots = cslots; ca.psi_global = cpsi_global;
       ca.G = cG; ca.ng = cng;
-      if (cng) { ca.Phi = f + oPhi; ca.ge = f + oge; ca.gd = f + ogd; ca.gY = f + ogY; ca.gX = f + ogX; }
+      if (cng) { ca.Theta = f + oTh; ca.ThetaT = f + oThT; ca.gY = f + ogY; ca.gX = f + ogX; }
       if (launch_corr_psi(ca, st) != cudaSuccess) return LQR_ERR_CUDA;
       ++launches;
       if (cng) {

@@ -213,20 +213,26 @@ int device_sm_count();
 cudaError_t raise_dyn_smem(const void* func, size_t bytes);
 
 // Refinement corrections that reuse the factorisation (correct.cu): FP32
-// arrays of one problem, K = the solve's segment count.
+// arrays of one problem, K = the solve's segment count. The step matrices of
+// the correction recursions are stored as blocks of n + 1 rows of stride ld
+// (corr_ld): rows 0..n-1 the matrix, row n the step's offset vector.
 struct CorrArgs {
   const float *A, *B, *K, *P, *Minv;   // the solve's data, policies, value matrices, M_uu^-1
   const float *cq, *cr, *cc, *cx0;     // correction data q~ ((T+1) n), r~ (T m), c~ (T n), x0~ (n)
-  float *Psi, *eps, *delta, *pb, *xb;  // K n n, K n, K n, (K+1) n, (K+1) n
+  float *Phit, *PhiTt;                 // T blocks: Phi_t with e_t, Phi_t' with w_t
+  float *Psi, *PsiT;                   // K blocks: Psi_j with eps_j, Psi_j' with delta_j
+  float* pcv;                          // P_{t+1} c~_t (T ld)
+  float *pb, *xb;                      // (K+1) n each: p and x~ at the segment boundaries
   float *dk, *dp, *dx, *du, *dl;       // the correction: k~, p, x~, u~, lambda~
   const int* skip;                     // set: converged, every kernel returns at once
   int* status;
   int n, m, T, nseg;
-  int slots;       // stage-data ring slots of the segment passes (2: prefetch, 1: no prefetch)
+  int slots;       // ring slots of the recursion kernel (2..6)
   int psi_global;  // 1: the closed-loop maps read B_t, K_t from global memory
-  // two-level link chains (ng > 0): groups of G consecutive links, their maps
-  // Phi_g (ng n n), offsets e_g / d_g (ng n) and group boundary values Y, X ((ng+1) n)
-  float *Phi, *ge, *gd, *gY, *gX;
+  // two-level link chains (ng > 0): groups of G consecutive links, blocks of
+  // their maps Theta_g with e_g and Theta_g' with d_g (ng each), group boundary
+  // values Y, X ((ng+1) n)
+  float *Theta, *ThetaT, *gY, *gX;
   int G, ng;
 };
 
@@ -260,9 +266,27 @@ cudaError_t launch_seg_sweep_tc(const ProbTable& tab, int nunits, int store_P, l
 // the FP32 fast sweeps (and with them the kept M_uu^-1) apply to (n, m)
 bool fast_sweep_supported(int n, int m, long long smem_budget);
 // refinement corrections that reuse the factorisation (correct.cu)
-size_t corr_seg_smem_bytes(int n, int m, int slots);
+// Outputs per consumer warp of a correction recursion step (a power of two,
+// 4..32): eight warps cover n, and 32 / corr_opw(n) lanes share each output.
+__host__ __device__ inline int corr_opw(int n) {
+  const int need = (n + 7) / 8;
+  int o = 4;
+  while (o < need) o <<= 1;
+  return o > 32 ? 32 : o;
+}
+// The row stride of the stored correction blocks: a multiple of 4 floats (16-byte
+// rows) at least n, and congruent to corr_opw(n) mod 32 when lanes share an
+// output, so that the lanes summing rows q, q + P, ... of one column block read
+// distinct shared-memory banks.
+__host__ __device__ inline int corr_ld(int n) {
+  const int opw = corr_opw(n);
+  int ld = (n + 3) & ~3;
+  if (opw < 32)
+    while ((ld & 31) != opw) ld += 4;
+  return ld;
+}
+size_t corr_rec_smem_bytes(int n, int slots);
 size_t corr_psi_smem_bytes(int n, int m, int psi_global);
-size_t corr_link_smem_bytes(int n);
 // the plan of the correction kernels for (n, m) within the shared-memory
 // budget (slots 0: they do not apply)
 void corr_plan(int n, int m, long long smem_budget, int* slots, int* psi_global);

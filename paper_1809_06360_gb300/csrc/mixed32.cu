@@ -48,24 +48,43 @@ __device__ __forceinline__ float convert_one<double, float>(double v) {
   return f64_to_f32_rn(v);
 }
 
-// Up to kMaxConv arrays converted in one launch; grid-stride over each.
+// Up to kMaxConv arrays converted in one launch; grid-stride over each, four
+// independent loads per thread in flight (coalesced across the warp).
+constexpr int kConvUnroll = 4;
 template <typename S, typename D>
-__global__ void convert_kernel(ConvTable<S, D> tab, const int* skip) {
+__global__ void __launch_bounds__(256) convert_kernel(ConvTable<S, D> tab, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (int a = 0; a < tab.count; ++a) {
-    const S* src = tab.src[a];
-    D* dst = tab.dst[a];
+    const S* __restrict__ src = tab.src[a];
+    D* __restrict__ dst = tab.dst[a];
     const size_t n = tab.n[a];
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride)
-      dst[e] = convert_one<S, D>(src[e]);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += kConvUnroll * stride) {
+      S v[kConvUnroll];
+#pragma unroll
+      for (int u = 0; u < kConvUnroll; ++u) {
+        const size_t i = e + u * stride;
+        v[u] = i < n ? src[i] : S(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kConvUnroll; ++u) {
+        const size_t i = e + u * stride;
+        if (i < n) dst[i] = convert_one<S, D>(v[u]);
+      }
+    }
   }
 }
 
 template <typename S, typename D>
 cudaError_t launch_convert(const ConvTable<S, D>& tab, const int* skip, cudaStream_t st) {
   if (tab.count == 0) return cudaSuccess;
-  convert_kernel<S, D><<<4 * device_sm_count(), 256, 0, st>>>(tab, skip);
+  // one wave: as many CTAs as the multiprocessors hold at once
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, convert_kernel<S, D>, 256, 0) != cudaSuccess ||
+       per_sm < 1))
+    per_sm = 4;
+  convert_kernel<S, D><<<per_sm * device_sm_count(), 256, 0, st>>>(tab, skip);
   return cudaGetLastError();
 }
 

@@ -399,14 +399,13 @@ __global__ void __launch_bounds__(kKktBlock, NC >= 4 ? 3 : 4)  // 80 / 64 regist
 
 // Turns the accumulators into eta, rel and the cost; decides convergence.
 // report: [0] cost, [1] eta, [2] rel, [3] refinement iterations applied.
-__device__ void finalize_body(ProbDesc pd, double* acc, int nblocks, double tol, int* skip, int is_final,
+// cost: the sum of the per-block objective partial sums of the pass.
+__device__ void finalize_body(ProbDesc pd, double* acc, double cost, double tol, int* skip, int is_final,
                               int check_convergence) {
   if (*(volatile int*)pd.status != 0) return;
   // already converged: the solution has not changed since the pass that found
   // it converged, whose numbers stand (the final pass was skipped as well)
   if (skip && *skip) return;
-  double cost = 0.0;
-  for (int b = 0; b < nblocks; ++b) cost += acc[RS_COUNT + b];
   const double r = acc[RS_RNORM], k = acc[RS_KNORM], w = acc[RS_WNORM], bn = acc[RS_BNORM];
   const double eta = r / (k * w + bn);
   const double rel = bn > 0.0 ? r / bn : r;
@@ -428,8 +427,13 @@ __device__ void finalize_body(ProbDesc pd, double* acc, int nblocks, double tol,
 __global__ void residual_finalize_kernel(ProbDesc pd, double* acc, int nblocks, double tol, int* skip,
                                          int is_final, int check_convergence, int loop,
                                          cudaGraphConditionalHandle cond) {
+  // the objective's block partial sums over the warp's lanes (one dependent
+  // FP64 add per 32 blocks instead of one per block)
+  double cost = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) cost += acc[RS_COUNT + b];
+  cost = kkt_warp_sum(cost);
   if (threadIdx.x != 0) return;
-  finalize_body(pd, acc, nblocks, tol, skip, is_final, check_convergence);
+  finalize_body(pd, acc, cost, tol, skip, is_final, check_convergence);
   if (loop > 0) {
     const int it = skip[2] + 1;
     skip[2] = it;
@@ -529,123 +533,158 @@ cudaError_t launch_kkt_residual(const ProbDesc& pd, double* acc, const KktOut& o
 // initial-condition rows (1). It depends on the data alone, so the mixed-
 // precision refinement takes it once per solve, in FP32 (it only scales the
 // reported backward error), instead of in an FP64 residual pass.
-__global__ void kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
+//
+// A CTA takes stages blockIdx.x, blockIdx.x + gridDim.x, ...; each stage is a
+// sequence of items (Q_t, A_t, B_t, S_t, R_t; Q_T alone for t = T), one matrix
+// each, copied whole into a ring of S shared-memory slots (16-byte cp.async
+// where aligned) S - 1 items ahead of the one being summed. Each row or column
+// sum is one thread's loop: columns read down (consecutive threads, distinct
+// banks), rows read from the thread's own diagonal on (thread i starts at
+// column i mod C), and a symmetrised row i of Q pairs row i with column i.
+template <int S>
+__global__ void __launch_bounds__(256) kkt_norm_f32_kernel(ProbDesc pd, double* acc) {
   extern __shared__ __align__(16) float nsm[];
   if (*(volatile int*)pd.status != 0) return;
-  const int n = pd.n, m = pd.m, T = pd.T;
-  const int d = n > m ? n : m, ld = d + 1;
+  const int n = pd.n, m = pd.m, T = pd.T, tid = threadIdx.x, nthr = blockDim.x;
   const size_t nn = (size_t)n * n, nm = (size_t)n * m, mm = (size_t)m * m;
+  const int slot = (int)((((nn > nm ? nn : nm) > mm ? (nn > nm ? nn : nm) : mm) + 3) & ~(size_t)3);
   const float* gA = static_cast<const float*>(pd.A);
   const float* gB = static_cast<const float*>(pd.B);
   const float* gQ = static_cast<const float*>(pd.Q);
   const float* gR = static_cast<const float*>(pd.R);
   const float* gS = static_cast<const float*>(pd.S);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  float* tile = nsm;            // a symmetric block, row stride d + 1
-  float* xr = tile + d * ld;    // x rows
-  float* dr = xr + n;           // dynamics rows
-  float* ur = dr + n;           // u rows
-  float* part = ur + m;         // [nw][d] column sums of each warp's rows
-  float kmax = 1.0f;            // the initial-condition rows
-  // row sums of |(M + M')/2| of the dd x dd block in the tile, added to out[i] by
-  // lane 0 of warp i % nw
-  auto sym_rows = [&](int dd, float* out) {
-    for (int i = warp; i < dd; i += nw) {
-      float s = 0.0f;
-      for (int k = lane; k < dd; k += 32) s += fabsf(0.5f * (tile[i * ld + k] + tile[k * ld + i]));
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) out[i] += s;
+  float* xr = nsm + S * slot;  // x rows
+  float* dr = xr + n;          // dynamics rows
+  float* ur = dr + n;          // u rows
+  const int ipt = gS ? 5 : 4;  // items of a stage t < T
+  const int nst = (T + 1 - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int last_t = (int)blockIdx.x + (nst - 1) * (int)gridDim.x;
+  const int nitems = nst <= 0 ? 0 : (nst - 1) * ipt + (last_t == T ? 1 : ipt);
+  // item k: stage t = blockIdx.x + (k / ipt) gridDim.x, matrix k % ipt (0 Q, 1 A, 2 B, 3 R, 4 S)
+  auto item_src = [&](int k, int* rows, int* cols) -> const float* {
+    const int t = (int)blockIdx.x + (k / ipt) * (int)gridDim.x, w = k % ipt;
+    switch (w) {
+      case 0: *rows = n; *cols = n; return gQ + nn * t;
+      case 1: *rows = n; *cols = n; return gA + nn * t;
+      case 2: *rows = n; *cols = m; return gB + nm * t;
+      case 3: *rows = m; *cols = m; return gR + mm * t;
+      default: *rows = m; *cols = n; return gS + nm * t;
     }
   };
-  // |M| of a row-major R x C block (C <= 256): row sums added to rows[i] by lane 0
-  // of warp i % nw; column sums of the warp's rows into part[warp][.] (columns to
-  // lanes, coalesced, in registers)
-  auto abs_pass = [&](const float* M, int R, int C, float* rows) {
-    float cs[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) cs[c] = 0.0f;
-    for (int i = warp; i < R; i += nw) {
+  auto issue = [&](int k) {
+    if (k < nitems) {
+      int r, c;
+      const float* src = item_src(k, &r, &c);
+      cta_copy_async(nsm + (k % S) * slot, src, (long long)r * c);
+    }
+    cp_async_commit();
+  };
+  // |M| row sums (rotated start) into rows[], column sums into cols[] (either may be null)
+  auto abs_sums = [&](const float* M, int R, int C, float* rows, float* cols) {
+    const int nr = rows ? R : 0, tasks = nr + (cols ? C : 0);
+    for (int x = tid; x < tasks; x += nthr) {
       float s = 0.0f;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int k = lane + 32 * c;
-        if (k < C) {
-          const float v = fabsf(M[(size_t)i * C + k]);
-          s += v;
-          cs[c] += v;
+      if (x < nr) {
+        const float* row = M + x * C;
+        int c = x % C;
+        for (int l = 0; l < C; ++l) {
+          s += fabsf(row[c]);
+          c = c + 1 == C ? 0 : c + 1;
         }
+        rows[x] += s;
+      } else {
+        const int j = x - nr;
+        for (int i = 0; i < R; ++i) s += fabsf(M[i * C + j]);
+        cols[j] += s;
       }
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) rows[i] += s;
-    }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int k = lane + 32 * c;
-      if (k < C) part[warp * d + k] = cs[c];
     }
   };
-  auto add_parts = [&](int C, float* cols) {  // after a barrier
-    for (int k = threadIdx.x; k < C; k += blockDim.x) {
+  // |(M + M')/2| row sums of a d x d block into rows[]
+  auto sym_sums = [&](const float* M, int d, float* rows) {
+    for (int i = tid; i < d; i += nthr) {
       float s = 0.0f;
-      for (int w = 0; w < nw; ++w) s += part[w * d + k];
-      cols[k] += s;
+      int c = i;
+      for (int l = 0; l < d; ++l) {
+        s += fabsf(0.5f * (M[i * d + c] + M[c * d + i]));
+        c = c + 1 == d ? 0 : c + 1;
+      }
+      rows[i] += s;
     }
   };
-  for (int t = blockIdx.x; t <= T; t += gridDim.x) {
-    const bool term = (t == T);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      xr[i] = 1.0f;
-      dr[i] = 1.0f;
+  float kmax = 1.0f;  // the initial-condition rows
+  for (int i = tid; i < n; i += nthr) xr[i] = dr[i] = 1.0f;
+  for (int a = tid; a < m; a += nthr) ur[a] = 0.0f;
+  for (int k = 0; k < S - 1; ++k) issue(k);
+  for (int k = 0; k < nitems; ++k) {
+    cp_async_wait<(S >= 2 ? S - 2 : 0)>();
+    __syncthreads();  // item k in its slot; item k - 1 (and its slot) finished
+    issue(k + S - 1);
+    if (S == 1) {
+      cp_async_wait<0>();
+      __syncthreads();
     }
-    for (int a = threadIdx.x; a < m; a += blockDim.x) ur[a] = 0.0f;
-    const float* Q = gQ + nn * t;
-    cta_for_rc(n, n, [&](int e, int i, int j) { tile[i * ld + j] = Q[e]; });
-    __syncthreads();
-    sym_rows(n, xr);  // x rows: |Q_sym| (the terminal rows: |Q_T,sym| + 1)
-    if (!term) {
-      abs_pass(gA + nn * t, n, n, dr);  // |A|: rows (dynamics), columns (x rows)
+    const float* M = nsm + (k % S) * slot;
+    const int w = k % ipt;
+    if (w == 0) sym_sums(M, n, xr);
+    else if (w == 1) abs_sums(M, n, n, dr, xr);
+    else if (w == 2) abs_sums(M, n, m, dr, ur);
+    else if (w == 3) sym_sums(M, m, ur);
+    else abs_sums(M, m, n, ur, xr);
+    const int t = (int)blockIdx.x + (k / ipt) * (int)gridDim.x;
+    if (w == ipt - 1 || t == T) {  // the stage's last item
       __syncthreads();
-      add_parts(n, xr);
-      __syncthreads();
-      abs_pass(gB + nm * t, n, m, dr);  // |B|: rows (dynamics), columns (u rows)
-      __syncthreads();
-      add_parts(m, ur);
-      __syncthreads();
-      if (gS) {
-        abs_pass(gS + nm * t, m, n, ur);  // |S|: rows (u rows), columns (x rows)
-        __syncthreads();
-        add_parts(n, xr);
-        __syncthreads();
+      for (int i = tid; i < n; i += nthr) {
+        kmax = fmaxf(kmax, t == T ? xr[i] : fmaxf(xr[i], dr[i]));
+        xr[i] = dr[i] = 1.0f;
       }
-      const float* R = gR + mm * t;
-      cta_for_rc(m, m, [&](int e, int i, int j) { tile[i * ld + j] = R[e]; });
-      __syncthreads();
-      sym_rows(m, ur);  // u rows: |R_sym|
+      for (int a = tid; a < m; a += nthr) {
+        if (t != T) kmax = fmaxf(kmax, ur[a]);
+        ur[a] = 0.0f;
+      }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) kmax = fmaxf(kmax, term ? xr[i] : fmaxf(xr[i], dr[i]));
-    if (!term)
-      for (int a = threadIdx.x; a < m; a += blockDim.x) kmax = fmaxf(kmax, ur[a]);
-    __syncthreads();
+    if (S == 1) __syncthreads();  // the single slot is refilled at the next item
   }
+  cp_async_wait<0>();
   __shared__ double red[32];
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
   const double v = warp_max((double)kmax);
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double b = red[0];
     for (int w = 1; w < nw; ++w) b = fmax(b, red[w]);
     atomic_max_nonneg(acc + RS_KNORM, b);
   }
 }
 
+static size_t kkt_norm_slot_floats(int n, int m) {
+  size_t s = (size_t)n * n;
+  if ((size_t)n * m > s) s = (size_t)n * m;
+  if ((size_t)m * m > s) s = (size_t)m * m;
+  return (s + 3) & ~(size_t)3;
+}
+
 cudaError_t launch_kkt_norm_f32(const ProbDesc& pd, double* acc, cudaStream_t st) {
-  const int d = pd.n > pd.m ? pd.n : pd.m;
-  const size_t bytes = sizeof(float) * ((size_t)d * (d + 1) + 2 * (size_t)pd.n + pd.m + 8 * (size_t)d);
-  cudaError_t e = raise_dyn_smem((const void*)kkt_norm_f32_kernel, bytes);
-  if (e != cudaSuccess) return e;
-  kkt_norm_f32_kernel<<<residual_grid(pd.T + 1), 256, bytes, st>>>(pd, acc);
-  return cudaGetLastError();
+  const size_t slot = kkt_norm_slot_floats(pd.n, pd.m), vec = 2 * (size_t)pd.n + pd.m;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return cudaGetLastError();
+  const size_t budget = (size_t)optin - 1024;
+  const int g = residual_grid(pd.T + 1);
+  for (int S = 3; S >= 1; --S) {
+    const size_t bytes = sizeof(float) * (S * slot + vec);
+    if (bytes > budget) continue;
+    const void* f = S == 3 ? (const void*)kkt_norm_f32_kernel<3>
+                           : S == 2 ? (const void*)kkt_norm_f32_kernel<2> : (const void*)kkt_norm_f32_kernel<1>;
+    cudaError_t e = raise_dyn_smem(f, bytes);
+    if (e != cudaSuccess) return e;
+    if (S == 3) kkt_norm_f32_kernel<3><<<g, 256, bytes, st>>>(pd, acc);
+    else if (S == 2) kkt_norm_f32_kernel<2><<<g, 256, bytes, st>>>(pd, acc);
+    else kkt_norm_f32_kernel<1><<<g, 256, bytes, st>>>(pd, acc);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_residual_finalize_loop(const ProbDesc& pd, double* acc, double tol, int* skip, int loop,

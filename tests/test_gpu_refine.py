@@ -156,20 +156,21 @@ def test_mixed_fp32_correction_paths(solver):
     reuse the solve's K_t, P_t and M_uu^-1 and the refinement loop runs as a
     CUDA graph whose loop body is one iteration: the residual pass writing the
     FP32 correction vectors (two kernels, double-FP32 and FP64, gated on the
-    iteration count), finalize, four segment passes, two link chains, update:
-    10 kernels per executed iteration when a chain is one kernel. With K >= 32
-    segments each link chain runs in two levels over groups of ceil(sqrt(K))
-    links (group offsets, the chain over the groups, the fill: three kernels),
-    14 kernels per iteration; K = 40 leaves a short last group, K = 49 none.
-    n=136: beyond the link-chain plan of the corrections and the register plan
-    of the residual kernels, so each correction is a whole FP32 solve launched
-    from the host (residual, finalize and update around the kernels of a plain
-    FP32 solve of that shape). All reach the oracle at 1e-9."""
-    cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, 10),
-             (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, 10),
-             (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, 10),
-             (workloads.make_problem(64, 32, 400, seed=615, rho_max=1.02), 40, 14),
-             (workloads.make_problem(128, 64, 392, seed=616, rho_max=1.02), 49, 14),
+    iteration count), finalize, the correction (three per-stage kernels, four
+    segment recursions, two link chains), update: 13 kernels per executed
+    iteration when a chain is one kernel. With K >= 32 segments each link
+    chain runs in two levels over groups of ceil(sqrt(K)) links (group
+    offsets, the chain over the groups, the fill: three kernels), 17 kernels
+    per iteration; K = 40 leaves a short last group, K = 49 none. n=136: the
+    closed-loop maps' plan does not fit the shared memory, so each correction
+    is a whole FP32 solve launched from the host (residual, finalize and update
+    around the kernels of a plain FP32 solve of that shape). All reach the
+    oracle at 1e-9."""
+    cases = [(workloads.make_problem(64, 32, 256, seed=611, rho_max=1.02), 16, 13),
+             (workloads.make_problem(72, 32, 288, seed=612, rho_max=1.02), 16, 13),
+             (workloads.make_problem(128, 64, 256, seed=613, rho_max=1.02), 16, 13),
+             (workloads.make_problem(64, 32, 400, seed=615, rho_max=1.02), 40, 17),
+             (workloads.make_problem(128, 64, 392, seed=616, rho_max=1.02), 49, 17),
              (workloads.make_problem(136, 8, 160, seed=614, rho_max=1.02), 4, None)]
     for prob, K, expect in cases:
         per = _launches_per_correction(solver, prob, K)
