@@ -134,6 +134,12 @@ typedef struct {
                          tensor-core sweep's waits for its own products) before it
                          gives up with LQR_ERR_TIMEOUT, releases its tensor memory and
                          returns; 0 = 2^26 (about two seconds)                       */
+  int refine_plain;   /* mixed modes: 0 = the refinement loop runs as one CUDA graph
+                         (a WHILE node around one iteration, ended on the device at
+                         convergence) where the graph can be built; 1 = the loop's
+                         kernels are launched one by one from the host, every
+                         iteration up to max_refine (a converged one returns at once
+                         on the device). Same kernels and results either way.     */
 } lqr_opts;
 
 /* Scalars of the last solve, read back by lqr_report(). */

@@ -620,7 +620,7 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
     cvec.q = (void*)cp.q; cvec.r = (void*)cp.r; cvec.c = (void*)cp.c; cvec.x0 = (void*)cp.x0; cvec.f32 = 1;
     h->last_iters = nullptr;
     bool looped = false;
-    if (reuse && o->max_refine > 0 && !h->rgraph_broken) {
+    if (reuse && o->max_refine > 0 && !h->rgraph_broken && !o->refine_plain) {
       // the loop as a graph: one iteration's kernels under a WHILE node
       RefineGraphArgs ga;
       memset(&ga, 0, sizeof(ga));

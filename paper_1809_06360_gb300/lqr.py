@@ -48,7 +48,7 @@ class lqr_solution(ctypes.Structure):
 class lqr_opts(ctypes.Structure):
     _fields_ = [("prec", c_int), ("num_segments", c_int), ("tol", c_double), ("max_refine", c_int),
                 ("debug_checks", c_int), ("form", c_int), ("residual", c_int), ("link", c_int),
-                ("spin_limit", ctypes.c_longlong)]
+                ("spin_limit", ctypes.c_longlong), ("refine_plain", c_int)]
 
 
 class lqr_report_t(ctypes.Structure):
@@ -325,7 +325,8 @@ class Solver:
         return out
 
     def solve(self, prob, num_segments=0, prec="fp64", out=None, want=("K", "k", "x", "u", "lam"),
-              stream=None, tol=1e-8, max_refine=0, form="multiplier", residual=False, link="auto", spin_limit=0):
+              stream=None, tol=1e-8, max_refine=0, form="multiplier", residual=False, link="auto", spin_limit=0,
+              refine_plain=False):
         """Enqueue a solve on `stream` (torch stream; default current). Returns the output tensors."""
         if out is None:
             out = self.alloc_solution(prob, want)
@@ -334,7 +335,7 @@ class Solver:
         s = lqr_solution(**{f: (out[f].data_ptr() if f in out else None) for f in SOLUTION_FIELDS})
         o = lqr_opts(prec=PRECISION[prec], num_segments=num_segments, tol=tol, max_refine=max_refine,
                      debug_checks=0, form=FORM[form], residual=1 if residual else 0, link=LINK[link],
-                     spin_limit=spin_limit)
+                     spin_limit=spin_limit, refine_plain=1 if refine_plain else 0)
         lqr_solve(self.h, p, o, s, self._stream(stream))
         return out
 

@@ -211,6 +211,28 @@ def test_refinement_graph_stops_at_convergence(solver):
     assert oracle.rel_err(res[8][1][1]["x"], ref["x"]) < 1e-9
 
 
+def test_refinement_plain_launches_match_graph(solver):
+    """refine_plain = 1 launches the refinement loop's kernels one by one from
+    the host instead of as the graph: the same kernels in the same order, so the
+    answer and the report are the same bit for bit; every iteration up to
+    max_refine is launched (the converged ones return at once on the device), so
+    the plain loop reports more launches."""
+    prob = workloads.make_problem(64, 32, 512, seed=619, rho_max=1.02)
+    dev = to_dev(prob)
+    outs, reps, counts = [], [], []
+    for plain in (False, True, False):
+        outs.append(host(solver.solve(dev, num_segments=32, prec="mixed_fp32", max_refine=8, tol=1e-10,
+                                      refine_plain=plain)))
+        reps.append(solver.report())
+        counts.append(solver.last_launch_count())
+    for rep in reps:
+        assert rep["status"] == 0 and rep["refine_iters"] == 2, rep
+    for k in ("x", "u", "lam", "k"):
+        assert np.array_equal(outs[0][k], outs[1][k]) and np.array_equal(outs[0][k], outs[2][k]), k
+    assert reps[0]["kkt_rel"] == reps[1]["kkt_rel"] and reps[0]["cost"] == reps[1]["cost"]
+    assert counts[0] == counts[2] < counts[1], counts
+
+
 @pytest.mark.parametrize("K", [64, 152])
 def test_mixed_fp32_config1(solver, K):
     """LQR_MIXED_FP32: FP64 data; the solve runs the FP32 path (FP32 sweeps,
