@@ -85,6 +85,9 @@ struct lqr_handle {
   // side stream: the A4 sweep runs on it next to the link tail (fork/join by events)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // lqr_solve_host: the policies' copy back to the host beside the refinement
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_kready = nullptr, ev_kdone = nullptr;
   // LQR_MIXED_FP32: FP32 copy of the data, FP32 solution and correction buffers
   unsigned char* f32 = nullptr;
   size_t f32_bytes = 0;
@@ -469,8 +472,12 @@ lqr_status enqueue_pipeline(lqr_handle* h, const ProbTable& tab, const SolvePlan
 
 // LQR_MIXED_FP32: the FP32 path on an FP32 copy of the data, solution kept in
 // FP64, FP64 residual and refinement corrections by the FP32 path.
+// src (may be null): the inputs as device-visible pointers to host memory; the
+// conversion then reads them once and also writes the FP64 copies into p's
+// arrays. k_ready (may be null) is recorded once s->K holds its final values.
 lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts* o, const lqr_solution* s,
-                             cudaStream_t st, bool summary_only, SolvePlan* sp_out, bool tensor_cores = false) {
+                             cudaStream_t st, bool summary_only, SolvePlan* sp_out, bool tensor_cores = false,
+                             const lqr_problem* src = nullptr, cudaEvent_t k_ready = nullptr) {
   SolvePlan sp;
   lqr_status rs = plan_solve(h, p, o, &sp);
   if (rs != LQR_OK) return rs;
@@ -528,15 +535,17 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
   {
     ConvTable<double, float> ct;
     ct.count = 0;
-    ct.add(p->A, (void*)p32.A, (size_t)T * nn);
-    ct.add(p->B, (void*)p32.B, (size_t)T * nm);
-    ct.add(p->c, (void*)p32.c, (size_t)T * n);
-    ct.add(p->Q, (void*)p32.Q, (size_t)(T + 1) * nn);
-    ct.add(p->R, (void*)p32.R, (size_t)T * mm);
-    ct.add(p->S, (void*)p32.S, (size_t)T * nm);
-    ct.add(p->q, (void*)p32.q, (size_t)(T + 1) * n);
-    ct.add(p->r, (void*)p32.r, (size_t)T * m);
-    ct.add(p->x0, (void*)p32.x0, (size_t)n);
+    const lqr_problem* cs = src ? src : p;  // where the conversion reads
+    auto raw = [&](const void* d) { return src ? const_cast<void*>(d) : nullptr; };
+    ct.add(cs->A, (void*)p32.A, (size_t)T * nn, raw(p->A));
+    ct.add(cs->B, (void*)p32.B, (size_t)T * nm, raw(p->B));
+    ct.add(cs->c, (void*)p32.c, (size_t)T * n, raw(p->c));
+    ct.add(cs->Q, (void*)p32.Q, (size_t)(T + 1) * nn, raw(p->Q));
+    ct.add(cs->R, (void*)p32.R, (size_t)T * mm, raw(p->R));
+    ct.add(cs->S, (void*)p32.S, (size_t)T * nm, raw(p->S));
+    ct.add(cs->q, (void*)p32.q, (size_t)(T + 1) * n, raw(p->q));
+    ct.add(cs->r, (void*)p32.r, (size_t)T * m, raw(p->r));
+    ct.add(cs->x0, (void*)p32.x0, (size_t)n, raw(p->x0));
     if (launch_convert(ct, nullptr, st) != cudaSuccess) return LQR_ERR_CUDA;
   }
   lqr_opts o32 = *o;
@@ -566,6 +575,8 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
     }
     if (launch_convert(ct, nullptr, st) != cudaSuccess) return LQR_ERR_CUDA;
     ++launches;
+    // K_t is final here (the refinement corrects k, x, u, lambda and p only)
+    if (k_ready && cudaEventRecord(k_ready, st) != cudaSuccess) return LQR_ERR_CUDA;
   }
   prof_mark(h, LQR_PHASE_REFINE, st);
   if (!summary_only && sp.rbase >= 0) {
@@ -1232,6 +1243,9 @@ lqr_status lqr_destroy(lqr_handle* h) {
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_kready) cudaEventDestroy(h->ev_kready);
+  if (h->ev_kdone) cudaEventDestroy(h->ev_kdone);
+  if (h->copy) cudaStreamDestroy(h->copy);
   if (h->side) cudaStreamDestroy(h->side);
   delete h;
   return LQR_OK;
@@ -1626,8 +1640,33 @@ lqr_status lqr_solve_host(lqr_handle* h, const lqr_problem* ph, const lqr_opts* 
   if (r != LQR_OK) return r;
   void* dptr[16];
   for (int i = 0; i < 16; ++i) dptr[i] = h->stage + off[i];
+  // LQR_MIXED_FP32 with every input in page-locked host memory mapped into the
+  // device's address space: the FP64 -> FP32 conversion reads the inputs over
+  // the host link once and writes both the FP32 working copy and the FP64 copy
+  // (the copy engines move the same bytes no faster; this saves the separate
+  // pass over the FP64 copy). Anything else: copies by the copy engines.
+  const void* mapped[9] = {nullptr};
+  bool zero_copy = (o->prec == LQR_MIXED_FP32);
+  for (int i = 0; i < 9 && zero_copy; ++i) {
+    if (!arrs[i].src) continue;
+    // both ends of the array mapped, at the same offset apart on the device side
+    const size_t bytes = arrs[i].elems * es;
+    const unsigned char* last = static_cast<const unsigned char*>(arrs[i].src) + bytes - 1;
+    cudaPointerAttributes at, at_end;
+    if (cudaPointerGetAttributes(&at, arrs[i].src) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+        at.devicePointer == nullptr || cudaPointerGetAttributes(&at_end, last) != cudaSuccess ||
+        at_end.type != cudaMemoryTypeHost ||
+        static_cast<const unsigned char*>(at_end.devicePointer) !=
+            static_cast<const unsigned char*>(at.devicePointer) + (bytes - 1)) {
+      cudaGetLastError();  // clear a lookup error of unregistered memory
+      zero_copy = false;
+    } else {
+      mapped[i] = at.devicePointer;
+    }
+  }
   for (int i = 0; i < 9; ++i) {
     if (!arrs[i].src) { dptr[i] = nullptr; continue; }
+    if (zero_copy) continue;
     if (cudaMemcpyAsync(dptr[i], arrs[i].src, arrs[i].elems * es, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return LQR_ERR_CUDA;
   }
@@ -1641,8 +1680,35 @@ lqr_status lqr_solve_host(lqr_handle* h, const lqr_problem* ph, const lqr_opts* 
   sd.P = sh->P ? dptr[13] : nullptr;
   sd.p = sh->p ? dptr[14] : nullptr;
   sd.lam = sh->lam ? dptr[15] : nullptr;
-  r = run_solve(h, &pd, o, &sd, st, false, nullptr);
-  if (r != LQR_OK) return r;
+  if (o->prec == LQR_MIXED_FP32) {
+    // the policies K_t go back on the copy stream while the refinement runs
+    const bool k_early = arrs[9].dst_host != nullptr && o->max_refine > 0;
+    if (k_early && !h->copy) {
+      if (cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_kready, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_kdone, cudaEventDisableTiming) != cudaSuccess)
+        return LQR_ERR_CUDA;
+    }
+    lqr_problem src = *ph;
+    if (zero_copy) {
+      src.A = mapped[0]; src.B = mapped[1]; src.c = mapped[2]; src.Q = mapped[3]; src.R = mapped[4];
+      src.S = mapped[5]; src.q = mapped[6]; src.r = mapped[7]; src.x0 = mapped[8];
+    }
+    r = run_solve_mixed32(h, &pd, o, &sd, st, false, nullptr, false, zero_copy ? &src : nullptr,
+                          k_early ? h->ev_kready : nullptr);
+    if (r != LQR_OK) return r;
+    if (k_early) {
+      if (cudaStreamWaitEvent(h->copy, h->ev_kready, 0) != cudaSuccess ||
+          cudaMemcpyAsync(arrs[9].dst_host, dptr[9], arrs[9].elems * es, cudaMemcpyDeviceToHost, h->copy) !=
+              cudaSuccess ||
+          cudaEventRecord(h->ev_kdone, h->copy) != cudaSuccess || cudaStreamWaitEvent(st, h->ev_kdone, 0) != cudaSuccess)
+        return LQR_ERR_CUDA;
+      arrs[9].dst_host = nullptr;  // copied
+    }
+  } else {
+    r = run_solve(h, &pd, o, &sd, st, false, nullptr);
+    if (r != LQR_OK) return r;
+  }
   for (int i = 9; i < 16; ++i) {
     if (!arrs[i].dst_host) continue;
     if (cudaMemcpyAsync(arrs[i].dst_host, dptr[i], arrs[i].elems * es, cudaMemcpyDeviceToHost, st) != cudaSuccess)

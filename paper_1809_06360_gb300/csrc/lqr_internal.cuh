@@ -303,12 +303,14 @@ template <typename S, typename D>
 struct ConvTable {
   const S* src[kMaxConv];
   D* dst[kMaxConv];
+  S* raw[kMaxConv];  // when non-null: also an unconverted copy of the source
   size_t n[kMaxConv];
   int count;
-  void add(const void* s, void* d, size_t cnt) {
+  void add(const void* s, void* d, size_t cnt, void* raw_copy = nullptr) {
     if (!s || !d || cnt == 0) return;
     src[count] = static_cast<const S*>(s);
     dst[count] = static_cast<D*>(d);
+    raw[count] = static_cast<S*>(raw_copy);
     n[count] = cnt;
     ++count;
   }

@@ -49,7 +49,9 @@ __device__ __forceinline__ float convert_one<double, float>(double v) {
 }
 
 // Up to kMaxConv arrays converted in one launch; grid-stride over each, four
-// independent loads per thread in flight (coalesced across the warp).
+// independent loads per thread in flight (coalesced across the warp). A source
+// may be host memory mapped into the device's address space, read once over the
+// host link, with `raw` taking the unconverted copy into device memory.
 constexpr int kConvUnroll = 4;
 template <typename S, typename D>
 __global__ void __launch_bounds__(256) convert_kernel(ConvTable<S, D> tab, const int* skip) {
@@ -58,6 +60,7 @@ __global__ void __launch_bounds__(256) convert_kernel(ConvTable<S, D> tab, const
   for (int a = 0; a < tab.count; ++a) {
     const S* __restrict__ src = tab.src[a];
     D* __restrict__ dst = tab.dst[a];
+    S* __restrict__ raw = tab.raw[a];
     const size_t n = tab.n[a];
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += kConvUnroll * stride) {
       S v[kConvUnroll];
@@ -69,7 +72,10 @@ __global__ void __launch_bounds__(256) convert_kernel(ConvTable<S, D> tab, const
 #pragma unroll
       for (int u = 0; u < kConvUnroll; ++u) {
         const size_t i = e + u * stride;
-        if (i < n) dst[i] = convert_one<S, D>(v[u]);
+        if (i < n) {
+          dst[i] = convert_one<S, D>(v[u]);
+          if (raw) raw[i] = v[u];
+        }
       }
     }
   }

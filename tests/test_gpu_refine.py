@@ -105,6 +105,25 @@ def test_mixed_host_entry_point(solver):
     assert oracle.rel_err(out["x"], ref["x"]) < 1e-9
 
 
+def test_mixed_fp32_host_entry_pinned_and_pageable(solver):
+    """lqr_solve_host in LQR_MIXED_FP32: with every input in mapped page-locked
+    host memory the conversion kernel reads the inputs over the host link and
+    writes the FP64 copy itself; with pageable inputs the copy engines stage
+    them; K_t goes back on a copy stream beside the refinement. Either way the
+    answer is the device entry point's, bit for bit."""
+    prob = workloads.make_problem(32, 8, 300, seed=620, rho_max=1.02)
+    want = ("K", "k", "x", "u", "lam")
+    dev_out = host(solver.solve(to_dev(prob), num_segments=8, prec="mixed_fp32", max_refine=8, tol=1e-10))
+    assert solver.report()["status"] == 0
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in prob.items()}
+    for inputs in (pinned, prob):
+        out = solver.solve_host(inputs, num_segments=8, prec="mixed_fp32", want=want, max_refine=8, tol=1e-10)
+        rep = solver.report()
+        assert rep["status"] == 0 and rep["refine_iters"] >= 1, rep
+        for k in want:
+            assert np.array_equal(out[k], dev_out[k]), k
+
+
 @pytest.mark.parametrize("prec", ["mixed", "mixed_fp32"])
 @pytest.mark.parametrize("n,m,T,K", [(3, 5, 20, 4), (8, 16, 96, 8), (2, 9, 40, 5)])
 def test_refinement_with_more_controls_than_states(solver, prec, n, m, T, K):
