@@ -74,19 +74,6 @@ __device__ __forceinline__ void copy_pad(float* dst, int ldd, const float* src, 
   cta_for_rc(rows, cols, [&](int, int i, int j) { cp_async4(dst + i * ldd + j, src + (long long)i * lds + j); });
 }
 
-// ---- bulk asynchronous copies into shared memory, completion on an mbarrier ----
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-// bytes a multiple of 16, both addresses 16-byte aligned
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   tc::smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(tc::smem_addr(bar))
-               : "memory");
-}
-
 }  // namespace
 
 size_t corr_rec_smem_bytes(int n, int slots) {
@@ -280,8 +267,8 @@ __global__ void __launch_bounds__(kRecBlock) corr_rec_kernel(RecArgs a, int dir)
     for (int e = tid; e < n; e += nthr) a.all[a.astride * hi + e] = ybuf[e];
   auto issue = [&](int idx, int sl) {  // one thread of the issuing warp
     const int k = dir == 0 ? hi - 1 - idx : lo + idx;
-    mbar_expect_tx(&s_bar[sl], bytes);
-    bulk_g2s(csm + sl * slot_f, a.C + a.cstride * k, bytes, &s_bar[sl]);
+    tc::mbar_expect_tx(&s_bar[sl], bytes);
+    tc::bulk_g2s(csm + sl * slot_f, a.C + a.cstride * k, bytes, &s_bar[sl]);
   };
   // Each step starts at a barrier of the whole CTA, after which: the consumers
   // have finished step idx - 1 (its slot may be refilled), the waiting warp has

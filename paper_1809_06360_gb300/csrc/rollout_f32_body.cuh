@@ -5,6 +5,7 @@
 
 #include "cta_linalg.cuh"
 #include "lqr_internal.cuh"
+#include "tc_sm100.cuh"
 
 namespace lqr {
 
@@ -31,9 +32,14 @@ __device__ __forceinline__ T roll_block_sum(T v, T* red) {
 //     g_t = (Q_t + Q_t')/2 x_t + S_t'u_t + q_t      (stored in lambda_t),
 // so that the backward walk lambda_t = A_t'lambda_{t+1} - g_t streams A_t only.
 // Row products: four threads per row, 128-bit loads; transposed products:
-// column partials over 512 / n4 row groups.
+// column partials over 512 / n4 row groups. With n and m multiples of 4 (and
+// 16-byte aligned arrays) every region of a slot has its array's global
+// layout, and one thread moves a stage with one bulk asynchronous copy per
+// array (completion counted in bytes on the slot's mbarrier); otherwise every
+// thread issues 16- or 4-byte cp.async copies.
 // ---------------------------------------------------------------------------
 constexpr int kRollBlock = 512;
+constexpr long long kRollSpin = 1LL << 25;  // polls of a stage-data wait (32 ns apart) before LQR_ERR_TIMEOUT
 
 struct FastRollSlot {
   int n4, m4;
@@ -90,6 +96,7 @@ __device__ __forceinline__ void rollout_f32_unit(const ProbTable& tab, int unit,
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag;
   __shared__ double s_red[kRollBlock / 32];
+  __shared__ __align__(8) uint64_t s_rbar[2];
   const ProbDesc& pd = prob_of_unit(tab, unit);
   if (cta_should_exit(pd, &s_flag)) return;
   const int seg = unit - pd.unit0;
@@ -130,14 +137,54 @@ __device__ __forceinline__ void rollout_f32_unit(const ProbTable& tab, int unit,
   const bool v16 = (n % 4 == 0) && (m % 4 == 0) && ral16(gA) && ral16(gB) && ral16(gQ) && ral16(gR) && ral16(gK) &&
                    (gS == nullptr || ral16(gS));
 
+  // bulk copies: slot regions laid out like the arrays (n4 = n, m4 = m)
+  const bool bulk = v16 && ral16(gc) && ral16(gq) && ral16(gk) && ral16(gr);
   // zero the ring and vectors once (padding stays zero)
   {
     const long long tot = 2 * stride + fast_roll_vec(nmax, mmax);
     float4* z4 = reinterpret_cast<float4*>(smem);
     for (long long i = tid; i < tot / 4; i += blockDim.x) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (bulk && tid == 0) {
+      tc::mbar_init(&s_rbar[0], 1);
+      tc::mbar_init(&s_rbar[1], 1);
+      tc::mbar_fence_init();
+    }
   }
   __syncthreads();
+  uint32_t rph = 0u;  // bit s: the parity of slot s's next completion
+  // waits for slot s (bulk) or for this thread's copies, then a barrier; false on
+  // a timeout (the same verdict in every thread)
+  auto slot_ready = [&](int s) -> bool {
+    bool ok = true;
+    if (bulk) {
+      ok = tc::mbar_wait(&s_rbar[s], (rph >> s) & 1u, kRollSpin);
+      rph ^= 1u << s;
+    } else {
+      cp_async_wait<0>();
+    }
+    return __syncthreads_or(!ok) == 0;
+  };
   auto fwd_issue = [&](int t) {
+    if (bulk) {
+      if (t < t1 && tid == 0) {
+        const int s = (t - t0) & 1;
+        float* d = ring + (long long)s * stride;
+        uint64_t* bar = &s_rbar[s];
+        const uint32_t bytes = (uint32_t)(4 * (2 * nm + 2 * nn + mm + (gS ? nm : 0) + 2 * n + 2 * m));
+        tc::mbar_expect_tx(bar, bytes);
+        tc::bulk_g2s(d + L.K, gK + nm * t, (uint32_t)(4 * nm), bar);
+        tc::bulk_g2s(d + L.A, gA + nn * t, (uint32_t)(4 * nn), bar);
+        tc::bulk_g2s(d + L.B, gB + nm * t, (uint32_t)(4 * nm), bar);
+        tc::bulk_g2s(d + L.Q, gQ + nn * t, (uint32_t)(4 * nn), bar);
+        tc::bulk_g2s(d + L.R, gR + mm * t, (uint32_t)(4 * mm), bar);
+        if (gS) tc::bulk_g2s(d + L.S, gS + nm * t, (uint32_t)(4 * nm), bar);
+        tc::bulk_g2s(d + L.c, gc + (long long)n * t, (uint32_t)(4 * n), bar);
+        tc::bulk_g2s(d + L.k, gk + (long long)m * t, (uint32_t)(4 * m), bar);
+        tc::bulk_g2s(d + L.q, gq + (long long)n * t, (uint32_t)(4 * n), bar);
+        tc::bulk_g2s(d + L.r, gr + (long long)m * t, (uint32_t)(4 * m), bar);
+      }
+      return;
+    }
     if (t < t1) {
       float* d = ring + (long long)((t - t0) & 1) * stride;
       roll_copy_rows(d + L.K, n4, gK + nm * t, n, m, n, v16);
@@ -196,9 +243,13 @@ __device__ __forceinline__ void rollout_f32_unit(const ProbTable& tab, int unit,
     for (int i = tid; i < n; i += blockDim.x) xb[i] = static_cast<float>(zj[i]);
   }
   double cost = 0.0;
+  bool timed_out = false;
   for (int t = t0; t < t1; ++t) {
-    cp_async_wait<0>();
-    __syncthreads();  // slot t and x_t ready; the previous stage is finished
+    // slot t and x_t ready; the previous stage is finished
+    if (!slot_ready((t - t0) & 1)) {
+      timed_out = true;
+      break;
+    }
     fwd_issue(t + 1);
     const float* d = ring + (long long)((t - t0) & 1) * stride;
     const float* xc = xb + ((t - t0) & 1) * n4x;
@@ -252,6 +303,15 @@ __device__ __forceinline__ void rollout_f32_unit(const ProbTable& tab, int unit,
       cost += static_cast<double>(ub[a]) *
               (0.5 * static_cast<double>(ru[a]) + (gS ? static_cast<double>(sx[a]) : 0.0) + static_cast<double>(d[L.r + a]));
   }
+  if (timed_out) {
+    // a stage's copy did not arrive: report it, give the copy issued after it one
+    // more bounded wait, stop
+    if (tid == 0) {
+      raise_status(pd.status, LQR_ERR_TIMEOUT, -1);
+      for (int s = 0; s < 2; ++s) tc::mbar_wait(&s_rbar[s], (rph >> s) & 1u, kRollSpin);
+    }
+    return;
+  }
   cp_async_wait<0>();
   __syncthreads();
   const float* xe = xb + ((t1 - t0) & 1) * n4x;  // x_{t1}
@@ -304,17 +364,39 @@ __device__ __forceinline__ void rollout_f32_unit(const ProbTable& tab, int unit,
     const double tot = roll_block_sum(cost, s_red);
     if (tid == 0) pd.ws[wl.costp + seg] = tot;
   }
-  if (!olam) return;
+  if (!olam) {
+    if (bulk) {
+      __syncthreads();
+      if (tid == 0) {
+        tc::mbar_inval(&s_rbar[0]);
+        tc::mbar_inval(&s_rbar[1]);
+      }
+    }
+    return;
+  }
   __syncthreads();
   // ---- backward: lambda_t = A_t'lambda_{t+1} - g_t, A_t streamed ----------------
   auto bwd_issue = [&](int t) {
-    if (t >= t0) roll_copy_rows(ring + (long long)((t1 - 1 - t) & 1) * stride + L.A, n4, gA + nn * t, n, n, n, v16);
+    const int s = (t1 - 1 - t) & 1;
+    if (bulk) {
+      if (t >= t0 && tid == 0) {
+        tc::mbar_expect_tx(&s_rbar[s], (uint32_t)(4 * nn));
+        tc::bulk_g2s(ring + (long long)s * stride + L.A, gA + nn * t, (uint32_t)(4 * nn), &s_rbar[s]);
+      }
+      return;
+    }
+    if (t >= t0) roll_copy_rows(ring + (long long)s * stride + L.A, n4, gA + nn * t, n, n, n, v16);
     cp_async_commit();
   };
   bwd_issue(t1 - 1);
   for (int t = t1 - 1; t >= t0; --t) {
-    cp_async_wait<0>();
-    __syncthreads();
+    if (!slot_ready((t1 - 1 - t) & 1)) {
+      if (tid == 0) {
+        raise_status(pd.status, LQR_ERR_TIMEOUT, -1);
+        for (int s = 0; s < 2; ++s) tc::mbar_wait(&s_rbar[s], (rph >> s) & 1u, kRollSpin);
+      }
+      return;
+    }
     bwd_issue(t - 1);
     const float* Ad = ring + (long long)((t1 - 1 - t) & 1) * stride + L.A;
     float* lnext = lb + (((t1 - 1 - t) + 1) & 1) * n4x;
@@ -330,6 +412,13 @@ __device__ __forceinline__ void rollout_f32_unit(const ProbTable& tab, int unit,
     lcur = lnext;
   }
   cp_async_wait<0>();
+  if (bulk) {
+    __syncthreads();
+    if (tid == 0) {
+      tc::mbar_inval(&s_rbar[0]);
+      tc::mbar_inval(&s_rbar[1]);
+    }
+  }
 }
 
 }  // namespace lqr
