@@ -55,6 +55,8 @@ def _perturbed(prob, seed, prec):
     (80, 16, 200, True, "fp64"),    # four columns for n, one for m
     (100, 70, 50, True, "fp64"),    # four columns for both
     (130, 5, 20, True, "fp64"),     # beyond the register plan: the generic loop
+    (130, 5, 20, False, "fp64"),    # the generic loop without S
+    (6, 130, 12, True, "fp64"),     # m > 128: the generic loop over the u rows
 ])
 def test_residual_at_perturbed_point_matches_oracle(solver, n, m, T, cross, prec):
     from paper_1809_06360_gb300 import lqr
