@@ -153,7 +153,7 @@ __device__ __forceinline__ void rollout_f32_unit(const ProbTable& tab, int unit,
   __syncthreads();
   uint32_t rph = 0u;  // bit s: the parity of slot s's next completion
   // waits for slot s (bulk) or for this thread's copies, then a barrier; false on
-  // a timeout (the same verdict in every thread)
+  // a timeout (the same answer in every thread)
   auto slot_ready = [&](int s) -> bool {
     bool ok = true;
     if (bulk) {
