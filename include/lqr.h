@@ -130,10 +130,13 @@ typedef struct {
   int residual;       /* 1 = compute the FP64 KKT residual of the returned solution
                          (needs x, u, lam); implied by max_refine > 0              */
   lqr_link link;      /* link-system solver, see lqr_link (0 = automatic)         */
-  long long spin_limit; /* polls (about 32 ns apart) of a bounded device wait (the
-                         tensor-core sweep's waits for its own products) before it
-                         gives up with LQR_ERR_TIMEOUT, releases its tensor memory and
-                         returns; 0 = 2^26 (about two seconds)                       */
+  long long spin_limit; /* polls (about 32 ns apart) of a bounded device wait before it
+                         gives up with LQR_ERR_TIMEOUT: the tensor-core sweep's waits
+                         for its own products (it then releases its tensor memory and
+                         returns; 0 = 2^26, about two seconds) and the refinement
+                         corrections' waits for their own bulk copies (the copies
+                         still in flight then get one more wait at the default limit;
+                         0 = 2^25)                                                  */
   int refine_plain;   /* mixed modes: 0 = the refinement loop runs as one CUDA graph
                          (a WHILE node around one iteration, ended on the device at
                          convergence) where the graph can be built; 1 = the loop's

@@ -231,6 +231,7 @@ struct RecArgs {
   float* end;
   long long estride;
   int n, ld, count, nruns, G, slots;
+  long long spin;  // polls of a copy wait (0: kCorrSpin)
   const int* skip;
   int* status;
 };
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kRecBlock) corr_rec_kernel(RecArgs a, int dir)
     for (int idx = 0; idx < cnt; ++idx) {
       int ok = 1;
       if (lane == 0) {
-        ok = tc::mbar_wait(&s_bar[s], par, kCorrSpin) ? 1 : 0;
+        ok = tc::mbar_wait(&s_bar[s], par, a.spin > 0 ? a.spin : kCorrSpin) ? 1 : 0;
         if (!ok) s_fail = idx + 1;
       }
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -615,7 +616,7 @@ cudaError_t launch_correction(const CorrArgs& a, cudaStream_t st, int* launches)
     RecArgs r;
     r.C = C; r.cstride = blk;
     r.y0 = y0; r.y0stride = y0s; r.all = all; r.astride = as; r.end = end; r.estride = blk;
-    r.n = n; r.ld = ld; r.count = count; r.nruns = nruns; r.G = G; r.slots = a.slots;
+    r.n = n; r.ld = ld; r.count = count; r.nruns = nruns; r.G = G; r.slots = a.slots; r.spin = a.spin;
     r.skip = a.skip; r.status = a.status;
     corr_rec_kernel<<<nruns, kRecBlock, rb, st>>>(r, dir);
     ++cnt;

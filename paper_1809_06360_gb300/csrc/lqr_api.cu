@@ -609,7 +609,7 @@ lqr_status run_solve_mixed32(lqr_handle* h, const lqr_problem* p, const lqr_opts
       ca.dk = f + odk; ca.dp = f + odp; ca.dx = f + odx; ca.du = f + odu; ca.dl = f + odl;
       ca.skip = skip; ca.status = h->d_status;
       ca.n = n; ca.m = m; ca.T = T; ca.nseg = K;
-      ca.slots = cslots; ca.psi_global = cpsi_global;
+      ca.slots = cslots; ca.psi_global = cpsi_global; ca.spin = o->spin_limit;
       ca.G = cG; ca.ng = cng;
       if (cng) { ca.Theta = f + oTh; ca.ThetaT = f + oThT; ca.gY = f + ogY; ca.gX = f + ogX; }
       if (launch_corr_psi(ca, st) != cudaSuccess) return LQR_ERR_CUDA;

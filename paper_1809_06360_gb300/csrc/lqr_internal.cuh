@@ -227,6 +227,7 @@ struct CorrArgs {
   const int* skip;                     // set: converged, every kernel returns at once
   int* status;
   int n, m, T, nseg;
+  long long spin;  // polls of a copy wait before LQR_ERR_TIMEOUT (0: the default)
   int slots;       // ring slots of the recursion kernel (2..6)
   int psi_global;  // 1: the closed-loop maps read B_t, K_t from global memory
   // two-level link chains (ng > 0): groups of G consecutive links, blocks of

@@ -105,6 +105,22 @@ def test_mixed_host_entry_point(solver):
     assert oracle.rel_err(out["x"], ref["x"]) < 1e-9
 
 
+def test_correction_copy_wait_timeout_is_reported(solver):
+    """The correction recursions wait for their own bulk copies with a bounded
+    poll count (opts.spin_limit): with a one-poll limit the first wait runs out
+    (an 18 KB block does not land within one poll), the solve reports
+    LQR_ERR_TIMEOUT instead of hanging, and the handle's next solve (default
+    limit) succeeds and reaches the oracle."""
+    prob = workloads.make_problem(64, 32, 512, seed=621, rho_max=1.02)
+    dev = to_dev(prob)
+    solver.solve(dev, num_segments=32, prec="mixed_fp32", max_refine=4, tol=1e-10, spin_limit=1)
+    rep = solver.report()
+    assert rep["status_name"] == "LQR_ERR_TIMEOUT", rep
+    out = host(solver.solve(dev, num_segments=32, prec="mixed_fp32", max_refine=4, tol=1e-10))
+    assert solver.report()["status"] == 0
+    assert oracle.rel_err(out["x"], oracle.riccati(prob)["x"]) < 1e-9
+
+
 def test_mixed_fp32_host_entry_pinned_and_pageable(solver):
     """lqr_solve_host in LQR_MIXED_FP32: with every input in mapped page-locked
     host memory the conversion kernel reads the inputs over the host link and
